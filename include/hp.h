@@ -1,0 +1,206 @@
+/*
+ * hp.h -- C ABI of the GB300 Gauss-Newton Hessian-action engine for the
+ * log-coefficient Poisson inverse problem (hIPPYlib paper, Villa/Petra/Ghattas).
+ *
+ * Problem (Section 5.1, eqs. (poi), (poisson_weak)):
+ *     -div(e^m grad u) = f  in the unit square (dim 2) or cube (dim 3),
+ *     u = u_top on the face x_last = 1, u = u_bottom on x_last = 0,
+ *     zero Neumann elsewhere;
+ * P1 elements on a structured mesh of N^dim cells (2 right triangles per
+ * square, 6 Kuhn tetrahedra per cube), nodes (N+1)^dim, lexicographic with the
+ * first axis fastest.  The element coefficient is the element mean of e^m.
+ *
+ * Prior (Section 5.1.1, eq. (PoissonPrior); Section 2.3): A = gamma*K(1) + delta*M
+ * with zero Neumann, precision R = A M^{-1} A.  Noise: Gamma = sigma^2 I,
+ * B = P1 interpolation at the observation points (Section 5.1.1).
+ *
+ * Conventions (all entry points):
+ *  - Vectors and blocks are DEVICE pointers to FP64, column-major, one column
+ *    per right-hand side, leading dimension ld >= n (in elements).  They are
+ *    owned by the caller; the library never frees them.
+ *  - The library owns the opaque handle and its device workspace.  All work is
+ *    enqueued on the stream set by hp_set_stream (default: the legacy stream)
+ *    and each call synchronises that stream before returning, so outputs are
+ *    ready when the call returns.  Scalars returned through host pointers are
+ *    host memory.
+ *  - Return value: HP_OK or a negative HP_ERR_* code; hp_status_string()
+ *    names it and hp_last_error() gives a one-line detail.  Nothing throws
+ *    across the ABI.  HP_ERR_NOT_CONVERGED leaves the best iterate in the
+ *    outputs.
+ *  - There is no CPU fallback: every numerical step runs in this library's
+ *    CUDA kernels (sm_103a).
+ */
+#ifndef HP_H
+#define HP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HP_OK 0
+#define HP_ERR_INVALID (-1)
+#define HP_ERR_NOT_CONVERGED (-2)
+#define HP_ERR_NONFINITE (-3)
+#define HP_ERR_CUDA (-4)
+#define HP_ERR_NOMEM (-5)
+#define HP_ERR_STATE (-6) /* a call needs hp_set_point first */
+
+/* precision of the PDE solves */
+#define HP_FP64_PLAIN 0 /* FP64 multigrid-preconditioned CG throughout       */
+#define HP_FP32_IR 1    /* FP32 MG-PCG inside FP64 iterative refinement     */
+
+/* flags of hp_hessian_apply */
+#define HP_MISFIT_ONLY 0 /* Y = H_misfit X                                 */
+#define HP_WITH_PRIOR 1  /* Y = (H_misfit + R) X                           */
+
+typedef struct hp_problem hp_problem;
+
+typedef struct {
+  int dim;               /* 2 or 3                                            */
+  int N;                 /* cells per axis (>= 1); nodes n = (N+1)^dim        */
+  double gamma, delta;   /* prior operator A = gamma K(1) + delta M (> 0)     */
+  double sigma;          /* noise standard deviation (> 0)                    */
+  int nobs;              /* number of pointwise observations (>= 0)          */
+  const double *obs_xyz; /* HOST, nobs*dim, point-major, inside [0,1]^dim     */
+  const double *d_obs;   /* HOST, nobs observed values (NULL = zeros)         */
+  const double *m_prior; /* HOST, n prior mean (NULL = 0)                     */
+  const double *f;       /* HOST, n nodal source, load = M f (NULL = 0)       */
+  double u_top, u_bottom;/* Dirichlet data on x_last = 1 / x_last = 0         */
+  int precision;         /* HP_FP64_PLAIN or HP_FP32_IR                       */
+  double rtol;           /* relative residual of every PDE solve (e.g. 1e-8)  */
+  int max_iter;          /* cap on CG iterations per solve (e.g. 500)         */
+} hp_problem_desc;
+
+typedef struct {
+  int iterations;        /* inner CG iterations (max over columns, summed over refinement steps) */
+  int outer;             /* FP64 refinement steps (0 for HP_FP64_PLAIN)                        */
+  int solves;            /* number of block solves performed by the call                     */
+  double rel_res;        /* max over columns of the final FP64 relative residual             */
+} hp_solve_stats;
+
+typedef struct {
+  double rel_tol;        /* stop when |g_i| <= rel_tol |g_0| (|g| = sqrt(g^T R^{-1} g)) */
+  double abs_tol;        /* ... or |g_i| <= abs_tol                                       */
+  int max_iter;          /* Newton iterations (Algorithm 1: max_iter)                     */
+  int max_backtrack;     /* Armijo backtracks (Algorithm 1: max_backtracking_iter)        */
+  double c_armijo;       /* Armijo constant (Section 4.1: 1e-5 .. 1e-4)                   */
+  int cg_max_iter;       /* inner CG cap                                                  */
+} hp_newton_opts;
+
+typedef struct {
+  int iterations;        /* Newton iterations taken                        */
+  int cg_iterations;     /* total inner CG iterations (Hessian actions)    */
+  int converged;         /* 1 if the gradient test was met                 */
+  double J0, J;          /* initial and final cost                         */
+  double gnorm0, gnorm;  /* initial and final |g|                          */
+  int pde_solves;        /* total PDE block solves (state, adjoint, incremental, prior, mass) */
+} hp_newton_stats;
+
+/* ---- lifetime ------------------------------------------------------------ */
+
+/* Validates desc, copies its host arrays to the device, builds the observation
+ * operator, the prior hierarchy and the workspace.  HP_ERR_INVALID on bad
+ * sizes or parameters (dim not 2/3, N < 1, gamma/delta/sigma <= 0, points
+ * outside the domain, coarsest multigrid grid too large). */
+int hp_problem_create(const hp_problem_desc *desc, hp_problem **out);
+void hp_problem_destroy(hp_problem *P);
+/* cudaStream_t passed as void*; NULL = legacy default stream. */
+int hp_set_stream(hp_problem *P, void *stream);
+int hp_set_precision(hp_problem *P, int precision);
+int hp_set_tolerance(hp_problem *P, double rtol, int max_iter);
+/* Replaces observed data (HOST array of nobs values) and sigma (> 0). */
+int hp_set_data(hp_problem *P, const double *d_obs_host, double sigma);
+int hp_num_nodes(const hp_problem *P);
+int hp_num_elements(const hp_problem *P);
+/* Copies the device observation vector back: d_out HOST, nobs values. */
+int hp_get_data(const hp_problem *P, double *d_out_host);
+
+/* ---- forward problem / cost / gradient (Section 5.1, Appendix A) -------- */
+
+/* Linearisation point: builds e^m coefficients and the multigrid hierarchy of
+ * K(m), solves the state u(m).  m_dev: n values.  If J_out != NULL the cost
+ * J(m) (eq. (cost-elliptic)) is written to J_out[0..2] = {J, misfit, reg}. */
+int hp_set_point(hp_problem *P, const double *m_dev, double *J_out);
+/* State u(m) (eq. (firststate)) into u_dev (n values, Dirichlet values included). */
+int hp_forward(hp_problem *P, const double *m_dev, double *u_dev, hp_solve_stats *st);
+/* y_dev[0..nobs) = B u for a device state u_dev. */
+int hp_observe(hp_problem *P, const double *u_dev, double *y_dev);
+/* Gradient g = R (m - m_pr) + C^T p with K p = -B^T (B u - d)/sigma^2
+ * (eqs. (firstadj), (firstcontrol)).  Sets the linearisation point to m.
+ * J_out (HOST, may be NULL) receives {J, misfit, reg}. */
+int hp_gradient(hp_problem *P, const double *m_dev, double *g_dev, double *J_out);
+
+/* ---- Hessian action (Appendix A, eqs. (incrementals1)-(incrementals3)) -- */
+
+/* Gauss-Newton Hessian action at the current linearisation point on a block
+ * of nrhs columns:  K Uh = -C X,  K Ph = -B^T B Uh / sigma^2,  Y = C^T Ph
+ * (+ R X if flags & HP_WITH_PRIOR).  X and Y may not alias. */
+int hp_hessian_apply(hp_problem *P, const double *X_dev, int ldx, double *Y_dev, int ldy,
+                     int nrhs, int flags, hp_solve_stats *st);
+
+/* ---- operator pieces (exposed for parity tests and composition) --------- */
+
+/* Y = K(m) X at the current point with Dirichlet rows as identity and the
+ * couplings to Dirichlet nodes removed (the zero-Dirichlet operator). */
+int hp_stiffness_apply(hp_problem *P, const double *X, int ldx, double *Y, int ldy, int nrhs);
+/* X = K(m)^{-1} B on the zero-Dirichlet space (Dirichlet rows of B ignored). */
+int hp_state_solve(hp_problem *P, const double *B, int ldb, double *X, int ldx, int nrhs,
+                   hp_solve_stats *st);
+/* Y = C X (all rows; C X = K(kappa_hat) u, kappa_hat = elem-mean(e^m X)). */
+int hp_C_apply(hp_problem *P, const double *X, int ldx, double *Y, int ldy, int nrhs);
+/* Y = C^T W,  (C^T W)_v = e^{m_v}/(dim+1) sum_{e ni v} |e| grad u . grad W. */
+int hp_Ct_apply(hp_problem *P, const double *W, int ldw, double *Y, int ldy, int nrhs);
+/* Prior operator A = gamma K(1) + delta M, mass M (Section 2.3). */
+int hp_prior_apply(hp_problem *P, const double *X, int ldx, double *Y, int ldy, int nrhs);
+int hp_mass_apply(hp_problem *P, const double *X, int ldx, double *Y, int ldy, int nrhs);
+/* X = A^{-1} B (multigrid PCG). */
+int hp_prior_solve(hp_problem *P, const double *B, int ldb, double *X, int ldx, int nrhs,
+                   hp_solve_stats *st);
+/* X = M^{-1} B (Jacobi PCG). */
+int hp_mass_solve(hp_problem *P, const double *B, int ldb, double *X, int ldx, int nrhs,
+                  hp_solve_stats *st);
+/* Y = R X = A M^{-1} A X  and  Y = R^{-1} X = A^{-1} M A^{-1} X. */
+int hp_R_apply(hp_problem *P, const double *X, int ldx, double *Y, int ldy, int nrhs);
+int hp_Rinv_apply(hp_problem *P, const double *X, int ldx, double *Y, int ldy, int nrhs);
+/* W = C_M eta: rectangular factor of M (Appendix C, eq. (rect_decomp)) with a
+ * degree-2 element rule.  eta: (dim+1)*nelems normals per column, element-major. */
+int hp_mass_factor_apply(hp_problem *P, const double *eta, int ldeta, double *W, int ldw, int nsamples);
+
+/* ---- algorithms (Section 4) ---------------------------------------------- */
+
+/* Inexact Newton-CG (Algorithm 1) from m_dev_inout (n values) to the MAP point.
+ * opts may be NULL (defaults: rel_tol 1e-6, abs_tol 0, max_iter 50,
+ * max_backtrack 10, c_armijo 1e-4, cg_max_iter 200).  The linearisation point
+ * is left at the returned m. */
+int hp_newton_cg_map(hp_problem *P, double *m_dev_inout, const hp_newton_opts *opts,
+                     hp_newton_stats *st);
+/* Double-pass randomized generalized eigensolver (Algorithm 2 with PreCholQR,
+ * Algorithm 4) for H_misfit v = lambda R v at m_map_dev.  Omega_dev: n x (k+p)
+ * Gaussian test matrix (caller-drawn), ld ldo.  Outputs: lambda_dev (k values,
+ * descending), V_dev (n x k, ld ldv, R-orthonormal, sign: largest-magnitude
+ * entry positive).  single_pass != 0 selects Algorithm 3 instead. */
+int hp_lowrank_eig(hp_problem *P, const double *m_map_dev, int k, int p, const double *Omega_dev,
+                   int ldo, double *lambda_dev, double *V_dev, int ldv, int single_pass,
+                   hp_solve_stats *st);
+/* Laplace-approximation samples (Section 4.3): for each column of eta
+ * ((dim+1)*nelems normals), prior sample m_pr + x with x = A^{-1} C_M eta
+ * (eq. (sample_prior)) and posterior sample m_map + x - V S V^T R x,
+ * S = diag(1 - 1/sqrt(1+lambda)) (eq. (sample_post)).  prior_dev / post_dev:
+ * n x nsamples, ld lds (either may be NULL). */
+int hp_laplace_sample(hp_problem *P, const double *m_map_dev, const double *lambda_dev,
+                      const double *V_dev, int ldv, int k, const double *eta_dev, int ldeta,
+                      int nsamples, double *prior_dev, double *post_dev, int lds,
+                      hp_solve_stats *st);
+
+/* ---- status --------------------------------------------------------------- */
+const char *hp_status_string(int status);
+const char *hp_last_error(void);
+/* Number of this library's kernel launches since load (for launch accounting). */
+unsigned long long hp_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HP_H */

@@ -1,0 +1,11 @@
+"""GB300-native Gauss-Newton Hessian-action engine for the log-coefficient
+Poisson inverse problem (hIPPYlib, Part I).
+
+The engine is the C-ABI library ``libhp.so`` (declared in include/hp.h, built
+from ``csrc/`` by ``build.py``); ``hp`` is its ctypes binding.  Importing the
+package does not load the library; the first call does, and raises if it is
+missing.
+"""
+from .hp import Problem, HPError, lib, kernel_launches, EXPORTED, LIB_PATH  # noqa: F401
+
+__all__ = ["Problem", "HPError", "lib", "kernel_launches", "EXPORTED", "LIB_PATH"]

@@ -1,0 +1,146 @@
+// common.cuh -- shared device helpers: structured-mesh combinatorics, block
+// reductions, launch accounting.  Internal to libhp.so.
+//
+// Mesh (Section 2.3 / Section 5.1): (N+1)^D nodes, lexicographic with the
+// first axis fastest.  Cell c = (c_0..c_{D-1}) holds D! simplices, one per
+// axis permutation pi: the chain of corner subsets
+//     S_0 = {} < S_1 = {pi_0} < ... < S_D = {0..D-1},
+// i.e. the vertices c + S_k (as 0/1 offsets).  In 2D this is the split of the
+// square along its (0,0)-(1,1) diagonal (pi = (0,1): lower triangle,
+// pi = (1,0): upper); in 3D the six Kuhn tetrahedra.  Element index =
+// cell_linear * D! + perm, perms in lexicographic order.
+//
+// On such a simplex the P1 barycentric gradients are differences of unit axis
+// vectors, so grad(lambda_{S_k}) . grad(lambda_{S_j}) is non-zero only for
+// |k - j| <= 1: the stiffness couples only "path" (axis) edges and the
+// element integral of grad u . grad w is (|e|/h^2) sum_k du_k dw_k with
+// du_k = u(S_{k+1}) - u(S_k).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define HP_MAXL 16
+
+struct GridDesc {
+  int dim;    // 2 or 3
+  int N;      // cells per axis
+  int np;     // N + 1
+  long n;     // nodes
+  double h;   // 1/N
+};
+
+// chain masks of the permutations, [perm][k], k = 0..D
+__constant__ static int c_chain2[2][3] = {{0, 1, 3}, {0, 2, 3}};
+__constant__ static int c_chain3[6][4] = {{0, 1, 3, 7}, {0, 1, 5, 7}, {0, 2, 3, 7},
+                                          {0, 2, 6, 7}, {0, 4, 5, 7}, {0, 4, 6, 7}};
+
+template <int D> struct MeshT;
+template <> struct MeshT<2> {
+  static constexpr int NPERM = 2;
+  static constexpr int NCORN = 4;
+  __device__ static __forceinline__ int chain(int p, int k) { return c_chain2[p][k]; }
+};
+template <> struct MeshT<3> {
+  static constexpr int NPERM = 6;
+  static constexpr int NCORN = 8;
+  __device__ static __forceinline__ int chain(int p, int k) { return c_chain3[p][k]; }
+};
+
+__host__ __device__ __forceinline__ int popc3(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1); }
+
+template <int D>
+__device__ __forceinline__ void node_coords(const GridDesc &g, long i, int c[3]) {
+  c[0] = (int)(i % g.np);
+  long t = i / g.np;
+  if (D == 2) {
+    c[1] = (int)t;
+    c[2] = 0;
+  } else {
+    c[1] = (int)(t % g.np);
+    c[2] = (int)(t / g.np);
+  }
+}
+
+// linear offset of a 0/1 corner mask
+__device__ __forceinline__ long mask_offset(const GridDesc &g, int b) {
+  return (long)(b & 1) + ((b >> 1) & 1) * (long)g.np + ((b >> 2) & 1) * (long)g.np * g.np;
+}
+
+template <int D>
+__device__ __forceinline__ long cell_linear(const GridDesc &g, const int c[3]) {
+  return D == 2 ? (long)c[0] + (long)g.N * c[1] : (long)c[0] + (long)g.N * (c[1] + (long)g.N * c[2]);
+}
+
+// |e| / h^2 for the simplices of this grid
+template <int D> __host__ __device__ __forceinline__ double vol_over_h2(double h) {
+  return D == 2 ? 0.5 : h / 6.0;
+}
+template <int D> __host__ __device__ __forceinline__ double elem_vol(double h) {
+  return D == 2 ? 0.5 * h * h : h * h * h / 6.0;
+}
+
+// Enumerate the simplices that contain both node v and node v + b (b a 0/1
+// mask; b = 0 enumerates the simplices containing v).  For each one calls
+// f(cell coords, perm, k) where v = cell + S_k.  A simplex contains both iff
+// its chain passes through p = v - cell and p | b.
+template <int D, class F>
+__device__ __forceinline__ void for_elems_with(const GridDesc &g, const int v[3], int b, F &&f) {
+  const int kb = popc3(b);
+#pragma unroll
+  for (int sh = 0; sh < (1 << D); ++sh) {
+    if (sh & b) continue;
+    int c[3] = {0, 0, 0};
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      c[a] = v[a] - ((sh >> a) & 1);
+      ok = ok && (c[a] >= 0) && (c[a] < g.N);
+    }
+    if (!ok) continue;
+    const int k = popc3(sh);
+#pragma unroll
+    for (int p = 0; p < MeshT<D>::NPERM; ++p) {
+      if (MeshT<D>::chain(p, k) == sh && MeshT<D>::chain(p, k + kb) == (sh | b)) f(c, p, k);
+    }
+  }
+}
+
+// ---- reductions -------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum (fixed order -> deterministic).  Result valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[NT / 32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = lane < NT / 32 ? sh[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;
+}
+
+// ---- host side --------------------------------------------------------------
+namespace hp {
+extern unsigned long long g_launches;
+inline void count_launch(unsigned long long k = 1) { g_launches += k; }
+constexpr int NT = 256;   // threads per block of the streaming kernels
+constexpr int NSM = 152;  // SMs of a GB300
+inline int blocks_for(long n, int s) {
+  long b = (n + NT - 1) / NT;
+  long cap = (long)(NSM * 16) / (s > 0 ? s : 1);
+  if (cap < 1) cap = 1;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+}  // namespace hp

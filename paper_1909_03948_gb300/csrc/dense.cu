@@ -1,0 +1,296 @@
+// dense.cu -- FP64 tall-skinny and small dense linear algebra of the
+// randomized eigensolver (Algorithms 2-4) and the low-rank sampling update.
+//
+//   gram          G = X^T Y (n x s1, n x s2), tiled, deterministic two-stage sum
+//   gemm_nn       Y = alpha X S + beta Y (X: n x s1, S: s1 x s2)
+//   cgs2_qr       orthonormal Z with range(Z) = range(Y): classical Gram-Schmidt
+//                 with one full re-orthogonalisation per column ("twice is
+//                 enough"), the thin-QR step of PreCholQR (Algorithm 4)
+//   small_cholesky, trsm_right_upper   R_Z = chol(Z^T Zb), Q = Z R_Z^{-1}
+//   small_symeig  cyclic Jacobi with a round-robin parallel ordering, sorted
+//                 descending (Algorithm 2: T = S Lambda S^T)
+// GB300's FP64 rate is low (a few percent of FP32), so these are written as
+// plain FP64 FMA kernels; they are a small share of the eigensolver's time,
+// which is dominated by the 2(k+p) Hessian actions.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace hp {
+
+constexpr int GT = 32;  // gram tile
+
+__global__ void k_gram_partial(const double *__restrict__ X, long ldx, int s1, const double *__restrict__ Y, long ldy,
+                               int s2, long n, long rows_per_chunk, double *__restrict__ part) {
+  __shared__ double xs[GT][GT + 1], ys[GT][GT + 1];
+  const int ta = blockIdx.x, tb = blockIdx.y, ch = blockIdx.z;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const long r0 = ch * rows_per_chunk, r1 = std::min<long>(n, r0 + rows_per_chunk);
+  double acc[4] = {0, 0, 0, 0};
+  for (long rb = r0; rb < r1; rb += GT) {
+    for (int k = ty; k < GT; k += 8) {
+      const long row = rb + tx;
+      const int ca = ta * GT + k, cb = tb * GT + k;
+      xs[k][tx] = (row < r1 && ca < s1) ? X[ldx * ca + row] : 0.0;
+      ys[k][tx] = (row < r1 && cb < s2) ? Y[ldy * cb + row] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < GT; ++rr) {
+      const double yv = ys[tx][rr];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += xs[ty + 8 * q][rr] * yv;
+    }
+    __syncthreads();
+  }
+  const int nta = gridDim.x, ntb = gridDim.y;
+  for (int q = 0; q < 4; ++q) {
+    const int a = ty + 8 * q, b = tx;
+    part[(((long)ch * nta + ta) * ntb + tb) * GT * GT + a * GT + b] = acc[q];
+  }
+}
+
+__global__ void k_gram_final(const double *__restrict__ part, int nchunk, int nta, int ntb, int s1, int s2,
+                             double *__restrict__ G, int ldg) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= s1 * s2) return;
+  const int a = idx % s1, b = idx / s1;
+  const int ta = a / GT, tb = b / GT;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += part[(((long)c * nta + ta) * ntb + tb) * GT * GT + (a % GT) * GT + (b % GT)];
+  G[a + (long)ldg * b] = s;
+}
+
+int gram(hp_problem *P, const double *X, long ldx, int s1, const double *Y, long ldy, int s2, double *G, int ldg,
+         long n) {
+  const int nta = (s1 + GT - 1) / GT, ntb = (s2 + GT - 1) / GT;
+  int nchunk = std::max(1, (2 * NSM) / (nta * ntb));
+  long rpc = (n + nchunk - 1) / nchunk;
+  rpc = (rpc + GT - 1) / GT * GT;
+  nchunk = (int)((n + rpc - 1) / rpc);
+  if (nchunk < 1) nchunk = 1;
+  const size_t need = sizeof(double) * (size_t)nchunk * nta * ntb * GT * GT;
+  HP_TRY(P->vtmp[5].ensure(need));
+  double *part = P->vtmp[5].as<double>();
+  k_gram_partial<<<dim3(nta, ntb, nchunk), 256, 0, P->st>>>(X, ldx, s1, Y, ldy, s2, n, rpc, part);
+  k_gram_final<<<(s1 * s2 + 255) / 256, 256, 0, P->st>>>(part, nchunk, nta, ntb, s1, s2, G, ldg);
+  count_launch(2);
+  return cuda_check(cudaGetLastError(), "gram");
+}
+
+__global__ void k_gemm_nn(const double *__restrict__ X, long ldx, int s1, const double *__restrict__ S, int lds,
+                          int s2, double *__restrict__ Y, long ldy, long n, double alpha, double beta) {
+  const int j = blockIdx.y;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < s1; ++k) acc += X[ldx * k + i] * __ldg(&S[k + (long)lds * j]);
+    const double y = beta == 0.0 ? 0.0 : beta * Y[ldy * j + i];
+    Y[ldy * j + i] = alpha * acc + y;
+  }
+}
+
+void launch_gemm_nn(const double *X, long ldx, int s1, const double *S, int lds, int s2, double *Y, long ldy, long n,
+                    double alpha, double beta, cudaStream_t st) {
+  k_gemm_nn<<<dim3(blocks_for(n, s2), s2), NT, 0, st>>>(X, ldx, s1, S, lds, s2, Y, ldy, n, alpha, beta);
+  count_launch();
+}
+
+// y <- y - Q c  with c (device, length j) ; then optionally report |y|^2
+__global__ void k_scale_col(double *__restrict__ y, long n, const double *__restrict__ nrm2) {
+  const double nv = sqrt(*nrm2);
+  const double inv = nv > 0.0 ? 1.0 / nv : 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) y[i] *= inv;
+}
+
+int cgs2_qr(hp_problem *P, double *Y, long ldy, long n, int s) {
+  HP_TRY(P->vtmp[4].ensure(sizeof(double) * (size_t)(s + 2)));
+  double *c = P->vtmp[4].as<double>();
+  for (int j = 0; j < s; ++j) {
+    double *y = Y + ldy * j;
+    for (int pass = 0; pass < 2 && j > 0; ++pass) {
+      HP_TRY(gram(P, Y, ldy, j, y, ldy, 1, c, j, n));
+      launch_gemm_nn(Y, ldy, j, c, j, 1, y, ldy, n, -1.0, 1.0, P->st);
+    }
+    HP_TRY(block_dot(P, y, ldy, y, ldy, n, 1, c + s));
+    k_scale_col<<<blocks_for(n, 1), NT, 0, P->st>>>(y, n, c + s);
+    count_launch();
+  }
+  return cuda_check(cudaGetLastError(), "cgs2_qr");
+}
+
+// lower Cholesky in place (row-major) == upper R in column-major
+__global__ void k_small_chol(double *A, int s, int *status) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < s; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = A[(long)k * s + k];
+      if (!(d > 0.0) || !isfinite(d)) bad = 1;
+      A[(long)k * s + k] = d > 0.0 ? sqrt(d) : 1.0;
+    }
+    __syncthreads();
+    const double dk = A[(long)k * s + k];
+    for (int i = k + 1 + threadIdx.x; i < s; i += blockDim.x) A[(long)i * s + k] /= dk;
+    __syncthreads();
+    const int m = s - k - 1;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      const int i = k + 1 + t / m, jj = k + 1 + t % m;
+      if (jj <= i) A[(long)i * s + jj] -= A[(long)i * s + k] * A[(long)jj * s + k];
+    }
+    __syncthreads();
+  }
+  // clear the strictly lower part of the column-major R (upper part of row-major)
+  for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
+    const int i = t / s, jj = t % s;
+    if (jj > i) A[(long)i * s + jj] = 0.0;
+  }
+  if (threadIdx.x == 0) *status = bad;
+}
+
+int small_cholesky(hp_problem *P, double *G, int s) {
+  int *d = P->sc.active.as<int>();
+  k_small_chol<<<1, 1024, 0, P->st>>>(G, s, d);
+  count_launch();
+  int h = 0;
+  HP_CUDA(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, P->st));
+  HP_CUDA(cudaStreamSynchronize(P->st));
+  if (h) return set_error(HP_ERR_NONFINITE, "Gram matrix of PreCholQR is not positive definite");
+  return 0;
+}
+
+// Y <- Y R^{-1} (R upper, column-major s x s): row-wise forward substitution
+__global__ void k_trsm_ru(double *__restrict__ Y, long ldy, long n, int s, const double *__restrict__ R) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    for (int j = 0; j < s; ++j) {
+      double v = Y[ldy * j + i];
+      for (int k = 0; k < j; ++k) v -= Y[ldy * k + i] * __ldg(&R[k + (long)s * j]);
+      Y[ldy * j + i] = v / __ldg(&R[j + (long)s * j]);
+    }
+  }
+}
+
+void launch_trsm_right_upper(double *Y, long ldy, long n, int s, const double *R, cudaStream_t st) {
+  k_trsm_ru<<<blocks_for(n, 1), NT, 0, st>>>(Y, ldy, n, s, R);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// cyclic Jacobi eigen-solver, one block.  A (s x s) and V in global scratch.
+// ---------------------------------------------------------------------------
+__global__ void k_jacobi_eig(double *A, double *V, int s, int m, double *lam_out, double *S_out, int max_sweeps) {
+  extern __shared__ double sh[];
+  double *cs = sh;          // m/2 cosines
+  double *sn = sh + m / 2;  // m/2 sines
+  int *pp = reinterpret_cast<int *>(sn + m / 2);
+  int *qq = pp + m / 2;
+  __shared__ double off_s, tot_s;
+  for (int t = threadIdx.x; t < s * s; t += blockDim.x) V[t] = (t % s == t / s) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // convergence test
+    if (threadIdx.x == 0) {
+      double off = 0.0, tot = 0.0;
+      for (int t = 0; t < s * s; ++t) {
+        const double v = A[t] * A[t];
+        tot += v;
+        if (t % s != t / s) off += v;
+      }
+      off_s = off;
+      tot_s = tot;
+    }
+    __syncthreads();
+    if (off_s <= 1e-30 * tot_s || off_s == 0.0) break;
+    for (int r = 0; r < m - 1; ++r) {
+      for (int k = threadIdx.x; k < m / 2; k += blockDim.x) {
+        int p, q;
+        if (k == 0) {
+          p = r;
+          q = m - 1;
+        } else {
+          p = (r + k) % (m - 1);
+          q = (r - k + (m - 1)) % (m - 1);
+        }
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        double c = 1.0, sv = 0.0;
+        if (q < s) {
+          const double apq = A[p + (long)s * q];
+          if (apq != 0.0) {
+            const double theta = (A[q + (long)s * q] - A[p + (long)s * p]) / (2.0 * apq);
+            const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            sv = t * c;
+          }
+        }
+        cs[k] = c;
+        sn[k] = sv;
+        pp[k] = p;
+        qq[k] = q;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int t = threadIdx.x; t < (m / 2) * s; t += blockDim.x) {
+        const int k = t / s, col = t % s;
+        const int p = pp[k], q = qq[k];
+        if (q >= s) continue;
+        const double c = cs[k], sv = sn[k];
+        const double ap = A[p + (long)s * col], aq = A[q + (long)s * col];
+        A[p + (long)s * col] = c * ap - sv * aq;
+        A[q + (long)s * col] = sv * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int t = threadIdx.x; t < (m / 2) * s; t += blockDim.x) {
+        const int k = t / s, row = t % s;
+        const int p = pp[k], q = qq[k];
+        if (q >= s) continue;
+        const double c = cs[k], sv = sn[k];
+        const double ap = A[row + (long)s * p], aq = A[row + (long)s * q];
+        A[row + (long)s * p] = c * ap - sv * aq;
+        A[row + (long)s * q] = sv * ap + c * aq;
+        const double vp = V[row + (long)s * p], vq = V[row + (long)s * q];
+        V[row + (long)s * p] = c * vp - sv * vq;
+        V[row + (long)s * q] = sv * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  // sort descending (selection order computed by thread 0), write outputs
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int a = 0; a < s; ++a) pp[a] = a;
+    for (int a = 0; a < s; ++a) {
+      int best = a;
+      for (int b = a + 1; b < s; ++b)
+        if (A[pp[b] + (long)s * pp[b]] > A[pp[best] + (long)s * pp[best]]) best = b;
+      const int t = pp[a];
+      pp[a] = pp[best];
+      pp[best] = t;
+    }
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < s; a += blockDim.x) lam_out[a] = A[pp[a] + (long)s * pp[a]];
+  for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
+    const int row = t % s, col = t / s;
+    S_out[row + (long)s * col] = V[row + (long)s * pp[col]];
+  }
+}
+
+int small_symeig(hp_problem *P, const double *T, int s, double *lambda, double *S) {
+  const int m = s + (s & 1);
+  HP_TRY(P->vtmp[3].ensure(sizeof(double) * 2 * (size_t)s * s));
+  double *A = P->vtmp[3].as<double>(), *V = A + (size_t)s * s;
+  HP_CUDA(cudaMemcpyAsync(A, T, sizeof(double) * s * s, cudaMemcpyDeviceToDevice, P->st));
+  const size_t shm = sizeof(double) * m + sizeof(int) * std::max(m, s) * 2 + 64;
+  k_jacobi_eig<<<1, 1024, shm, P->st>>>(A, V, s, m, lambda, S, 60);
+  count_launch();
+  return cuda_check(cudaGetLastError(), "small_symeig");
+}
+
+}  // namespace hp

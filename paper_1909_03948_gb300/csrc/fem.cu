@@ -1,0 +1,655 @@
+// fem.cu -- operators of the discretised log-coefficient Poisson problem.
+//
+// Coefficient:  kappa_e = mean_{v in e} e^{m_v}  (exact element integral of the
+//               P1 interpolant of e^m, divided by |e|).
+// Stiffness K(kappa): only axis (path) edges couple (see common.cuh), with
+//               edge weight w = (|e|/h^2) sum_{e contains the edge} kappa_e; stored
+//               as a 5-point (2D) / 7-point (3D) symmetric stencil.  Dirichlet
+//               rows (last coordinate 0 or N) become identity rows and their
+//               couplings are removed; the removed couplings times the Dirichlet
+//               data form the lifting right-hand side (Section 5.1.3 boundary
+//               conditions).
+// Multigrid coarse operators: the meshes are nested (the fine simplices refine
+//               the coarse ones, 2^D children each) and P1 interpolation is the
+//               prolongation, so the Galerkin operator P^T K(kappa) P is the coarse
+//               FE stiffness with kappa_coarse = mean of the children's kappa.
+// Prior A = gamma K(1) + delta M (Section 5.1.1, eq. (PoissonPrior), Theta = I,
+//               zero Neumann) and mass M couple along all 2^D - 1 Kuhn edge
+//               directions (7-point / 15-point).
+// C X   = K(kappa_hat) u, kappa_hat_e = mean_{v in e}(e^m X)_v   (Appendix A,
+//               eq. (incrementals1): the term (mhat e^m grad u, grad p~)).
+// C^T W = e^{m_v}/(D+1) sum_{e ni v} |e| grad u . grad W          (Appendix A,
+//               eqs. (firstcontrol), (incrementals3)).
+// B     = P1 interpolation at the observation points (Section 5.1.1).
+// C_M   = rectangular factor of M from a degree-2 element rule (Appendix C,
+//               eq. (rect_decomp)).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace hp {
+
+// children of each coarse simplex: (fine cell offset mask) | (fine perm << 3)
+__constant__ int c_child2[2][4];
+__constant__ int c_child3[6][8];
+
+// quadrature: barycentric coordinate of vertex k at point q (degree-2 rules)
+__constant__ double c_quad2[3][3] = {{0.5, 0.5, 0.0}, {0.0, 0.5, 0.5}, {0.5, 0.0, 0.5}};
+
+static int g_children_ready = 0;
+
+// The coarse simplex (cell C, perm pi) = {x in C : x_{pi_0} >= x_{pi_1} >= ...}
+// (local coordinates); a fine simplex belongs to it iff its centroid does.
+static void compute_children(int D, std::vector<std::vector<int>> &out) {
+  std::vector<std::vector<int>> perms;
+  std::vector<int> a(D);
+  for (int i = 0; i < D; ++i) a[i] = i;
+  do perms.push_back(a);
+  while (std::next_permutation(a.begin(), a.end()));
+  out.assign(perms.size(), {});
+  for (size_t cp = 0; cp < perms.size(); ++cp) {
+    for (int o = 0; o < (1 << D); ++o) {
+      for (size_t fp = 0; fp < perms.size(); ++fp) {
+        double s[3] = {0, 0, 0};
+        for (int ax = 0; ax < D; ++ax) s[ax] = (o >> ax) & 1;
+        for (int j = 0; j < D; ++j) s[perms[fp][j]] += double(D - j) / double(D + 1);
+        bool in = true;
+        for (int j = 0; j + 1 < D; ++j) in = in && (s[perms[cp][j]] > s[perms[cp][j + 1]]);
+        if (in) out[cp].push_back(o | (int(fp) << 3));
+      }
+    }
+  }
+}
+
+static int ensure_children() {
+  if (g_children_ready) return 0;
+  std::vector<std::vector<int>> c2, c3;
+  compute_children(2, c2);
+  compute_children(3, c3);
+  int t2[2][4], t3[6][8];
+  for (int p = 0; p < 2; ++p) {
+    if (c2[p].size() != 4) return set_error(HP_ERR_INVALID, "internal: 2D refinement table");
+    for (int q = 0; q < 4; ++q) t2[p][q] = c2[p][q];
+  }
+  for (int p = 0; p < 6; ++p) {
+    if (c3[p].size() != 8) return set_error(HP_ERR_INVALID, "internal: 3D refinement table");
+    for (int q = 0; q < 8; ++q) t3[p][q] = c3[p][q];
+  }
+  HP_CUDA(cudaMemcpyToSymbol(c_child2, t2, sizeof(t2)));
+  HP_CUDA(cudaMemcpyToSymbol(c_child3, t3, sizeof(t3)));
+  g_children_ready = 1;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// element coefficients
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_elem_kappa_fine(GridDesc g, const double *__restrict__ E, double *__restrict__ kappa,
+                                  long nelems) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nelems; e += (long)gridDim.x * blockDim.x) {
+    const long cell = e / MeshT<D>::NPERM;
+    const int p = (int)(e % MeshT<D>::NPERM);
+    int c[3];
+    c[0] = (int)(cell % g.N);
+    const long t = cell / g.N;
+    c[1] = D == 2 ? (int)t : (int)(t % g.N);
+    c[2] = D == 2 ? 0 : (int)(t / g.N);
+    const long base = c[0] + (long)g.np * (c[1] + (long)g.np * c[2]);
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k <= D; ++k) s += E[base + mask_offset(g, MeshT<D>::chain(p, k))];
+    kappa[e] = s / (D + 1);
+  }
+}
+
+template <int D>
+__global__ void k_elem_kappa_coarsen(GridDesc gc, GridDesc gf, const double *__restrict__ kf,
+                                     double *__restrict__ kc, long nelems_c) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nelems_c; e += (long)gridDim.x * blockDim.x) {
+    const long cell = e / MeshT<D>::NPERM;
+    const int p = (int)(e % MeshT<D>::NPERM);
+    int c[3];
+    c[0] = (int)(cell % gc.N);
+    const long t = cell / gc.N;
+    c[1] = D == 2 ? (int)t : (int)(t % gc.N);
+    c[2] = D == 2 ? 0 : (int)(t / gc.N);
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < (1 << D); ++q) {
+      const int code = D == 2 ? c_child2[p][q] : c_child3[p][q];
+      const int o = code & 7, fp = code >> 3;
+      int fc[3] = {2 * c[0] + (o & 1), 2 * c[1] + ((o >> 1) & 1), 2 * c[2] + ((o >> 2) & 1)};
+      s += kf[cell_linear<D>(gf, fc) * MeshT<D>::NPERM + fp];
+    }
+    kc[e] = s / (1 << D);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stencils
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ bool is_dirichlet(const GridDesc &g, const int v[3]) {
+  return v[D - 1] == 0 || v[D - 1] == g.N;
+}
+
+template <int D>
+__device__ __forceinline__ double edge_weight(const GridDesc &g, const double *__restrict__ kappa, const int v[3],
+                                              int b) {
+  double s = 0.0;
+  for_elems_with<D>(g, v, b, [&](const int c[3], int p, int k) {
+    s += kappa[cell_linear<D>(g, c) * MeshT<D>::NPERM + p];
+  });
+  return s * vol_over_h2<D>(g.h);
+}
+
+template <int D>
+__global__ void k_build_K(GridDesc g, const double *__restrict__ kappa, double *diag, double *invdiag, double *c,
+                          float *diag32, float *invdiag32, float *c32, double *lift, double u_top,
+                          double u_bottom) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
+    int v[3];
+    node_coords<D>(g, i, v);
+    const bool dv = is_dirichlet<D>(g, v);
+    double dsum = 0.0, lf = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      double wf = 0.0, wb = 0.0;
+      int vn[3] = {v[0], v[1], v[2]};
+      if (v[a] < g.N) {
+        wf = edge_weight<D>(g, kappa, v, 1 << a);
+        vn[a] = v[a] + 1;
+        const bool dn = is_dirichlet<D>(g, vn);
+        const double cf = (dv || dn) ? 0.0 : -wf;
+        c[(long)a * g.n + i] = cf;
+        c32[(long)a * g.n + i] = (float)cf;
+        if (!dv && dn) lf += wf * (vn[D - 1] == g.N ? u_top : u_bottom);
+      } else {
+        c[(long)a * g.n + i] = 0.0;
+        c32[(long)a * g.n + i] = 0.0f;
+      }
+      if (v[a] > 0) {
+        int vb[3] = {v[0], v[1], v[2]};
+        vb[a] = v[a] - 1;
+        wb = edge_weight<D>(g, kappa, vb, 1 << a);
+        if (!dv && is_dirichlet<D>(g, vb)) lf += wb * (vb[D - 1] == g.N ? u_top : u_bottom);
+      }
+      dsum += wf + wb;
+    }
+    const double dg = dv ? 1.0 : dsum;
+    diag[i] = dg;
+    invdiag[i] = 1.0 / dg;
+    diag32[i] = (float)dg;
+    invdiag32[i] = (float)(1.0 / dg);
+    if (lift) lift[i] = dv ? 0.0 : lf;
+  }
+}
+
+template <int D>
+__device__ __forceinline__ int count_elems(const GridDesc &g, const int v[3], int b) {
+  int n = 0;
+  for_elems_with<D>(g, v, b, [&](const int *, int, int) { ++n; });
+  return n;
+}
+
+// A = gamma K(1) + delta M with zero Neumann (no Dirichlet rows)
+template <int D>
+__global__ void k_build_A(GridDesc g, double gamma, double delta, double *diag, double *invdiag, double *c,
+                          float *diag32, float *invdiag32, float *c32) {
+  const double vh2 = vol_over_h2<D>(g.h);
+  const double mc = elem_vol<D>(g.h) / ((D + 1) * (D + 2));
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
+    int v[3];
+    node_coords<D>(g, i, v);
+    for (int f = 0; f < (1 << D) - 1; ++f) {
+      const int b = f + 1;
+      bool fwd = true;
+      for (int a = 0; a < D; ++a)
+        if ((b >> a) & 1) fwd = fwd && (v[a] < g.N);
+      double cf = 0.0;
+      if (fwd) {
+        const int cnt = count_elems<D>(g, v, b);
+        const double k1 = popc3(b) == 1 ? -vh2 * cnt : 0.0;
+        cf = gamma * k1 + delta * mc * cnt;
+      }
+      c[(long)f * g.n + i] = cf;
+      c32[(long)f * g.n + i] = (float)cf;
+    }
+    double k1d = 0.0;
+    for (int a = 0; a < D; ++a) {
+      if (v[a] < g.N) k1d += vh2 * count_elems<D>(g, v, 1 << a);
+      if (v[a] > 0) {
+        int vb[3] = {v[0], v[1], v[2]};
+        vb[a] -= 1;
+        k1d += vh2 * count_elems<D>(g, vb, 1 << a);
+      }
+    }
+    const double md = 2.0 * mc * count_elems<D>(g, v, 0);
+    const double dg = gamma * k1d + delta * md;
+    diag[i] = dg;
+    invdiag[i] = 1.0 / dg;
+    diag32[i] = (float)dg;
+    invdiag32[i] = (float)(1.0 / dg);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// dense coarse-grid inverse
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_dense_from_stencil(GridDesc g, const double *diag, const double *c, int nf, bool full,
+                                     double *A) {
+  const long nc = g.n;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nc; i += (long)gridDim.x * blockDim.x) {
+    int v[3];
+    node_coords<D>(g, i, v);
+    A[i * nc + i] = diag[i];
+    for (int f = 0; f < nf; ++f) {
+      const int b = full ? f + 1 : (1 << f);
+      bool fwd = true;
+      for (int a = 0; a < D; ++a)
+        if ((b >> a) & 1) fwd = fwd && (v[a] < g.N);
+      if (!fwd) continue;
+      const long j = i + mask_offset(g, b);
+      const double w = c[(long)f * g.n + i];
+      A[i * nc + j] = w;
+      A[j * nc + i] = w;
+    }
+  }
+}
+
+// In-place lower Cholesky of a dense SPD matrix (row-major), one block.
+__global__ void k_dense_cholesky(double *A, int nc, int *status) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < nc; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = A[(long)k * nc + k];
+      if (!(d > 0.0) || !isfinite(d)) bad = 1;
+      A[(long)k * nc + k] = (d > 0.0) ? sqrt(d) : 1.0;
+    }
+    __syncthreads();
+    const double dk = A[(long)k * nc + k];
+    for (int i = k + 1 + threadIdx.x; i < nc; i += blockDim.x) A[(long)i * nc + k] /= dk;
+    __syncthreads();
+    const int m = nc - k - 1;
+    for (long t = threadIdx.x; t < (long)m * m; t += blockDim.x) {
+      const int i = k + 1 + (int)(t / m), j = k + 1 + (int)(t % m);
+      if (j <= i) A[(long)i * nc + j] -= A[(long)i * nc + k] * A[(long)j * nc + k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *status = bad;
+}
+
+// column j of the inverse from the Cholesky factor (one thread per column)
+__global__ void k_dense_inverse(const double *L, int nc, double *inv, float *inv32) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nc) return;
+  double *x = inv + (long)j * nc;  // column j (inverse is symmetric)
+  for (int i = 0; i < nc; ++i) {    // L y = e_j
+    double s = (i == j) ? 1.0 : 0.0;
+    for (int k = 0; k < i; ++k) s -= L[(long)i * nc + k] * x[k];
+    x[i] = s / L[(long)i * nc + i];
+  }
+  for (int i = nc - 1; i >= 0; --i) {  // L^T x = y
+    double s = x[i];
+    for (int k = i + 1; k < nc; ++k) s -= L[(long)k * nc + i] * x[k];
+    x[i] = s / L[(long)i * nc + i];
+  }
+  for (int i = 0; i < nc; ++i) inv32[(long)j * nc + i] = (float)x[i];
+}
+
+int coarse_setup(hp_problem *P, OpKind op) {
+  const Level &lc = P->lv[P->L - 1];
+  CoarseInv &C = op == OP_K ? P->cK : P->cA;
+  const Stencil<double> &S = op == OP_K ? lc.K64 : lc.A64;
+  const long nc = lc.g.n;
+  HP_CUDA(cudaMemsetAsync(C.dense, 0, sizeof(double) * nc * nc, P->st));
+  const int nb = (int)std::min<long>((nc + 255) / 256, 1024);
+  if (P->dim == 2)
+    k_dense_from_stencil<2><<<nb, 256, 0, P->st>>>(lc.g, S.diag, S.c, S.nf, S.full, C.dense);
+  else
+    k_dense_from_stencil<3><<<nb, 256, 0, P->st>>>(lc.g, S.diag, S.c, S.nf, S.full, C.dense);
+  int *dstat = P->sc.active.as<int>();
+  k_dense_cholesky<<<1, 1024, 0, P->st>>>(C.dense, (int)nc, dstat);
+  k_dense_inverse<<<(int)((nc + 127) / 128), 128, 0, P->st>>>(C.dense, (int)nc, C.inv64, C.inv32);
+  count_launch(3);
+  int h = 0;
+  HP_CUDA(cudaMemcpyAsync(&h, dstat, sizeof(int), cudaMemcpyDeviceToHost, P->st));
+  HP_CUDA(cudaStreamSynchronize(P->st));
+  HP_CUDA(cudaGetLastError());
+  if (h) return set_error(HP_ERR_NONFINITE, "coarse-grid operator is not SPD (non-finite coefficient?)");
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// setup
+// ---------------------------------------------------------------------------
+static int alloc_stencil(Stencil<double> &S64, Stencil<float> &S32, long n, int nf, bool full) {
+  S64.nf = S32.nf = nf;
+  S64.full = S32.full = full;
+  HP_CUDA(cudaMalloc(&S64.diag, sizeof(double) * n));
+  HP_CUDA(cudaMalloc(&S64.invdiag, sizeof(double) * n));
+  HP_CUDA(cudaMalloc(&S64.c, sizeof(double) * n * nf));
+  HP_CUDA(cudaMalloc(&S32.diag, sizeof(float) * n));
+  HP_CUDA(cudaMalloc(&S32.invdiag, sizeof(float) * n));
+  HP_CUDA(cudaMalloc(&S32.c, sizeof(float) * n * nf));
+  return 0;
+}
+
+static int grid_blocks(long n) { return (int)std::max<long>(1, std::min<long>((n + 255) / 256, 8192)); }
+
+int build_hierarchy_geometry(hp_problem *P) {
+  HP_TRY(ensure_children());
+  const int D = P->dim;
+  const int ncmax = D == 2 ? 8 : 4;
+  int N = P->N, L = 1;
+  while (N % 2 == 0 && N > ncmax && L < HP_MAXL) {
+    N /= 2;
+    ++L;
+  }
+  long nc = 1;
+  for (int a = 0; a < D; ++a) nc *= (N + 1);
+  if (nc > 1600)
+    return set_error(HP_ERR_INVALID, "coarsest multigrid grid too large: N must be 2^k times a small factor");
+  P->L = L;
+  const int nfK = D, nfA = (1 << D) - 1;
+  const int nperm = D == 2 ? 2 : 6;
+  for (int l = 0; l < L; ++l) {
+    Level &lv = P->lv[l];
+    lv.g.dim = D;
+    lv.g.N = P->N >> l;
+    lv.g.np = lv.g.N + 1;
+    lv.g.n = 1;
+    for (int a = 0; a < D; ++a) lv.g.n *= lv.g.np;
+    lv.g.h = 1.0 / lv.g.N;
+    lv.nelems = nperm;
+    for (int a = 0; a < D; ++a) lv.nelems *= lv.g.N;
+    HP_CUDA(cudaMalloc(&lv.kappa, sizeof(double) * lv.nelems));
+    HP_TRY(alloc_stencil(lv.K64, lv.K32, lv.g.n, nfK, false));
+    HP_TRY(alloc_stencil(lv.A64, lv.A32, lv.g.n, nfA, true));
+    const int nb = grid_blocks(lv.g.n);
+    if (D == 2)
+      k_build_A<2><<<nb, 256, 0, P->st>>>(lv.g, P->gamma, P->delta, lv.A64.diag, lv.A64.invdiag, lv.A64.c,
+                                          lv.A32.diag, lv.A32.invdiag, lv.A32.c);
+    else
+      k_build_A<3><<<nb, 256, 0, P->st>>>(lv.g, P->gamma, P->delta, lv.A64.diag, lv.A64.invdiag, lv.A64.c,
+                                          lv.A32.diag, lv.A32.invdiag, lv.A32.c);
+    count_launch();
+  }
+  // mass matrix on the fine grid
+  const Level &l0 = P->lv[0];
+  HP_TRY(alloc_stencil(P->M64, P->M32, l0.g.n, nfA, true));
+  if (D == 2)
+    k_build_A<2><<<grid_blocks(l0.g.n), 256, 0, P->st>>>(l0.g, 0.0, 1.0, P->M64.diag, P->M64.invdiag, P->M64.c,
+                                                         P->M32.diag, P->M32.invdiag, P->M32.c);
+  else
+    k_build_A<3><<<grid_blocks(l0.g.n), 256, 0, P->st>>>(l0.g, 0.0, 1.0, P->M64.diag, P->M64.invdiag, P->M64.c,
+                                                         P->M32.diag, P->M32.invdiag, P->M32.c);
+  count_launch();
+  // coarse inverses
+  const long ncn = P->lv[L - 1].g.n;
+  for (CoarseInv *C : {&P->cK, &P->cA}) {
+    C->nc = (int)ncn;
+    HP_CUDA(cudaMalloc(&C->dense, sizeof(double) * ncn * ncn));
+    HP_CUDA(cudaMalloc(&C->inv64, sizeof(double) * ncn * ncn));
+    HP_CUDA(cudaMalloc(&C->inv32, sizeof(float) * ncn * ncn));
+  }
+  HP_TRY(coarse_setup(P, OP_A));
+  return 0;
+}
+
+int build_point(hp_problem *P, const double *m_dev) {
+  const long n = P->n;
+  HP_CUDA(cudaMemcpyAsync(P->m, m_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->st));
+  launch_ew_exp(P->m, P->E, n, P->st);
+  const int D = P->dim;
+  Level &l0 = P->lv[0];
+  if (D == 2)
+    k_elem_kappa_fine<2><<<grid_blocks(l0.nelems), 256, 0, P->st>>>(l0.g, P->E, l0.kappa, l0.nelems);
+  else
+    k_elem_kappa_fine<3><<<grid_blocks(l0.nelems), 256, 0, P->st>>>(l0.g, P->E, l0.kappa, l0.nelems);
+  count_launch();
+  for (int l = 1; l < P->L; ++l) {
+    Level &lc = P->lv[l], &lf = P->lv[l - 1];
+    if (D == 2)
+      k_elem_kappa_coarsen<2><<<grid_blocks(lc.nelems), 256, 0, P->st>>>(lc.g, lf.g, lf.kappa, lc.kappa, lc.nelems);
+    else
+      k_elem_kappa_coarsen<3><<<grid_blocks(lc.nelems), 256, 0, P->st>>>(lc.g, lf.g, lf.kappa, lc.kappa, lc.nelems);
+    count_launch();
+  }
+  for (int l = 0; l < P->L; ++l) {
+    Level &lv = P->lv[l];
+    double *lift = l == 0 ? P->lift : nullptr;
+    if (D == 2)
+      k_build_K<2><<<grid_blocks(lv.g.n), 256, 0, P->st>>>(lv.g, lv.kappa, lv.K64.diag, lv.K64.invdiag, lv.K64.c,
+                                                           lv.K32.diag, lv.K32.invdiag, lv.K32.c, lift, P->u_top,
+                                                           P->u_bottom);
+    else
+      k_build_K<3><<<grid_blocks(lv.g.n), 256, 0, P->st>>>(lv.g, lv.kappa, lv.K64.diag, lv.K64.invdiag, lv.K64.c,
+                                                           lv.K32.diag, lv.K32.invdiag, lv.K32.c, lift, P->u_top,
+                                                           P->u_bottom);
+    count_launch();
+  }
+  HP_CUDA(cudaGetLastError());
+  HP_TRY(coarse_setup(P, OP_K));
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// C, C^T
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_C_apply(GridDesc g, const double *__restrict__ E, const double *__restrict__ u,
+                          const double *__restrict__ X, long ldx, double *__restrict__ Y, long ldy, double scale) {
+  const int j = blockIdx.y;
+  const double *x = X + ldx * j;
+  double *y = Y + ldy * j;
+  const double vh2 = vol_over_h2<D>(g.h);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
+    int v[3];
+    node_coords<D>(g, i, v);
+    double acc = 0.0;
+#pragma unroll
+    for (int sh = 0; sh < (1 << D); ++sh) {
+      bool ok = true;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int ca = v[a] - ((sh >> a) & 1);
+        ok = ok && ca >= 0 && ca < g.N;
+      }
+      if (!ok) continue;
+      const long base = i - mask_offset(g, sh);
+      double ex[1 << D], uu[1 << D];
+#pragma unroll
+      for (int q = 0; q < (1 << D); ++q) {
+        const long o = base + mask_offset(g, q);
+        ex[q] = E[o] * x[o];
+        uu[q] = u[o];
+      }
+      const int k = popc3(sh);
+#pragma unroll
+      for (int p = 0; p < MeshT<D>::NPERM; ++p) {
+        if (MeshT<D>::chain(p, k) != sh) continue;
+        double kh = 0.0;
+#pragma unroll
+        for (int t = 0; t <= D; ++t) kh += ex[MeshT<D>::chain(p, t)];
+        double du = 0.0;
+        if (k > 0) du += uu[sh] - uu[MeshT<D>::chain(p, k - 1)];
+        if (k < D) du += uu[sh] - uu[MeshT<D>::chain(p, k + 1)];
+        acc += kh * du;
+      }
+    }
+    y[i] = scale * vh2 * acc / (D + 1);
+  }
+}
+
+template <int D>
+__global__ void k_Ct_apply(GridDesc g, const double *__restrict__ E, const double *__restrict__ u,
+                           const double *__restrict__ W, long ldw, double *__restrict__ Y, long ldy, double scale,
+                           double beta) {
+  const int j = blockIdx.y;
+  const double *w = W + ldw * j;
+  double *y = Y + ldy * j;
+  const double vh2 = vol_over_h2<D>(g.h);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
+    int v[3];
+    node_coords<D>(g, i, v);
+    double acc = 0.0;
+#pragma unroll
+    for (int sh = 0; sh < (1 << D); ++sh) {
+      bool ok = true;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int ca = v[a] - ((sh >> a) & 1);
+        ok = ok && ca >= 0 && ca < g.N;
+      }
+      if (!ok) continue;
+      const long base = i - mask_offset(g, sh);
+      double ww[1 << D], uu[1 << D];
+#pragma unroll
+      for (int q = 0; q < (1 << D); ++q) {
+        const long o = base + mask_offset(g, q);
+        ww[q] = w[o];
+        uu[q] = u[o];
+      }
+      const int k = popc3(sh);
+#pragma unroll
+      for (int p = 0; p < MeshT<D>::NPERM; ++p) {
+        if (MeshT<D>::chain(p, k) != sh) continue;
+#pragma unroll
+        for (int t = 0; t < D; ++t) {
+          const int a0 = MeshT<D>::chain(p, t), a1 = MeshT<D>::chain(p, t + 1);
+          acc += (uu[a1] - uu[a0]) * (ww[a1] - ww[a0]);
+        }
+      }
+    }
+    const double val = scale * E[i] * vh2 * acc / (D + 1);
+    y[i] = beta == 0.0 ? val : val + beta * y[i];
+  }
+}
+
+void launch_C_apply(hp_problem *P, const double *X, long ldx, double *Y, long ldy, int s, double scale) {
+  dim3 grid(blocks_for(P->n, s), s);
+  if (P->dim == 2)
+    k_C_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, P->u, X, ldx, Y, ldy, scale);
+  else
+    k_C_apply<3><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, P->u, X, ldx, Y, ldy, scale);
+  count_launch();
+}
+
+void launch_Ct_apply(hp_problem *P, const double *W, long ldw, double *Y, long ldy, int s, double scale,
+                     double beta) {
+  dim3 grid(blocks_for(P->n, s), s);
+  if (P->dim == 2)
+    k_Ct_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, P->u, W, ldw, Y, ldy, scale, beta);
+  else
+    k_Ct_apply<3><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, P->u, W, ldw, Y, ldy, scale, beta);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// observation operator
+// ---------------------------------------------------------------------------
+__global__ void k_obs_gather(const int *__restrict__ node, const double *__restrict__ w, int nobs, int nv,
+                             const double *__restrict__ X, long ldx, double *__restrict__ Yq) {
+  const int j = blockIdx.y;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nobs; o += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < nv; ++k) s += w[o * nv + k] * X[ldx * j + node[o * nv + k]];
+    Yq[(long)nobs * j + o] = s;
+  }
+}
+
+__global__ void k_obs_scatter(long n, const int *__restrict__ row, const int *__restrict__ ptr,
+                              const int *__restrict__ ent, const double *__restrict__ w, int nobs, int nv,
+                              const double *__restrict__ Yq, double *__restrict__ X, long ldx, double scale) {
+  const int j = blockIdx.y;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int r = row[i];
+    double s = 0.0;
+    if (r >= 0) {
+      for (int t = ptr[r]; t < ptr[r + 1]; ++t) {
+        const int e = ent[t];
+        s += w[e] * Yq[(long)nobs * j + e / nv];
+      }
+    }
+    X[ldx * j + i] = scale * s;
+  }
+}
+
+void launch_obs_gather(hp_problem *P, const double *X, long ldx, double *Yq, int s) {
+  if (P->nobs == 0) return;
+  dim3 grid((P->nobs + 127) / 128, s);
+  k_obs_gather<<<grid, 128, 0, P->st>>>(P->obs_node, P->obs_w, P->nobs, P->dim + 1, X, ldx, Yq);
+  count_launch();
+}
+
+void launch_obs_scatter(hp_problem *P, const double *Yq, double *X, long ldx, int s, double scale) {
+  dim3 grid(blocks_for(P->n, s), s);
+  k_obs_scatter<<<grid, NT, 0, P->st>>>(P->n, P->bt_row, P->bt_ptr, P->bt_ent, P->obs_w, P->nobs, P->dim + 1,
+                                        Yq, X, ldx, scale);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// rectangular factor of the mass matrix
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_mass_factor(GridDesc g, const double *__restrict__ eta, long ldeta, double *__restrict__ W,
+                              long ldw) {
+  const int j = blockIdx.y;
+  const double *et = eta + ldeta * j;
+  const double sw = sqrt(elem_vol<D>(g.h) / (D + 1));
+  const double qa = (5.0 + 3.0 * sqrt(5.0)) / 20.0, qb = (5.0 - sqrt(5.0)) / 20.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
+    int v[3];
+    node_coords<D>(g, i, v);
+    double acc = 0.0;
+    for_elems_with<D>(g, v, 0, [&](const int c[3], int p, int k) {
+      const long e = cell_linear<D>(g, c) * MeshT<D>::NPERM + p;
+#pragma unroll
+      for (int q = 0; q <= D; ++q) {
+        const double lam = D == 2 ? c_quad2[q][k] : (q == k ? qa : qb);
+        acc += lam * et[e * (D + 1) + q];
+      }
+    });
+    W[ldw * j + i] = sw * acc;
+  }
+}
+
+void launch_mass_factor(hp_problem *P, const double *eta, long ldeta, double *W, long ldw, int s) {
+  dim3 grid(blocks_for(P->n, s), s);
+  if (P->dim == 2)
+    k_mass_factor<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, eta, ldeta, W, ldw);
+  else
+    k_mass_factor<3><<<grid, NT, 0, P->st>>>(P->lv[0].g, eta, ldeta, W, ldw);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Dirichlet rows
+// ---------------------------------------------------------------------------
+__global__ void k_zero_dirichlet(long face, long top_off, double *X, long ldx) {
+  const int j = blockIdx.y;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < face; t += (long)gridDim.x * blockDim.x) {
+    X[ldx * j + t] = 0.0;
+    X[ldx * j + top_off + t] = 0.0;
+  }
+}
+
+void launch_zero_dirichlet(hp_problem *P, double *X, long ldx, int s) {
+  const GridDesc &g = P->lv[0].g;
+  const long face = P->dim == 2 ? g.np : (long)g.np * g.np;
+  dim3 grid((unsigned)std::max<long>(1, std::min<long>((face + 255) / 256, 64)), s);
+  k_zero_dirichlet<<<grid, 256, 0, P->st>>>(face, g.n - face, X, ldx);
+  count_launch();
+}
+
+}  // namespace hp

@@ -1,0 +1,174 @@
+// internal.h -- library-internal types and the host launchers shared between
+// the translation units of libhp.so.  Not part of the ABI (see include/hp.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hp.h"
+#include "common.cuh"
+
+namespace hp {
+
+// Symmetric stencil stored by "forward" couplings: y_i = diag_i x_i +
+// sum_f [c_f(i) x_{i+o_f} + c_f(i-o_f) x_{i-o_f}], with o_f the 0/1 corner
+// masks of the Kuhn edges.  full = false: axis offsets only (stiffness,
+// 5-/7-point); full = true: all 2^D - 1 edge directions (prior / mass,
+// 7-/15-point).  Coefficient f of node i is at c[f * n + i].
+template <typename T> struct Stencil {
+  T *diag = nullptr;
+  T *invdiag = nullptr;
+  T *c = nullptr;
+  int nf = 0;
+  bool full = false;
+};
+
+struct Level {
+  GridDesc g{};
+  long nelems = 0;
+  double *kappa = nullptr;   // element coefficients of K on this level
+  Stencil<double> K64, A64;
+  Stencil<float> K32, A32;
+};
+
+struct CoarseInv {
+  int nc = 0;
+  double *dense = nullptr;   // work: nc x nc
+  double *inv64 = nullptr;
+  float *inv32 = nullptr;
+};
+
+enum OpKind { OP_K = 0, OP_A = 1, OP_M = 2 };
+
+// growable device buffer
+struct DBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t b);
+  void release();
+  template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+template <typename T> struct BlockWS {
+  int scap = 0;       // column capacity
+  long ldn = 0;       // padded column stride
+  DBuf x, r, z, p, q;               // PCG vectors
+  DBuf lr[HP_MAXL], la[HP_MAXL], lb[HP_MAXL];  // MG level vectors (level 0 uses r/z and lb[0])
+};
+
+struct ScalarWS {
+  int scap = 0;
+  DBuf rz, pq, rr, bb, alpha, beta, scale, tmp;   // double per column
+  DBuf active;                                     // int per column
+  DBuf partial;                                    // double [slot][col][block]
+  DBuf counter;                                    // unsigned [slot][col]
+  std::vector<int> h_active;
+  std::vector<double> h_rr, h_bb;
+};
+
+}  // namespace hp
+
+struct hp_problem {
+  // description
+  int dim = 2, N = 0, L = 0;
+  long n = 0, nelems = 0;
+  double gamma = 0, delta = 0, sigma = 1, u_top = 1, u_bottom = 0;
+  int precision = HP_FP32_IR;
+  double rtol = 1e-8;
+  int max_iter = 500;
+  double inner_rtol = 1e-5;     // FP32 inner tolerance of the refinement
+  int max_outer = 12;
+  int nu = 2;                   // pre/post Jacobi sweeps
+  double omega = 0.7;           // Jacobi damping
+  cudaStream_t st = nullptr;
+
+  hp::Level lv[HP_MAXL];
+  hp::CoarseInv cK, cA;
+  hp::Stencil<double> M64;
+  hp::Stencil<float> M32;
+
+  // point-dependent state
+  bool have_point = false;
+  double *m = nullptr, *E = nullptr, *u = nullptr, *lift = nullptr;
+  // data
+  double *m_prior = nullptr, *f_load = nullptr, *d_obs = nullptr;
+  int nobs = 0;
+  int *obs_node = nullptr;      // nobs * (dim+1)
+  double *obs_w = nullptr;      // nobs * (dim+1)
+  int *bt_row = nullptr;        // n: CSR row of B^T for the node, -1 if untouched
+  int *bt_ptr = nullptr;        // rows + 1
+  int *bt_ent = nullptr;        // entries: obs * (dim+1) + k
+  int bt_rows = 0;
+
+  // workspaces
+  hp::BlockWS<float> w32;
+  hp::BlockWS<double> w64;
+  hp::ScalarWS sc;
+  hp::DBuf r64, b64, t64a, t64b, t64c, obsbuf, small, vtmp[6];
+};
+
+namespace hp {
+
+int set_error(int code, const std::string &msg);
+int cuda_check(cudaError_t e, const char *where);
+#define HP_CUDA(call)                                              \
+  do {                                                             \
+    int _rc = ::hp::cuda_check((call), #call);                     \
+    if (_rc) return _rc;                                           \
+  } while (0)
+#define HP_TRY(call)              \
+  do {                            \
+    int _rc = (call);             \
+    if (_rc) return _rc;          \
+  } while (0)
+
+// ---- fem.cu -------------------------------------------------------------
+int build_hierarchy_geometry(hp_problem *P);  // levels, allocs, prior/mass stencils, coarse A inverse
+int build_point(hp_problem *P, const double *m_dev);  // E, kappa hierarchy, K stencils, lift, coarse K inverse
+void launch_C_apply(hp_problem *P, const double *X, long ldx, double *Y, long ldy, int s, double scale);
+void launch_Ct_apply(hp_problem *P, const double *W, long ldw, double *Y, long ldy, int s, double scale,
+                     double beta);
+void launch_obs_gather(hp_problem *P, const double *X, long ldx, double *Yq, int s);
+void launch_obs_scatter(hp_problem *P, const double *Yq, double *X, long ldx, int s, double scale);
+void launch_mass_factor(hp_problem *P, const double *eta, long ldeta, double *W, long ldw, int s);
+void launch_zero_dirichlet(hp_problem *P, double *X, long ldx, int s);
+template <typename T>
+void launch_stencil_apply(const hp_problem *P, const GridDesc &g, const Stencil<T> &S, const T *X, long ldx,
+                          T *Y, long ldy, int s, cudaStream_t st);
+int coarse_setup(hp_problem *P, hp::OpKind op);
+
+// ---- vec.cu ---------------------------------------------------------------
+void launch_copy(const double *X, long ldx, double *Y, long ldy, long n, int s, cudaStream_t st);
+void launch_fill(double *X, long ldx, long n, int s, double v, cudaStream_t st);
+void launch_axpby(double a, const double *X, long ldx, double b, double *Y, long ldy, long n, int s,
+                  cudaStream_t st);   // Y = a X + b Y
+void launch_ew_exp(const double *m, double *E, long n, cudaStream_t st);
+// per-column deterministic dots: out[j] = sum_i X_ij Y_ij (FP64)
+int block_dot(hp_problem *P, const double *X, long ldx, const double *Y, long ldy, long n, int s,
+              double *out_dev);
+
+// ---- solver.cu --------------------------------------------------------------
+int ensure_scalars(hp_problem *P, int s);
+int solve_block(hp_problem *P, OpKind op, const double *B, long ldb, double *X, long ldx, int s,
+                double rtol, hp_solve_stats *st);
+int apply_op64(hp_problem *P, OpKind op, const double *X, long ldx, double *Y, long ldy, int s);
+
+// ---- dense.cu ---------------------------------------------------------------
+// G (s1 x s2, column-major, ldg) = X^T Y ; X: n x s1, Y: n x s2 (FP64)
+int gram(hp_problem *P, const double *X, long ldx, int s1, const double *Y, long ldy, int s2, double *G,
+         int ldg, long n);
+// Y (n x s2) = X (n x s1) * S (s1 x s2, ld lds) [+ beta * Y]
+void launch_gemm_nn(const double *X, long ldx, int s1, const double *S, int lds, int s2, double *Y,
+                    long ldy, long n, double alpha, double beta, cudaStream_t st);
+// in-place CGS2 orthonormalisation of the columns of Y (n x s)
+int cgs2_qr(hp_problem *P, double *Y, long ldy, long n, int s);
+// upper Cholesky R^T R = G (s x s, ld s) in place; returns HP_ERR_NONFINITE if not SPD
+int small_cholesky(hp_problem *P, double *G, int s);
+// Y <- Y R^{-1}, R upper (s x s)
+void launch_trsm_right_upper(double *Y, long ldy, long n, int s, const double *R, cudaStream_t st);
+// symmetric eigen-decomposition of T (s x s) by cyclic Jacobi: lambda (s), S (s x s) columns
+int small_symeig(hp_problem *P, const double *T, int s, double *lambda, double *S);
+
+}  // namespace hp

@@ -1,0 +1,362 @@
+"""ctypes binding of libhp.so (include/hp.h).
+
+Argument marshalling only: every numerical step runs in the library's CUDA
+kernels.  Blocks of vectors are torch tensors of shape (s, n), float64,
+contiguous, on the CUDA device -- i.e. column-major n x s with leading
+dimension n, one column per row of the tensor.  A 1-D tensor of length n is a
+block of one column.  PyTorch only provides device memory and streams.
+
+There is no fallback: if libhp.so is missing or fails to load, or a tensor is
+not a CUDA float64 tensor, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhp.so")
+
+HP_OK = 0
+HP_ERR_INVALID = -1
+HP_ERR_NOT_CONVERGED = -2
+HP_ERR_NONFINITE = -3
+HP_ERR_CUDA = -4
+HP_ERR_NOMEM = -5
+HP_ERR_STATE = -6
+HP_FP64_PLAIN = 0
+HP_FP32_IR = 1
+HP_MISFIT_ONLY = 0
+HP_WITH_PRIOR = 1
+
+
+class HPError(RuntimeError):
+    def __init__(self, code, where, detail):
+        super().__init__(f"{where}: {detail} (status {code})")
+        self.code = code
+
+
+class Desc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("N", C.c_int), ("gamma", C.c_double), ("delta", C.c_double),
+                ("sigma", C.c_double), ("nobs", C.c_int), ("obs_xyz", C.POINTER(C.c_double)),
+                ("d_obs", C.POINTER(C.c_double)), ("m_prior", C.POINTER(C.c_double)),
+                ("f", C.POINTER(C.c_double)), ("u_top", C.c_double), ("u_bottom", C.c_double),
+                ("precision", C.c_int), ("rtol", C.c_double), ("max_iter", C.c_int)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("outer", C.c_int), ("solves", C.c_int), ("rel_res", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class NewtonOpts(C.Structure):
+    _fields_ = [("rel_tol", C.c_double), ("abs_tol", C.c_double), ("max_iter", C.c_int),
+                ("max_backtrack", C.c_int), ("c_armijo", C.c_double), ("cg_max_iter", C.c_int)]
+
+
+class NewtonStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("cg_iterations", C.c_int), ("converged", C.c_int),
+                ("J0", C.c_double), ("J", C.c_double), ("gnorm0", C.c_double), ("gnorm", C.c_double),
+                ("pde_solves", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+_P = C.c_void_p
+_D = C.c_void_p     # device pointer
+_I = C.c_int
+
+_SIGS = {
+    "hp_problem_create": (_I, [C.POINTER(Desc), C.POINTER(C.c_void_p)]),
+    "hp_problem_destroy": (None, [_P]),
+    "hp_set_stream": (_I, [_P, C.c_void_p]),
+    "hp_set_precision": (_I, [_P, _I]),
+    "hp_set_tolerance": (_I, [_P, C.c_double, _I]),
+    "hp_set_data": (_I, [_P, C.POINTER(C.c_double), C.c_double]),
+    "hp_get_data": (_I, [_P, C.POINTER(C.c_double)]),
+    "hp_num_nodes": (_I, [_P]),
+    "hp_num_elements": (_I, [_P]),
+    "hp_set_point": (_I, [_P, _D, C.POINTER(C.c_double)]),
+    "hp_forward": (_I, [_P, _D, _D, C.POINTER(SolveStats)]),
+    "hp_observe": (_I, [_P, _D, _D]),
+    "hp_gradient": (_I, [_P, _D, _D, C.POINTER(C.c_double)]),
+    "hp_hessian_apply": (_I, [_P, _D, _I, _D, _I, _I, _I, C.POINTER(SolveStats)]),
+    "hp_stiffness_apply": (_I, [_P, _D, _I, _D, _I, _I]),
+    "hp_state_solve": (_I, [_P, _D, _I, _D, _I, _I, C.POINTER(SolveStats)]),
+    "hp_C_apply": (_I, [_P, _D, _I, _D, _I, _I]),
+    "hp_Ct_apply": (_I, [_P, _D, _I, _D, _I, _I]),
+    "hp_prior_apply": (_I, [_P, _D, _I, _D, _I, _I]),
+    "hp_mass_apply": (_I, [_P, _D, _I, _D, _I, _I]),
+    "hp_prior_solve": (_I, [_P, _D, _I, _D, _I, _I, C.POINTER(SolveStats)]),
+    "hp_mass_solve": (_I, [_P, _D, _I, _D, _I, _I, C.POINTER(SolveStats)]),
+    "hp_R_apply": (_I, [_P, _D, _I, _D, _I, _I]),
+    "hp_Rinv_apply": (_I, [_P, _D, _I, _D, _I, _I]),
+    "hp_mass_factor_apply": (_I, [_P, _D, _I, _D, _I, _I]),
+    "hp_newton_cg_map": (_I, [_P, _D, C.POINTER(NewtonOpts), C.POINTER(NewtonStats)]),
+    "hp_lowrank_eig": (_I, [_P, _D, _I, _I, _D, _I, _D, _D, _I, _I, C.POINTER(SolveStats)]),
+    "hp_laplace_sample": (_I, [_P, _D, _D, _D, _I, _I, _D, _I, _I, _D, _D, _I, C.POINTER(SolveStats)]),
+    "hp_status_string": (C.c_char_p, [_I]),
+    "hp_last_error": (C.c_char_p, []),
+    "hp_kernel_launches": (C.c_ulonglong, []),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def lib():
+    """Load libhp.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} not found: build it with `python -m paper_1909_03948_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def kernel_launches() -> int:
+    return int(lib().hp_kernel_launches())
+
+
+def _check(code, where):
+    if code != HP_OK:
+        L = lib()
+        raise HPError(code, where, L.hp_last_error().decode() or L.hp_status_string(code).decode())
+
+
+def _dptr(t: torch.Tensor):
+    return C.c_void_p(t.data_ptr())
+
+
+def _block(t: torch.Tensor, n: int, name: str):
+    """(s, n) or (n,) CUDA float64 contiguous -> (tensor2d, s, ld)."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name}: expected a CUDA float64 tensor")
+    t2 = t.reshape(1, -1) if t.dim() == 1 else t
+    if t2.dim() != 2 or t2.shape[1] != n or not t2.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous (s, {n}) block")
+    return t2, t2.shape[0], n
+
+
+def _hptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+@dataclass
+class Stats:
+    iterations: int = 0
+    outer: int = 0
+    solves: int = 0
+    rel_res: float = 0.0
+
+
+class Problem:
+    """One inverse problem instance (owns an hp_problem handle)."""
+
+    def __init__(self, dim: int, N: int, gamma: float, delta: float, sigma: float, obs_xyz,
+                 d_obs=None, m_prior=None, f=None, u_top: float = 1.0, u_bottom: float = 0.0,
+                 precision: str = "fp32_ir", rtol: float = 1e-8, max_iter: int = 500):
+        L = lib()
+        self._keep = []
+        obs = np.ascontiguousarray(np.asarray(obs_xyz, dtype=np.float64).reshape(-1, dim))
+        self._keep.append(obs)
+
+        def opt(a, length):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+            if a.size != length:
+                raise ValueError("wrong length")
+            self._keep.append(a)
+            return _hptr(a)
+
+        n = (N + 1) ** dim
+        d = Desc(dim=dim, N=N, gamma=gamma, delta=delta, sigma=sigma, nobs=obs.shape[0],
+                 obs_xyz=_hptr(obs) if obs.size else None, d_obs=opt(d_obs, obs.shape[0]),
+                 m_prior=opt(m_prior, n), f=opt(f, n), u_top=u_top, u_bottom=u_bottom,
+                 precision=HP_FP32_IR if precision == "fp32_ir" else HP_FP64_PLAIN,
+                 rtol=rtol, max_iter=max_iter)
+        h = C.c_void_p()
+        _check(L.hp_problem_create(C.byref(d), C.byref(h)), "hp_problem_create")
+        self._h = h
+        self.dim, self.N = dim, N
+        self.n = L.hp_num_nodes(h)
+        self.nelems = L.hp_num_elements(h)
+        self.nobs = obs.shape[0]
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hp_problem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- configuration ----------------------------------------------------
+    def set_stream(self, stream=None):
+        ptr = None if stream is None else C.c_void_p(stream.cuda_stream)
+        _check(lib().hp_set_stream(self._h, ptr), "hp_set_stream")
+
+    def set_precision(self, precision: str):
+        _check(lib().hp_set_precision(self._h, HP_FP32_IR if precision == "fp32_ir" else HP_FP64_PLAIN),
+               "hp_set_precision")
+
+    def set_tolerance(self, rtol: float, max_iter: int = 500):
+        _check(lib().hp_set_tolerance(self._h, rtol, max_iter), "hp_set_tolerance")
+
+    def set_data(self, d_obs, sigma: float):
+        a = np.ascontiguousarray(np.asarray(d_obs, dtype=np.float64))
+        _check(lib().hp_set_data(self._h, _hptr(a), sigma), "hp_set_data")
+
+    def get_data(self):
+        out = np.zeros(self.nobs)
+        _check(lib().hp_get_data(self._h, _hptr(out)), "hp_get_data")
+        return out
+
+    # ---- helpers -------------------------------------------------------------
+    def zeros(self, s=None):
+        return torch.zeros((self.n,) if s is None else (s, self.n), dtype=torch.float64, device=self.device)
+
+    def _vec(self, t, name):
+        t2, s, _ = _block(t, self.n, name)
+        if s != 1:
+            raise ValueError(f"{name}: expected a single vector")
+        return t2
+
+    # ---- forward / cost / gradient -------------------------------------------
+    def set_point(self, m):
+        m = self._vec(m, "m")
+        J = (C.c_double * 3)()
+        _check(lib().hp_set_point(self._h, _dptr(m), J), "hp_set_point")
+        return tuple(J)
+
+    def forward(self, m):
+        m = self._vec(m, "m")
+        u = self.zeros()
+        st = SolveStats()
+        _check(lib().hp_forward(self._h, _dptr(m), _dptr(u), C.byref(st)), "hp_forward")
+        return u, st.as_dict()
+
+    def observe(self, u):
+        u = self._vec(u, "u")
+        y = torch.zeros(max(self.nobs, 1), dtype=torch.float64, device=self.device)
+        _check(lib().hp_observe(self._h, _dptr(u), _dptr(y)), "hp_observe")
+        return y[: self.nobs]
+
+    def gradient(self, m):
+        m = self._vec(m, "m")
+        g = self.zeros()
+        J = (C.c_double * 3)()
+        _check(lib().hp_gradient(self._h, _dptr(m), _dptr(g), J), "hp_gradient")
+        return g, tuple(J)
+
+    # ---- Hessian / operators --------------------------------------------------
+    def hessian_apply(self, X, with_prior: bool = False, out=None):
+        X2, s, n = _block(X, self.n, "X")
+        Y = torch.empty_like(X2) if out is None else _block(out, self.n, "out")[0]
+        st = SolveStats()
+        _check(lib().hp_hessian_apply(self._h, _dptr(X2), n, _dptr(Y), n, s,
+                                      HP_WITH_PRIOR if with_prior else HP_MISFIT_ONLY, C.byref(st)),
+               "hp_hessian_apply")
+        return (Y.reshape(X.shape) if out is None else out), st.as_dict()
+
+    def _unary(self, fname, X, with_stats=False):
+        X2, s, n = _block(X, self.n, "X")
+        Y = torch.empty_like(X2)
+        if with_stats:
+            st = SolveStats()
+            _check(getattr(lib(), fname)(self._h, _dptr(X2), n, _dptr(Y), n, s, C.byref(st)), fname)
+            return Y.reshape(X.shape), st.as_dict()
+        _check(getattr(lib(), fname)(self._h, _dptr(X2), n, _dptr(Y), n, s), fname)
+        return Y.reshape(X.shape)
+
+    def stiffness_apply(self, X):
+        return self._unary("hp_stiffness_apply", X)
+
+    def state_solve(self, B):
+        return self._unary("hp_state_solve", B, True)
+
+    def C_apply(self, X):
+        return self._unary("hp_C_apply", X)
+
+    def Ct_apply(self, W):
+        return self._unary("hp_Ct_apply", W)
+
+    def prior_apply(self, X):
+        return self._unary("hp_prior_apply", X)
+
+    def mass_apply(self, X):
+        return self._unary("hp_mass_apply", X)
+
+    def prior_solve(self, B):
+        return self._unary("hp_prior_solve", B, True)
+
+    def mass_solve(self, B):
+        return self._unary("hp_mass_solve", B, True)
+
+    def R_apply(self, X):
+        return self._unary("hp_R_apply", X)
+
+    def Rinv_apply(self, X):
+        return self._unary("hp_Rinv_apply", X)
+
+    def mass_factor_apply(self, eta):
+        ne = self.nelems * (self.dim + 1)
+        E2, s, _ = _block(eta, ne, "eta")
+        W = torch.empty((s, self.n), dtype=torch.float64, device=self.device)
+        _check(lib().hp_mass_factor_apply(self._h, _dptr(E2), ne, _dptr(W), self.n, s), "hp_mass_factor_apply")
+        return W if eta.dim() == 2 else W[0]
+
+    # ---- algorithms --------------------------------------------------------------
+    def newton_cg_map(self, m0=None, rel_tol=1e-6, abs_tol=0.0, max_iter=50, max_backtrack=10,
+                      c_armijo=1e-4, cg_max_iter=200):
+        m = self.zeros() if m0 is None else self._vec(m0, "m0").clone().reshape(-1)
+        o = NewtonOpts(rel_tol, abs_tol, max_iter, max_backtrack, c_armijo, cg_max_iter)
+        st = NewtonStats()
+        rc = lib().hp_newton_cg_map(self._h, _dptr(m), C.byref(o), C.byref(st))
+        if rc not in (HP_OK, HP_ERR_NOT_CONVERGED):
+            _check(rc, "hp_newton_cg_map")
+        return m, st.as_dict()
+
+    def lowrank_eig(self, m_map, k, p, Omega, single_pass=False):
+        m_map = self._vec(m_map, "m_map")
+        O2, s, n = _block(Omega, self.n, "Omega")
+        if s != k + p:
+            raise ValueError("Omega must have k + p columns")
+        lam = torch.zeros(k, dtype=torch.float64, device=self.device)
+        V = torch.zeros((k, self.n), dtype=torch.float64, device=self.device)
+        st = SolveStats()
+        _check(lib().hp_lowrank_eig(self._h, _dptr(m_map), k, p, _dptr(O2), n, _dptr(lam), _dptr(V), n,
+                                    1 if single_pass else 0, C.byref(st)), "hp_lowrank_eig")
+        return lam, V, st.as_dict()
+
+    def laplace_sample(self, m_map, lam, V, eta, want_prior=True, want_post=True):
+        ne = self.nelems * (self.dim + 1)
+        E2, N, _ = _block(eta, ne, "eta")
+        k = 0 if V is None else V.shape[0]
+        prior = torch.empty((N, self.n), dtype=torch.float64, device=self.device) if want_prior else None
+        post = torch.empty((N, self.n), dtype=torch.float64, device=self.device) if want_post else None
+        st = SolveStats()
+        null = C.c_void_p(0)
+        _check(lib().hp_laplace_sample(
+            self._h, _dptr(self._vec(m_map, "m_map")) if want_post else null,
+            _dptr(lam) if want_post else null, _dptr(V) if want_post else null, self.n, k,
+            _dptr(E2), ne, N, _dptr(prior) if want_prior else null, _dptr(post) if want_post else null,
+            self.n, C.byref(st)), "hp_laplace_sample")
+        return prior, post, st.as_dict()
