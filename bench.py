@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark: Gauss-Newton Hessian actions per second at relative residual 1e-8.
+
+One step = one block of k+p Gauss-Newton Hessian actions (the block the
+double-pass eigensolver applies, Algorithm 2) at the MAP point of a seeded
+synthetic problem: per column one incremental forward and one incremental
+adjoint solve (FP32 multigrid PCG inside FP64 iterative refinement, every
+column to relative residual 1e-8), plus the C X, B^T B and C^T kernels.
+Inputs are resident on the device; L2 is flushed (a 512 MB write) before every
+timed step and each step is timed with CUDA events on the library's stream.
+
+Also reported: e2e (same metric through the C ABI with the block copied from
+pinned host memory and the result read back inside the timed region), the
+time to MAP (Newton-CG, Algorithm 1) plus the rank-k eigenpairs (Algorithm 2),
+the roofline of the dominant kernel measured live with CUDA events, clocks
+sampled during the timed region, and the FP64 CPU oracle on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload medium2d|small2d|cube3d] [--precision fp32_ir|fp64]
+"""
+from __future__ import annotations
+
+import os
+
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+import argparse
+import hashlib
+import json
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+import workloads as W  # noqa: E402
+
+METRIC = "Hessian actions/s at rel-res 1e-8"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="medium2d", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--precision", default="fp32_ir", choices=["fp32_ir", "fp64"])
+    ap.add_argument("--no-map", action="store_true", help="linearise at the true parameter instead of the MAP")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    return ap.parse_args()
+
+
+def workload_desc(w, precision):
+    prec = "FP32 MG-PCG in FP64 refinement" if precision == "fp32_ir" else "FP64 MG-PCG"
+    return (f"{w.name}: {w.dim}D {'x'.join([str(w.N)] * w.dim)} P1 "
+            f"({'right triangles' if w.dim == 2 else 'Kuhn tetrahedra'}), n={w.nnodes}, q={w.nobs}, "
+            f"block of k+p={w.k + w.p} Gauss-Newton Hessian actions at the MAP, {prec}, rel-res 1e-8")
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (the only place besides --impl reference that runs oracle/)
+# ---------------------------------------------------------------------------
+def oracle_rate(w, ncols_sample, seconds_hint=20.0):
+    """Oracle Hessian actions/s for a (k+p)-column block, from a bounded sample:
+    one factorisation at the linearisation point + ncols_sample columns,
+    extrapolated to the full block."""
+    from oracle.inverse import make_problem
+    dr = W.draws(w)
+    prob, m_true, _ = make_problem(w, dr)
+    m = m_true
+    s_full = w.k + w.p
+    X = W.omega(w)
+    t0 = time.perf_counter()
+    u = prob.forward(m)                       # factorises K(m)
+    t_fac = time.perf_counter() - t0
+    cols = 0
+    t1 = time.perf_counter()
+    while cols < ncols_sample:
+        prob.hessian_misfit(m, u, X[:, cols:cols + 1])
+        cols += 1
+        if time.perf_counter() - t1 > seconds_hint:
+            break
+    t_cols = time.perf_counter() - t1
+    per_col = t_cols / cols
+    block_time = t_fac + s_full * per_col
+    return s_full / block_time, cols, t_fac, per_col
+
+
+def cpu_baseline_block(w):
+    ncols = {"small2d": 30, "medium2d": 8, "cube3d": 2}[w.name]
+    rate, cols, t_fac, per_col = oracle_rate(w, ncols)
+    return {"value": rate, "unit": "actions/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 scipy oracle (sparse direct solves), one K(m) factorisation ({t_fac:.2f} s) + "
+                       f"{cols} of {w.k + w.p} columns ({per_col * 1e3:.1f} ms each), extrapolated to the "
+                       f"{w.k + w.p}-column block, 1 thread")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = W.WORKLOADS[args.workload]
+    from oracle.inverse import make_problem
+    dr = W.draws(w)
+    prob, m_true, _ = make_problem(w, dr)
+    m = m_true
+    X = W.omega(w)
+    s_ref = {"small2d": 10, "medium2d": 2, "cube3d": 1}[w.name]
+    u = prob.forward(m)
+    for i in range(args.warmup):
+        prob.hessian_misfit(m, u, X[:, :s_ref])
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        prob.hessian_misfit(m, u, X[:, (i * s_ref) % (w.k + w.p):(i * s_ref) % (w.k + w.p) + s_ref])
+    dt = time.perf_counter() - t0
+    val = args.steps * s_ref / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "actions/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(w, "fp64") + f"; reference arm: {s_ref} columns per step",
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": val, "unit": "actions/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{s_ref} Hessian-action columns per step, K(m) factorised once in warm-up"},
+        "e2e": {"value": val, "unit": "actions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(prefix="hp_clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if key in d:
+                    return float(d[key]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback (6.8 TB/s recipe figure; MEASURED_PEAKS.json absent)"
+
+
+def family_bytes(fam, n, s, dim, fp32):
+    """Algorithmic DRAM bytes of one launch of a level-0 kernel family on n nodes x s columns."""
+    w = 4 if fp32 else 8
+    nf = dim  # forward couplings of the stiffness stencil
+    if fam == "matvec":       # read p, write q, coefficients (diag + nf)
+        return n * (2 * s * w + (nf + 1) * w)
+    if fam == "smooth":       # read x, b, write y, coefficients (diag, invdiag, nf)
+        return n * (3 * s * w + (nf + 2) * w)
+    if fam == "resid_mg":     # read x, b, write r, coefficients
+        return n * (3 * s * w + (nf + 1) * w)
+    if fam == "resid64":      # FP64 refinement residual
+        return n * (3 * s * 8 + (nf + 1) * 8)
+    if fam == "cg_update":    # read p, q, x, r; write x, r
+        return n * 6 * s * w
+    return None
+
+
+def traffic_record(fam, workload):
+    """ncu DRAM bytes per launch recorded in profiles/traffic.json, valid only while
+    the kernel sources are unchanged (sha256 of csrc/solver.cu + common.cuh)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        h = hashlib.sha256()
+        for f in ("solver.cu", "common.cuh"):
+            h.update(open(os.path.join(ROOT, "paper_1909_03948_gb300", "csrc", f), "rb").read())
+        rec = d.get(workload, {}).get(fam)
+        if rec and rec.get("src_sha256") == h.hexdigest():
+            return rec.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+    return None
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_1909_03948_gb300 import Problem, kernel_launches
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = W.WORKLOADS[args.workload]
+    wr = W.Workload(**{**w.__dict__, "seed": w.seed + 1000 * rank})     # weak scaling: own replica per rank
+    dr = W.draws(wr)
+    s = w.k + w.p
+    # ---- problem set-up (untimed): synthetic truth and data on the GPU path ----
+    P = Problem(w.dim, w.N, w.gamma, w.delta, 1.0, dr.obs_xyz, precision=args.precision, rtol=1e-8)
+    eta = torch.tensor(dr.eta_true.reshape(1, -1), device=dev)
+    m_true, _, _ = P.laplace_sample(None, None, None, eta, want_prior=True, want_post=False)
+    m_true = m_true[0].contiguous()
+    u_true, _ = P.forward(m_true)
+    sigma = w.noise_level * float(u_true.abs().max())
+    d = P.observe(u_true).cpu().numpy() + sigma * dr.xi_noise
+    P.set_data(d, sigma)
+    Omega = torch.tensor(np.ascontiguousarray(W.omega(wr).T), device=dev)
+    # ---- time to MAP + rank-k eigenpairs (once) ----
+    extra = {}
+    if not args.no_map:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m_map, nst = P.newton_cg_map(rel_tol=1e-6)
+        lam, V, est = P.lowrank_eig(m_map, w.k, w.p, Omega)
+        torch.cuda.synchronize()
+        t_me = time.perf_counter() - t0
+        extra = {"time_to_map_eig_s": t_me, "newton_iterations": nst["iterations"],
+                 "newton_cg_iterations": nst["cg_iterations"], "newton_converged": bool(nst["converged"]),
+                 "lambda_1": float(lam[0]), "lambda_k": float(lam[-1])}
+        m_lin = m_map
+    else:
+        m_lin = m_true
+    P.set_point(m_lin)
+    Y = torch.empty_like(Omega)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        return P.hessian_apply(Omega, out=Y)[1]
+
+    for _ in range(max(args.warmup, 3)):
+        st = step()
+    # ---- timed region (device-resident inputs) ----
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    l0 = kernel_launches()
+    times, iters, outers = [], [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = step()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        iters.append(st["iterations"])
+        outers.append(st["outer"])
+    torch.cuda.synchronize()
+    launches = kernel_launches() - l0
+    clk = clocks.stop()
+    t_total = sum(times)
+    # ---- same K steps again with CUDA events around the level-0 kernels (roofline) ----
+    P.profile_enable(True)
+    t_prof = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        e1.synchronize()
+        t_prof += e0.elapsed_time(e1) / 1e3
+    prof = P.profile_read()
+    P.profile_enable(False)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t)
+    value = world * args.steps * s / t_total
+    # ---- e2e through the C ABI with host buffers ----
+    Xh = torch.empty((s, P.n), dtype=torch.float64).pin_memory()
+    Xh.copy_(Omega.cpu())
+    Yh = torch.empty_like(Xh).pin_memory()
+    Xd = torch.empty_like(Omega)
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        Xd.copy_(Xh, non_blocking=True)
+        P.hessian_apply(Xd, out=Y)
+        Yh.copy_(Y, non_blocking=False)
+        e2e_times.append(time.perf_counter() - ta)
+    e2e_val = world * args.steps * s / sum(e2e_times) if e2e_times else None
+    # ---- roofline of the dominant level-0 kernel family ----
+    fams = {k: v for k, v in prof.items() if k != "vcycle" and v[0] > 0}
+    dom = max(fams, key=lambda k: fams[k][1]) if fams else None
+    roof = None
+    if dom:
+        cnt, ms = fams[dom]
+        fp32 = args.precision == "fp32_ir" and dom != "resid64"
+        bpl = family_bytes(dom, P.n, s, w.dim, fp32)
+        avg_s = ms / cnt / 1e3
+        peak, src = measured_peak()
+        ach = bpl / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": traffic_record(dom, w.name), "kernel": dom, "launches": cnt,
+                "avg_launch_us": avg_s * 1e6, "algorithmic_bytes_per_launch": bpl, "peak_source": src,
+                "share_of_step": ms / 1e3 / t_prof,
+                "measured_in": "a second pass of the same K steps with CUDA events around each launch",
+                "families": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu and world == 1:
+        try:
+            cpu = cpu_baseline_block(w)
+        except Exception as ex:  # pragma: no cover
+            cpu = {"value": None, "unit": "actions/s", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "actions/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-in-f64-IR" if args.precision == "fp32_ir" else "f64",
+        "data": "synthetic (seeded prior draw, pointwise observations with 1% noise)",
+        "config": {"workload": workload_desc(w, args.precision), "block_columns": s,
+                   "l2": "flushed (512 MB write) before every timed step", "replicas": world},
+        "e2e": {"value": e2e_val, "unit": "actions/s", "h2d_bytes_per_step": s * P.n * 8,
+                "d2h_bytes_per_step": s * P.n * 8},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "pcg": {"inner_iterations_per_step": statistics.median(iters), "refinement_steps": statistics.median(outers)},
+        **extra,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

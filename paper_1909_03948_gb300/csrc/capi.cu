@@ -467,11 +467,15 @@ void hp_problem_destroy(hp_problem *P) {
       W->lb[l].release();
     }
   }
+  drop_graphs(P);
+  if (P->cap) cudaStreamDestroy(P->cap);
+  free_scalars_host(P);
   ScalarWS &S = P->sc;
-  for (DBuf *b : {&S.rz, &S.pq, &S.rr, &S.bb, &S.alpha, &S.beta, &S.scale, &S.tmp, &S.active, &S.partial, &S.counter})
+  for (DBuf *b : {&S.iter, &S.rz, &S.pq, &S.rr, &S.bb, &S.alpha, &S.beta, &S.scale, &S.tmp, &S.active, &S.partial, &S.counter})
     b->release();
   for (DBuf *b : {&P->r64, &P->b64, &P->t64a, &P->t64b, &P->t64c, &P->obsbuf, &P->small}) b->release();
   for (int i = 0; i < 6; ++i) P->vtmp[i].release();
+  for (cudaEvent_t e : P->prof_ev) cudaEventDestroy(e);
   delete P;
 }
 
@@ -504,6 +508,33 @@ int hp_set_data(hp_problem *P, const double *d_obs_host, double sigma) {
 int hp_get_data(const hp_problem *P, double *d_out_host) {
   if (!P || !d_out_host) return set_error(HP_ERR_INVALID, "null");
   if (P->nobs) HP_CUDA(cudaMemcpy(d_out_host, P->d_obs, sizeof(double) * P->nobs, cudaMemcpyDeviceToHost));
+  return HP_OK;
+}
+
+int hp_profile_enable(hp_problem *P, int on) {
+  if (!P) return set_error(HP_ERR_INVALID, "null problem");
+  HP_CUDA(cudaStreamSynchronize(P->st));
+  P->prof_on = on != 0;
+  P->prof_used = 0;
+  return HP_OK;
+}
+
+int hp_profile_read(hp_problem *P, int nids, int *counts, double *total_ms) {
+  if (!P || nids < 0 || (nids > 0 && (!counts || !total_ms))) return set_error(HP_ERR_INVALID, "arguments");
+  HP_CUDA(cudaStreamSynchronize(P->st));
+  for (int i = 0; i < nids; ++i) {
+    counts[i] = 0;
+    total_ms[i] = 0.0;
+  }
+  for (size_t r = 0; r < P->prof_used; ++r) {
+    const int id = P->prof_id[r];
+    if (id < 0 || id >= nids) continue;
+    float ms = 0.f;
+    HP_CUDA(cudaEventElapsedTime(&ms, P->prof_ev[2 * r], P->prof_ev[2 * r + 1]));
+    counts[id] += 1;
+    total_ms[id] += ms;
+  }
+  P->prof_used = 0;
   return HP_OK;
 }
 

@@ -64,8 +64,10 @@ struct ScalarWS {
   DBuf active;                                     // int per column
   DBuf partial;                                    // double [slot][col][block]
   DBuf counter;                                    // unsigned [slot][col]
-  std::vector<int> h_active;
-  std::vector<double> h_rr, h_bb;
+  DBuf iter;                                       // int: PCG iteration counter
+  int hcap = 0;                                    // pinned host mirrors
+  int *h_active = nullptr, *h_iter = nullptr;
+  double *h_rr = nullptr, *h_bb = nullptr;
 };
 
 }  // namespace hp
@@ -83,6 +85,8 @@ struct hp_problem {
   int nu = 2;                   // pre/post Jacobi sweeps
   double omega = 0.7;           // Jacobi damping
   cudaStream_t st = nullptr;
+  cudaStream_t cap = nullptr;   // private stream used to capture CUDA graphs
+  bool use_graphs = true;       // inner PCG loops as graphs with a device-side while node
 
   hp::Level lv[HP_MAXL];
   hp::CoarseInv cK, cA;
@@ -107,6 +111,12 @@ struct hp_problem {
   hp::BlockWS<double> w64;
   hp::ScalarWS sc;
   hp::DBuf r64, b64, t64a, t64b, t64c, obsbuf, small, vtmp[6];
+
+  // optional CUDA-event timing of selected kernels (hp_profile_*)
+  bool prof_on = false;
+  std::vector<int> prof_id;
+  std::vector<cudaEvent_t> prof_ev;   // 2 per record
+  size_t prof_used = 0;
 };
 
 namespace hp {
@@ -123,6 +133,19 @@ int cuda_check(cudaError_t e, const char *where);
     int _rc = (call);             \
     if (_rc) return _rc;          \
   } while (0)
+
+// ---- profiling ids (kernel families timed by hp_profile_*) ----------------
+enum ProfId {
+  PROF_MATVEC = 0,     // level-0 stencil apply fused with <p, Kp> (PCG matvec)
+  PROF_SMOOTH = 1,     // level-0 damped-Jacobi sweep
+  PROF_RESID_MG = 2,   // level-0 residual inside the V-cycle
+  PROF_RESID64 = 3,    // FP64 refinement residual
+  PROF_CG_UPDATE = 4,  // x += a p, r -= a q, <r, r>
+  PROF_VCYCLE = 5,     // whole preconditioner application
+  PROF_COUNT = 6
+};
+int prof_start(hp_problem *P, int id);   // returns a record index or -1
+void prof_stop(hp_problem *P, int rec);
 
 // ---- fem.cu -------------------------------------------------------------
 int build_hierarchy_geometry(hp_problem *P);  // levels, allocs, prior/mass stencils, coarse A inverse
@@ -151,6 +174,8 @@ int block_dot(hp_problem *P, const double *X, long ldx, const double *Y, long ld
 
 // ---- solver.cu --------------------------------------------------------------
 int ensure_scalars(hp_problem *P, int s);
+void drop_graphs(hp_problem *P);
+void free_scalars_host(hp_problem *P);
 int solve_block(hp_problem *P, OpKind op, const double *B, long ldb, double *X, long ldx, int s,
                 double rtol, hp_solve_stats *st);
 int apply_op64(hp_problem *P, OpKind op, const double *X, long ldx, double *Y, long ldy, int s);

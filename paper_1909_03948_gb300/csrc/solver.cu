@@ -22,6 +22,8 @@
 
 namespace hp {
 
+void drop_graphs(hp_problem *P);
+
 enum { FIN_STORE = 0, FIN_ALPHA = 1, FIN_RR = 2, FIN_BETA = 3, FIN_INIT = 4 };
 
 struct Fin {
@@ -30,6 +32,7 @@ struct Fin {
   int kind = FIN_STORE;
   double *rz = nullptr, *alpha = nullptr, *beta = nullptr, *rr = nullptr, *bb = nullptr, *out = nullptr;
   int *active = nullptr;
+  int *iter = nullptr;   // PCG iteration counter (FIN_BETA: beta = 0 on the first iteration)
   double tol2 = 0.0;
 };
 
@@ -42,7 +45,7 @@ __device__ __forceinline__ void fin_apply(const Fin &f, int j, double s) {
       f.active[j] = f.active[j] && (s > f.tol2 * f.bb[j]);
       break;
     case FIN_BETA: {
-      const double b = (f.active[j] && f.rz[j] != 0.0) ? s / f.rz[j] : 0.0;
+      const double b = (*f.iter > 0 && f.active[j] && f.rz[j] != 0.0) ? s / f.rz[j] : 0.0;
       f.beta[j] = b;
       f.rz[j] = s;
     } break;
@@ -230,13 +233,29 @@ __global__ void k_cg_update(long n, const T *__restrict__ p, const T *__restrict
 }
 
 template <typename T>
-__global__ void k_p_update(long n, const T *__restrict__ z, T *__restrict__ p, long ld, const double *__restrict__ beta,
-                           int first) {
+__global__ void k_p_update(long n, const T *__restrict__ z, T *__restrict__ p, long ld, const double *__restrict__ beta) {
   const int j = blockIdx.y;
-  const T b = first ? T(0) : (T)beta[j];
+  const T b = (T)beta[j];
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const long o = ld * j + i;
-    p[o] = first ? z[o] : z[o] + b * p[o];
+    p[o] = z[o] + b * p[o];
+  }
+}
+
+// End of a PCG iteration: count it and decide whether another one runs.  In
+// graph mode the decision drives the device-side while loop.
+__global__ void k_pcg_cond(const int *__restrict__ active, int s, int *iter, int maxit, int bump,
+                           cudaGraphConditionalHandle h, int use_handle) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < s; j += blockDim.x)
+    if (active[j]) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int it = *iter + bump;
+    *iter = it;
+    if (use_handle) cudaGraphSetConditional(h, (any && it < maxit) ? 1u : 0u);
   }
 }
 
@@ -271,6 +290,31 @@ __global__ void k_accum(long n, const T *__restrict__ d, long ldd, const double 
   const double inv = 1.0 / sc;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     X[ldx * j + i] += inv * (double)d[ldd * j + i];
+}
+
+// ---------------------------------------------------------------------------
+// profiling: a pair of events around selected launches (off by default)
+// ---------------------------------------------------------------------------
+int prof_start(hp_problem *P, int id) {
+  if (!P->prof_on || id < 0) return -1;
+  const size_t r = P->prof_used;
+  while (P->prof_ev.size() < 2 * (r + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    P->prof_ev.push_back(e);
+  }
+  if (P->prof_id.size() < r + 1) P->prof_id.resize(r + 1);
+  P->prof_id[r] = -1;  // open
+  cudaEventRecord(P->prof_ev[2 * r], P->st);
+  P->prof_used = r + 1;
+  P->prof_id[r] = -(id + 2);
+  return (int)r;
+}
+
+void prof_stop(hp_problem *P, int rec) {
+  if (rec < 0) return;
+  cudaEventRecord(P->prof_ev[2 * rec + 1], P->st);
+  P->prof_id[rec] = -P->prof_id[rec] - 2;  // closed: store the id
 }
 
 // ---------------------------------------------------------------------------
@@ -343,7 +387,17 @@ template <typename T> static int ensure_ws(hp_problem *P, int s) {
     HP_TRY(W.lb[l].ensure(b));
   }
   W.scap = s;
+  drop_graphs(P);  // captured graphs hold the old workspace pointers
   return 0;
+}
+
+void free_scalars_host(hp_problem *P) {
+  ScalarWS &S = P->sc;
+  for (void *p : {(void *)S.h_active, (void *)S.h_iter, (void *)S.h_rr, (void *)S.h_bb})
+    if (p) cudaFreeHost(p);
+  S.h_active = S.h_iter = nullptr;
+  S.h_rr = S.h_bb = nullptr;
+  S.hcap = 0;
 }
 
 int ensure_scalars(hp_problem *P, int s) {
@@ -361,10 +415,17 @@ int ensure_scalars(hp_problem *P, int s) {
   HP_TRY(S.active.ensure(sizeof(int) * std::max(s, 4)));
   HP_TRY(S.partial.ensure(sizeof(double) * (size_t)nbmax * s));
   HP_TRY(S.counter.ensure(sizeof(unsigned) * s));
+  HP_TRY(S.iter.ensure(sizeof(int) * 4));
   HP_CUDA(cudaMemsetAsync(S.counter.p, 0, sizeof(unsigned) * s, P->st));
-  S.h_active.resize(s);
-  S.h_rr.resize(s);
-  S.h_bb.resize(s);
+  if (S.hcap < s) {
+    free_scalars_host(P);
+    HP_CUDA(cudaMallocHost(&S.h_active, sizeof(int) * s));
+    HP_CUDA(cudaMallocHost(&S.h_iter, sizeof(int) * 4));
+    HP_CUDA(cudaMallocHost(&S.h_rr, sizeof(double) * s));
+    HP_CUDA(cudaMallocHost(&S.h_bb, sizeof(double) * s));
+    S.hcap = s;
+  }
+  drop_graphs(P);  // captured graphs hold the old scalar pointers
   S.scap = s;
   return 0;
 }
@@ -380,6 +441,7 @@ static Fin make_fin(hp_problem *P, int kind, double tol2 = 0.0, double *out = nu
   f.rr = P->sc.rr.as<double>();
   f.bb = P->sc.bb.as<double>();
   f.active = P->sc.active.as<int>();
+  f.iter = P->sc.iter.as<int>();
   f.tol2 = tol2;
   f.out = out;
   return f;
@@ -426,10 +488,16 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
     k_jacobi0<T><<<dim3(blocks_for(g.n, s), s), NT, 0, st>>>(g.n, S.invdiag, rl[l], ld[l], c, ld[l], om, nofin, 0);
     count_launch();
     for (int k = 1; k < P->nu; ++k) {
+      const int pr = prof_start(P, l == 0 ? PROF_SMOOTH : -1);
       stencil_launch<T, M_JACOBI>(g, S, c, ld[l], rl[l], ld[l], o, ld[l], s, om, nofin, st);
+      prof_stop(P, pr);
       std::swap(c, o);
     }
-    stencil_launch<T, M_RESID>(g, S, c, ld[l], rl[l], ld[l], o, ld[l], s, om, nofin, st);
+    {
+      const int pr = prof_start(P, l == 0 ? PROF_RESID_MG : -1);
+      stencil_launch<T, M_RESID>(g, S, c, ld[l], rl[l], ld[l], o, ld[l], s, om, nofin, st);
+      prof_stop(P, pr);
+    }
     const GridDesc &gc = P->lv[l + 1].g;
     dim3 grid(blocks_for(gc.n, s), s);
     T *rc = const_cast<T *>(rl[l + 1]);
@@ -459,10 +527,12 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
     count_launch();
     T *c = cur[l], *o = oth[l];
     for (int k = 0; k < P->nu; ++k) {
+      const int pr = prof_start(P, l == 0 ? PROF_SMOOTH : -1);
       if (l == 0 && k == P->nu - 1)
         stencil_launch<T, M_JACOBI_DOT>(g, S, c, ld[l], rl[l], ld[l], o, ld[l], s, om, fin, st);
       else
         stencil_launch<T, M_JACOBI>(g, S, c, ld[l], rl[l], ld[l], o, ld[l], s, om, nofin, st);
+      prof_stop(P, pr);
       std::swap(c, o);
     }
     cur[l] = c;
@@ -478,9 +548,28 @@ __global__ void k_dot2(long n, const T *__restrict__ a, const T *__restrict__ b,
   dot_finish((double)acc, fin, j);
 }
 
-// PCG on W.r (overwritten) -> W.x.  Returns iterations in *its.
+// PCG on W.r (overwritten) -> W.x.
+//   init:  x = 0, p = 0, bb = rr = <r, r>, active = bb > 0, iter = 0
+//   body:  z = M r, beta = <r,z>/rz (0 at iter 0), p = z + beta p,
+//          q = K p, alpha = rz/<p,q>, x += alpha p, r -= alpha q, rr = <r,r>,
+//          active &= rr > tol^2 bb, iter += 1; repeat while any active and iter < maxit.
 template <typename T>
-static int pcg(hp_problem *P, OpKind op, int s, double rtol, int maxit, int *its) {
+static void pcg_init(hp_problem *P, OpKind op, int s, cudaGraphConditionalHandle h, int use_handle, int maxit) {
+  BlockWS<T> &W = ws_of<T>(P);
+  cudaStream_t st = P->st;
+  const long n = P->n, ld = W.ldn;
+  dim3 grid(blocks_for(n, s), s);
+  cudaMemsetAsync(W.x.p, 0, sizeof(T) * ld * s, st);
+  cudaMemsetAsync(W.p.p, 0, sizeof(T) * ld * s, st);
+  cudaMemsetAsync(P->sc.iter.p, 0, sizeof(int), st);
+  k_selfdot<T><<<grid, NT, 0, st>>>(n, W.r.template as<T>(), ld, make_fin(P, FIN_INIT));
+  k_pcg_cond<<<1, 256, 0, st>>>(P->sc.active.as<int>(), s, P->sc.iter.as<int>(), maxit, 0, h, use_handle);
+  count_launch(2);
+}
+
+template <typename T>
+static void pcg_body(hp_problem *P, OpKind op, int s, double tol2, cudaGraphConditionalHandle h, int use_handle,
+                     int maxit) {
   BlockWS<T> &W = ws_of<T>(P);
   cudaStream_t st = P->st;
   const long n = P->n, ld = W.ldn;
@@ -489,41 +578,146 @@ static int pcg(hp_problem *P, OpKind op, int s, double rtol, int maxit, int *its
   const GridDesc &g0 = P->lv[0].g;
   const Stencil<T> &S0 = stencil_of<T>(P, op, 0);
   dim3 grid(blocks_for(n, s), s);
-  HP_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * ld * s, st));
-  k_selfdot<T><<<grid, NT, 0, st>>>(n, r, ld, make_fin(P, FIN_INIT));
-  count_launch();
-  // z0 = M r0, rz = <r0, z0>
-  const bool single_level = (op != OP_M && P->L == 1);
-  precondition<T>(P, op, s, r, z, make_fin(P, FIN_STORE, 0.0, P->sc.rz.as<double>()));
-  if (single_level) {
-    k_dot2<T><<<grid, NT, 0, st>>>(n, r, z, ld, make_fin(P, FIN_STORE, 0.0, P->sc.rz.as<double>()));
+  int pr = prof_start(P, PROF_VCYCLE);
+  precondition<T>(P, op, s, r, z, make_fin(P, FIN_BETA));
+  prof_stop(P, pr);
+  if (op != OP_M && P->L == 1) {
+    k_dot2<T><<<grid, NT, 0, st>>>(n, r, z, ld, make_fin(P, FIN_BETA));
     count_launch();
   }
-  k_p_update<T><<<grid, NT, 0, st>>>(n, z, p, ld, P->sc.beta.as<double>(), 1);
+  k_p_update<T><<<grid, NT, 0, st>>>(n, z, p, ld, P->sc.beta.as<double>());
   count_launch();
-  int *hact = P->sc.h_active.data();
-  int it = 0;
+  pr = prof_start(P, PROF_MATVEC);
+  stencil_launch<T, M_APPLY_DOT>(g0, S0, p, ld, nullptr, 0, q, ld, s, T(0), make_fin(P, FIN_ALPHA), st);
+  prof_stop(P, pr);
+  pr = prof_start(P, PROF_CG_UPDATE);
+  k_cg_update<T><<<grid, NT, 0, st>>>(n, p, q, x, r, ld, P->sc.alpha.as<double>(), make_fin(P, FIN_RR, tol2));
+  prof_stop(P, pr);
+  k_pcg_cond<<<1, 256, 0, st>>>(P->sc.active.as<int>(), s, P->sc.iter.as<int>(), maxit, 1, h, use_handle);
+  count_launch(2);
+}
+
+struct PcgGraph {
+  int op, fp32, s, maxit;
+  double tol;
+  cudaGraphExec_t exec;
+  int nkernels;
+};
+static std::vector<std::pair<hp_problem *, PcgGraph>> g_graphs;
+
+void drop_graphs(hp_problem *P) {
+  for (auto it = g_graphs.begin(); it != g_graphs.end();) {
+    if (it->first == P) {
+      cudaGraphExecDestroy(it->second.exec);
+      it = g_graphs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+// Captures init + a conditional WHILE node whose body is one PCG iteration.
+template <typename T>
+static int build_graph(hp_problem *P, OpKind op, int s, double tol, int maxit, PcgGraph *out) {
+  if (!P->cap) HP_CUDA(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
+  cudaStream_t saved = P->st;
+  const bool saved_prof = P->prof_on;
+  P->prof_on = false;
+  P->st = P->cap;
+  const unsigned long long l0 = g_launches;
+  cudaGraph_t g = nullptr;
+  int rc = 0;
+  auto fail = [&](cudaError_t e, const char *w) {
+    rc = cuda_check(e, w);
+    P->st = saved;
+    P->prof_on = saved_prof;
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  };
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return fail(e, "cudaGraphCreate");
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return fail(e, "cudaGraphConditionalHandleCreate");
+  e = cudaStreamBeginCaptureToGraph(P->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return fail(e, "capture init");
+  pcg_init<T>(P, op, s, h, 1, maxit);
+  e = cudaStreamEndCapture(P->cap, &g);
+  if (e != cudaSuccess) return fail(e, "end capture init");
+  size_t nn = 0;
+  cudaGraphGetNodes(g, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  cudaGraphGetNodes(g, nodes.data(), &nn);
+  cudaGraphNode_t leaf = nullptr;
+  for (auto nd : nodes) {
+    size_t nd_out = 0;
+    cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &nd_out);
+    if (nd_out == 0) leaf = nd;
+  }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cn;
+  e = cudaGraphAddNode(&cn, g, leaf ? &leaf : nullptr, nullptr, leaf ? 1 : 0, &cp);
+  if (e != cudaSuccess) return fail(e, "add conditional node");
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(P->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return fail(e, "capture body");
+  pcg_body<T>(P, op, s, tol * tol, h, 1, maxit);
+  e = cudaStreamEndCapture(P->cap, &body);
+  if (e != cudaSuccess) return fail(e, "end capture body");
+  cudaGraphExec_t ex;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  if (e != cudaSuccess) return fail(e, "instantiate");
+  cudaGraphDestroy(g);
+  P->st = saved;
+  P->prof_on = saved_prof;
+  g_launches = l0;  // captured launches are counted when the graph runs
+  *out = PcgGraph{(int)op, sizeof(T) == 4, s, maxit, tol, ex, 0};
+  return 0;
+}
+
+template <typename T>
+static int pcg(hp_problem *P, OpKind op, int s, double rtol, int maxit, int *its) {
+  cudaStream_t st = P->st;
+  int *h_it = P->sc.h_iter;
+  if (P->use_graphs && !P->prof_on) {
+    PcgGraph *G = nullptr;
+    for (auto &pg : g_graphs)
+      if (pg.first == P && pg.second.op == (int)op && pg.second.fp32 == (sizeof(T) == 4) && pg.second.s == s &&
+          pg.second.maxit == maxit && pg.second.tol == rtol)
+        G = &pg.second;
+    if (!G) {
+      PcgGraph ng;
+      HP_TRY(build_graph<T>(P, op, s, rtol, maxit, &ng));
+      g_graphs.push_back({P, ng});
+      G = &g_graphs.back().second;
+    }
+    HP_CUDA(cudaGraphLaunch(G->exec, st));
+    HP_CUDA(cudaMemcpyAsync(h_it, P->sc.iter.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HP_CUDA(cudaStreamSynchronize(st));
+    const int per_it = 12 + 7 * P->L;  // approximate kernels per iteration, for launch accounting
+    count_launch((unsigned long long)(*h_it) * per_it + 3);
+    *its = *h_it;
+    return *h_it >= maxit ? HP_ERR_NOT_CONVERGED : 0;
+  }
   const double tol2 = rtol * rtol;
-  for (it = 1; it <= maxit; ++it) {
-    stencil_launch<T, M_APPLY_DOT>(g0, S0, p, ld, nullptr, 0, q, ld, s, T(0), make_fin(P, FIN_ALPHA), st);
-    k_cg_update<T><<<grid, NT, 0, st>>>(n, p, q, x, r, ld, P->sc.alpha.as<double>(), make_fin(P, FIN_RR, tol2));
-    count_launch();
+  pcg_init<T>(P, op, s, 0, 0, maxit);
+  int *hact = P->sc.h_active;
+  for (;;) {
+    pcg_body<T>(P, op, s, tol2, 0, 0, maxit);
     HP_CUDA(cudaMemcpyAsync(hact, P->sc.active.p, sizeof(int) * s, cudaMemcpyDeviceToHost, st));
+    HP_CUDA(cudaMemcpyAsync(h_it, P->sc.iter.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     HP_CUDA(cudaStreamSynchronize(st));
     int nact = 0;
     for (int j = 0; j < s; ++j) nact += hact[j] != 0;
-    if (nact == 0) break;
-    precondition<T>(P, op, s, r, z, make_fin(P, FIN_BETA));
-    if (single_level) {
-      k_dot2<T><<<grid, NT, 0, st>>>(n, r, z, ld, make_fin(P, FIN_BETA));
-      count_launch();
-    }
-    k_p_update<T><<<grid, NT, 0, st>>>(n, z, p, ld, P->sc.beta.as<double>(), 0);
-    count_launch();
+    if (nact == 0 || *h_it >= maxit) break;
   }
-  *its = std::min(it, maxit);
+  *its = *h_it;
   HP_CUDA(cudaGetLastError());
-  return it > maxit ? HP_ERR_NOT_CONVERGED : 0;
+  return *h_it >= maxit ? HP_ERR_NOT_CONVERGED : 0;
 }
 
 int apply_op64(hp_problem *P, OpKind op, const double *X, long ldx, double *Y, long ldy, int s) {
@@ -534,8 +728,10 @@ int apply_op64(hp_problem *P, OpKind op, const double *X, long ldx, double *Y, l
 // FP64 residual R = B - S X with per-column |R|^2 -> rr (host)
 static int residual64(hp_problem *P, OpKind op, const double *B, long ldb, const double *X, long ldx, double *R,
                       long ldr, int s) {
+  const int pr = prof_start(P, PROF_RESID64);
   stencil_launch<double, M_RESID>(P->lv[0].g, stencil_of<double>(P, op, 0), X, ldx, B, ldb, R, ldr, s, 0.0, Fin{},
                                   P->st);
+  prof_stop(P, pr);
   HP_TRY(block_dot(P, R, ldr, R, ldr, P->n, s, P->sc.rr.as<double>()));
   return 0;
 }
@@ -556,13 +752,13 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
   HP_TRY(block_dot(P, b64, ld64, b64, ld64, n, s, P->sc.bb.as<double>()));
   launch_copy(b64, ld64, r64, ld64, n, s, st);
   HP_TRY(block_dot(P, r64, ld64, r64, ld64, n, s, P->sc.rr.as<double>()));
-  std::vector<double> &hrr = P->sc.h_rr, &hbb = P->sc.h_bb;
-  HP_CUDA(cudaMemcpyAsync(hbb.data(), P->sc.bb.p, sizeof(double) * s, cudaMemcpyDeviceToHost, st));
+  double *hrr = P->sc.h_rr, *hbb = P->sc.h_bb;
+  HP_CUDA(cudaMemcpyAsync(hbb, P->sc.bb.p, sizeof(double) * s, cudaMemcpyDeviceToHost, st));
   std::vector<double> hscale(s);
   int total_its = 0, outer = 0, rc = 0;
   double worst = 0.0;
   for (outer = 0; outer <= P->max_outer; ++outer) {
-    HP_CUDA(cudaMemcpyAsync(hrr.data(), P->sc.rr.p, sizeof(double) * s, cudaMemcpyDeviceToHost, st));
+    HP_CUDA(cudaMemcpyAsync(hrr, P->sc.rr.p, sizeof(double) * s, cudaMemcpyDeviceToHost, st));
     HP_CUDA(cudaStreamSynchronize(st));
     int nact = 0;
     worst = 0.0;

@@ -103,6 +103,8 @@ _SIGS = {
     "hp_newton_cg_map": (_I, [_P, _D, C.POINTER(NewtonOpts), C.POINTER(NewtonStats)]),
     "hp_lowrank_eig": (_I, [_P, _D, _I, _I, _D, _I, _D, _D, _I, _I, C.POINTER(SolveStats)]),
     "hp_laplace_sample": (_I, [_P, _D, _D, _D, _I, _I, _D, _I, _I, _D, _D, _I, C.POINTER(SolveStats)]),
+    "hp_profile_enable": (_I, [_P, _I]),
+    "hp_profile_read": (_I, [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "hp_status_string": (C.c_char_p, [_I]),
     "hp_last_error": (C.c_char_p, []),
     "hp_kernel_launches": (C.c_ulonglong, []),
@@ -322,6 +324,19 @@ class Problem:
         W = torch.empty((s, self.n), dtype=torch.float64, device=self.device)
         _check(lib().hp_mass_factor_apply(self._h, _dptr(E2), ne, _dptr(W), self.n, s), "hp_mass_factor_apply")
         return W if eta.dim() == 2 else W[0]
+
+    # ---- measurement -------------------------------------------------------------
+    PROF_NAMES = ("matvec", "smooth", "resid_mg", "resid64", "cg_update", "vcycle")
+
+    def profile_enable(self, on: bool = True):
+        _check(lib().hp_profile_enable(self._h, 1 if on else 0), "hp_profile_enable")
+
+    def profile_read(self):
+        k = len(self.PROF_NAMES)
+        cnt = (C.c_int * k)()
+        ms = (C.c_double * k)()
+        _check(lib().hp_profile_read(self._h, k, cnt, ms), "hp_profile_read")
+        return {name: (cnt[i], ms[i]) for i, name in enumerate(self.PROF_NAMES)}
 
     # ---- algorithms --------------------------------------------------------------
     def newton_cg_map(self, m0=None, rel_tol=1e-6, abs_tol=0.0, max_iter=50, max_backtrack=10,

@@ -1,0 +1,179 @@
+"""GPU parity of the algorithms (Section 4) against the FP64 oracle:
+  MAP point (Algorithm 1)                       relative 1e-6 (both at relative gradient 1e-9)
+  eigenvalues > 0.1 (Algorithms 2, 4)           relative 1e-6 with the same Omega
+  eigenvectors (lambda_i > 0.1, gap > 10 %)     |v_gpu^T R v_oracle| within 1e-5 of 1
+  samples with identical normals (Section 4.3)  relative 1e-8
+  sample statistics                             within 3 Monte-Carlo standard errors of the exact
+                                                prior / posterior variances (eq. (post_mvar))
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import algorithms as A
+from oracle.inverse import make_problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def _gpu_problem(orc, w, rtol=1e-10, precision="fp32_ir"):
+    from paper_1909_03948_gb300 import Problem
+    return Problem(w.dim, w.N, w.gamma, w.delta, orc.sigma, orc.obs_xyz, d_obs=orc.d_obs, rtol=rtol,
+                   precision=precision)
+
+
+@pytest.fixture(scope="module")
+def small2d():
+    w = W.WORKLOADS["small2d"]
+    orc, m_true, _ = make_problem(w, W.draws(w))
+    res = A.newton_cg(orc, rel_tol=1e-9)
+    assert res.converged
+    P = _gpu_problem(orc, w)
+    yield dict(w=w, orc=orc, m_map=res.m, res=res, P=P)
+    P.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32_ir", "fp64"])
+def test_newton_map_matches_oracle(small2d, precision):
+    orc, w = small2d["orc"], small2d["w"]
+    P = _gpu_problem(orc, w, precision=precision)
+    m, st = P.newton_cg_map(rel_tol=1e-9)
+    P.close()
+    assert st["converged"]
+    ref = small2d["m_map"]
+    assert np.linalg.norm(m.cpu().numpy() - ref) <= 1e-6 * np.linalg.norm(ref)
+    assert abs(st["J"] - orc.cost(ref)[0]) <= 1e-8 * abs(st["J"])
+
+
+def test_newton_baseline_tolerance(small2d):
+    """At the workload's relative gradient tolerance 1e-6 the GPU and the oracle take the
+    same Newton path (same eta_i, same CG) to within one iteration."""
+    orc, w = small2d["orc"], small2d["w"]
+    P = _gpu_problem(orc, w, rtol=1e-8)
+    m, st = P.newton_cg_map(rel_tol=1e-6)
+    P.close()
+    ref = A.newton_cg(orc, rel_tol=1e-6)
+    assert st["converged"] and abs(st["iterations"] - ref.iterations) <= 1
+    assert st["gnorm"] <= 1e-6 * st["gnorm0"]
+    # both stopped inside the same gradient ball: the GPU iterate is no farther from the
+    # MAP than twice the oracle's own 1e-6 iterate (plus rounding slack)
+    m_map = small2d["m_map"]
+    d_or = np.linalg.norm(ref.m - m_map)
+    assert np.linalg.norm(m.cpu().numpy() - m_map) <= 2 * d_or + 1e-6 * np.linalg.norm(m_map)
+
+
+def test_lowrank_eig_matches_oracle(small2d):
+    orc, w, P = small2d["orc"], small2d["w"], small2d["P"]
+    m_map = small2d["m_map"]
+    Om = W.omega(w)
+    lam_ref, V_ref = A.lowrank_eig(orc, m_map, Om, w.k)
+    lam, V, st = P.lowrank_eig(torch.tensor(m_map, device=DEV), w.k, w.p,
+                               torch.tensor(np.ascontiguousarray(Om.T), device=DEV))
+    lam, V = lam.cpu().numpy(), V.cpu().numpy().T
+    big = lam_ref > 0.1
+    assert np.all(np.abs(lam[big] - lam_ref[big]) <= 1e-6 * lam_ref[big])
+    R = lambda X: orc.R_apply(X)
+    VtRV = V.T @ R(V)
+    assert np.allclose(VtRV, np.eye(w.k), atol=1e-7)
+    gap = np.ones(w.k, dtype=bool)
+    gap[1:] &= lam_ref[1:] < 0.9 * lam_ref[:-1]
+    gap[:-1] &= lam_ref[1:] < 0.9 * lam_ref[:-1]
+    sel = big & gap
+    c = np.abs(np.einsum("ij,ij->j", V[:, sel], R(V_ref[:, sel])))
+    assert np.all(np.abs(c - 1) < 1e-5), c
+
+
+def test_samples_with_identical_normals(small2d):
+    orc, w, P = small2d["orc"], small2d["w"], small2d["P"]
+    m_map = small2d["m_map"]
+    lam, V = A.lowrank_eig(orc, m_map, W.omega(w), w.k)
+    eta = W.sample_normals(w, 7)
+    pr_ref, po_ref = A.laplace_samples(orc, m_map, lam, V, eta)
+    pr, po, _ = P.laplace_sample(torch.tensor(m_map, device=DEV), torch.tensor(lam, device=DEV),
+                                 torch.tensor(np.ascontiguousarray(V.T), device=DEV),
+                                 torch.tensor(np.ascontiguousarray(eta.T), device=DEV))
+    pr, po = pr.cpu().numpy().T, po.cpu().numpy().T
+    for a, b in ((pr, pr_ref), (po, po_ref)):
+        for j in range(b.shape[1]):
+            assert np.linalg.norm(a[:, j] - b[:, j]) <= 1e-8 * np.linalg.norm(b[:, j])
+
+
+def test_sample_statistics_within_three_standard_errors():
+    """Prior and Laplace-posterior pointwise variances of N GPU samples against the exact
+    diag(R^{-1}) and diag(R^{-1}) - sum lambda/(1+lambda) v^2 at 16 seeded nodes (Bonferroni-free
+    3-SE band per node; the normals are fixed so the test is deterministic)."""
+    w = W.make_workload(2, 16, 12, seed=W.SEED_BASE + 77)
+    orc, m_true, _ = make_problem(w, W.draws(w))
+    m = 0.5 * m_true
+    u = orc.forward(m)
+    import scipy.linalg as sla
+    n = orc.n
+    H = orc.hessian_misfit(m, u, np.eye(n))
+    H = 0.5 * (H + H.T)
+    R = orc.R_apply(np.eye(n))
+    R = 0.5 * (R + R.T)
+    lam, V = sla.eigh(H, R)
+    lam, V = np.ascontiguousarray(lam[::-1][:12]), np.ascontiguousarray(V[:, ::-1][:, :12])
+    P = _gpu_problem(orc, w)
+    Ns = 4000
+    eta = W.sample_normals(w, Ns, seed_offset=9)
+    pr, po, _ = P.laplace_sample(torch.tensor(m, device=DEV), torch.tensor(lam, device=DEV),
+                                 torch.tensor(np.ascontiguousarray(V.T), device=DEV),
+                                 torch.tensor(np.ascontiguousarray(eta.T), device=DEV))
+    P.close()
+    pr, po = pr.cpu().numpy(), po.cpu().numpy()
+    nodes = np.random.default_rng(5).choice(n, 16, replace=False)
+    var_pr = A.prior_variance_exact(orc, nodes)
+    var_po = A.posterior_variance_lowrank(orc, lam, V, nodes)
+    for S, mean, var in ((pr, np.zeros(n), var_pr), (po, m, var_po)):
+        smean = S[:, nodes].mean(axis=0)
+        svar = S[:, nodes].var(axis=0, ddof=1)
+        se_mean = np.sqrt(var / Ns)
+        se_var = var * np.sqrt(2.0 / (Ns - 1))
+        assert np.all(np.abs(smean - mean[nodes]) <= 3 * se_mean + 1e-12)
+        assert np.all(np.abs(svar - var) <= 3 * se_var)
+
+
+def test_3d_eig_and_samples():
+    w = W.make_workload(3, 8, 20, seed=W.SEED_BASE + 88)
+    w = W.Workload(**{**w.__dict__, "k": 8, "p": 4, "gamma": 0.05})
+    orc, m_true, _ = make_problem(w, W.draws(w))
+    m = 0.5 * m_true
+    Om = W.omega(w)
+    lam_ref, V_ref = A.lowrank_eig(orc, m, Om, w.k)
+    P = _gpu_problem(orc, w)
+    lam, V, _ = P.lowrank_eig(torch.tensor(m, device=DEV), w.k, w.p,
+                              torch.tensor(np.ascontiguousarray(Om.T), device=DEV))
+    lam = lam.cpu().numpy()
+    big = lam_ref > 0.1
+    assert np.all(np.abs(lam[big] - lam_ref[big]) <= 1e-6 * lam_ref[big])
+    eta = W.sample_normals(w, 3)
+    pr_ref, po_ref = A.laplace_samples(orc, m, lam_ref, V_ref, eta)
+    pr, po, _ = P.laplace_sample(torch.tensor(m, device=DEV), torch.tensor(lam_ref, device=DEV),
+                                 torch.tensor(np.ascontiguousarray(V_ref.T), device=DEV),
+                                 torch.tensor(np.ascontiguousarray(eta.T), device=DEV))
+    P.close()
+    assert np.linalg.norm(po.cpu().numpy().T - po_ref) <= 1e-8 * np.linalg.norm(po_ref)
+    assert np.linalg.norm(pr.cpu().numpy().T - pr_ref) <= 1e-8 * np.linalg.norm(pr_ref)
+
+
+def test_invalid_arguments_are_rejected():
+    from paper_1909_03948_gb300 import HPError, Problem
+    with pytest.raises(HPError):
+        Problem(4, 8, 0.1, 0.5, 0.01, np.zeros((1, 4)))
+    with pytest.raises(HPError):
+        Problem(2, 8, -0.1, 0.5, 0.01, np.zeros((1, 2)))
+    with pytest.raises(HPError):
+        Problem(2, 8, 0.1, 0.5, 0.01, np.array([[1.5, 0.5]]))
+    P = Problem(2, 8, 0.1, 0.5, 0.01, np.array([[0.5, 0.5]]))
+    X = torch.zeros((2, P.n), dtype=torch.float64, device=DEV)
+    with pytest.raises(HPError):          # no linearisation point yet
+        P.hessian_apply(X)
+    with pytest.raises(TypeError):
+        P.hessian_apply(X.float())
+    m = torch.full((P.n,), float("nan"), dtype=torch.float64, device=DEV)
+    with pytest.raises(HPError):          # non-finite coefficient is reported, not propagated
+        P.set_point(m)
+    P.close()
