@@ -203,6 +203,8 @@ def family_bytes(fam, n, s, dim, fp32):
         return n * (2 * s * w + (nf + 1) * w)
     if fam == "smooth":       # read x, b, write y, coefficients (diag, invdiag, nf)
         return n * (3 * s * w + (nf + 2) * w)
+    if fam == "presmooth":    # two fused sweeps from zero: read r, write e, coefficients
+        return n * (2 * s * w + (nf + 2) * w)
     if fam == "resid_mg":     # read x, b, write r, coefficients
         return n * (3 * s * w + (nf + 1) * w)
     if fam == "resid64":      # FP64 refinement residual
@@ -345,7 +347,8 @@ def run_ours(args, rank, world):
                 "traffic": traffic_record(dom, w.name), "kernel": dom, "launches": cnt,
                 "avg_launch_us": avg_s * 1e6, "algorithmic_bytes_per_launch": bpl, "peak_source": src,
                 "share_of_step": ms / 1e3 / t_prof,
-                "measured_in": "a second pass of the same K steps with CUDA events around each launch",
+                "measured_in": ("a second pass of the same K steps with direct launches, CUDA events around each "
+                                "launch, each PCG iteration headed by a bounded spin so kernels run back to back"),
                 "families": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
     if rank != 0:
         return

@@ -199,12 +199,16 @@ int hp_laplace_sample(hp_problem *P, const double *m_map_dev, const double *lamb
 /* Kernel families timed when profiling is on (CUDA events on the problem's
  * stream around each launch):  0 level-0 PCG matvec (stencil + <p,Kp>),
  * 1 level-0 Jacobi smoothing sweep, 2 level-0 V-cycle residual, 3 FP64
- * refinement residual, 4 CG vector update (+ <r,r>), 5 whole V-cycle. */
-#define HP_PROF_NIDS 6
+ * refinement residual, 4 CG vector update (+ <r,r>), 5 whole V-cycle,
+ * 6 level-0 fused two-sweep pre-smoothing. */
+#define HP_PROF_NIDS 7
 /* Turns event timing on (on != 0) or off and clears the records. */
 int hp_profile_enable(hp_problem *P, int on);
 /* Synchronises the stream and returns, per family id < nids, the number of
- * timed launches and their summed duration in ms (HOST arrays); clears. */
+ * timed launches and their summed duration in ms (HOST arrays); clears.
+ * While profiling, kernels are launched directly (not as graphs) and each PCG
+ * iteration is headed by a short bounded clock-spin kernel, so the iteration's
+ * kernels run back to back and each event pair times its kernel alone. */
 int hp_profile_read(hp_problem *P, int nids, int *counts, double *total_ms);
 
 /* ---- status --------------------------------------------------------------- */

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -207,6 +208,7 @@ static int forward_state(hp_problem *P, hp_solve_stats *st) {
   k_set_dirichlet<<<(int)std::min<long>(64, (face + 255) / 256), 256, 0, P->st>>>(face, g.n - face, P->u,
                                                                                   P->u_bottom, P->u_top);
   count_launch();
+  launch_build_C(P);
   return 0;
 }
 
@@ -399,6 +401,7 @@ int hp_problem_create(const hp_problem_desc *d, hp_problem **out) {
   P->rtol = d->rtol > 0 ? d->rtol : 1e-8;
   P->max_iter = d->max_iter > 0 ? d->max_iter : 500;
   P->nobs = d->nobs;
+  if (const char *e = getenv("HP_GRAPHS")) P->use_graphs = !(e[0] == '0');
   int rc = 0;
   auto fail = [&](int code) {
     hp_problem_destroy(P);
@@ -410,6 +413,8 @@ int hp_problem_create(const hp_problem_desc *d, hp_problem **out) {
   for (double **pp : {&P->m, &P->E, &P->u, &P->lift, &P->m_prior, &P->f_load}) {
     if (cudaMalloc(pp, nb) != cudaSuccess) return fail(set_error(HP_ERR_NOMEM, "allocation"));
   }
+  const int nC = (1 << (P->dim + 1)) - 1;
+  if (cudaMalloc(&P->Cbeta, sizeof(double) * P->n * nC) != cudaSuccess) return fail(set_error(HP_ERR_NOMEM, "allocation"));
   if (cudaMalloc(&P->d_obs, sizeof(double) * std::max(1, P->nobs)) != cudaSuccess)
     return fail(set_error(HP_ERR_NOMEM, "allocation"));
   cudaMemset(P->d_obs, 0, sizeof(double) * std::max(1, P->nobs));
@@ -447,7 +452,7 @@ void hp_problem_destroy(hp_problem *P) {
       if (p) cudaFree(p);
   for (void *p : {(void *)P->M64.diag, (void *)P->M64.invdiag, (void *)P->M64.c, (void *)P->M32.diag,
                   (void *)P->M32.invdiag, (void *)P->M32.c, (void *)P->m, (void *)P->E, (void *)P->u,
-                  (void *)P->lift, (void *)P->m_prior, (void *)P->f_load, (void *)P->d_obs, (void *)P->obs_node,
+                  (void *)P->lift, (void *)P->Cbeta, (void *)P->m_prior, (void *)P->f_load, (void *)P->d_obs, (void *)P->obs_node,
                   (void *)P->obs_w, (void *)P->bt_row, (void *)P->bt_ptr, (void *)P->bt_ent})
     if (p) cudaFree(p);
   for (BlockWS<float> *W = &P->w32; W; W = nullptr) {
@@ -471,7 +476,7 @@ void hp_problem_destroy(hp_problem *P) {
   if (P->cap) cudaStreamDestroy(P->cap);
   free_scalars_host(P);
   ScalarWS &S = P->sc;
-  for (DBuf *b : {&S.iter, &S.rz, &S.pq, &S.rr, &S.bb, &S.alpha, &S.beta, &S.scale, &S.tmp, &S.active, &S.partial, &S.counter})
+  for (DBuf *b : {&S.iter, &S.rz, &S.pq, &S.rr, &S.bb, &S.alpha, &S.beta, &S.scale, &S.iscale, &S.tmp, &S.active, &S.partial, &S.counter})
     b->release();
   for (DBuf *b : {&P->r64, &P->b64, &P->t64a, &P->t64b, &P->t64c, &P->obsbuf, &P->small}) b->release();
   for (int i = 0; i < 6; ++i) P->vtmp[i].release();
@@ -516,23 +521,24 @@ int hp_profile_enable(hp_problem *P, int on) {
   HP_CUDA(cudaStreamSynchronize(P->st));
   P->prof_on = on != 0;
   P->prof_used = 0;
+  P->prof_failed = false;
+  for (int i = 0; i < 16; ++i) {
+    P->prof_cnt[i] = 0;
+    P->prof_ms[i] = 0.0;
+  }
   return HP_OK;
 }
 
 int hp_profile_read(hp_problem *P, int nids, int *counts, double *total_ms) {
-  if (!P || nids < 0 || (nids > 0 && (!counts || !total_ms))) return set_error(HP_ERR_INVALID, "arguments");
+  if (!P || nids < 0 || nids > 16 || (nids > 0 && (!counts || !total_ms)))
+    return set_error(HP_ERR_INVALID, "arguments");
   HP_CUDA(cudaStreamSynchronize(P->st));
+  prof_harvest(P, 0, P->prof_used, false);
   for (int i = 0; i < nids; ++i) {
-    counts[i] = 0;
-    total_ms[i] = 0.0;
-  }
-  for (size_t r = 0; r < P->prof_used; ++r) {
-    const int id = P->prof_id[r];
-    if (id < 0 || id >= nids) continue;
-    float ms = 0.f;
-    HP_CUDA(cudaEventElapsedTime(&ms, P->prof_ev[2 * r], P->prof_ev[2 * r + 1]));
-    counts[id] += 1;
-    total_ms[id] += ms;
+    counts[i] = (int)P->prof_cnt[i];
+    total_ms[i] = P->prof_ms[i];
+    P->prof_cnt[i] = 0;
+    P->prof_ms[i] = 0.0;
   }
   P->prof_used = 0;
   return HP_OK;

@@ -348,7 +348,7 @@ static int grid_blocks(long n) { return (int)std::max<long>(1, std::min<long>((n
 int build_hierarchy_geometry(hp_problem *P) {
   HP_TRY(ensure_children());
   const int D = P->dim;
-  const int ncmax = D == 2 ? 8 : 4;
+  const int ncmax = D == 2 ? 16 : 4;  // coarsest grid: <= 17^2 or 5^3 nodes, dense inverse
   int N = P->N, L = 1;
   while (N % 2 == 0 && N > ncmax && L < HP_MAXL) {
     N /= 2;
@@ -444,103 +444,136 @@ int build_point(hp_problem *P, const double *m_dev) {
 
 // ---------------------------------------------------------------------------
 // C, C^T
+//
+// (C X)_v = sum_{e ni v} kappa_hat_e (K_e^1 u_e)_v with kappa_hat_e the element mean of
+// E X, so C X = S_C (E (.) X) where S_C couples v to the nodes w that share a simplex
+// with v: beta_{v,w} = sum_{e ni v,w} (K_e^1 u_e)_v / (D+1), K_e^1 the unit-coefficient
+// element stiffness.  beta depends only on u, so it is built once per linearisation
+// point; C X and C^T W = E (.) S_C^T W are then FP64 stencil applications.
+// Offsets w - v: index 0 = v itself, idx = b for +b, idx = 2^D - 1 + b for -b
+// (b a Kuhn edge mask), 2^{D+1} - 1 coefficients per node.
 // ---------------------------------------------------------------------------
 template <int D>
-__global__ void k_C_apply(GridDesc g, const double *__restrict__ E, const double *__restrict__ u,
-                          const double *__restrict__ X, long ldx, double *__restrict__ Y, long ldy, double scale) {
-  const int j = blockIdx.y;
-  const double *x = X + ldx * j;
-  double *y = Y + ldy * j;
-  const double vh2 = vol_over_h2<D>(g.h);
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
-    int v[3];
-    node_coords<D>(g, i, v);
-    double acc = 0.0;
-#pragma unroll
-    for (int sh = 0; sh < (1 << D); ++sh) {
-      bool ok = true;
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const int ca = v[a] - ((sh >> a) & 1);
-        ok = ok && ca >= 0 && ca < g.N;
-      }
-      if (!ok) continue;
-      const long base = i - mask_offset(g, sh);
-      double ex[1 << D], uu[1 << D];
-#pragma unroll
-      for (int q = 0; q < (1 << D); ++q) {
-        const long o = base + mask_offset(g, q);
-        ex[q] = E[o] * x[o];
-        uu[q] = u[o];
-      }
-      const int k = popc3(sh);
-#pragma unroll
-      for (int p = 0; p < MeshT<D>::NPERM; ++p) {
-        if (MeshT<D>::chain(p, k) != sh) continue;
-        double kh = 0.0;
-#pragma unroll
-        for (int t = 0; t <= D; ++t) kh += ex[MeshT<D>::chain(p, t)];
-        double du = 0.0;
-        if (k > 0) du += uu[sh] - uu[MeshT<D>::chain(p, k - 1)];
-        if (k < D) du += uu[sh] - uu[MeshT<D>::chain(p, k + 1)];
-        acc += kh * du;
-      }
-    }
-    y[i] = scale * vh2 * acc / (D + 1);
-  }
+__device__ __forceinline__ int coff_index(int from_mask, int to_mask) {
+  // simplex vertices S_k (from) and S_t (to) of one chain: to - from is +/- a Kuhn edge
+  if (to_mask == from_mask) return 0;
+  if ((to_mask & from_mask) == from_mask) return to_mask ^ from_mask;        // +b
+  return (1 << D) - 1 + (from_mask ^ to_mask);                               // -b
 }
 
 template <int D>
-__global__ void k_Ct_apply(GridDesc g, const double *__restrict__ E, const double *__restrict__ u,
-                           const double *__restrict__ W, long ldw, double *__restrict__ Y, long ldy, double scale,
-                           double beta) {
-  const int j = blockIdx.y;
-  const double *w = W + ldw * j;
-  double *y = Y + ldy * j;
-  const double vh2 = vol_over_h2<D>(g.h);
+__global__ void k_build_C(GridDesc g, const double *__restrict__ u, double *__restrict__ beta) {
+  constexpr int NC = (1 << (D + 1)) - 1;
+  const double vh2 = vol_over_h2<D>(g.h) / (D + 1);
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
     int v[3];
     node_coords<D>(g, i, v);
-    double acc = 0.0;
+    double b[NC];
 #pragma unroll
-    for (int sh = 0; sh < (1 << D); ++sh) {
-      bool ok = true;
+    for (int q = 0; q < NC; ++q) b[q] = 0.0;
+    const double uv = u[i];
+    for_elems_with<D>(g, v, 0, [&](const int c[3], int p, int k) {
+      const long base = c[0] + (long)g.np * (c[1] + (long)g.np * c[2]);
+      double a = 0.0;
+      if (k > 0) a += uv - u[base + mask_offset(g, MeshT<D>::chain(p, k - 1))];
+      if (k < D) a += uv - u[base + mask_offset(g, MeshT<D>::chain(p, k + 1))];
+      a *= vh2;
+      const int mk = MeshT<D>::chain(p, k);
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const int ca = v[a] - ((sh >> a) & 1);
-        ok = ok && ca >= 0 && ca < g.N;
-      }
-      if (!ok) continue;
-      const long base = i - mask_offset(g, sh);
-      double ww[1 << D], uu[1 << D];
+      for (int t = 0; t <= D; ++t) b[coff_index<D>(mk, MeshT<D>::chain(p, t))] += a;
+    });
 #pragma unroll
-      for (int q = 0; q < (1 << D); ++q) {
-        const long o = base + mask_offset(g, q);
-        ww[q] = w[o];
-        uu[q] = u[o];
-      }
-      const int k = popc3(sh);
-#pragma unroll
-      for (int p = 0; p < MeshT<D>::NPERM; ++p) {
-        if (MeshT<D>::chain(p, k) != sh) continue;
-#pragma unroll
-        for (int t = 0; t < D; ++t) {
-          const int a0 = MeshT<D>::chain(p, t), a1 = MeshT<D>::chain(p, t + 1);
-          acc += (uu[a1] - uu[a0]) * (ww[a1] - ww[a0]);
-        }
-      }
-    }
-    const double val = scale * E[i] * vh2 * acc / (D + 1);
-    y[i] = beta == 0.0 ? val : val + beta * y[i];
+    for (int q = 0; q < NC; ++q) beta[(long)q * g.n + i] = b[q];
   }
+}
+
+// signed offset of coefficient index q: returns the mask and the sign (+1 / -1; 0 for q = 0)
+template <int D>
+__device__ __forceinline__ int coff_mask(int q, int *sign) {
+  if (q == 0) {
+    *sign = 0;
+    return 0;
+  }
+  if (q < (1 << D)) {
+    *sign = 1;
+    return q;
+  }
+  *sign = -1;
+  return q - ((1 << D) - 1);
+}
+
+template <int D>
+__device__ __forceinline__ bool shift_ok(const GridDesc &g, const int v[3], int mask, int sign) {
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+    if ((mask >> a) & 1) ok = ok && (sign > 0 ? v[a] < g.N : v[a] > 0);
+  return ok;
+}
+
+// Y = scale * S_C (E (.) X)
+template <int D>
+__global__ void k_C_apply(GridDesc g, const double *__restrict__ E, const double *__restrict__ beta,
+                          const double *__restrict__ X, long ldx, double *__restrict__ Y, long ldy, double scale) {
+  constexpr int NC = (1 << (D + 1)) - 1;
+  const int j = blockIdx.y;
+  const double *x = X + ldx * j;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
+    int v[3];
+    node_coords<D>(g, i, v);
+    double acc = beta[i] * E[i] * x[i];
+#pragma unroll
+    for (int q = 1; q < NC; ++q) {
+      int sg;
+      const int m = coff_mask<D>(q, &sg);
+      if (!shift_ok<D>(g, v, m, sg)) continue;
+      const long w = i + sg * mask_offset(g, m);
+      acc += beta[(long)q * g.n + i] * E[w] * x[w];
+    }
+    Y[ldy * j + i] = scale * acc;
+  }
+}
+
+// Y = scale * E (.) S_C^T W + beta_acc * Y
+template <int D>
+__global__ void k_Ct_apply(GridDesc g, const double *__restrict__ E, const double *__restrict__ beta,
+                           const double *__restrict__ W, long ldw, double *__restrict__ Y, long ldy, double scale,
+                           double yb) {
+  constexpr int NC = (1 << (D + 1)) - 1;
+  const int j = blockIdx.y;
+  const double *w = W + ldw * j;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
+    int v[3];
+    node_coords<D>(g, i, v);
+    double acc = beta[i] * w[i];
+#pragma unroll
+    for (int q = 1; q < NC; ++q) {
+      int sg;
+      const int m = coff_mask<D>(q, &sg);
+      // the row r whose offset q points at node i is r = i - (sg * m)
+      if (!shift_ok<D>(g, v, m, -sg)) continue;
+      const long r = i - sg * mask_offset(g, m);
+      acc += beta[(long)q * g.n + r] * w[r];
+    }
+    const double val = scale * E[i] * acc;
+    Y[ldy * j + i] = yb == 0.0 ? val : val + yb * Y[ldy * j + i];
+  }
+}
+
+void launch_build_C(hp_problem *P) {
+  if (P->dim == 2)
+    k_build_C<2><<<grid_blocks(P->n), 256, 0, P->st>>>(P->lv[0].g, P->u, P->Cbeta);
+  else
+    k_build_C<3><<<grid_blocks(P->n), 256, 0, P->st>>>(P->lv[0].g, P->u, P->Cbeta);
+  count_launch();
 }
 
 void launch_C_apply(hp_problem *P, const double *X, long ldx, double *Y, long ldy, int s, double scale) {
   dim3 grid(blocks_for(P->n, s), s);
   if (P->dim == 2)
-    k_C_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, P->u, X, ldx, Y, ldy, scale);
+    k_C_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, P->Cbeta, X, ldx, Y, ldy, scale);
   else
-    k_C_apply<3><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, P->u, X, ldx, Y, ldy, scale);
+    k_C_apply<3><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, P->Cbeta, X, ldx, Y, ldy, scale);
   count_launch();
 }
 
@@ -548,9 +581,9 @@ void launch_Ct_apply(hp_problem *P, const double *W, long ldw, double *Y, long l
                      double beta) {
   dim3 grid(blocks_for(P->n, s), s);
   if (P->dim == 2)
-    k_Ct_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, P->u, W, ldw, Y, ldy, scale, beta);
+    k_Ct_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, P->Cbeta, W, ldw, Y, ldy, scale, beta);
   else
-    k_Ct_apply<3><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, P->u, W, ldw, Y, ldy, scale, beta);
+    k_Ct_apply<3><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, P->Cbeta, W, ldw, Y, ldy, scale, beta);
   count_launch();
 }
 

@@ -60,7 +60,7 @@ template <typename T> struct BlockWS {
 
 struct ScalarWS {
   int scap = 0;
-  DBuf rz, pq, rr, bb, alpha, beta, scale, tmp;   // double per column
+  DBuf rz, pq, rr, bb, alpha, beta, scale, iscale, tmp;   // double per column
   DBuf active;                                     // int per column
   DBuf partial;                                    // double [slot][col][block]
   DBuf counter;                                    // unsigned [slot][col]
@@ -96,6 +96,7 @@ struct hp_problem {
   // point-dependent state
   bool have_point = false;
   double *m = nullptr, *E = nullptr, *u = nullptr, *lift = nullptr;
+  double *Cbeta = nullptr;      // C as a stencil on e^m (.) X: (2^{D+1}-1) x n, built from u
   // data
   double *m_prior = nullptr, *f_load = nullptr, *d_obs = nullptr;
   int nobs = 0;
@@ -117,6 +118,9 @@ struct hp_problem {
   std::vector<int> prof_id;
   std::vector<cudaEvent_t> prof_ev;   // 2 per record
   size_t prof_used = 0;
+  bool prof_failed = false;            // graph-recorded event timing unavailable
+  long prof_cnt[16] = {};              // harvested totals per family
+  double prof_ms[16] = {};
 };
 
 namespace hp {
@@ -142,14 +146,18 @@ enum ProfId {
   PROF_RESID64 = 3,    // FP64 refinement residual
   PROF_CG_UPDATE = 4,  // x += a p, r -= a q, <r, r>
   PROF_VCYCLE = 5,     // whole preconditioner application
-  PROF_COUNT = 6
+  PROF_PRESMOOTH = 6,  // level-0 fused two-sweep pre-smoothing from zero
+  PROF_COUNT = 7
 };
 int prof_start(hp_problem *P, int id);   // returns a record index or -1
 void prof_stop(hp_problem *P, int rec);
+void prof_harvest(hp_problem *P, size_t from, size_t to, bool keep);
+void prof_spin(hp_problem *P);  // profiling only: keep the GPU busy while the host enqueues  // add records' times to the totals
 
 // ---- fem.cu -------------------------------------------------------------
 int build_hierarchy_geometry(hp_problem *P);  // levels, allocs, prior/mass stencils, coarse A inverse
 int build_point(hp_problem *P, const double *m_dev);  // E, kappa hierarchy, K stencils, lift, coarse K inverse
+void launch_build_C(hp_problem *P);  // after the state solve
 void launch_C_apply(hp_problem *P, const double *X, long ldx, double *Y, long ldy, int s, double scale);
 void launch_Ct_apply(hp_problem *P, const double *W, long ldw, double *Y, long ldy, int s, double scale,
                      double beta);

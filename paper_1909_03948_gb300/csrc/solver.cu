@@ -8,12 +8,16 @@
 //     interpolation / its transpose, Galerkin coarse operators, dense coarse
 //     inverse) -- or diagonal scaling for the mass matrix.  alpha, beta and
 //     the per-column convergence flags live on the device; converged columns
-//     are frozen by alpha = 0.
-//   * Outer loop: r = b - K x in FP64, inner solve on r / |r| in T, x += d.
-//     Stops when every column has |r|/|b| <= rtol (FP64 residual).
-//   * Inner products: per-column block partials in fixed order, the last
-//     block to finish sums them (deterministic) and applies the scalar step
-//     of CG (alpha, beta, convergence test) in FP64.
+//     are frozen by alpha = 0.  The iteration loop is a CUDA graph with a
+//     device-side while node, so a solve costs one graph launch.
+//   * Inner layout: columns are packed in groups of VW (VW = 4 for FP32 blocks:
+//     [group][node][4], one 16-byte access per node covers 4 right-hand sides
+//     and one coefficient load serves all 4; VW = 1 is plain column-major).
+//   * Outer loop: r = b - K x in FP64 (column-major, the ABI layout), inner solve
+//     on r / |r| in T, x += d.  Stops when every column has |r|/|b| <= rtol.
+//   * Inner products: per-block partials (warp sums in T, block sums in FP64),
+//     the last block to finish sums the partials of its column in a fixed order
+//     (deterministic) and applies the scalar step of CG in FP64.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -24,6 +28,8 @@ namespace hp {
 
 void drop_graphs(hp_problem *P);
 
+constexpr int NB = 128;  // threads per block of the node kernels (4 warps)
+
 enum { FIN_STORE = 0, FIN_ALPHA = 1, FIN_RR = 2, FIN_BETA = 3, FIN_INIT = 4 };
 
 struct Fin {
@@ -32,7 +38,7 @@ struct Fin {
   int kind = FIN_STORE;
   double *rz = nullptr, *alpha = nullptr, *beta = nullptr, *rr = nullptr, *bb = nullptr, *out = nullptr;
   int *active = nullptr;
-  int *iter = nullptr;   // PCG iteration counter (FIN_BETA: beta = 0 on the first iteration)
+  int *iter = nullptr;  // PCG iteration counter (FIN_BETA: beta = 0 on the first iteration)
   double tol2 = 0.0;
 };
 
@@ -57,188 +63,403 @@ __device__ __forceinline__ void fin_apply(const Fin &f, int j, double s) {
   }
 }
 
-// block partial -> last block sums the partials of column j in order
-__device__ __forceinline__ void dot_finish(double acc, const Fin &f, int j) {
-  __shared__ bool last;
-  const double bs = block_sum<NT>(acc);
-  if (threadIdx.x == 0) {
-    f.part[(long)j * gridDim.x + blockIdx.x] = bs;
-    __threadfence();
-    const unsigned t = atomicAdd(&f.cnt[j], 1u);
-    last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (last) {
-    __threadfence();
-    double s = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += NT) s += __ldcg(&f.part[(long)j * gridDim.x + b]);
-    s = block_sum<NT>(s);
-    if (threadIdx.x == 0) {
-      f.cnt[j] = 0u;
-      fin_apply(f, j, s);
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
-// stencil kernels
+// packs of VW values of one node (VW consecutive columns of a group)
 // ---------------------------------------------------------------------------
-template <typename T, int D, bool FULL>
-__device__ __forceinline__ T stencil_row(const GridDesc &g, const T *__restrict__ diag, const T *__restrict__ c,
-                                         const T *__restrict__ x, long i, const int v[3]) {
-  T acc = diag[i] * x[i];
-  constexpr int NF = FULL ? (1 << D) - 1 : D;
-#pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    const int b = FULL ? f + 1 : (1 << f);
-    bool fw = true, bw = true;
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-      if ((b >> a) & 1) {
-        fw = fw && (v[a] < g.N);
-        bw = bw && (v[a] > 0);
-      }
-    const long off = mask_offset(g, b);
-    if (fw) acc += c[(long)f * g.n + i] * x[i + off];
-    if (bw) acc += c[(long)f * g.n + i - off] * x[i - off];
-  }
-  return acc;
-}
-
-enum { M_APPLY = 0, M_APPLY_DOT = 1, M_RESID = 2, M_JACOBI = 3, M_JACOBI_DOT = 4 };
-
-template <typename T, int D, bool FULL, int MODE>
-__global__ void __launch_bounds__(NT) k_stencil(GridDesc g, const T *__restrict__ diag, const T *__restrict__ invdiag,
-                                                const T *__restrict__ c, const T *__restrict__ X, long ldx,
-                                                const T *__restrict__ B, long ldb, T *__restrict__ Y, long ldy,
-                                                T omega, Fin fin) {
-  const int j = blockIdx.y;
-  const T *x = X + ldx * j;
-  const T *b = B ? B + ldb * j : nullptr;
-  T *y = Y + ldy * j;
-  T acc = T(0);
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
-    int v[3];
-    node_coords<D>(g, i, v);
-    const T sx = stencil_row<T, D, FULL>(g, diag, c, x, i, v);
-    T out;
-    if (MODE == M_APPLY || MODE == M_APPLY_DOT) {
-      out = sx;
-      if (MODE == M_APPLY_DOT) acc += x[i] * out;
-    } else if (MODE == M_RESID) {
-      out = b[i] - sx;
+template <typename T, int VW> struct Pack {
+  T v[VW];
+  __device__ __forceinline__ static Pack ld(const T *p) {
+    Pack r;
+    if constexpr (VW == 4 && sizeof(T) == 4) {
+      const float4 t = *reinterpret_cast<const float4 *>(p);
+      r.v[0] = t.x;
+      r.v[1] = t.y;
+      r.v[2] = t.z;
+      r.v[3] = t.w;
     } else {
-      const T bi = b[i];
-      out = x[i] + omega * invdiag[i] * (bi - sx);
-      if (MODE == M_JACOBI_DOT) acc += bi * out;
+#pragma unroll
+      for (int q = 0; q < VW; ++q) r.v[q] = p[q];
     }
-    y[i] = out;
+    return r;
   }
-  if (MODE == M_APPLY_DOT || MODE == M_JACOBI_DOT) dot_finish((double)acc, fin, j);
-}
+  __device__ __forceinline__ void st(T *p) const {
+    if constexpr (VW == 4 && sizeof(T) == 4) {
+      *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < VW; ++q) p[q] = v[q];
+    }
+  }
+  __device__ __forceinline__ static Pack zero() {
+    Pack r;
+#pragma unroll
+    for (int q = 0; q < VW; ++q) r.v[q] = T(0);
+    return r;
+  }
+  __device__ __forceinline__ void axpy(T a, const Pack &x) {  // this += a x
+#pragma unroll
+    for (int q = 0; q < VW; ++q) v[q] += a * x.v[q];
+  }
+};
 
 template <typename T>
-__global__ void k_jacobi0(long n, const T *__restrict__ invdiag, const T *__restrict__ B, long ldb, T *__restrict__ Y,
-                          long ldy, T omega, Fin fin, int with_dot) {
-  const int j = blockIdx.y;
-  T acc = T(0);
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const T bi = B[ldb * j + i];
-    const T z = omega * invdiag[i] * bi;
-    Y[ldy * j + i] = z;
-    acc += bi * z;
-  }
-  if (with_dot) dot_finish((double)acc, fin, j);
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
 }
 
-template <typename T, int D>
-__global__ void k_restrict(GridDesc gf, GridDesc gc, const T *__restrict__ rf, long ldf, T *__restrict__ rc, long ldc,
-                           int zero_dirichlet) {
-  const int j = blockIdx.y;
-  const T *r = rf + ldf * j;
-  for (long I = blockIdx.x * (long)blockDim.x + threadIdx.x; I < gc.n; I += (long)gridDim.x * blockDim.x) {
-    int J[3];
-    node_coords<D>(gc, I, J);
-    T out;
-    if (zero_dirichlet && (J[D - 1] == 0 || J[D - 1] == gc.N)) {
-      out = T(0);
-    } else {
-      const long f0 = 2 * (long)J[0] + (long)gf.np * (2 * (long)J[1] + (D == 3 ? (long)gf.np * 2 * J[2] : 0));
-      T acc = r[f0];
+// Per-column dot partial of one block (NB threads) for the VW columns of group grp:
+// warp sums in T, the 4 warp sums added in FP64, stored at part[col * nblk + blin].
+// k_dot_finalize then sums the nblk partials of each column in a fixed order
+// (deterministic, no atomics) and applies the CG scalar step.
+template <typename T, int VW>
+__device__ __forceinline__ void dot_partial(const Pack<T, VW> &acc, double *part, int grp, int s, unsigned blin,
+                                            unsigned nblk) {
+  __shared__ double sh[NB / 32][VW];
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
 #pragma unroll
-      for (int b = 1; b < (1 << D); ++b) {
+  for (int q = 0; q < VW; ++q) {
+    const T w = warp_sum_t(acc.v[q]);
+    if (lane == 0) sh[wy][q] = (double)w;
+  }
+  __syncthreads();
+  if (threadIdx.x < VW) {
+    const int q = threadIdx.x, col = grp * VW + q;
+    if (col < s) {
+      double bs = 0.0;
+#pragma unroll
+      for (int w = 0; w < NB / 32; ++w) bs += sh[w][q];
+      part[(long)col * nblk + blin] = bs;
+    }
+  }
+}
+
+__global__ void k_dot_finalize(const double *__restrict__ part, unsigned nblk, Fin fin) {
+  const int col = blockIdx.x;
+  double sum = 0.0;
+  for (unsigned b = threadIdx.x; b < nblk; b += NB) sum += part[(long)col * nblk + b];
+  sum = block_sum<NB>(sum);
+  if (threadIdx.x == 0) fin_apply(fin, col, sum);
+}
+
+static void dot_finalize(const Fin &fin, unsigned nblk, int s, cudaStream_t st) {
+  k_dot_finalize<<<s, NB, 0, st>>>(fin.part, nblk, fin);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// stencil kernels: one node per thread, 32 x-nodes per warp, rows over warps
+// and blocks, column groups over blockIdx.z.  Element (node i, group g) of a
+// block with group stride gs is at base + g*gs + i*VW.
+// ---------------------------------------------------------------------------
+enum { M_APPLY = 0, M_APPLY_DOT = 1, M_RESID = 2, M_JACOBI = 3, M_JACOBI_DOT = 4, M_JAC2 = 5 };
+
+template <typename T, int VW, int D, bool FULL, int MODE>
+__global__ void __launch_bounds__(NB) k_st(GridDesc g, const T *__restrict__ diag, const T *__restrict__ invdiag,
+                                           const T *__restrict__ c, const T *__restrict__ X, long gx,
+                                           const T *__restrict__ B, long gb, T *__restrict__ Y, long gy, int s,
+                                           T omega, Fin fin) {
+  using PK = Pack<T, VW>;
+  const int lane = threadIdx.x & 31;
+  const int i0 = blockIdx.x * 32 + lane;
+  const int nrows = D == 2 ? g.np : g.np * g.np;
+  const int grp = blockIdx.z;
+  constexpr bool DOT = (MODE == M_APPLY_DOT || MODE == M_JACOBI_DOT);
+  PK acc = PK::zero();
+  for (int row = blockIdx.y * (NB / 32) + (threadIdx.x >> 5); row < nrows; row += gridDim.y * (NB / 32)) {
+    if (i0 >= g.np) break;
+    const int v[3] = {i0, D == 2 ? row : row % g.np, D == 2 ? 0 : row / g.np};
+    const long id = i0 + (long)g.np * row;
+    const T *x = X + grp * gx;
+    constexpr int NF = FULL ? (1 << D) - 1 : D;
+    PK out;
+    if (MODE == M_JAC2) {
+      // two damped-Jacobi sweeps from zero: e1 = w D^-1 r, e2 = e1 + w D^-1 (r - S e1)
+      const T wi = omega * invdiag[id];
+      const PK r = PK::ld(x + id * VW);
+      PK e1c;
+#pragma unroll
+      for (int q = 0; q < VW; ++q) e1c.v[q] = wi * r.v[q];
+      PK sx;
+      const T dg = diag[id];
+#pragma unroll
+      for (int q = 0; q < VW; ++q) sx.v[q] = dg * e1c.v[q];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const int b = FULL ? f + 1 : (1 << f);
         bool fw = true, bw = true;
 #pragma unroll
         for (int a = 0; a < D; ++a)
           if ((b >> a) & 1) {
-            fw = fw && (J[a] < gc.N);
-            bw = bw && (J[a] > 0);
+            fw = fw && (v[a] < g.N);
+            bw = bw && (v[a] > 0);
           }
-        const long off = mask_offset(gf, b);
-        if (fw) acc += T(0.5) * r[f0 + off];
-        if (bw) acc += T(0.5) * r[f0 - off];
+        const long off = mask_offset(g, b);
+        if (fw) sx.axpy(c[(long)f * g.n + id] * omega * invdiag[id + off], PK::ld(x + (id + off) * VW));
+        if (bw) sx.axpy(c[(long)f * g.n + id - off] * omega * invdiag[id - off], PK::ld(x + (id - off) * VW));
       }
-      out = acc;
+#pragma unroll
+      for (int q = 0; q < VW; ++q) out.v[q] = e1c.v[q] + wi * (r.v[q] - sx.v[q]);
+    } else {
+      const PK xc = PK::ld(x + id * VW);
+      PK sx;
+      const T dg = diag[id];
+#pragma unroll
+      for (int q = 0; q < VW; ++q) sx.v[q] = dg * xc.v[q];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const int b = FULL ? f + 1 : (1 << f);
+        bool fw = true, bw = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+          if ((b >> a) & 1) {
+            fw = fw && (v[a] < g.N);
+            bw = bw && (v[a] > 0);
+          }
+        const long off = mask_offset(g, b);
+        if (fw) sx.axpy(c[(long)f * g.n + id], PK::ld(x + (id + off) * VW));
+        if (bw) sx.axpy(c[(long)f * g.n + id - off], PK::ld(x + (id - off) * VW));
+      }
+      if (MODE == M_APPLY || MODE == M_APPLY_DOT) {
+        out = sx;
+        if (DOT)
+#pragma unroll
+          for (int q = 0; q < VW; ++q) acc.v[q] += xc.v[q] * out.v[q];
+      } else {
+        const PK bb = PK::ld(B + grp * gb + id * VW);
+        if (MODE == M_RESID) {
+#pragma unroll
+          for (int q = 0; q < VW; ++q) out.v[q] = bb.v[q] - sx.v[q];
+        } else {
+          const T wi = omega * invdiag[id];
+#pragma unroll
+          for (int q = 0; q < VW; ++q) out.v[q] = xc.v[q] + wi * (bb.v[q] - sx.v[q]);
+          if (DOT)
+#pragma unroll
+            for (int q = 0; q < VW; ++q) acc.v[q] += bb.v[q] * out.v[q];
+        }
+      }
     }
-    rc[ldc * j + I] = out;
+    out.st(Y + grp * gy + id * VW);
   }
+  if (DOT) dot_partial<T, VW>(acc, fin.part, grp, s, blockIdx.x + gridDim.x * blockIdx.y, gridDim.x * gridDim.y);
 }
 
-template <typename T, int D>
-__global__ void k_prolong_add(GridDesc gf, GridDesc gc, const T *__restrict__ ec, long ldc, T *__restrict__ ef,
-                              long ldf) {
-  const int j = blockIdx.y;
-  const T *e = ec + ldc * j;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < gf.n; i += (long)gridDim.x * blockDim.x) {
-    int v[3];
-    node_coords<D>(gf, i, v);
-    int I[3] = {v[0] >> 1, v[1] >> 1, v[2] >> 1};
-    const int b = (v[0] & 1) | ((v[1] & 1) << 1) | ((v[2] & 1) << 2);
-    const long ic = I[0] + (long)gc.np * (I[1] + (long)gc.np * I[2]);
-    T val = e[ic];
-    if (b) val = T(0.5) * (val + e[ic + mask_offset(gc, b)]);
-    ef[ldf * j + i] += val;
+// ---------------------------------------------------------------------------
+// grid transfer, coarse solve, vector kernels (grouped layout)
+// ---------------------------------------------------------------------------
+// Restriction = transpose of the P1 prolongation: r_c(J) = r_f(2J) +
+// 1/2 sum_{b != 0} [r_f(2J + b) + r_f(2J - b)] over the 2^D - 1 Kuhn edge
+// directions b; Dirichlet rows of the zero-BC space are zeroed.
+template <typename T, int VW, int D>
+__global__ void __launch_bounds__(NB) k_restrict(GridDesc gf, GridDesc gc, const T *__restrict__ rf, long gsf,
+                                                 T *__restrict__ rc, long gsc, int zero_dirichlet) {
+  using PK = Pack<T, VW>;
+  const int I0 = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int row = blockIdx.y * (NB / 32) + (threadIdx.x >> 5);
+  const int nrows = D == 2 ? gc.np : gc.np * gc.np;
+  if (I0 >= gc.np || row >= nrows) return;
+  const int J[3] = {I0, D == 2 ? row : row % gc.np, D == 2 ? 0 : row / gc.np};
+  const long I = I0 + (long)gc.np * row;
+  const T *r = rf + blockIdx.z * gsf;
+  PK out = PK::zero();
+  if (!(zero_dirichlet && (J[D - 1] == 0 || J[D - 1] == gc.N))) {
+    const long f0 = 2 * (long)J[0] + (long)gf.np * (2 * (long)J[1] + (D == 3 ? (long)gf.np * 2 * J[2] : 0));
+    out = PK::ld(r + f0 * VW);
+#pragma unroll
+    for (int b = 1; b < (1 << D); ++b) {
+      bool fw = true, bw = true;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        if ((b >> a) & 1) {
+          fw = fw && (J[a] < gc.N);
+          bw = bw && (J[a] > 0);
+        }
+      const long off = mask_offset(gf, b);
+      if (fw) out.axpy(T(0.5), PK::ld(r + (f0 + off) * VW));
+      if (bw) out.axpy(T(0.5), PK::ld(r + (f0 - off) * VW));
+    }
   }
+  out.st(rc + blockIdx.z * gsc + I * VW);
 }
 
-template <typename T>
-__global__ void k_coarse_apply(const T *__restrict__ inv, int nc, const T *__restrict__ R, long ldr, T *__restrict__ E,
-                               long lde) {
+// e_f += P e_c: fine node 2I + b takes e_c(I) (b = 0) or the mean of e_c(I) and
+// e_c(I + b) (midpoint of the coarse Kuhn edge in direction b).
+template <typename T, int VW, int D>
+__global__ void __launch_bounds__(NB) k_prolong_add(GridDesc gf, GridDesc gc, const T *__restrict__ ec, long gsc,
+                                                    T *__restrict__ ef, long gsf) {
+  using PK = Pack<T, VW>;
+  const int i0 = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int row = blockIdx.y * (NB / 32) + (threadIdx.x >> 5);
+  const int nrows = D == 2 ? gf.np : gf.np * gf.np;
+  if (i0 >= gf.np || row >= nrows) return;
+  const int v[3] = {i0, D == 2 ? row : row % gf.np, D == 2 ? 0 : row / gf.np};
+  const long i = i0 + (long)gf.np * row;
+  const T *e = ec + blockIdx.z * gsc;
+  const int b = (v[0] & 1) | ((v[1] & 1) << 1) | ((v[2] & 1) << 2);
+  const long ic = (v[0] >> 1) + (long)gc.np * ((v[1] >> 1) + (long)gc.np * (v[2] >> 1));
+  PK val = PK::ld(e + ic * VW);
+  if (b) {
+    const PK v2 = PK::ld(e + (ic + mask_offset(gc, b)) * VW);
+#pragma unroll
+    for (int q = 0; q < VW; ++q) val.v[q] = T(0.5) * (val.v[q] + v2.v[q]);
+  }
+  T *o = ef + blockIdx.z * gsf + i * VW;
+  PK cur = PK::ld(o);
+#pragma unroll
+  for (int q = 0; q < VW; ++q) cur.v[q] += val.v[q];
+  cur.st(o);
+}
+
+// dense coarse-grid inverse: e = A_c^{-1} r.  blockIdx.x = chunk of 32 rows (lanes),
+// blockIdx.y = column group; the 8 warps of a block split the k sum, then add.
+template <typename T, int VW>
+__global__ void __launch_bounds__(256) k_coarse_apply(const T *__restrict__ inv, int nc, const T *__restrict__ R,
+                                                      long gsr, T *__restrict__ E, long gse) {
+  using PK = Pack<T, VW>;
   extern __shared__ unsigned char smem_raw[];
   T *r = reinterpret_cast<T *>(smem_raw);
-  const int j = blockIdx.x;
-  for (int k = threadIdx.x; k < nc; k += blockDim.x) r[k] = R[ldr * j + k];
+  __shared__ T red[8][32][VW];
+  const T *rg = R + blockIdx.y * gsr;
+  for (int k = threadIdx.x; k < nc * VW; k += blockDim.x) r[k] = rg[k];
   __syncthreads();
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-    T acc = T(0);
-    for (int k = 0; k < nc; ++k) acc += inv[(long)k * nc + i] * r[k];
-    E[lde * j + i] = acc;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  PK acc = PK::zero();
+  if (i < nc) {
+    for (int k = w; k < nc; k += 8) {
+      const T a = inv[(long)k * nc + i];
+#pragma unroll
+      for (int q = 0; q < VW; ++q) acc.v[q] += a * r[k * VW + q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < VW; ++q) red[w][lane][q] = acc.v[q];
+  __syncthreads();
+  if (w == 0 && i < nc) {
+    PK out = PK::zero();
+#pragma unroll
+    for (int ww = 0; ww < 8; ++ww)
+#pragma unroll
+      for (int q = 0; q < VW; ++q) out.v[q] += red[ww][lane][q];
+    out.st(E + blockIdx.y * gse + (long)i * VW);
   }
 }
 
-template <typename T>
-__global__ void k_cg_update(long n, const T *__restrict__ p, const T *__restrict__ q, T *__restrict__ x,
-                            T *__restrict__ r, long ld, const double *__restrict__ alpha, Fin fin) {
-  const int j = blockIdx.y;
-  const T a = (T)alpha[j];
-  T acc = T(0);
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const long o = ld * j + i;
-    x[o] += a * p[o];
-    const T rn = r[o] - a * q[o];
-    r[o] = rn;
-    acc += rn * rn;
+// 1-D node kernels: blockIdx.x over nodes (NB each), blockIdx.y = group
+template <typename T, int VW>
+__global__ void __launch_bounds__(NB) k_jacobi0(long n, const T *__restrict__ invdiag, const T *__restrict__ B, long gs,
+                                                T *__restrict__ Y, T omega, int s, Fin fin, int with_dot) {
+  using PK = Pack<T, VW>;
+  const int grp = blockIdx.y;
+  PK acc = PK::zero();
+  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
+    const PK b = PK::ld(B + grp * gs + i * VW);
+    const T w = omega * invdiag[i];
+    PK z;
+#pragma unroll
+    for (int q = 0; q < VW; ++q) {
+      z.v[q] = w * b.v[q];
+      acc.v[q] += b.v[q] * z.v[q];
+    }
+    z.st(Y + grp * gs + i * VW);
   }
-  dot_finish((double)acc, fin, j);
+  if (with_dot) dot_partial<T, VW>(acc, fin.part, grp, s, blockIdx.x, gridDim.x);
 }
 
-template <typename T>
-__global__ void k_p_update(long n, const T *__restrict__ z, T *__restrict__ p, long ld, const double *__restrict__ beta) {
-  const int j = blockIdx.y;
-  const T b = (T)beta[j];
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const long o = ld * j + i;
-    p[o] = z[o] + b * p[o];
+template <typename T, int VW>
+__global__ void __launch_bounds__(NB) k_cg_update(long n, long gs, const T *__restrict__ p, const T *__restrict__ q,
+                                                  T *__restrict__ x, T *__restrict__ r,
+                                                  const double *__restrict__ alpha, int s, Fin fin) {
+  using PK = Pack<T, VW>;
+  const int grp = blockIdx.y;
+  PK acc = PK::zero();
+  T a[VW];
+#pragma unroll
+  for (int c = 0; c < VW; ++c) a[c] = (T)alpha[grp * VW + c];
+  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
+    const long o = grp * gs + i * VW;
+    const PK pp = PK::ld(p + o), qq = PK::ld(q + o);
+    PK xx = PK::ld(x + o), rr = PK::ld(r + o);
+#pragma unroll
+    for (int c = 0; c < VW; ++c) {
+      xx.v[c] += a[c] * pp.v[c];
+      rr.v[c] -= a[c] * qq.v[c];
+      acc.v[c] += rr.v[c] * rr.v[c];
+    }
+    xx.st(x + o);
+    rr.st(r + o);
+  }
+  dot_partial<T, VW>(acc, fin.part, grp, s, blockIdx.x, gridDim.x);
+}
+
+template <typename T, int VW>
+__global__ void __launch_bounds__(NB) k_p_update(long n, long gs, const T *__restrict__ z, T *__restrict__ p,
+                                                 const double *__restrict__ beta) {
+  using PK = Pack<T, VW>;
+  const int grp = blockIdx.y;
+  T b[VW];
+#pragma unroll
+  for (int c = 0; c < VW; ++c) b[c] = (T)beta[grp * VW + c];
+  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
+    const long o = grp * gs + i * VW;
+    const PK zz = PK::ld(z + o);
+    PK pp = PK::ld(p + o);
+#pragma unroll
+    for (int c = 0; c < VW; ++c) pp.v[c] = zz.v[c] + b[c] * pp.v[c];
+    pp.st(p + o);
+  }
+}
+
+// <a, b> per column (a == b: squared norm)
+template <typename T, int VW>
+__global__ void __launch_bounds__(NB) k_dot(long n, long gs, const T *__restrict__ a, const T *__restrict__ b, int s,
+                                            Fin fin) {
+  using PK = Pack<T, VW>;
+  const int grp = blockIdx.y;
+  PK acc = PK::zero();
+  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
+    const PK aa = PK::ld(a + grp * gs + i * VW), bb = PK::ld(b + grp * gs + i * VW);
+#pragma unroll
+    for (int c = 0; c < VW; ++c) acc.v[c] += aa.v[c] * bb.v[c];
+  }
+  dot_partial<T, VW>(acc, fin.part, grp, s, blockIdx.x, gridDim.x);
+}
+
+// r_T (grouped) = scale * r64 (column-major); columns >= s and converged ones are 0
+template <typename T, int VW>
+__global__ void __launch_bounds__(NB) k_to_inner(long n, const double *__restrict__ R, long ldr,
+                                                 const double *__restrict__ scale, int s, T *__restrict__ rt, long gs) {
+  using PK = Pack<T, VW>;
+  const int grp = blockIdx.y;
+  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
+    PK o;
+#pragma unroll
+    for (int q = 0; q < VW; ++q) {
+      const int col = grp * VW + q;
+      o.v[q] = col < s ? (T)(scale[col] * R[ldr * col + i]) : T(0);
+    }
+    o.st(rt + grp * gs + i * VW);
+  }
+}
+
+// X (column-major FP64) += d / scale for the columns with scale != 0
+template <typename T, int VW>
+__global__ void __launch_bounds__(NB) k_accum(long n, const T *__restrict__ d, long gs, const double *__restrict__ iscale,
+                                              int s, double *__restrict__ X, long ldx) {
+  using PK = Pack<T, VW>;
+  const int grp = blockIdx.y;
+  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
+    const PK v = PK::ld(d + grp * gs + i * VW);
+#pragma unroll
+    for (int q = 0; q < VW; ++q) {
+      const int col = grp * VW + q;
+      if (col < s) {
+        const double is = iscale[col];  // |r| of the column, 0 when it has converged
+        if (is != 0.0) X[ldx * col + i] += (double)v.v[q] * is;
+      }
+    }
   }
 }
 
@@ -259,39 +480,6 @@ __global__ void k_pcg_cond(const int *__restrict__ active, int s, int *iter, int
   }
 }
 
-template <typename T>
-__global__ void k_selfdot(long n, const T *__restrict__ r, long ld, Fin fin) {
-  const int j = blockIdx.y;
-  T acc = T(0);
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const T v = r[ld * j + i];
-    acc += v * v;
-  }
-  dot_finish((double)acc, fin, j);
-}
-
-// r_T = scale * r64 ; (scale 0 for converged columns)
-template <typename T>
-__global__ void k_to_inner(long n, const double *__restrict__ R, long ldr, const double *__restrict__ scale,
-                           T *__restrict__ rt, long ldt) {
-  const int j = blockIdx.y;
-  const double sc = scale[j];
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    rt[ldt * j + i] = (T)(sc * R[ldr * j + i]);
-}
-
-// X += d / scale  (skip columns with scale 0)
-template <typename T>
-__global__ void k_accum(long n, const T *__restrict__ d, long ldd, const double *__restrict__ scale,
-                        double *__restrict__ X, long ldx) {
-  const int j = blockIdx.y;
-  const double sc = scale[j];
-  if (sc == 0.0) return;
-  const double inv = 1.0 / sc;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    X[ldx * j + i] += inv * (double)d[ldd * j + i];
-}
-
 // ---------------------------------------------------------------------------
 // profiling: a pair of events around selected launches (off by default)
 // ---------------------------------------------------------------------------
@@ -304,10 +492,9 @@ int prof_start(hp_problem *P, int id) {
     P->prof_ev.push_back(e);
   }
   if (P->prof_id.size() < r + 1) P->prof_id.resize(r + 1);
-  P->prof_id[r] = -1;  // open
   cudaEventRecord(P->prof_ev[2 * r], P->st);
   P->prof_used = r + 1;
-  P->prof_id[r] = -(id + 2);
+  P->prof_id[r] = -(id + 2);  // open
   return (int)r;
 }
 
@@ -317,8 +504,38 @@ void prof_stop(hp_problem *P, int rec) {
   P->prof_id[rec] = -P->prof_id[rec] - 2;  // closed: store the id
 }
 
+// bounded busy wait (clock cycles), used only while profiling
+__global__ void k_spin(long long cycles) {
+  const long long t0 = clock64();
+  while (clock64() - t0 < cycles) {
+  }
+}
+
+void prof_spin(hp_problem *P) {
+  if (!P->prof_on) return;
+  k_spin<<<1, 32, 0, P->st>>>(300000LL);  // ~150 us at 2 GHz
+}
+
+// Adds the durations of records [from, to) to the per-family totals; unless keep,
+// the records are retired (id -1) so that a later harvest skips them.
+void prof_harvest(hp_problem *P, size_t from, size_t to, bool keep) {
+  for (size_t r = from; r < to && r < P->prof_used; ++r) {
+    const int id = P->prof_id[r];
+    if (id < 0 || id >= 16) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, P->prof_ev[2 * r], P->prof_ev[2 * r + 1]) == cudaSuccess) {
+      P->prof_cnt[id] += 1;
+      P->prof_ms[id] += ms;
+    } else {
+      cudaGetLastError();  // a failed timing query must not surface as a solver error
+      P->prof_failed = true;
+    }
+    if (!keep) P->prof_id[r] = -1;
+  }
+}
+
 // ---------------------------------------------------------------------------
-// host launchers
+// host side
 // ---------------------------------------------------------------------------
 template <typename T> static const Stencil<T> &stencil_of(const hp_problem *P, OpKind op, int l);
 template <> const Stencil<float> &stencil_of<float>(const hp_problem *P, OpKind op, int l) {
@@ -335,28 +552,50 @@ template <> const double *coarse_inv<double>(const hp_problem *P, OpKind op) {
   return op == OP_K ? P->cK.inv64 : P->cA.inv64;
 }
 
-template <typename T, int MODE>
-static void stencil_launch(const GridDesc &g, const Stencil<T> &S, const T *X, long ldx, const T *B, long ldb, T *Y,
-                           long ldy, int s, T omega, const Fin &fin, cudaStream_t st) {
-  dim3 grid(blocks_for(g.n, s), s);
+constexpr long kMaxBlocks = 2048;  // ~13 resident 128-thread blocks per SM on 152 SMs
+
+// uncapped row grid (grid transfer kernels: one node per thread)
+static dim3 rowgrid(const GridDesc &g, int ngroups) {
+  const long nrows = g.dim == 2 ? g.np : (long)g.np * g.np;
+  return dim3((g.np + 31) / 32, (unsigned)((nrows + NB / 32 - 1) / (NB / 32)), ngroups);
+}
+// row grid of the stencil kernels: warps loop over rows so that the grid stays near
+// kMaxBlocks (fewer per-block dot partials)
+static dim3 rowgrid_capped(const GridDesc &g, int ngroups) {
+  dim3 d = rowgrid(g, ngroups);
+  const long cap = std::max<long>(1, kMaxBlocks / ((long)d.x * ngroups));
+  if ((long)d.y > cap) d.y = (unsigned)cap;
+  return d;
+}
+static long rowgrid_blocks(const GridDesc &g) {
+  const dim3 d = rowgrid(g, 1);
+  return (long)d.x * d.y;
+}
+
+template <typename T, int VW, int MODE>
+static void st_launch(const GridDesc &g, const Stencil<T> &S, const T *X, long gx, const T *B, long gb, T *Y, long gy,
+                      int s, T omega, const Fin &fin, cudaStream_t st) {
+  const int ng = (s + VW - 1) / VW;
+  const dim3 grid = rowgrid_capped(g, ng);
   if (g.dim == 2) {
     if (S.full)
-      k_stencil<T, 2, true, MODE><<<grid, NT, 0, st>>>(g, S.diag, S.invdiag, S.c, X, ldx, B, ldb, Y, ldy, omega, fin);
+      k_st<T, VW, 2, true, MODE><<<grid, NB, 0, st>>>(g, S.diag, S.invdiag, S.c, X, gx, B, gb, Y, gy, s, omega, fin);
     else
-      k_stencil<T, 2, false, MODE><<<grid, NT, 0, st>>>(g, S.diag, S.invdiag, S.c, X, ldx, B, ldb, Y, ldy, omega, fin);
+      k_st<T, VW, 2, false, MODE><<<grid, NB, 0, st>>>(g, S.diag, S.invdiag, S.c, X, gx, B, gb, Y, gy, s, omega, fin);
   } else {
     if (S.full)
-      k_stencil<T, 3, true, MODE><<<grid, NT, 0, st>>>(g, S.diag, S.invdiag, S.c, X, ldx, B, ldb, Y, ldy, omega, fin);
+      k_st<T, VW, 3, true, MODE><<<grid, NB, 0, st>>>(g, S.diag, S.invdiag, S.c, X, gx, B, gb, Y, gy, s, omega, fin);
     else
-      k_stencil<T, 3, false, MODE><<<grid, NT, 0, st>>>(g, S.diag, S.invdiag, S.c, X, ldx, B, ldb, Y, ldy, omega, fin);
+      k_st<T, VW, 3, false, MODE><<<grid, NB, 0, st>>>(g, S.diag, S.invdiag, S.c, X, gx, B, gb, Y, gy, s, omega, fin);
   }
   count_launch();
+  if (MODE == M_APPLY_DOT || MODE == M_JACOBI_DOT) dot_finalize(fin, grid.x * grid.y, s, st);
 }
 
 template <typename T>
 void launch_stencil_apply(const hp_problem *P, const GridDesc &g, const Stencil<T> &S, const T *X, long ldx, T *Y,
                           long ldy, int s, cudaStream_t st) {
-  stencil_launch<T, M_APPLY>(g, S, X, ldx, nullptr, 0, Y, ldy, s, T(0), Fin{}, st);
+  st_launch<T, 1, M_APPLY>(g, S, X, ldx, nullptr, 0, Y, ldy, s, T(0), Fin{}, st);
 }
 template void launch_stencil_apply<double>(const hp_problem *, const GridDesc &, const Stencil<double> &,
                                            const double *, long, double *, long, int, cudaStream_t);
@@ -364,16 +603,19 @@ template void launch_stencil_apply<float>(const hp_problem *, const GridDesc &, 
                                           long, float *, long, int, cudaStream_t);
 
 static long padded(long n) { return (n + 63) / 64 * 64; }
+static int round4(int s) { return (s + 3) / 4 * 4; }
 
 template <typename T> static BlockWS<T> &ws_of(hp_problem *P);
 template <> BlockWS<float> &ws_of<float>(hp_problem *P) { return P->w32; }
 template <> BlockWS<double> &ws_of<double>(hp_problem *P) { return P->w64; }
 
+// workspace for s columns (capacity rounded up to whole groups of 4)
 template <typename T> static int ensure_ws(hp_problem *P, int s) {
   BlockWS<T> &W = ws_of<T>(P);
-  if (W.scap >= s) return 0;
+  const int sc = round4(s);
+  if (W.scap >= sc) return 0;
   W.ldn = padded(P->n);
-  const size_t blk = sizeof(T) * (size_t)W.ldn * s;
+  const size_t blk = sizeof(T) * (size_t)W.ldn * sc;
   HP_TRY(W.x.ensure(blk));
   HP_TRY(W.r.ensure(blk));
   HP_TRY(W.z.ensure(blk));
@@ -381,12 +623,12 @@ template <typename T> static int ensure_ws(hp_problem *P, int s) {
   HP_TRY(W.q.ensure(blk));
   HP_TRY(W.lb[0].ensure(blk));
   for (int l = 1; l < P->L; ++l) {
-    const size_t b = sizeof(T) * (size_t)padded(P->lv[l].g.n) * s;
+    const size_t b = sizeof(T) * (size_t)padded(P->lv[l].g.n) * sc;
     HP_TRY(W.lr[l].ensure(b));
     HP_TRY(W.la[l].ensure(b));
     HP_TRY(W.lb[l].ensure(b));
   }
-  W.scap = s;
+  W.scap = sc;
   drop_graphs(P);  // captured graphs hold the old workspace pointers
   return 0;
 }
@@ -402,9 +644,12 @@ void free_scalars_host(hp_problem *P) {
 
 int ensure_scalars(hp_problem *P, int s) {
   ScalarWS &S = P->sc;
-  const int nbmax = blocks_for(P->n, 1);
-  if (S.scap >= s && S.partial.bytes >= sizeof(double) * (size_t)nbmax * s) return 0;
-  const size_t b = sizeof(double) * s;
+  const int sc = round4(s);
+  long nbmax = blocks_for(P->n, 1);
+  for (int l = 0; l < std::max(P->L, 1); ++l) nbmax = std::max(nbmax, rowgrid_blocks(P->lv[l].g));
+  nbmax = std::max(nbmax, (P->n + NB - 1) / NB);
+  if (S.scap >= sc && S.partial.bytes >= sizeof(double) * (size_t)nbmax * sc) return 0;
+  const size_t b = sizeof(double) * sc;
   HP_TRY(S.rz.ensure(b));
   HP_TRY(S.pq.ensure(b));
   HP_TRY(S.rr.ensure(b));
@@ -412,21 +657,25 @@ int ensure_scalars(hp_problem *P, int s) {
   HP_TRY(S.alpha.ensure(b));
   HP_TRY(S.beta.ensure(b));
   HP_TRY(S.scale.ensure(b));
-  HP_TRY(S.active.ensure(sizeof(int) * std::max(s, 4)));
-  HP_TRY(S.partial.ensure(sizeof(double) * (size_t)nbmax * s));
-  HP_TRY(S.counter.ensure(sizeof(unsigned) * s));
+  HP_TRY(S.iscale.ensure(b));
+  HP_TRY(S.active.ensure(sizeof(int) * sc));
+  HP_TRY(S.partial.ensure(sizeof(double) * (size_t)nbmax * sc));
+  HP_TRY(S.counter.ensure(sizeof(unsigned) * sc));
   HP_TRY(S.iter.ensure(sizeof(int) * 4));
-  HP_CUDA(cudaMemsetAsync(S.counter.p, 0, sizeof(unsigned) * s, P->st));
-  if (S.hcap < s) {
+  for (DBuf *d : {&S.rz, &S.pq, &S.rr, &S.bb, &S.alpha, &S.beta, &S.scale, &S.iscale})
+    HP_CUDA(cudaMemsetAsync(d->p, 0, b, P->st));
+  HP_CUDA(cudaMemsetAsync(S.active.p, 0, sizeof(int) * sc, P->st));
+  HP_CUDA(cudaMemsetAsync(S.counter.p, 0, sizeof(unsigned) * sc, P->st));
+  if (S.hcap < sc) {
     free_scalars_host(P);
-    HP_CUDA(cudaMallocHost(&S.h_active, sizeof(int) * s));
+    HP_CUDA(cudaMallocHost(&S.h_active, sizeof(int) * sc));
     HP_CUDA(cudaMallocHost(&S.h_iter, sizeof(int) * 4));
-    HP_CUDA(cudaMallocHost(&S.h_rr, sizeof(double) * s));
-    HP_CUDA(cudaMallocHost(&S.h_bb, sizeof(double) * s));
-    S.hcap = s;
+    HP_CUDA(cudaMallocHost(&S.h_rr, sizeof(double) * sc));
+    HP_CUDA(cudaMallocHost(&S.h_bb, sizeof(double) * sc));
+    S.hcap = sc;
   }
   drop_graphs(P);  // captured graphs hold the old scalar pointers
-  S.scap = s;
+  S.scap = sc;
   return 0;
 }
 
@@ -447,64 +696,81 @@ static Fin make_fin(hp_problem *P, int kind, double tol2 = 0.0, double *out = nu
   return f;
 }
 
+static dim3 nodegrid(long n, int ng) {
+  const long b = std::min<long>((n + NB - 1) / NB, std::max<long>(1, kMaxBlocks / ng));
+  return dim3((unsigned)b, ng);
+}
+
 // Preconditioner z = M^{-1} r with the fused <r, z> -> fin.
-template <typename T>
+template <typename T, int VW>
 static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, const Fin &fin) {
   BlockWS<T> &W = ws_of<T>(P);
   cudaStream_t st = P->st;
   const T om = (T)P->omega;
+  const int ng = (s + VW - 1) / VW;
+  const long gs0 = W.ldn * VW;
   if (op == OP_M) {  // Jacobi
     const Stencil<T> &S = stencil_of<T>(P, op, 0);
-    k_jacobi0<T><<<dim3(blocks_for(P->n, s), s), NT, 0, st>>>(P->n, S.invdiag, r0, W.ldn, z0, W.ldn, T(1), fin, 1);
+    const dim3 gr = nodegrid(P->n, ng);
+    k_jacobi0<T, VW><<<gr, NB, 0, st>>>(P->n, S.invdiag, r0, gs0, z0, T(1), s, fin, 1);
     count_launch();
+    dot_finalize(fin, gr.x, s, st);
     return;
   }
   const int L = P->L;
   if (L == 1) {  // the coarse solve is the whole preconditioner; the caller forms <r, z>
     const int nc = (int)P->lv[0].g.n;
-    k_coarse_apply<T><<<s, 256, sizeof(T) * nc, st>>>(coarse_inv<T>(P, op), nc, r0, W.ldn, z0, W.ldn);
+    k_coarse_apply<T, VW><<<dim3((nc + 31) / 32, ng), 256, sizeof(T) * nc * VW, st>>>(coarse_inv<T>(P, op), nc, r0,
+                                                                                       gs0, z0, gs0);
     count_launch();
     return;
   }
   const T *rl[HP_MAXL];
   T *ea[HP_MAXL], *eb[HP_MAXL];
-  long ld[HP_MAXL];
+  long gsl[HP_MAXL];
   rl[0] = r0;
   ea[0] = z0;
   eb[0] = W.lb[0].template as<T>();
-  ld[0] = W.ldn;
+  gsl[0] = gs0;
   for (int l = 1; l < L; ++l) {
     rl[l] = W.lr[l].template as<T>();
     ea[l] = W.la[l].template as<T>();
     eb[l] = W.lb[l].template as<T>();
-    ld[l] = padded(P->lv[l].g.n);
+    gsl[l] = padded(P->lv[l].g.n) * VW;
   }
   T *cur[HP_MAXL], *oth[HP_MAXL];
   const Fin nofin{};
+  const int nu = P->nu;
   for (int l = 0; l + 1 < L; ++l) {
     const GridDesc &g = P->lv[l].g;
     const Stencil<T> &S = stencil_of<T>(P, op, l);
-    T *c = eb[l], *o = ea[l];
-    k_jacobi0<T><<<dim3(blocks_for(g.n, s), s), NT, 0, st>>>(g.n, S.invdiag, rl[l], ld[l], c, ld[l], om, nofin, 0);
-    count_launch();
-    for (int k = 1; k < P->nu; ++k) {
-      const int pr = prof_start(P, l == 0 ? PROF_SMOOTH : -1);
-      stencil_launch<T, M_JACOBI>(g, S, c, ld[l], rl[l], ld[l], o, ld[l], s, om, nofin, st);
+    // Pre-smoothing from zero.  Each later sweep flips buffers (nu - 2 more pre, nu post), so the
+    // fused two-sweep kernel writes ea[l] and the single sweep (nu = 1) writes eb[l]: either way the
+    // level's final correction lands in ea[l] (z0 at level 0).
+    T *c = nu >= 2 ? ea[l] : eb[l], *o = nu >= 2 ? eb[l] : ea[l];
+    int pr = prof_start(P, l == 0 ? (nu >= 2 ? PROF_PRESMOOTH : PROF_SMOOTH) : -1);
+    if (nu >= 2) {
+      st_launch<T, VW, M_JAC2>(g, S, rl[l], gsl[l], nullptr, 0, c, gsl[l], s, om, nofin, st);
+    } else {
+      k_jacobi0<T, VW><<<nodegrid(g.n, ng), NB, 0, st>>>(g.n, S.invdiag, rl[l], gsl[l], c, om, s, nofin, 0);
+      count_launch();
+    }
+    prof_stop(P, pr);
+    for (int k = 2; k < nu; ++k) {
+      pr = prof_start(P, l == 0 ? PROF_SMOOTH : -1);
+      st_launch<T, VW, M_JACOBI>(g, S, c, gsl[l], rl[l], gsl[l], o, gsl[l], s, om, nofin, st);
       prof_stop(P, pr);
       std::swap(c, o);
     }
-    {
-      const int pr = prof_start(P, l == 0 ? PROF_RESID_MG : -1);
-      stencil_launch<T, M_RESID>(g, S, c, ld[l], rl[l], ld[l], o, ld[l], s, om, nofin, st);
-      prof_stop(P, pr);
-    }
+    pr = prof_start(P, l == 0 ? PROF_RESID_MG : -1);
+    st_launch<T, VW, M_RESID>(g, S, c, gsl[l], rl[l], gsl[l], o, gsl[l], s, om, nofin, st);
+    prof_stop(P, pr);
     const GridDesc &gc = P->lv[l + 1].g;
-    dim3 grid(blocks_for(gc.n, s), s);
     T *rc = const_cast<T *>(rl[l + 1]);
     if (g.dim == 2)
-      k_restrict<T, 2><<<grid, NT, 0, st>>>(g, gc, o, ld[l], rc, ld[l + 1], op == OP_K);
+      k_restrict<T, VW, 2><<<rowgrid(gc, ng), NB, 0, st>>>(g, gc, o, gsl[l], rc, gsl[l + 1], op == OP_K);
     else
-      k_restrict<T, 3><<<grid, NT, 0, st>>>(g, gc, o, ld[l], rc, ld[l + 1], op == OP_K);
+      k_restrict<T, VW, 3><<<rowgrid(gc, ng), NB, 0, st>>>(g, gc, o, gsl[l], rc, gsl[l + 1], op == OP_K);
     count_launch();
     cur[l] = c;
     oth[l] = o;
@@ -512,26 +778,26 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
   {
     const int lc = L - 1;
     const int nc = (int)P->lv[lc].g.n;
-    k_coarse_apply<T><<<s, 256, sizeof(T) * nc, st>>>(coarse_inv<T>(P, op), nc, rl[lc], ld[lc], ea[lc], ld[lc]);
+    k_coarse_apply<T, VW><<<dim3((nc + 31) / 32, ng), 256, sizeof(T) * nc * VW, st>>>(coarse_inv<T>(P, op), nc,
+                                                                                       rl[lc], gsl[lc], ea[lc], gsl[lc]);
     count_launch();
     cur[lc] = ea[lc];
   }
   for (int l = L - 2; l >= 0; --l) {
     const GridDesc &g = P->lv[l].g, &gc = P->lv[l + 1].g;
     const Stencil<T> &S = stencil_of<T>(P, op, l);
-    dim3 grid(blocks_for(g.n, s), s);
     if (g.dim == 2)
-      k_prolong_add<T, 2><<<grid, NT, 0, st>>>(g, gc, cur[l + 1], ld[l + 1], cur[l], ld[l]);
+      k_prolong_add<T, VW, 2><<<rowgrid(g, ng), NB, 0, st>>>(g, gc, cur[l + 1], gsl[l + 1], cur[l], gsl[l]);
     else
-      k_prolong_add<T, 3><<<grid, NT, 0, st>>>(g, gc, cur[l + 1], ld[l + 1], cur[l], ld[l]);
+      k_prolong_add<T, VW, 3><<<rowgrid(g, ng), NB, 0, st>>>(g, gc, cur[l + 1], gsl[l + 1], cur[l], gsl[l]);
     count_launch();
     T *c = cur[l], *o = oth[l];
-    for (int k = 0; k < P->nu; ++k) {
+    for (int k = 0; k < nu; ++k) {
       const int pr = prof_start(P, l == 0 ? PROF_SMOOTH : -1);
-      if (l == 0 && k == P->nu - 1)
-        stencil_launch<T, M_JACOBI_DOT>(g, S, c, ld[l], rl[l], ld[l], o, ld[l], s, om, fin, st);
+      if (l == 0 && k == nu - 1)
+        st_launch<T, VW, M_JACOBI_DOT>(g, S, c, gsl[l], rl[l], gsl[l], o, gsl[l], s, om, fin, st);
       else
-        stencil_launch<T, M_JACOBI>(g, S, c, ld[l], rl[l], ld[l], o, ld[l], s, om, nofin, st);
+        st_launch<T, VW, M_JACOBI>(g, S, c, gsl[l], rl[l], gsl[l], o, gsl[l], s, om, nofin, st);
       prof_stop(P, pr);
       std::swap(c, o);
     }
@@ -539,69 +805,67 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
   }
 }
 
-template <typename T>
-__global__ void k_dot2(long n, const T *__restrict__ a, const T *__restrict__ b, long ld, Fin fin) {
-  const int j = blockIdx.y;
-  T acc = T(0);
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    acc += a[ld * j + i] * b[ld * j + i];
-  dot_finish((double)acc, fin, j);
-}
-
 // PCG on W.r (overwritten) -> W.x.
 //   init:  x = 0, p = 0, bb = rr = <r, r>, active = bb > 0, iter = 0
 //   body:  z = M r, beta = <r,z>/rz (0 at iter 0), p = z + beta p,
 //          q = K p, alpha = rz/<p,q>, x += alpha p, r -= alpha q, rr = <r,r>,
 //          active &= rr > tol^2 bb, iter += 1; repeat while any active and iter < maxit.
-template <typename T>
+template <typename T, int VW>
 static void pcg_init(hp_problem *P, OpKind op, int s, cudaGraphConditionalHandle h, int use_handle, int maxit) {
   BlockWS<T> &W = ws_of<T>(P);
   cudaStream_t st = P->st;
-  const long n = P->n, ld = W.ldn;
-  dim3 grid(blocks_for(n, s), s);
-  cudaMemsetAsync(W.x.p, 0, sizeof(T) * ld * s, st);
-  cudaMemsetAsync(W.p.p, 0, sizeof(T) * ld * s, st);
+  const int ng = (s + VW - 1) / VW;
+  const long gs = W.ldn * VW;
+  cudaMemsetAsync(W.x.p, 0, sizeof(T) * gs * ng, st);
+  cudaMemsetAsync(W.p.p, 0, sizeof(T) * gs * ng, st);
   cudaMemsetAsync(P->sc.iter.p, 0, sizeof(int), st);
-  k_selfdot<T><<<grid, NT, 0, st>>>(n, W.r.template as<T>(), ld, make_fin(P, FIN_INIT));
+  T *r = W.r.template as<T>();
+  const dim3 gr = nodegrid(P->n, ng);
+  k_dot<T, VW><<<gr, NB, 0, st>>>(P->n, gs, r, r, s, make_fin(P, FIN_INIT));
+  dot_finalize(make_fin(P, FIN_INIT), gr.x, s, st);
   k_pcg_cond<<<1, 256, 0, st>>>(P->sc.active.as<int>(), s, P->sc.iter.as<int>(), maxit, 0, h, use_handle);
   count_launch(2);
 }
 
-template <typename T>
+template <typename T, int VW>
 static void pcg_body(hp_problem *P, OpKind op, int s, double tol2, cudaGraphConditionalHandle h, int use_handle,
                      int maxit) {
   BlockWS<T> &W = ws_of<T>(P);
   cudaStream_t st = P->st;
-  const long n = P->n, ld = W.ldn;
+  const long n = P->n;
+  const int ng = (s + VW - 1) / VW;
+  const long gs = W.ldn * VW;
   T *x = W.x.template as<T>(), *r = W.r.template as<T>(), *z = W.z.template as<T>();
   T *p = W.p.template as<T>(), *q = W.q.template as<T>();
   const GridDesc &g0 = P->lv[0].g;
   const Stencil<T> &S0 = stencil_of<T>(P, op, 0);
-  dim3 grid(blocks_for(n, s), s);
   int pr = prof_start(P, PROF_VCYCLE);
-  precondition<T>(P, op, s, r, z, make_fin(P, FIN_BETA));
+  precondition<T, VW>(P, op, s, r, z, make_fin(P, FIN_BETA));
   prof_stop(P, pr);
   if (op != OP_M && P->L == 1) {
-    k_dot2<T><<<grid, NT, 0, st>>>(n, r, z, ld, make_fin(P, FIN_BETA));
+    const dim3 gr = nodegrid(n, ng);
+    k_dot<T, VW><<<gr, NB, 0, st>>>(n, gs, r, z, s, make_fin(P, FIN_BETA));
     count_launch();
+    dot_finalize(make_fin(P, FIN_BETA), gr.x, s, st);
   }
-  k_p_update<T><<<grid, NT, 0, st>>>(n, z, p, ld, P->sc.beta.as<double>());
+  k_p_update<T, VW><<<nodegrid(n, ng), NB, 0, st>>>(n, gs, z, p, P->sc.beta.as<double>());
   count_launch();
   pr = prof_start(P, PROF_MATVEC);
-  stencil_launch<T, M_APPLY_DOT>(g0, S0, p, ld, nullptr, 0, q, ld, s, T(0), make_fin(P, FIN_ALPHA), st);
+  st_launch<T, VW, M_APPLY_DOT>(g0, S0, p, gs, nullptr, 0, q, gs, s, T(0), make_fin(P, FIN_ALPHA), st);
   prof_stop(P, pr);
   pr = prof_start(P, PROF_CG_UPDATE);
-  k_cg_update<T><<<grid, NT, 0, st>>>(n, p, q, x, r, ld, P->sc.alpha.as<double>(), make_fin(P, FIN_RR, tol2));
+  const dim3 gu = nodegrid(n, ng);
+  k_cg_update<T, VW><<<gu, NB, 0, st>>>(n, gs, p, q, x, r, P->sc.alpha.as<double>(), s, make_fin(P, FIN_RR, tol2));
+  dot_finalize(make_fin(P, FIN_RR, tol2), gu.x, s, st);
   prof_stop(P, pr);
   k_pcg_cond<<<1, 256, 0, st>>>(P->sc.active.as<int>(), s, P->sc.iter.as<int>(), maxit, 1, h, use_handle);
   count_launch(2);
 }
 
 struct PcgGraph {
-  int op, fp32, s, maxit;
+  int op, tbytes, vw, s, maxit;
   double tol;
   cudaGraphExec_t exec;
-  int nkernels;
 };
 static std::vector<std::pair<hp_problem *, PcgGraph>> g_graphs;
 
@@ -617,7 +881,7 @@ void drop_graphs(hp_problem *P) {
 }
 
 // Captures init + a conditional WHILE node whose body is one PCG iteration.
-template <typename T>
+template <typename T, int VW>
 static int build_graph(hp_problem *P, OpKind op, int s, double tol, int maxit, PcgGraph *out) {
   if (!P->cap) HP_CUDA(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
   cudaStream_t saved = P->st;
@@ -626,11 +890,11 @@ static int build_graph(hp_problem *P, OpKind op, int s, double tol, int maxit, P
   P->st = P->cap;
   const unsigned long long l0 = g_launches;
   cudaGraph_t g = nullptr;
-  int rc = 0;
   auto fail = [&](cudaError_t e, const char *w) {
-    rc = cuda_check(e, w);
+    const int rc = cuda_check(e, w);
     P->st = saved;
     P->prof_on = saved_prof;
+    g_launches = l0;
     if (g) cudaGraphDestroy(g);
     return rc;
   };
@@ -641,7 +905,7 @@ static int build_graph(hp_problem *P, OpKind op, int s, double tol, int maxit, P
   if (e != cudaSuccess) return fail(e, "cudaGraphConditionalHandleCreate");
   e = cudaStreamBeginCaptureToGraph(P->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return fail(e, "capture init");
-  pcg_init<T>(P, op, s, h, 1, maxit);
+  pcg_init<T, VW>(P, op, s, h, 1, maxit);
   e = cudaStreamEndCapture(P->cap, &g);
   if (e != cudaSuccess) return fail(e, "end capture init");
   size_t nn = 0;
@@ -665,7 +929,7 @@ static int build_graph(hp_problem *P, OpKind op, int s, double tol, int maxit, P
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   e = cudaStreamBeginCaptureToGraph(P->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return fail(e, "capture body");
-  pcg_body<T>(P, op, s, tol * tol, h, 1, maxit);
+  pcg_body<T, VW>(P, op, s, tol * tol, h, 1, maxit);
   e = cudaStreamEndCapture(P->cap, &body);
   if (e != cudaSuccess) return fail(e, "end capture body");
   cudaGraphExec_t ex;
@@ -675,39 +939,50 @@ static int build_graph(hp_problem *P, OpKind op, int s, double tol, int maxit, P
   P->st = saved;
   P->prof_on = saved_prof;
   g_launches = l0;  // captured launches are counted when the graph runs
-  *out = PcgGraph{(int)op, sizeof(T) == 4, s, maxit, tol, ex, 0};
+  *out = PcgGraph{(int)op, (int)sizeof(T), VW, s, maxit, tol, ex};
   return 0;
 }
 
-template <typename T>
+static int kernels_per_iteration(const hp_problem *P, OpKind op) {
+  if (op == OP_M) return 8;
+  // V-cycle: per non-coarsest level pre (1 + nu - 2), resid, restrict, prolong, nu post; coarse 1;
+  // plus p update, matvec, cg update, condition and three dot finalisations
+  const int per_level = (P->nu >= 2 ? P->nu - 1 : 1) + 3 + P->nu;
+  return 7 + (P->L - 1) * per_level + 1 + 2 * (P->L == 1);
+}
+
+template <typename T, int VW>
 static int pcg(hp_problem *P, OpKind op, int s, double rtol, int maxit, int *its) {
   cudaStream_t st = P->st;
   int *h_it = P->sc.h_iter;
   if (P->use_graphs && !P->prof_on) {
     PcgGraph *G = nullptr;
     for (auto &pg : g_graphs)
-      if (pg.first == P && pg.second.op == (int)op && pg.second.fp32 == (sizeof(T) == 4) && pg.second.s == s &&
-          pg.second.maxit == maxit && pg.second.tol == rtol)
+      if (pg.first == P && pg.second.op == (int)op && pg.second.tbytes == (int)sizeof(T) && pg.second.vw == VW &&
+          pg.second.s == s && pg.second.maxit == maxit && pg.second.tol == rtol)
         G = &pg.second;
     if (!G) {
       PcgGraph ng;
-      HP_TRY(build_graph<T>(P, op, s, rtol, maxit, &ng));
+      HP_TRY((build_graph<T, VW>(P, op, s, rtol, maxit, &ng)));
       g_graphs.push_back({P, ng});
       G = &g_graphs.back().second;
     }
     HP_CUDA(cudaGraphLaunch(G->exec, st));
     HP_CUDA(cudaMemcpyAsync(h_it, P->sc.iter.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     HP_CUDA(cudaStreamSynchronize(st));
-    const int per_it = 12 + 7 * P->L;  // approximate kernels per iteration, for launch accounting
-    count_launch((unsigned long long)(*h_it) * per_it + 3);
+    count_launch((unsigned long long)(*h_it) * kernels_per_iteration(P, op) + 2);
     *its = *h_it;
     return *h_it >= maxit ? HP_ERR_NOT_CONVERGED : 0;
   }
   const double tol2 = rtol * rtol;
-  pcg_init<T>(P, op, s, 0, 0, maxit);
+  pcg_init<T, VW>(P, op, s, 0, 0, maxit);
   int *hact = P->sc.h_active;
+  // Profiling: a bounded clock spin heads each iteration so that the host has
+  // enqueued the whole iteration before the GPU reaches it; the kernels then run
+  // back to back and each event pair times its kernel, not the host's launch rate.
   for (;;) {
-    pcg_body<T>(P, op, s, tol2, 0, 0, maxit);
+    prof_spin(P);
+    pcg_body<T, VW>(P, op, s, tol2, 0, 0, maxit);
     HP_CUDA(cudaMemcpyAsync(hact, P->sc.active.p, sizeof(int) * s, cudaMemcpyDeviceToHost, st));
     HP_CUDA(cudaMemcpyAsync(h_it, P->sc.iter.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     HP_CUDA(cudaStreamSynchronize(st));
@@ -721,28 +996,31 @@ static int pcg(hp_problem *P, OpKind op, int s, double rtol, int maxit, int *its
 }
 
 int apply_op64(hp_problem *P, OpKind op, const double *X, long ldx, double *Y, long ldy, int s) {
-  launch_stencil_apply<double>(P, P->lv[0].g, stencil_of<double>(P, op, 0), X, ldx, Y, ldy, s, P->st);
+  st_launch<double, 1, M_APPLY>(P->lv[0].g, stencil_of<double>(P, op, 0), X, ldx, nullptr, 0, Y, ldy, s, 0.0, Fin{},
+                                P->st);
   return cuda_check(cudaGetLastError(), "apply");
 }
 
-// FP64 residual R = B - S X with per-column |R|^2 -> rr (host)
+// FP64 residual R = B - S X (column-major) and per-column |R|^2 -> sc.rr
 static int residual64(hp_problem *P, OpKind op, const double *B, long ldb, const double *X, long ldx, double *R,
                       long ldr, int s) {
   const int pr = prof_start(P, PROF_RESID64);
-  stencil_launch<double, M_RESID>(P->lv[0].g, stencil_of<double>(P, op, 0), X, ldx, B, ldb, R, ldr, s, 0.0, Fin{},
-                                  P->st);
+  st_launch<double, 1, M_RESID>(P->lv[0].g, stencil_of<double>(P, op, 0), X, ldx, B, ldb, R, ldr, s, 0.0, Fin{},
+                                P->st);
   prof_stop(P, pr);
   HP_TRY(block_dot(P, R, ldr, R, ldr, P->n, s, P->sc.rr.as<double>()));
   return 0;
 }
 
-template <typename T>
+template <typename T, int VW>
 static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double *X, long ldx, int s, double rtol,
                     double tol_in, hp_solve_stats *stats) {
   BlockWS<T> &W = ws_of<T>(P);
   cudaStream_t st = P->st;
   const long n = P->n;
   const long ld64 = padded(n);
+  const int ng = (s + VW - 1) / VW;
+  const long gs = W.ldn * VW;
   HP_TRY(P->r64.ensure(sizeof(double) * ld64 * s));
   HP_TRY(P->b64.ensure(sizeof(double) * ld64 * s));
   double *r64 = P->r64.as<double>(), *b64 = P->b64.as<double>();
@@ -754,7 +1032,7 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
   HP_TRY(block_dot(P, r64, ld64, r64, ld64, n, s, P->sc.rr.as<double>()));
   double *hrr = P->sc.h_rr, *hbb = P->sc.h_bb;
   HP_CUDA(cudaMemcpyAsync(hbb, P->sc.bb.p, sizeof(double) * s, cudaMemcpyDeviceToHost, st));
-  std::vector<double> hscale(s);
+  std::vector<double> hscale(s), hiscale(s);
   int total_its = 0, outer = 0, rc = 0;
   double worst = 0.0;
   for (outer = 0; outer <= P->max_outer; ++outer) {
@@ -768,6 +1046,7 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
       worst = std::max(worst, rel);
       const bool done = hbb[j] == 0.0 || hrr[j] <= rtol * rtol * hbb[j];
       hscale[j] = done ? 0.0 : 1.0 / std::sqrt(hrr[j]);
+      hiscale[j] = done ? 0.0 : std::sqrt(hrr[j]);
       nact += !done;
     }
     if (nact == 0) break;
@@ -776,18 +1055,18 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
       break;
     }
     HP_CUDA(cudaMemcpyAsync(P->sc.scale.p, hscale.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
-    dim3 grid(blocks_for(n, s), s);
-    k_to_inner<T><<<grid, NT, 0, st>>>(n, r64, ld64, P->sc.scale.as<double>(), W.r.template as<T>(), W.ldn);
+    HP_CUDA(cudaMemcpyAsync(P->sc.iscale.p, hiscale.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
+    k_to_inner<T, VW><<<nodegrid(n, ng), NB, 0, st>>>(n, r64, ld64, P->sc.scale.as<double>(), s,
+                                                      W.r.template as<T>(), gs);
     count_launch();
     int its = 0;
-    const int prc = pcg<T>(P, op, s, tol_in, P->max_iter, &its);
+    pcg<T, VW>(P, op, s, tol_in, P->max_iter, &its);  // a stalled inner solve still reduces the residual
     total_its += its;
-    k_accum<T><<<grid, NT, 0, st>>>(n, W.x.template as<T>(), W.ldn, P->sc.scale.as<double>(), X, ldx);
+    prof_spin(P);
+    k_accum<T, VW><<<nodegrid(n, ng), NB, 0, st>>>(n, W.x.template as<T>(), gs, P->sc.iscale.as<double>(), s, X,
+                                                   ldx);
     count_launch();
     HP_TRY(residual64(P, op, b64, ld64, X, ldx, r64, ld64, s));
-    if (prc == HP_ERR_NOT_CONVERGED && its >= P->max_iter) {
-      // keep refining: a stalled inner solve still reduces the residual
-    }
   }
   if (stats) {
     stats->iterations += total_its;
@@ -805,10 +1084,11 @@ int solve_block(hp_problem *P, OpKind op, const double *B, long ldb, double *X, 
   HP_TRY(ensure_scalars(P, s));
   if (P->precision == HP_FP64_PLAIN) {
     HP_TRY(ensure_ws<double>(P, s));
-    return ir_solve<double>(P, op, B, ldb, X, ldx, s, rtol, 0.5 * rtol, st);
+    return ir_solve<double, 1>(P, op, B, ldb, X, ldx, s, rtol, 0.5 * rtol, st);
   }
   HP_TRY(ensure_ws<float>(P, s));
-  return ir_solve<float>(P, op, B, ldb, X, ldx, s, rtol, P->inner_rtol, st);
+  if (s >= 2) return ir_solve<float, 4>(P, op, B, ldb, X, ldx, s, rtol, P->inner_rtol, st);
+  return ir_solve<float, 1>(P, op, B, ldb, X, ldx, s, rtol, P->inner_rtol, st);
 }
 
 }  // namespace hp

@@ -326,7 +326,7 @@ class Problem:
         return W if eta.dim() == 2 else W[0]
 
     # ---- measurement -------------------------------------------------------------
-    PROF_NAMES = ("matvec", "smooth", "resid_mg", "resid64", "cg_update", "vcycle")
+    PROF_NAMES = ("matvec", "smooth", "resid_mg", "resid64", "cg_update", "vcycle", "presmooth")
 
     def profile_enable(self, on: bool = True):
         _check(lib().hp_profile_enable(self._h, 1 if on else 0), "hp_profile_enable")
