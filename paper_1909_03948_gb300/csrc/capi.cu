@@ -476,7 +476,7 @@ void hp_problem_destroy(hp_problem *P) {
   if (P->cap) cudaStreamDestroy(P->cap);
   free_scalars_host(P);
   ScalarWS &S = P->sc;
-  for (DBuf *b : {&S.iter, &S.rz, &S.pq, &S.rr, &S.bb, &S.alpha, &S.beta, &S.scale, &S.iscale, &S.tmp, &S.active, &S.partial, &S.counter})
+  for (DBuf *b : {&S.iter, &S.rz, &S.pq, &S.rr, &S.bb, &S.alpha, &S.beta, &S.scale, &S.iscale, &S.tol2col, &S.tmp, &S.active, &S.partial, &S.counter})
     b->release();
   for (DBuf *b : {&P->r64, &P->b64, &P->t64a, &P->t64b, &P->t64c, &P->obsbuf, &P->small}) b->release();
   for (int i = 0; i < 6; ++i) P->vtmp[i].release();

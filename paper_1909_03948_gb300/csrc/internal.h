@@ -60,7 +60,7 @@ template <typename T> struct BlockWS {
 
 struct ScalarWS {
   int scap = 0;
-  DBuf rz, pq, rr, bb, alpha, beta, scale, iscale, tmp;   // double per column
+  DBuf rz, pq, rr, bb, alpha, beta, scale, iscale, tol2col, tmp;   // double per column
   DBuf active;                                     // int per column
   DBuf partial;                                    // double [slot][col][block]
   DBuf counter;                                    // unsigned [slot][col]

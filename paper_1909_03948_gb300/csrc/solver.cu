@@ -39,6 +39,7 @@ struct Fin {
   double *rz = nullptr, *alpha = nullptr, *beta = nullptr, *rr = nullptr, *bb = nullptr, *out = nullptr;
   int *active = nullptr;
   int *iter = nullptr;  // PCG iteration counter (FIN_BETA: beta = 0 on the first iteration)
+  const double *tol2col = nullptr;  // per-column squared relative tolerance (FIN_RR), else tol2
   double tol2 = 0.0;
 };
 
@@ -48,7 +49,7 @@ __device__ __forceinline__ void fin_apply(const Fin &f, int j, double s) {
     case FIN_ALPHA: f.alpha[j] = (f.active[j] && s > 0.0) ? f.rz[j] / s : 0.0; break;
     case FIN_RR:
       f.rr[j] = s;
-      f.active[j] = f.active[j] && (s > f.tol2 * f.bb[j]);
+      f.active[j] = f.active[j] && (s > (f.tol2col ? f.tol2col[j] : f.tol2) * f.bb[j]);
       break;
     case FIN_BETA: {
       const double b = (*f.iter > 0 && f.active[j] && f.rz[j] != 0.0) ? s / f.rz[j] : 0.0;
@@ -658,11 +659,12 @@ int ensure_scalars(hp_problem *P, int s) {
   HP_TRY(S.beta.ensure(b));
   HP_TRY(S.scale.ensure(b));
   HP_TRY(S.iscale.ensure(b));
+  HP_TRY(S.tol2col.ensure(b));
   HP_TRY(S.active.ensure(sizeof(int) * sc));
   HP_TRY(S.partial.ensure(sizeof(double) * (size_t)nbmax * sc));
   HP_TRY(S.counter.ensure(sizeof(unsigned) * sc));
   HP_TRY(S.iter.ensure(sizeof(int) * 4));
-  for (DBuf *d : {&S.rz, &S.pq, &S.rr, &S.bb, &S.alpha, &S.beta, &S.scale, &S.iscale})
+  for (DBuf *d : {&S.rz, &S.pq, &S.rr, &S.bb, &S.alpha, &S.beta, &S.scale, &S.iscale, &S.tol2col})
     HP_CUDA(cudaMemsetAsync(d->p, 0, b, P->st));
   HP_CUDA(cudaMemsetAsync(S.active.p, 0, sizeof(int) * sc, P->st));
   HP_CUDA(cudaMemsetAsync(S.counter.p, 0, sizeof(unsigned) * sc, P->st));
@@ -691,6 +693,7 @@ static Fin make_fin(hp_problem *P, int kind, double tol2 = 0.0, double *out = nu
   f.bb = P->sc.bb.as<double>();
   f.active = P->sc.active.as<int>();
   f.iter = P->sc.iter.as<int>();
+  f.tol2col = P->sc.tol2col.as<double>();
   f.tol2 = tol2;
   f.out = out;
   return f;
@@ -1032,7 +1035,7 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
   HP_TRY(block_dot(P, r64, ld64, r64, ld64, n, s, P->sc.rr.as<double>()));
   double *hrr = P->sc.h_rr, *hbb = P->sc.h_bb;
   HP_CUDA(cudaMemcpyAsync(hbb, P->sc.bb.p, sizeof(double) * s, cudaMemcpyDeviceToHost, st));
-  std::vector<double> hscale(s), hiscale(s);
+  std::vector<double> hscale(s), hiscale(s), htol2(s);
   int total_its = 0, outer = 0, rc = 0;
   double worst = 0.0;
   for (outer = 0; outer <= P->max_outer; ++outer) {
@@ -1047,6 +1050,11 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
       const bool done = hbb[j] == 0.0 || hrr[j] <= rtol * rtol * hbb[j];
       hscale[j] = done ? 0.0 : 1.0 / std::sqrt(hrr[j]);
       hiscale[j] = done ? 0.0 : std::sqrt(hrr[j]);
+      // inner relative tolerance: the finer of tol_in and what is left to reach rtol
+      // (with a factor 1/4 of margin), so the last refinement step does no extra work
+      const double need = hrr[j] > 0 ? 0.25 * rtol * std::sqrt(hbb[j] / hrr[j]) : 1.0;
+      const double t = std::min(0.5, std::max(tol_in, need));
+      htol2[j] = t * t;
       nact += !done;
     }
     if (nact == 0) break;
@@ -1056,6 +1064,7 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
     }
     HP_CUDA(cudaMemcpyAsync(P->sc.scale.p, hscale.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
     HP_CUDA(cudaMemcpyAsync(P->sc.iscale.p, hiscale.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
+    HP_CUDA(cudaMemcpyAsync(P->sc.tol2col.p, htol2.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
     k_to_inner<T, VW><<<nodegrid(n, ng), NB, 0, st>>>(n, r64, ld64, P->sc.scale.as<double>(), s,
                                                       W.r.template as<T>(), gs);
     count_launch();
