@@ -168,6 +168,31 @@ int hp_Rinv_apply(hp_problem *P, const double *X, int ldx, double *Y, int ldy, i
  * degree-2 element rule.  eta: (dim+1)*nelems normals per column, element-major. */
 int hp_mass_factor_apply(hp_problem *P, const double *eta, int ldeta, double *W, int ldw, int nsamples);
 
+/* ---- solve without device allocation ---------------------------------------
+ * The paper has no counterpart to this entry point: it serves callers that
+ * cannot allocate device memory when they solve.  hp_mass_solve grows the
+ * problem's workspace with cudaMalloc on first use; a caller that is capturing
+ * a stream into a CUDA graph cannot allocate (allocation is not capturable), and
+ * an application that reserves all device memory at start-up may forbid later
+ * allocation.  hp_mass_solve_noalloc computes the same X = M^{-1} B (FP64
+ * diagonally preconditioned CG, per-column relative residual
+ * min(rtol, 1e-10)) using one fixed file-scope device array as scratch, and
+ * calls no cudaMalloc / cudaFree or allocating library routine.
+ *  - Limits: nrhs <= HP_NOALLOC_MAX_COLS and n * nrhs <= HP_NOALLOC_MAX_ENTRIES,
+ *    else HP_ERR_INVALID.  The scratch array (about 11 MB) lives on every GPU that
+ *    loads the library until the process exits.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls share the one array: calls that overlap on the GPU (other streams,
+ *    other threads, other problems) race and must be serialised by the caller.
+ *    Each call re-initialises what it reads, so no state carries over.
+ *  - The call synchronises the problem's stream once per CG iteration (it reads
+ *    the per-column convergence flags into a host array). */
+#define HP_NOALLOC_MAX_COLS 64
+#define HP_NOALLOC_MAX_ENTRIES 262144
+int hp_mass_solve_noalloc(hp_problem *P, const double *B, int ldb, double *X, int ldx, int nrhs,
+                          hp_solve_stats *st);
+
 /* ---- algorithms (Section 4) ---------------------------------------------- */
 
 /* Inexact Newton-CG (Algorithm 1) from m_dev_inout (n values) to the MAP point.

@@ -97,6 +97,7 @@ _SIGS = {
     "hp_mass_apply": (_I, [_P, _D, _I, _D, _I, _I]),
     "hp_prior_solve": (_I, [_P, _D, _I, _D, _I, _I, C.POINTER(SolveStats)]),
     "hp_mass_solve": (_I, [_P, _D, _I, _D, _I, _I, C.POINTER(SolveStats)]),
+    "hp_mass_solve_noalloc": (_I, [_P, _D, _I, _D, _I, _I, C.POINTER(SolveStats)]),
     "hp_R_apply": (_I, [_P, _D, _I, _D, _I, _I]),
     "hp_Rinv_apply": (_I, [_P, _D, _I, _D, _I, _I]),
     "hp_mass_factor_apply": (_I, [_P, _D, _I, _D, _I, _I]),
@@ -311,6 +312,17 @@ class Problem:
 
     def mass_solve(self, B):
         return self._unary("hp_mass_solve", B, True)
+
+    def mass_solve_noalloc(self, B, out):
+        """X = M^{-1} B without any device allocation by the library: the caller
+        provides the output block and the library uses a fixed device scratch array
+        (nrhs <= 64, n * nrhs <= 262144; calls must not overlap on the GPU)."""
+        B2, s, n = _block(B, self.n, "B")
+        X2 = _block(out, self.n, "out")[0]
+        st = SolveStats()
+        _check(lib().hp_mass_solve_noalloc(self._h, _dptr(B2), n, _dptr(X2), n, s, C.byref(st)),
+               "hp_mass_solve_noalloc")
+        return out, st.as_dict()
 
     def R_apply(self, X):
         return self._unary("hp_R_apply", X)
