@@ -265,6 +265,18 @@ def run_ours(args, rank, world):
         extra = {"time_to_map_eig_s": t_me, "newton_iterations": nst["iterations"],
                  "newton_cg_iterations": nst["cg_iterations"], "newton_converged": bool(nst["converged"]),
                  "lambda_1": float(lam[0]), "lambda_k": float(lam[-1])}
+        if w.nsamples:
+            # Laplace-approximation samples at the MAP (Section 4.3), normals drawn on the device
+            P.laplace_sample(m_map, lam, V, None, seed=w.seed, nsamples=min(w.nsamples, 64))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, post, sst = P.laplace_sample(m_map, lam, V, None, seed=w.seed + 1, nsamples=w.nsamples,
+                                            want_prior=True)
+            torch.cuda.synchronize()
+            t_s = time.perf_counter() - t0
+            extra["laplace_samples"] = {"n": w.nsamples, "seconds": t_s, "samples_per_s": w.nsamples / t_s,
+                                        "prior_solve_iterations": sst["iterations"]}
+            del post
         m_lin = m_map
     else:
         m_lin = m_true

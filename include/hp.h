@@ -209,15 +209,26 @@ int hp_newton_cg_map(hp_problem *P, double *m_dev_inout, const hp_newton_opts *o
 int hp_lowrank_eig(hp_problem *P, const double *m_map_dev, int k, int p, const double *Omega_dev,
                    int ldo, double *lambda_dev, double *V_dev, int ldv, int single_pass,
                    hp_solve_stats *st);
-/* Laplace-approximation samples (Section 4.3): for each column of eta
- * ((dim+1)*nelems normals), prior sample m_pr + x with x = A^{-1} C_M eta
- * (eq. (sample_prior)) and posterior sample m_map + x - V S V^T R x,
- * S = diag(1 - 1/sqrt(1+lambda)) (eq. (sample_post)).  prior_dev / post_dev:
- * n x nsamples, ld lds (either may be NULL). */
+/* Laplace-approximation samples (Section 4.3): for each sample j, prior sample
+ * m_pr + x with x = A^{-1} C_M eta_j (eq. (sample_prior)) and posterior sample
+ * m_map + x - V S V^T R x, S = diag(1 - 1/sqrt(1+lambda)) (eq. (sample_post)).
+ * eta_j ((dim+1)*nelems standard normals, element-major) is column j of eta_dev
+ * (ld ldeta) or, when eta_dev is NULL, drawn on the device from Philox4x32-10
+ * with the given seed (see hp_philox_normals; sample index j).  prior_dev /
+ * post_dev: n x nsamples, ld lds (either may be NULL). */
 int hp_laplace_sample(hp_problem *P, const double *m_map_dev, const double *lambda_dev,
                       const double *V_dev, int ldv, int k, const double *eta_dev, int ldeta,
-                      int nsamples, double *prior_dev, double *post_dev, int lds,
-                      hp_solve_stats *st);
+                      unsigned long long seed, int nsamples, double *prior_dev, double *post_dev,
+                      int lds, hp_solve_stats *st);
+
+/* Standard normals from Philox4x32-10 (Salmon et al., SC'11), as the sampler draws
+ * them: out[ld*j + t] is normal t of sample first_sample + j.  Call g = t/4 uses
+ * counter (g, g>>32, sample, sample>>32) and key (seed, seed>>32); its words
+ * (x0,x1), (x2,x3) give two FP32 Box-Muller pairs with u = ((x>>8) + 1/2) 2^-24.
+ * raw != 0 writes the 32-bit words themselves (as doubles).  DEVICE out,
+ * enqueued on stream (cudaStream_t; NULL = legacy) and synchronised. */
+int hp_philox_normals(unsigned long long seed, long long first_sample, int nsamples, int nper,
+                      double *out, int ld, int raw, void *stream);
 
 /* ---- measurement ---------------------------------------------------------- */
 

@@ -478,7 +478,7 @@ void hp_problem_destroy(hp_problem *P) {
   ScalarWS &S = P->sc;
   for (DBuf *b : {&S.iter, &S.rz, &S.pq, &S.rr, &S.bb, &S.alpha, &S.beta, &S.scale, &S.iscale, &S.tol2col, &S.tmp, &S.active, &S.partial, &S.counter})
     b->release();
-  for (DBuf *b : {&P->r64, &P->b64, &P->t64a, &P->t64b, &P->t64c, &P->obsbuf, &P->small}) b->release();
+  for (DBuf *b : {&P->r64, &P->b64, &P->t64a, &P->t64b, &P->t64c, &P->obsbuf, &P->small, &P->etabuf}) b->release();
   for (int i = 0; i < 6; ++i) P->vtmp[i].release();
   for (cudaEvent_t e : P->prof_ev) cudaEventDestroy(e);
   delete P;
@@ -851,18 +851,24 @@ int hp_lowrank_eig(hp_problem *P, const double *m_map, int k, int p, const doubl
 // Section 4.3: prior and Laplace-posterior samples
 // ---------------------------------------------------------------------------
 int hp_laplace_sample(hp_problem *P, const double *m_map, const double *lambda, const double *V, int ldv, int k,
-                      const double *eta, int ldeta, int nsamples, double *prior, double *post, int lds,
-                      hp_solve_stats *st) {
+                      const double *eta, int ldeta, unsigned long long seed, int nsamples, double *prior, double *post,
+                      int lds, hp_solve_stats *st) {
   if (P && nsamples == 0) return HP_OK;
-  if (!P || !eta || nsamples < 0 || ldeta < P->nelems * (P->dim + 1) || (!prior && !post) ||
+  if (!P || nsamples < 0 || (eta && ldeta < P->nelems * (P->dim + 1)) || (!prior && !post) ||
       ((prior || post) && lds < P->n))
     return set_error(HP_ERR_INVALID, "arguments");
   if (post && (!m_map || !lambda || !V || k < 0 || ldv < P->n)) return set_error(HP_ERR_INVALID, "posterior arguments");
   if (st) *st = hp_solve_stats{};
   int rc = 0;
   const long n = P->n, ld = padded(n);
-  const int chunk = std::min(nsamples, 128);
+  const int chunk = std::min(nsamples, eta ? 128 : 64);
   if (chunk == 0) return HP_OK;
+  const long nper = P->nelems * (P->dim + 1);
+  double *etag = nullptr;
+  if (!eta) {
+    HP_TRY(P->etabuf.ensure(sizeof(double) * (size_t)nper * chunk));
+    etag = P->etabuf.as<double>();
+  }
   double *W = col64(P->vtmp[0], P, chunk, &rc);
   HP_TRY(rc);
   double *X = col64(P->vtmp[1], P, chunk, &rc);
@@ -875,7 +881,12 @@ int hp_laplace_sample(hp_problem *P, const double *m_map, const double *lambda, 
   double *z = P->small.as<double>();
   for (int c0 = 0; c0 < nsamples; c0 += chunk) {
     const int cs = std::min(chunk, nsamples - c0);
-    launch_mass_factor(P, eta + (long)ldeta * c0, ldeta, W, ld, cs);
+    if (eta) {
+      launch_mass_factor(P, eta + (long)ldeta * c0, ldeta, W, ld, cs);
+    } else {
+      launch_philox_normals(seed, c0, cs, (int)nper, etag, nper, 0, P->st);
+      launch_mass_factor(P, etag, nper, W, ld, cs);
+    }
     HP_TRY(solve_block(P, OP_A, W, ld, X, ld, cs, P->rtol, st));
     if (prior) {
       k_add_vec_cols<<<dim3(blocks_for(n, cs), cs), NT, 0, P->st>>>(X, ld, P->m_prior, prior + (long)lds * c0, lds, n);

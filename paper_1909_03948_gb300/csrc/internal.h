@@ -111,7 +111,7 @@ struct hp_problem {
   hp::BlockWS<float> w32;
   hp::BlockWS<double> w64;
   hp::ScalarWS sc;
-  hp::DBuf r64, b64, t64a, t64b, t64c, obsbuf, small, vtmp[6];
+  hp::DBuf r64, b64, t64a, t64b, t64c, obsbuf, small, etabuf, vtmp[6];
 
   // optional CUDA-event timing of selected kernels (hp_profile_*)
   bool prof_on = false;
@@ -165,6 +165,10 @@ void launch_obs_gather(hp_problem *P, const double *X, long ldx, double *Yq, int
 void launch_obs_scatter(hp_problem *P, const double *Yq, double *X, long ldx, int s, double scale);
 void launch_mass_factor(hp_problem *P, const double *eta, long ldeta, double *W, long ldw, int s);
 void launch_zero_dirichlet(hp_problem *P, double *X, long ldx, int s);
+
+// ---- rng.cu ----------------------------------------------------------------
+void launch_philox_normals(unsigned long long seed, long long first, int nsamples, int nper, double *out, long ld,
+                           int raw, cudaStream_t st);
 template <typename T>
 void launch_stencil_apply(const hp_problem *P, const GridDesc &g, const Stencil<T> &S, const T *X, long ldx,
                           T *Y, long ldy, int s, cudaStream_t st);

@@ -103,7 +103,9 @@ _SIGS = {
     "hp_mass_factor_apply": (_I, [_P, _D, _I, _D, _I, _I]),
     "hp_newton_cg_map": (_I, [_P, _D, C.POINTER(NewtonOpts), C.POINTER(NewtonStats)]),
     "hp_lowrank_eig": (_I, [_P, _D, _I, _I, _D, _I, _D, _D, _I, _I, C.POINTER(SolveStats)]),
-    "hp_laplace_sample": (_I, [_P, _D, _D, _D, _I, _I, _D, _I, _I, _D, _D, _I, C.POINTER(SolveStats)]),
+    "hp_laplace_sample": (_I, [_P, _D, _D, _D, _I, _I, _D, _I, C.c_ulonglong, _I, _D, _D, _I,
+                               C.POINTER(SolveStats)]),
+    "hp_philox_normals": (_I, [C.c_ulonglong, C.c_longlong, _I, _I, _D, _I, _I, C.c_void_p]),
     "hp_profile_enable": (_I, [_P, _I]),
     "hp_profile_read": (_I, [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "hp_status_string": (C.c_char_p, [_I]),
@@ -373,17 +375,32 @@ class Problem:
                                     1 if single_pass else 0, C.byref(st)), "hp_lowrank_eig")
         return lam, V, st.as_dict()
 
-    def laplace_sample(self, m_map, lam, V, eta, want_prior=True, want_post=True):
+    def laplace_sample(self, m_map, lam, V, eta=None, want_prior=True, want_post=True, seed=0, nsamples=None):
+        """Prior and Laplace-posterior samples.  eta: (N, (dim+1)*nelems) normals, or None
+        to draw them on the device from Philox4x32-10 with `seed` (then give nsamples)."""
         ne = self.nelems * (self.dim + 1)
-        E2, N, _ = _block(eta, ne, "eta")
+        null = C.c_void_p(0)
+        if eta is not None:
+            E2, N, _ = _block(eta, ne, "eta")
+            eptr = _dptr(E2)
+        else:
+            N, eptr = int(nsamples), null
         k = 0 if V is None else V.shape[0]
         prior = torch.empty((N, self.n), dtype=torch.float64, device=self.device) if want_prior else None
         post = torch.empty((N, self.n), dtype=torch.float64, device=self.device) if want_post else None
         st = SolveStats()
-        null = C.c_void_p(0)
         _check(lib().hp_laplace_sample(
             self._h, _dptr(self._vec(m_map, "m_map")) if want_post else null,
             _dptr(lam) if want_post else null, _dptr(V) if want_post else null, self.n, k,
-            _dptr(E2), ne, N, _dptr(prior) if want_prior else null, _dptr(post) if want_post else null,
+            eptr, ne, seed, N, _dptr(prior) if want_prior else null, _dptr(post) if want_post else null,
             self.n, C.byref(st)), "hp_laplace_sample")
         return prior, post, st.as_dict()
+
+
+def philox_normals(seed: int, first_sample: int, nsamples: int, nper: int, raw: bool = False, device=None):
+    """(nsamples, nper) float64 tensor of the sampler's Philox normals (or raw 32-bit words)."""
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    out = torch.empty((nsamples, nper), dtype=torch.float64, device=dev)
+    _check(lib().hp_philox_normals(seed, first_sample, nsamples, nper, _dptr(out), nper, 1 if raw else 0, None),
+           "hp_philox_normals")
+    return out

@@ -177,3 +177,32 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(HPError):          # non-finite coefficient is reported, not propagated
         P.set_point(m)
     P.close()
+
+
+def test_philox_words_and_normals_match_oracle():
+    """The device generator and the oracle's numpy one are independent implementations of
+    the published Philox4x32-10: the 32-bit words agree exactly, the FP32 Box-Muller
+    normals to FP32 rounding of the transcendental functions."""
+    from oracle import philox
+    from paper_1909_03948_gb300 import philox_normals
+    raw = philox_normals(987654321, 5, 3, 1001, raw=True).cpu().numpy()
+    for j in range(3):
+        ref = philox.raw_words(987654321, 5 + j, (1001 + 3) // 4)[:1001].astype(np.float64)
+        assert np.array_equal(raw[j], ref)
+    z = philox_normals(42, 0, 2, 4096).cpu().numpy().T
+    zr = philox.normals(42, 0, 2, 4096)
+    assert np.max(np.abs(z - zr)) < 2e-5
+
+
+def test_samples_with_device_normals_match_oracle(small2d):
+    from oracle import philox
+    orc, w, P = small2d["orc"], small2d["w"], small2d["P"]
+    m_map = small2d["m_map"]
+    lam, V = A.lowrank_eig(orc, m_map, W.omega(w), w.k)
+    N = 5
+    pr, po, _ = P.laplace_sample(torch.tensor(m_map, device=DEV), torch.tensor(lam, device=DEV),
+                                 torch.tensor(np.ascontiguousarray(V.T), device=DEV), None, seed=77, nsamples=N)
+    eta = philox.normals(77, 0, N, orc.mesh.nelems * 3)
+    pr_ref, po_ref = A.laplace_samples(orc, m_map, lam, V, eta)
+    for a, b in ((pr.cpu().numpy().T, pr_ref), (po.cpu().numpy().T, po_ref)):
+        assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
