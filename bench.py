@@ -233,6 +233,19 @@ def traffic_record(fam, workload):
     return None
 
 
+def weak_scaling_value(t_local, units_per_rank, world, device="cpu"):
+    """Whole-job throughput for replicas on `world` ranks: every rank processes
+    units_per_rank units; the job takes the slowest rank's time (max over ranks)."""
+    t_max = float(t_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([t_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t)
+    return world * units_per_rank / t_max, t_max
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_1909_03948_gb300 import Problem, kernel_launches
@@ -323,12 +336,7 @@ def run_ours(args, rank, world):
         t_prof += e0.elapsed_time(e1) / 1e3
     prof = P.profile_read()
     P.profile_enable(False)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t)
-    value = world * args.steps * s / t_total
+    value, t_total = weak_scaling_value(t_total, args.steps * s, world, dev)
     # ---- e2e through the C ABI with host buffers ----
     Xh = torch.empty((s, P.n), dtype=torch.float64).pin_memory()
     Xh.copy_(Omega.cpu())
@@ -343,7 +351,7 @@ def run_ours(args, rank, world):
         P.hessian_apply(Xd, out=Y)
         Yh.copy_(Y, non_blocking=False)
         e2e_times.append(time.perf_counter() - ta)
-    e2e_val = world * args.steps * s / sum(e2e_times) if e2e_times else None
+    e2e_val = weak_scaling_value(sum(e2e_times), args.steps * s, world, dev)[0] if e2e_times else None
     # ---- roofline of the dominant level-0 kernel family ----
     fams = {k: v for k, v in prof.items() if k != "vcycle" and v[0] > 0}
     dom = max(fams, key=lambda k: fams[k][1]) if fams else None
