@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="medium2d", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--workload", default="medium2d", choices=sorted(W.WORKLOADS) + ["batch64"])
     ap.add_argument("--precision", default="fp32_ir", choices=["fp32_ir", "fp64"])
     ap.add_argument("--no-map", action="store_true", help="linearise at the true parameter instead of the MAP")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
@@ -397,6 +397,87 @@ def run_ours(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def synthetic_problem(w, dev, precision="fp32_ir"):
+    """GPU-side synthetic instance: truth = prior draw from the workload's normals,
+    data = B u(truth) + sigma xi with sigma = 1 % of max|u|."""
+    import torch
+    from paper_1909_03948_gb300 import Problem
+    dr = W.draws(w)
+    P = Problem(w.dim, w.N, w.gamma, w.delta, 1.0, dr.obs_xyz, precision=precision, rtol=1e-8)
+    eta = torch.tensor(dr.eta_true.reshape(1, -1), device=dev)
+    m_true = P.laplace_sample(None, None, None, eta, want_prior=True, want_post=False)[0][0].contiguous()
+    u_true, _ = P.forward(m_true)
+    sigma = w.noise_level * float(u_true.abs().max())
+    P.set_data(P.observe(u_true).cpu().numpy() + sigma * dr.xi_noise, sigma)
+    return P
+
+
+def run_batch(args, rank, world):
+    """64 uneven problems concurrently: MAP + k=30 eigenpairs for all, then one block of
+    k+p = 40 Hessian actions per problem at its MAP (the timed step)."""
+    import torch
+    from paper_1909_03948_gb300 import Batch, kernel_launches
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ws = W.batch_workloads(seed=W.SEED_BASE + 3 + 1000 * rank)
+    Ps = [synthetic_problem(w, dev, args.precision) for w in ws]
+    Om = [torch.tensor(np.ascontiguousarray(W.omega(w).T), device=dev) for w in ws]
+    B = Batch(Ps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ms, lams, Vs, nst = B.map_and_eig([P.zeros() for P in Ps], 30, 10, Om)
+    torch.cuda.synchronize()
+    t_me = time.perf_counter() - t0
+    B.set_point(ms)
+    for _ in range(max(args.warmup, 3)):
+        B.hessian_apply(Om)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    times = []
+    l0 = kernel_launches()
+    clocks = ClockSampler(torch.cuda.current_device())
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        B.hessian_apply(Om)            # returns after every problem's stream has finished
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    clk = clocks.stop()
+    launches = kernel_launches() - l0
+    units = sum(w.k + w.p for w in ws)
+    value, t_total = weak_scaling_value(sum(times), args.steps * units, world, dev)
+    # the same blocks one problem after another (no concurrency), for the per-problem rates
+    alone = []
+    for P, X in zip(Ps, Om):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        P.hessian_apply(X)
+        torch.cuda.synchronize()
+        alone.append(time.perf_counter() - a)
+    B.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "actions/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-in-f64-IR", "data": "synthetic",
+        "config": {"workload": f"batch64: {len(ws)} independent 2D problems, N log-uniform in [64, 512] "
+                               f"(multiples of 32), q in [100, 800], one block of k+p=40 GN Hessian actions per "
+                               f"problem at its MAP, problems concurrent on per-problem streams",
+                   "l2": "flushed (512 MB write) before every timed step"},
+        "gpu_launches": launches, "clocks": clk, "e2e": None, "roofline": None, "cpu_baseline": None,
+        "time_to_map_eig_s": t_me,
+        "map_eig_actions_per_s": sum(x["cg_iterations"] + 2 * 40 for x in nst) / t_me,
+        "sequential_seconds_per_step": sum(alone), "concurrency_speedup": sum(alone) / (t_total / args.steps),
+        "per_problem": [{"N": w.N, "q": w.nobs, "newton_iterations": x["iterations"], "alone_actions_per_s": 40 / a}
+                        for w, x, a in zip(ws, nst, alone)],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -409,7 +490,10 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    run_ours(args, rank, world)
+    if args.workload == "batch64":
+        run_batch(args, rank, world)
+    else:
+        run_ours(args, rank, world)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()

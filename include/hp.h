@@ -168,6 +168,31 @@ int hp_Rinv_apply(hp_problem *P, const double *X, int ldx, double *Y, int ldy, i
  * degree-2 element rule.  eta: (dim+1)*nelems normals per column, element-major. */
 int hp_mass_factor_apply(hp_problem *P, const double *eta, int ldeta, double *W, int ldw, int nsamples);
 
+/* ---- batches of independent problems ---------------------------------------
+ * Many independent inverse problems of uneven size on one GPU (the batched
+ * workload of the build; the paper treats one problem at a time).  Each problem
+ * gets its own non-blocking CUDA stream (set with hp_set_stream; restored to the
+ * legacy stream by hp_batch_destroy) and a pool of nthreads host threads (0 =
+ * min(hardware threads, 16)) drives the problems, so their kernel sequences
+ * run concurrently.  The problems stay owned by the caller.  Per-problem
+ * arrays are indexed by problem; status[i] receives each problem's return
+ * code and the call returns the first failure, else HP_OK.  Results equal
+ * those of the same calls made on each problem alone. */
+typedef struct hp_batch hp_batch;
+int hp_batch_create(hp_problem *const *problems, int nproblems, int nthreads, hp_batch **out);
+void hp_batch_destroy(hp_batch *B);
+/* hp_set_point on every problem (m[i]: device, n_i values). */
+int hp_batch_set_point(hp_batch *B, const double *const *m, int *status);
+/* hp_newton_cg_map then hp_lowrank_eig (Algorithms 1, 2, 4) on every problem:
+ * m_inout[i] (device, n_i) in: start, out: MAP point; Omega[i] n_i x (k+p), ld
+ * ldo[i]; lambda[i] (k) and V[i] (n_i x k, ld ldv[i]) out; nstats may be NULL. */
+int hp_batch_map_and_eig(hp_batch *B, double *const *m_inout, const hp_newton_opts *opts, int k, int p,
+                         const double *const *Omega, const int *ldo, double *const *lambda,
+                         double *const *V, const int *ldv, hp_newton_stats *nstats, int *status);
+/* hp_hessian_apply on every problem at its current point. */
+int hp_batch_hessian_apply(hp_batch *B, const double *const *X, const int *ldx, double *const *Y,
+                           const int *ldy, const int *nrhs, int flags, int *status);
+
 /* ---- solve without device allocation ---------------------------------------
  * The paper has no counterpart to this entry point: it serves callers that
  * cannot allocate device memory when they solve.  hp_mass_solve grows the

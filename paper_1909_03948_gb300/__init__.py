@@ -6,6 +6,6 @@ from ``csrc/`` by ``build.py``); ``hp`` is its ctypes binding.  Importing the
 package does not load the library; the first call does, and raises if it is
 missing.
 """
-from .hp import Problem, HPError, lib, kernel_launches, philox_normals, EXPORTED, LIB_PATH  # noqa: F401
+from .hp import Batch, Problem, HPError, lib, kernel_launches, philox_normals, EXPORTED, LIB_PATH  # noqa: F401
 
-__all__ = ["Problem", "HPError", "lib", "kernel_launches", "philox_normals", "EXPORTED", "LIB_PATH"]
+__all__ = ["Batch", "Problem", "HPError", "lib", "kernel_launches", "philox_normals", "EXPORTED", "LIB_PATH"]

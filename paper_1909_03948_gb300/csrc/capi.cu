@@ -374,7 +374,7 @@ const char *hp_status_string(int s) {
 }
 
 const char *hp_last_error(void) { return g_err.c_str(); }
-unsigned long long hp_kernel_launches(void) { return g_launches; }
+unsigned long long hp_kernel_launches(void) { return g_launches.load(); }
 
 int hp_problem_create(const hp_problem_desc *d, hp_problem **out) {
   if (!d || !out) return set_error(HP_ERR_INVALID, "null argument");

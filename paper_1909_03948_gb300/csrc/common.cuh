@@ -130,9 +130,13 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 // ---- host side --------------------------------------------------------------
+#include <atomic>
 namespace hp {
-extern unsigned long long g_launches;
-inline void count_launch(unsigned long long k = 1) { g_launches += k; }
+extern std::atomic<unsigned long long> g_launches;
+extern thread_local int tl_no_count;  // set while capturing graphs: launches count when the graph runs
+inline void count_launch(unsigned long long k = 1) {
+  if (!tl_no_count) g_launches.fetch_add(k, std::memory_order_relaxed);
+}
 constexpr int NT = 256;   // threads per block of the streaming kernels
 constexpr int NSM = 152;  // SMs of a GB300
 inline int blocks_for(long n, int s) {

@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -39,6 +40,7 @@ __constant__ int c_child3[6][8];
 // quadrature: barycentric coordinate of vertex k at point q (degree-2 rules)
 __constant__ double c_quad2[3][3] = {{0.5, 0.5, 0.0}, {0.0, 0.5, 0.5}, {0.5, 0.0, 0.5}};
 
+static std::mutex g_children_mutex;
 static int g_children_ready = 0;
 
 // The coarse simplex (cell C, perm pi) = {x in C : x_{pi_0} >= x_{pi_1} >= ...}
@@ -65,6 +67,7 @@ static void compute_children(int D, std::vector<std::vector<int>> &out) {
 }
 
 static int ensure_children() {
+  std::lock_guard<std::mutex> lock(g_children_mutex);
   if (g_children_ready) return 0;
   std::vector<std::vector<int>> c2, c3;
   compute_children(2, c2);

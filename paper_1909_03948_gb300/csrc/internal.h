@@ -58,6 +58,13 @@ template <typename T> struct BlockWS {
   DBuf lr[HP_MAXL], la[HP_MAXL], lb[HP_MAXL];  // MG level vectors (level 0 uses r/z and lb[0])
 };
 
+// a captured PCG loop (init + device-side while node), cached per configuration
+struct PcgGraph {
+  int op, tbytes, vw, s, maxit;
+  double tol;
+  cudaGraphExec_t exec;
+};
+
 struct ScalarWS {
   int scap = 0;
   DBuf rz, pq, rr, bb, alpha, beta, scale, iscale, tol2col, tmp;   // double per column
@@ -87,6 +94,7 @@ struct hp_problem {
   cudaStream_t st = nullptr;
   cudaStream_t cap = nullptr;   // private stream used to capture CUDA graphs
   bool use_graphs = true;       // inner PCG loops as graphs with a device-side while node
+  std::vector<hp::PcgGraph> graphs;
 
   hp::Level lv[HP_MAXL];
   hp::CoarseInv cK, cA;

@@ -865,22 +865,9 @@ static void pcg_body(hp_problem *P, OpKind op, int s, double tol2, cudaGraphCond
   count_launch(2);
 }
 
-struct PcgGraph {
-  int op, tbytes, vw, s, maxit;
-  double tol;
-  cudaGraphExec_t exec;
-};
-static std::vector<std::pair<hp_problem *, PcgGraph>> g_graphs;
-
 void drop_graphs(hp_problem *P) {
-  for (auto it = g_graphs.begin(); it != g_graphs.end();) {
-    if (it->first == P) {
-      cudaGraphExecDestroy(it->second.exec);
-      it = g_graphs.erase(it);
-    } else {
-      ++it;
-    }
-  }
+  for (auto &g : P->graphs) cudaGraphExecDestroy(g.exec);
+  P->graphs.clear();
 }
 
 // Captures init + a conditional WHILE node whose body is one PCG iteration.
@@ -891,13 +878,13 @@ static int build_graph(hp_problem *P, OpKind op, int s, double tol, int maxit, P
   const bool saved_prof = P->prof_on;
   P->prof_on = false;
   P->st = P->cap;
-  const unsigned long long l0 = g_launches;
+  tl_no_count = 1;
   cudaGraph_t g = nullptr;
   auto fail = [&](cudaError_t e, const char *w) {
     const int rc = cuda_check(e, w);
     P->st = saved;
     P->prof_on = saved_prof;
-    g_launches = l0;
+    tl_no_count = 0;
     if (g) cudaGraphDestroy(g);
     return rc;
   };
@@ -941,7 +928,7 @@ static int build_graph(hp_problem *P, OpKind op, int s, double tol, int maxit, P
   cudaGraphDestroy(g);
   P->st = saved;
   P->prof_on = saved_prof;
-  g_launches = l0;  // captured launches are counted when the graph runs
+  tl_no_count = 0;  // captured launches are counted when the graph runs
   *out = PcgGraph{(int)op, (int)sizeof(T), VW, s, maxit, tol, ex};
   return 0;
 }
@@ -960,15 +947,15 @@ static int pcg(hp_problem *P, OpKind op, int s, double rtol, int maxit, int *its
   int *h_it = P->sc.h_iter;
   if (P->use_graphs && !P->prof_on) {
     PcgGraph *G = nullptr;
-    for (auto &pg : g_graphs)
-      if (pg.first == P && pg.second.op == (int)op && pg.second.tbytes == (int)sizeof(T) && pg.second.vw == VW &&
-          pg.second.s == s && pg.second.maxit == maxit && pg.second.tol == rtol)
-        G = &pg.second;
+    for (auto &pg : P->graphs)
+      if (pg.op == (int)op && pg.tbytes == (int)sizeof(T) && pg.vw == VW && pg.s == s && pg.maxit == maxit &&
+          pg.tol == rtol)
+        G = &pg;
     if (!G) {
       PcgGraph ng;
       HP_TRY((build_graph<T, VW>(P, op, s, rtol, maxit, &ng)));
-      g_graphs.push_back({P, ng});
-      G = &g_graphs.back().second;
+      P->graphs.push_back(ng);
+      G = &P->graphs.back();
     }
     HP_CUDA(cudaGraphLaunch(G->exec, st));
     HP_CUDA(cudaMemcpyAsync(h_it, P->sc.iter.p, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -6,7 +6,8 @@
 
 namespace hp {
 
-unsigned long long g_launches = 0;
+std::atomic<unsigned long long> g_launches{0};
+thread_local int tl_no_count = 0;
 
 int DBuf::ensure(size_t b) {
   if (b <= bytes) return 0;

@@ -108,6 +108,15 @@ _SIGS = {
     "hp_philox_normals": (_I, [C.c_ulonglong, C.c_longlong, _I, _I, _D, _I, _I, C.c_void_p]),
     "hp_profile_enable": (_I, [_P, _I]),
     "hp_profile_read": (_I, [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "hp_batch_create": (_I, [C.POINTER(C.c_void_p), _I, _I, C.POINTER(C.c_void_p)]),
+    "hp_batch_destroy": (None, [C.c_void_p]),
+    "hp_batch_set_point": (_I, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int)]),
+    "hp_batch_map_and_eig": (_I, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(NewtonOpts), _I, _I,
+                                  C.POINTER(C.c_void_p), C.POINTER(C.c_int), C.POINTER(C.c_void_p),
+                                  C.POINTER(C.c_void_p), C.POINTER(C.c_int), C.POINTER(NewtonStats),
+                                  C.POINTER(C.c_int)]),
+    "hp_batch_hessian_apply": (_I, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int), C.POINTER(C.c_void_p),
+                                    C.POINTER(C.c_int), C.POINTER(C.c_int), _I, C.POINTER(C.c_int)]),
     "hp_status_string": (C.c_char_p, [_I]),
     "hp_last_error": (C.c_char_p, []),
     "hp_kernel_launches": (C.c_ulonglong, []),
@@ -404,3 +413,66 @@ def philox_normals(seed: int, first_sample: int, nsamples: int, nper: int, raw: 
     _check(lib().hp_philox_normals(seed, first_sample, nsamples, nper, _dptr(out), nper, 1 if raw else 0, None),
            "hp_philox_normals")
     return out
+
+
+def _ptrs(ts):
+    return (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+
+def _ints(v):
+    return (C.c_int * len(v))(*v)
+
+
+class Batch:
+    """Independent problems of uneven size run concurrently (one stream and one host
+    worker per problem at a time).  Problems stay owned by the caller."""
+
+    def __init__(self, problems, nthreads: int = 0):
+        self.problems = list(problems)
+        hs = (C.c_void_p * len(self.problems))(*[p._h.value for p in self.problems])
+        h = C.c_void_p()
+        _check(lib().hp_batch_create(hs, len(self.problems), nthreads, C.byref(h)), "hp_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _status(self, rc, st, where):
+        if rc != HP_OK:
+            bad = [i for i, v in enumerate(st) if v != HP_OK]
+            raise HPError(rc, where, f"problems {bad} failed with {[st[i] for i in bad]}")
+
+    def set_point(self, ms):
+        st = (C.c_int * len(self.problems))()
+        rc = lib().hp_batch_set_point(self._h, _ptrs([m.reshape(-1) for m in ms]), st)
+        self._status(rc, list(st), "hp_batch_set_point")
+
+    def map_and_eig(self, m0s, k, p, Omegas, rel_tol=1e-6, max_iter=50):
+        ms = [m.clone().reshape(-1) for m in m0s]
+        lams = [torch.zeros(k, dtype=torch.float64, device=m.device) for m in ms]
+        Vs = [torch.zeros((k, pr.n), dtype=torch.float64, device=m.device) for m, pr in zip(ms, self.problems)]
+        o = NewtonOpts(rel_tol, 0.0, max_iter, 10, 1e-4, 200)
+        nst = (NewtonStats * len(ms))()
+        st = (C.c_int * len(ms))()
+        ns = [pr.n for pr in self.problems]
+        rc = lib().hp_batch_map_and_eig(self._h, _ptrs(ms), C.byref(o), k, p, _ptrs(Omegas), _ints(ns), _ptrs(lams),
+                                        _ptrs(Vs), _ints(ns), nst, st)
+        self._status(rc, list(st), "hp_batch_map_and_eig")
+        return ms, lams, Vs, [x.as_dict() for x in nst]
+
+    def hessian_apply(self, Xs, with_prior=False):
+        Ys = [torch.empty_like(X) for X in Xs]
+        ns = [pr.n for pr in self.problems]
+        st = (C.c_int * len(Xs))()
+        rc = lib().hp_batch_hessian_apply(self._h, _ptrs(Xs), _ints(ns), _ptrs(Ys), _ints(ns),
+                                          _ints([X.shape[0] for X in Xs]), HP_WITH_PRIOR if with_prior else 0, st)
+        self._status(rc, list(st), "hp_batch_hessian_apply")
+        return Ys

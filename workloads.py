@@ -56,6 +56,21 @@ WORKLOADS = {
 }
 
 
+def batch_workloads(nprob: int = 64, seed: int = SEED_BASE + 3) -> list:
+    """Uneven batch: nprob independent 2D problems, N log-uniform in [64, 512] rounded to a
+    multiple of 32 (so that the multigrid hierarchy ends on a grid of at most 17^2
+    nodes), q uniform in {100..800}, gamma in [0.05, 0.2], delta in [0.2, 1.0], k=30, p=10."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(nprob):
+        N = int(np.clip(32 * np.round(np.exp(rng.uniform(np.log(64), np.log(512))) / 32), 64, 512))
+        q = int(rng.integers(100, 801))
+        gamma = float(rng.uniform(0.05, 0.2))
+        delta = float(rng.uniform(0.2, 1.0))
+        out.append(Workload(f"batch{i:02d}", 2, N, q, gamma, delta, 30, 10, seed=seed + 1000 + i))
+    return out
+
+
 def make_workload(dim: int, N: int, nobs: int, gamma: float = 0.1, delta: float = 0.5,
                   k: int = 10, p: int = 5, seed: int = SEED_BASE + 100) -> Workload:
     """Ad-hoc workload (test sizes)."""
