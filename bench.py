@@ -294,6 +294,8 @@ def run_ours(args, rank, world):
     else:
         m_lin = m_true
     P.set_point(m_lin)
+    from paper_1909_03948_gb300 import tuning
+    tune, tune_ms, tune_src = tuning.tuned(P, s, args.precision)
     Y = torch.empty_like(Omega)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -384,7 +386,8 @@ def run_ours(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32-in-f64-IR" if args.precision == "fp32_ir" else "f64",
         "data": "synthetic (seeded prior draw, pointwise observations with 1% noise)",
         "config": {"workload": workload_desc(w, args.precision), "block_columns": s,
-                   "l2": "flushed (512 MB write) before every timed step", "replicas": world},
+                   "l2": "flushed (512 MB write) before every timed step", "replicas": world,
+                   "tuning": {**tune, "source": tune_src}},
         "e2e": {"value": e2e_val, "unit": "actions/s", "h2d_bytes_per_step": s * P.n * 8,
                 "d2h_bytes_per_step": s * P.n * 8},
         "gpu_launches": launches,

@@ -255,6 +255,27 @@ int hp_laplace_sample(hp_problem *P, const double *m_map_dev, const double *lamb
 int hp_philox_normals(unsigned long long seed, long long first_sample, int nsamples, int nper,
                       double *out, int ld, int raw, void *stream);
 
+/* ---- tuning ----------------------------------------------------------------
+ * Knobs of the PDE solver (no counterpart in the paper): nu damped-Jacobi sweeps
+ * before and after each coarse correction and damping omega, the number of RHS
+ * columns solved together (0 = all), and the grid-size cap of the node kernels.
+ * Defaults: nu 2, omega 0.7, col_chunk 0, max_blocks 2048.  Every setting
+ * solves to the same tolerance; only speed changes. */
+typedef struct {
+  int nu;          /* 1..4 */
+  double omega;    /* (0, 1) */
+  int col_chunk;   /* >= 0 */
+  int max_blocks;  /* >= 64 */
+} hp_tuning;
+int hp_set_tuning(hp_problem *P, const hp_tuning *t);
+int hp_get_tuning(const hp_problem *P, hp_tuning *t);
+/* Times one block of nrhs Gauss-Newton Hessian actions at the current point
+ * (CUDA events, reps timed runs after a warm-up per candidate) over a small
+ * candidate set by coordinate descent (smoother, column chunk, grid cap) and
+ * applies the fastest.  best / best_ms (HOST, may be NULL) receive it.  Needs
+ * hp_set_point first; allocates its test block (setup-time call). */
+int hp_autotune(hp_problem *P, int nrhs, int reps, hp_tuning *best, double *best_ms);
+
 /* ---- measurement ---------------------------------------------------------- */
 
 /* Kernel families timed when profiling is on (CUDA events on the problem's

@@ -89,8 +89,10 @@ struct hp_problem {
   int max_iter = 500;
   double inner_rtol = 1e-5;     // FP32 inner tolerance of the refinement
   int max_outer = 12;
-  int nu = 2;                   // pre/post Jacobi sweeps
-  double omega = 0.7;           // Jacobi damping
+  int nu = 2;                   // pre/post Jacobi sweeps            (tuning)
+  double omega = 0.7;           // Jacobi damping                     (tuning)
+  int col_chunk = 0;            // RHS columns per solve, 0 = all     (tuning)
+  long max_blocks = 2048;       // grid cap of the node kernels       (tuning)
   cudaStream_t st = nullptr;
   cudaStream_t cap = nullptr;   // private stream used to capture CUDA graphs
   bool use_graphs = true;       // inner PCG loops as graphs with a device-side while node

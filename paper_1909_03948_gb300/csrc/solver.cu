@@ -553,7 +553,9 @@ template <> const double *coarse_inv<double>(const hp_problem *P, OpKind op) {
   return op == OP_K ? P->cK.inv64 : P->cA.inv64;
 }
 
-constexpr long kMaxBlocks = 2048;  // ~13 resident 128-thread blocks per SM on 152 SMs
+// grid-size cap of the node kernels (a tuning knob; default ~13 resident 128-thread blocks
+// per SM on 152 SMs), set per solve from the problem's tuning
+static thread_local long tl_max_blocks = 2048;
 
 // uncapped row grid (grid transfer kernels: one node per thread)
 static dim3 rowgrid(const GridDesc &g, int ngroups) {
@@ -561,10 +563,10 @@ static dim3 rowgrid(const GridDesc &g, int ngroups) {
   return dim3((g.np + 31) / 32, (unsigned)((nrows + NB / 32 - 1) / (NB / 32)), ngroups);
 }
 // row grid of the stencil kernels: warps loop over rows so that the grid stays near
-// kMaxBlocks (fewer per-block dot partials)
+// the grid-size cap (fewer per-block dot partials)
 static dim3 rowgrid_capped(const GridDesc &g, int ngroups) {
   dim3 d = rowgrid(g, ngroups);
-  const long cap = std::max<long>(1, kMaxBlocks / ((long)d.x * ngroups));
+  const long cap = std::max<long>(1, tl_max_blocks / ((long)d.x * ngroups));
   if ((long)d.y > cap) d.y = (unsigned)cap;
   return d;
 }
@@ -700,7 +702,7 @@ static Fin make_fin(hp_problem *P, int kind, double tol2 = 0.0, double *out = nu
 }
 
 static dim3 nodegrid(long n, int ng) {
-  const long b = std::min<long>((n + NB - 1) / NB, std::max<long>(1, kMaxBlocks / ng));
+  const long b = std::min<long>((n + NB - 1) / NB, std::max<long>(1, tl_max_blocks / ng));
   return dim3((unsigned)b, ng);
 }
 
@@ -1074,9 +1076,8 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
   return cuda_check(cudaGetLastError(), "ir_solve");
 }
 
-int solve_block(hp_problem *P, OpKind op, const double *B, long ldb, double *X, long ldx, int s, double rtol,
-                hp_solve_stats *st) {
-  if (s <= 0) return 0;
+static int solve_chunk(hp_problem *P, OpKind op, const double *B, long ldb, double *X, long ldx, int s, double rtol,
+                       hp_solve_stats *st) {
   HP_TRY(ensure_scalars(P, s));
   if (P->precision == HP_FP64_PLAIN) {
     HP_TRY(ensure_ws<double>(P, s));
@@ -1085,6 +1086,19 @@ int solve_block(hp_problem *P, OpKind op, const double *B, long ldb, double *X, 
   HP_TRY(ensure_ws<float>(P, s));
   if (s >= 2) return ir_solve<float, 4>(P, op, B, ldb, X, ldx, s, rtol, P->inner_rtol, st);
   return ir_solve<float, 1>(P, op, B, ldb, X, ldx, s, rtol, P->inner_rtol, st);
+}
+
+// Solves the s columns in chunks of the tuned width (0: all at once).
+int solve_block(hp_problem *P, OpKind op, const double *B, long ldb, double *X, long ldx, int s, double rtol,
+                hp_solve_stats *st) {
+  if (s <= 0) return 0;
+  tl_max_blocks = P->max_blocks;
+  const int w = (P->col_chunk > 0 && P->col_chunk < s) ? P->col_chunk : s;
+  for (int c0 = 0; c0 < s; c0 += w) {
+    const int cs = std::min(w, s - c0);
+    HP_TRY(solve_chunk(P, op, B + ldb * c0, ldb, X + ldx * c0, ldx, cs, rtol, st));
+  }
+  return 0;
 }
 
 }  // namespace hp

@@ -1,0 +1,130 @@
+// tune.cu -- solver tuning knobs and the autotuner.
+//
+// Knobs: Jacobi sweeps nu and damping omega of the V-cycle, the RHS column
+// chunk processed per solve (0 = all columns at once) and the grid-size cap of
+// the node kernels.  hp_autotune times one block of Gauss-Newton Hessian
+// actions at the current linearisation point (CUDA events on the problem's
+// stream) for each candidate, by coordinate descent over the three groups of
+// knobs, and keeps the fastest.  Every candidate solves to the same tolerance,
+// so tuning changes speed, not the stopping rule.
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+using namespace hp;
+
+extern "C" {
+
+int hp_set_tuning(hp_problem *P, const hp_tuning *t) {
+  if (!P || !t) return set_error(HP_ERR_INVALID, "hp_set_tuning: null");
+  if (t->nu < 1 || t->nu > 4 || !(t->omega > 0.0 && t->omega < 1.0) || t->col_chunk < 0 || t->max_blocks < 64 ||
+      t->max_blocks > (1 << 20))
+    return set_error(HP_ERR_INVALID, "hp_set_tuning: nu in [1,4], omega in (0,1), col_chunk >= 0, max_blocks >= 64");
+  HP_CUDA(cudaStreamSynchronize(P->st));
+  if (t->nu != P->nu || t->omega != P->omega || t->max_blocks != P->max_blocks) drop_graphs(P);
+  P->nu = t->nu;
+  P->omega = t->omega;
+  P->col_chunk = t->col_chunk;
+  P->max_blocks = t->max_blocks;
+  return HP_OK;
+}
+
+int hp_get_tuning(const hp_problem *P, hp_tuning *t) {
+  if (!P || !t) return set_error(HP_ERR_INVALID, "hp_get_tuning: null");
+  t->nu = P->nu;
+  t->omega = P->omega;
+  t->col_chunk = P->col_chunk;
+  t->max_blocks = (int)P->max_blocks;
+  return HP_OK;
+}
+
+int hp_autotune(hp_problem *P, int nrhs, int reps, hp_tuning *best, double *best_ms) {
+  if (!P || nrhs < 1 || reps < 1) return set_error(HP_ERR_INVALID, "hp_autotune: arguments");
+  if (!P->have_point) return set_error(HP_ERR_STATE, "hp_set_point must be called first");
+  const long n = P->n;
+  double *X = nullptr, *Y = nullptr;
+  HP_CUDA(cudaMalloc(&X, sizeof(double) * n * nrhs));
+  if (cudaMalloc(&Y, sizeof(double) * n * nrhs) != cudaSuccess) {
+    cudaFree(X);
+    return set_error(HP_ERR_NOMEM, "hp_autotune: workspace");
+  }
+  launch_philox_normals(0x7475ULL, 0, nrhs, (int)n, X, n, 0, P->st);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto cleanup = [&](int rc) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(X);
+    cudaFree(Y);
+    return rc;
+  };
+  auto time_it = [&](const hp_tuning &t, double *ms) -> int {
+    int rc = hp_set_tuning(P, &t);
+    if (rc) return rc;
+    rc = hp_hessian_apply(P, X, (int)n, Y, (int)n, nrhs, HP_MISFIT_ONLY, nullptr);  // warm: builds graphs
+    if (rc) return rc;
+    double acc = 0.0;
+    for (int r = 0; r < reps; ++r) {
+      cudaEventRecord(e0, P->st);
+      rc = hp_hessian_apply(P, X, (int)n, Y, (int)n, nrhs, HP_MISFIT_ONLY, nullptr);
+      if (rc) return rc;
+      cudaEventRecord(e1, P->st);
+      cudaEventSynchronize(e1);
+      float f = 0.f;
+      cudaEventElapsedTime(&f, e0, e1);
+      acc += f;
+    }
+    *ms = acc / reps;
+    return 0;
+  };
+  hp_tuning cur;
+  hp_get_tuning(P, &cur);
+  double cur_ms = 0.0;
+  int rc = time_it(cur, &cur_ms);
+  if (rc) return cleanup(rc);
+  struct Smooth {
+    int nu;
+    double omega;
+  };
+  const Smooth smooth[] = {{1, 0.8}, {2, 0.7}, {2, 0.8}, {3, 0.7}};
+  for (const Smooth &sm : smooth) {
+    hp_tuning t = cur;
+    t.nu = sm.nu;
+    t.omega = sm.omega;
+    double ms;
+    if ((rc = time_it(t, &ms))) return cleanup(rc);
+    if (ms < cur_ms) {
+      cur = t;
+      cur_ms = ms;
+    }
+  }
+  for (int w : {0, 32, 16}) {
+    if (w >= nrhs) continue;
+    hp_tuning t = cur;
+    t.col_chunk = w;
+    double ms;
+    if ((rc = time_it(t, &ms))) return cleanup(rc);
+    if (ms < cur_ms) {
+      cur = t;
+      cur_ms = ms;
+    }
+  }
+  for (int mb : {1024, 2048, 4096}) {
+    hp_tuning t = cur;
+    t.max_blocks = mb;
+    double ms;
+    if ((rc = time_it(t, &ms))) return cleanup(rc);
+    if (ms < cur_ms) {
+      cur = t;
+      cur_ms = ms;
+    }
+  }
+  if ((rc = hp_set_tuning(P, &cur))) return cleanup(rc);
+  if (best) *best = cur;
+  if (best_ms) *best_ms = cur_ms;
+  return cleanup(HP_OK);
+}
+
+}  // extern "C"

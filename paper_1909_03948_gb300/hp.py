@@ -55,6 +55,13 @@ class SolveStats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class Tuning(C.Structure):
+    _fields_ = [("nu", C.c_int), ("omega", C.c_double), ("col_chunk", C.c_int), ("max_blocks", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class NewtonOpts(C.Structure):
     _fields_ = [("rel_tol", C.c_double), ("abs_tol", C.c_double), ("max_iter", C.c_int),
                 ("max_backtrack", C.c_int), ("c_armijo", C.c_double), ("cg_max_iter", C.c_int)]
@@ -117,6 +124,9 @@ _SIGS = {
                                   C.POINTER(C.c_int)]),
     "hp_batch_hessian_apply": (_I, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int), C.POINTER(C.c_void_p),
                                     C.POINTER(C.c_int), C.POINTER(C.c_int), _I, C.POINTER(C.c_int)]),
+    "hp_set_tuning": (_I, [_P, C.POINTER(Tuning)]),
+    "hp_get_tuning": (_I, [_P, C.POINTER(Tuning)]),
+    "hp_autotune": (_I, [_P, _I, _I, C.POINTER(Tuning), C.POINTER(C.c_double)]),
     "hp_status_string": (C.c_char_p, [_I]),
     "hp_last_error": (C.c_char_p, []),
     "hp_kernel_launches": (C.c_ulonglong, []),
@@ -347,6 +357,23 @@ class Problem:
         W = torch.empty((s, self.n), dtype=torch.float64, device=self.device)
         _check(lib().hp_mass_factor_apply(self._h, _dptr(E2), ne, _dptr(W), self.n, s), "hp_mass_factor_apply")
         return W if eta.dim() == 2 else W[0]
+
+    # ---- tuning ------------------------------------------------------------------
+    def get_tuning(self):
+        t = Tuning()
+        _check(lib().hp_get_tuning(self._h, C.byref(t)), "hp_get_tuning")
+        return t.as_dict()
+
+    def set_tuning(self, nu=2, omega=0.7, col_chunk=0, max_blocks=2048):
+        t = Tuning(nu, omega, col_chunk, max_blocks)
+        _check(lib().hp_set_tuning(self._h, C.byref(t)), "hp_set_tuning")
+
+    def autotune(self, nrhs, reps=2):
+        """Runs the autotuner at the current point; returns (settings, ms per block)."""
+        t = Tuning()
+        ms = C.c_double()
+        _check(lib().hp_autotune(self._h, nrhs, reps, C.byref(t), C.byref(ms)), "hp_autotune")
+        return t.as_dict(), ms.value
 
     # ---- measurement -------------------------------------------------------------
     PROF_NAMES = ("matvec", "smooth", "resid_mg", "resid64", "cg_update", "vcycle", "presmooth")

@@ -206,3 +206,18 @@ def test_samples_with_device_normals_match_oracle(small2d):
     pr_ref, po_ref = A.laplace_samples(orc, m_map, lam, V, eta)
     for a, b in ((pr.cpu().numpy().T, pr_ref), (po.cpu().numpy().T, po_ref)):
         assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
+
+
+def test_autotune_keeps_results(small2d):
+    """The autotuner only changes speed: the Hessian block with the chosen settings equals
+    the default-settings result to the solve tolerance, and the settings are valid."""
+    orc, w, P = small2d["orc"], small2d["w"], small2d["P"]
+    m = small2d["m_map"]
+    P.set_point(torch.tensor(m, device=DEV))
+    X = torch.tensor(np.ascontiguousarray(W.random_block(orc.n, 8, 55).T), device=DEV)
+    Y0, _ = P.hessian_apply(X)
+    best, ms = P.autotune(8)
+    assert 1 <= best["nu"] <= 4 and 0 < best["omega"] < 1 and ms > 0
+    Y1, _ = P.hessian_apply(X)
+    assert float((Y1 - Y0).norm() / Y0.norm()) < 1e-7
+    P.set_tuning()  # back to the defaults for the other tests
