@@ -17,10 +17,19 @@ with 16, 32, 64 and 128 channels:
 
 3x3 convolutions are cross-correlations with zero padding and a bias; pooling is the
 2x2 mean; upsampling repeats each value on a 2x2 block; concatenation puts the
-upsampled channels first.  Loss of a batch of N samples, each weighted by the norm
-of its own masked target (a sample whose masked target is zero counts 0):
+upsampled channels first.
 
-    L = 1/(2N) sum_n |mask_n (y_n - t_n)|^2 / |mask_n t_n|^2
+Training loss: the relative residual of the guess in the stiffness system.  Each
+sample carries, on the grid (row iy, column ix), its right-hand side b and the
+symmetric 5-point stencil of K (diag, cx = coupling to the right neighbour, cy =
+coupling to the neighbour below) in aux = (b, diag, cx, cy); the free-node mask is
+input channel 2.  With S = mask K mask,
+
+    L = 1/(2N) sum_n |mask_n b_n - S_n y_n|^2 / |mask_n b_n|^2
+
+(a sample with a zero right-hand side counts 0).  On the free nodes of a P1 Kuhn
+triangulation K is exactly 5-point: the diagonal edge is opposite a right angle in
+both of its triangles, so its coupling vanishes.
 """
 from __future__ import annotations
 
@@ -122,13 +131,44 @@ def forward(params, x):
     return y, cache
 
 
-def loss(y, t, mask):
-    """Returns (L, dL/dy)."""
+def stencil_apply(v, aux, mask):
+    """mask * K (mask * v) for the grid stencil aux[:, 1:4] = (diag, cx, cy)."""
+    v = v * mask
+    d, cx, cy = aux[:, 1:2], aux[:, 2:3], aux[:, 3:4]
+    out = d * v
+    out[:, :, :, :-1] += cx[:, :, :, :-1] * v[:, :, :, 1:]
+    out[:, :, :, 1:] += cx[:, :, :, :-1] * v[:, :, :, :-1]
+    out[:, :, :-1, :] += cy[:, :, :-1, :] * v[:, :, 1:, :]
+    out[:, :, 1:, :] += cy[:, :, :-1, :] * v[:, :, :-1, :]
+    return out * mask
+
+
+def residual_loss(y, x, aux):
+    """Returns (L, dL/dy) for network output y, input x (mask = channel 2) and aux."""
     N = y.shape[0]
-    r = (y - t) * mask
-    tn = ((t * mask) ** 2).sum(axis=(1, 2, 3))
-    w = np.where(tn > 0, 1.0 / (N * np.where(tn > 0, tn, 1.0)), 0.0)[:, None, None, None]
-    return float(0.5 * (w * r * r).sum()), w * r * mask
+    mask = x[:, 2:3]
+    b = aux[:, 0:1] * mask
+    r = b - stencil_apply(y, aux, mask)
+    bn = (b * b).sum(axis=(1, 2, 3))
+    w = np.where(bn > 0, 1.0 / (N * np.where(bn > 0, bn, 1.0)), 0.0)[:, None, None, None]
+    # S is symmetric, so d/dy (1/2) w |b - S y|^2 = -S (w r)
+    return float(0.5 * (w * r * r).sum()), -stencil_apply(w * r, aux, mask)
+
+
+def stencil_channels(K, nper, H, W):
+    """(3, H, W) grid channels (diag, cx, cy) of a 2D nodal matrix K (node ix + nper iy at
+    row iy, column ix); couplings leave the grid as zero."""
+    K = K.tocsr()
+    out = np.zeros((3, H, W))
+    for iy in range(nper):
+        for ix in range(nper):
+            i = ix + nper * iy
+            out[0, iy, ix] = K[i, i]
+            if ix + 1 < nper:
+                out[1, iy, ix] = K[i, i + 1]
+            if iy + 1 < nper:
+                out[2, iy, ix] = K[i, i + nper]
+    return out
 
 
 def backward(params, cache, dy):

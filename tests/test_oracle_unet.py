@@ -1,12 +1,31 @@
 """Pins for oracle/unet.py: the 3x3 convolution against scipy's 2-D cross-correlation,
-pooling / upsampling as adjoint pairs, the loss against its closed forms, the whole
-network (forward and gradients) against the same architecture assembled from
-torch.nn.functional in FP64 with autograd, and the backward pass against central
-finite differences of the loss."""
+pooling / upsampling as adjoint pairs, the grid stencil against the assembled P1
+stiffness matrix (oracle/fem.py), the residual loss against its closed forms (zero at
+the exact solve), the whole network (forward and gradients) against the same
+architecture assembled from torch.nn.functional in FP64 with autograd and a dense
+stencil matrix, and the backward pass against central finite differences."""
 import numpy as np
+import scipy.sparse.linalg as spla
 from scipy import signal
 
 from oracle import unet
+from oracle.fem import Mesh
+
+
+def _real_stencil(N, H, W, seed):
+    """Grid channels of K(m) for a random m on an N x N mesh, and the free-node mask."""
+    mesh = Mesh(2, N)
+    m = np.random.default_rng(seed).standard_normal(mesh.n) * 0.5
+    K = mesh.stiffness(mesh.elem_mean(np.exp(m)))
+    free = np.zeros((H, W))
+    free[:N + 1, :N + 1] = (~mesh.dirichlet_mask).reshape(N + 1, N + 1)
+    return mesh, m, K, unet.stencil_channels(K, N + 1, H, W), free
+
+
+def _random_aux(rng, N, H, W):
+    aux = rng.standard_normal((N, 4, H, W))
+    aux[:, 1] = 4.0 + rng.uniform(size=(N, H, W))          # a diagonally dominant stencil
+    return aux
 
 
 def test_conv_equals_scipy_correlation():
@@ -30,22 +49,51 @@ def test_pool_up_are_adjoint_to_their_backward():
     assert np.isclose((unet.up(d) * u).sum(), (d * unet.up_backward(u)).sum())
 
 
-def test_loss_closed_forms():
-    rng = np.random.default_rng(4)
-    t = rng.standard_normal((3, 1, 8, 8))
-    t[2] = 0.0                                   # a zero target counts 0
-    mask = (rng.uniform(size=(3, 1, 8, 8)) > 0.3).astype(float)
-    # y = 0: every nonzero sample contributes exactly 1/(2N)
-    assert np.isclose(unet.loss(np.zeros_like(t), t, mask)[0], 0.5 * 2 / 3)
-    # y = 2t: the same (|y - t| = |t|); y = t: zero loss and gradient
-    assert np.isclose(unet.loss(2 * t, t, mask)[0], 0.5 * 2 / 3)
-    L0, d0 = unet.loss(t.copy(), t, mask)
-    assert L0 == 0.0 and not d0.any()
-    # invariant under a common scale of y and t, and blind to unmasked pixels
-    y = rng.standard_normal(t.shape)
-    assert np.isclose(unet.loss(7.0 * y, 7.0 * t, mask)[0], unet.loss(y, t, mask)[0])
-    y2 = y + 5.0 * (1 - mask)
-    assert np.isclose(unet.loss(y2, t, mask)[0], unet.loss(y, t, mask)[0])
+def test_stencil_is_the_assembled_stiffness_on_free_nodes():
+    N, H, W = 6, 8, 8
+    mesh, m, K, ch, free = _real_stencil(N, H, W, 0)
+    # K is exactly 5-point: rebuilding it from the channels loses nothing
+    nper = N + 1
+    Kd = K.toarray()
+    rows, cols = np.nonzero(np.abs(Kd) > 1e-13 * np.abs(Kd).max())
+    d = np.abs(rows - cols)
+    assert set(d.tolist()) <= {0, 1, nper}        # the diagonal-edge couplings cancel to rounding
+    v = np.random.default_rng(1).standard_normal((1, 1, H, W))
+    aux = np.concatenate([np.zeros((1, 1, H, W)), ch[None]], axis=1)
+    Sv = unet.stencil_apply(v, aux, free[None, None])
+    fv = free[:nper, :nper].ravel()
+    ref = fv * (K @ (fv * v[0, 0, :nper, :nper].ravel()))
+    assert np.allclose(Sv[0, 0, :nper, :nper].ravel(), ref, atol=1e-12)
+    assert not Sv[0, 0, nper:, :].any() and not Sv[0, 0, :, nper:].any()
+
+
+def test_residual_loss_closed_forms():
+    N, H, W = 6, 8, 8
+    mesh, m, K, ch, free = _real_stencil(N, H, W, 2)
+    rng = np.random.default_rng(3)
+    nper = N + 1
+    x = np.zeros((3, 3, H, W))
+    x[:, 2] = free
+    aux = np.zeros((3, 4, H, W))
+    aux[:, 1:] = ch
+    aux[:, 0] = rng.standard_normal((3, H, W))
+    aux[2, 0] = 0.0                                        # a zero right-hand side counts 0
+    # y = 0: each nonzero sample contributes 1/(2N)
+    assert np.isclose(unet.residual_loss(np.zeros((3, 1, H, W)), x, aux)[0], 0.5 * 2 / 3)
+    # y = the exact solve of K_ff y = b_f: zero loss
+    f = ~mesh.dirichlet_mask
+    y = np.zeros((3, 1, H, W))
+    Kff = K[f][:, f].tocsc()
+    for j in range(2):
+        yy = np.zeros(mesh.n)
+        yy[f] = spla.spsolve(Kff, aux[j, 0, :nper, :nper].ravel()[f])
+        y[j, 0, :nper, :nper] = yy.reshape(nper, nper)
+    assert unet.residual_loss(y, x, aux)[0] < 1e-24
+    # invariant under a common scale of y and b
+    y2 = rng.standard_normal((3, 1, H, W))
+    a2 = aux.copy()
+    a2[:, 0] *= 5.0
+    assert np.isclose(unet.residual_loss(5.0 * y2, x, a2)[0], unet.residual_loss(y2, x, aux)[0])
 
 
 def test_network_matches_torch_functional():
@@ -54,10 +102,10 @@ def test_network_matches_torch_functional():
     rng = np.random.default_rng(5)
     params = [(w, rng.standard_normal(b.shape) * 0.1) for w, b in unet.init_params(6)]
     x = rng.standard_normal((2, 3, 16, 24))
-    t = rng.standard_normal((2, 1, 16, 24))
-    mask = (rng.uniform(size=(2, 1, 16, 24)) > 0.25).astype(float)
+    x[:, 2] = (rng.uniform(size=(2, 16, 24)) > 0.25)
+    aux = _random_aux(rng, 2, 16, 24)
     y, cache = unet.forward(params, x)
-    L, dy = unet.loss(y, t, mask)
+    L, dy = unet.residual_loss(y, x, aux)
     grads = unet.backward(params, cache, dy)
 
     tp = [(torch.tensor(w, requires_grad=True), torch.tensor(b, requires_grad=True)) for w, b in params]
@@ -77,9 +125,26 @@ def test_network_matches_torch_functional():
     bt = block(F.avg_pool2d(s3, 2), "bota", "botb")
     d1 = dec(dec(dec(bt, s3, "dec3a", "dec3b"), s2, "dec2a", "dec2b"), s1, "dec1a", "dec1b")
     yt = F.conv2d(d1, *P["out"])
-    mt, tt = torch.tensor(mask), torch.tensor(t)
-    tn = ((tt * mt) ** 2).sum(dim=(1, 2, 3))
-    Lt = 0.5 * ((((yt - tt) * mt) ** 2).sum(dim=(1, 2, 3)) / tn).mean()
+    H, W = 16, 24
+
+    def dense_S(n):                      # mask K mask as a dense (HW x HW) matrix, built entry by entry
+        S = np.zeros((H * W, H * W))
+        for r in range(H):
+            for c in range(W):
+                i = r * W + c
+                S[i, i] = aux[n, 1, r, c]
+                if c + 1 < W:
+                    S[i, i + 1] = S[i + 1, i] = aux[n, 2, r, c]
+                if r + 1 < H:
+                    S[i, i + W] = S[i + W, i] = aux[n, 3, r, c]
+        mk = x[n, 2].ravel()
+        return torch.tensor(mk[:, None] * S * mk[None, :])
+
+    Lt = 0.0
+    for n in range(2):
+        b = torch.tensor(aux[n, 0].ravel() * x[n, 2].ravel())
+        r = b - dense_S(n) @ yt[n, 0].reshape(-1)
+        Lt = Lt + 0.5 * (r @ r) / (b @ b) / 2
     Lt.backward()
     assert np.allclose(y, yt.detach().numpy(), rtol=1e-12, atol=1e-12)
     assert np.isclose(L, Lt.item(), rtol=1e-12)
@@ -92,15 +157,15 @@ def test_backward_matches_finite_differences():
     rng = np.random.default_rng(2)
     params = unet.init_params(3)
     x = rng.standard_normal((2, 3, 16, 16))
-    t = rng.standard_normal((2, 1, 16, 16))
-    t[1] *= 3.0
-    mask = (rng.uniform(size=(2, 1, 16, 16)) > 0.2).astype(float)
+    x[:, 2] = (rng.uniform(size=(2, 16, 16)) > 0.2)
+    aux = _random_aux(rng, 2, 16, 16)
+    aux[1, 0] *= 3.0
 
     def L(ps):
-        return unet.loss(unet.forward(ps, x)[0], t, mask)[0]
+        return unet.residual_loss(unet.forward(ps, x)[0], x, aux)[0]
 
     y, cache = unet.forward(params, x)
-    _, dy = unet.loss(y, t, mask)
+    _, dy = unet.residual_loss(y, x, aux)
     grads = unet.backward(params, cache, dy)
     eps = 1e-6
     for li in [0, 3, 7, 8, 12, 14]:
