@@ -276,6 +276,75 @@ int hp_get_tuning(const hp_problem *P, hp_tuning *t);
  * hp_set_point first; allocates its test block (setup-time call). */
 int hp_autotune(hp_problem *P, int nrhs, int reps, hp_tuning *best, double *best_ms);
 
+/* ---- learned warm start (2D stiffness solves; no counterpart in the paper) --
+ * A 4-level U-Net (16-32-64-128 channels, 3x3 convolutions with zero padding,
+ * 2x2 mean pooling, nearest 2x upsampling, skip concatenation [upsampled, skip],
+ * ReLU, 1x1 output layer) on an H x W grid, H and W multiples of 8.  Weights are
+ * kept in FP32 (master copy, Adam) and used by every kernel as BF16; activations
+ * and accumulation are FP32.  All tensors are NCHW FP32, batch first.
+ * Parameters are packed layer by layer, each layer its weights (co, ci, k, k)
+ * then its biases (co), in the order enc1a 3->16, enc1b 16->16, enc2a 16->32,
+ * enc2b 32->32, enc3a 32->64, enc3b 64->64, bota 64->128, botb 128->128,
+ * dec3a 192->64, dec3b 64->64, dec2a 96->32, dec2b 32->32, dec1a 48->16,
+ * dec1b 16->16, out 16->1 (1x1).  A network is used by one thread at a time.
+ *
+ * Training loss: the relative residual of the output y in the sample's own
+ * stiffness system.  A sample is an input x (3,H,W), whose channel 2 is the 0/1
+ * mask of the free nodes, and loss data aux (4,H,W) = (b, diag, cx, cy): the
+ * right-hand side and the symmetric 5-point stencil of K on the grid (cx couples
+ * a pixel to its right neighbour, cy to the one below).  With S = mask K mask,
+ *   L = 1/(2N) sum_n |mask_n b_n - S_n y_n|^2 / |mask_n b_n|^2
+ * (a sample with a zero right-hand side counts 0). */
+typedef struct hp_unet hp_unet;
+/* batch_cap: largest N of a forward / gradient call.  Parameters start at zero:
+ * set them with hp_unet_set_params. */
+int hp_unet_create(int H, int W, int batch_cap, hp_unet **out);
+void hp_unet_destroy(hp_unet *U);
+long hp_unet_num_params(const hp_unet *U);
+/* HOST arrays of hp_unet_num_params floats.  set_params also rounds the weights
+ * to BF16 for the kernels and resets the Adam state. */
+int hp_unet_set_params(hp_unet *U, const float *params);
+int hp_unet_get_params(const hp_unet *U, float *params);
+/* y (N,1,H,W) = net(x (N,3,H,W)); DEVICE arrays, 1 <= N <= batch_cap; synchronous. */
+int hp_unet_forward(hp_unet *U, const float *x, int N, float *y);
+/* Loss (HOST double, may be NULL) and its gradient with respect to the packed
+ * parameters (HOST floats, may be NULL) for DEVICE x (N,3,H,W) and aux (N,4,H,W). */
+int hp_unet_loss_grad(hp_unet *U, const float *x, const float *aux, int N, double *loss, float *grad);
+/* Adam (beta 0.9, 0.999, eps 1e-8, step size lr) over `epochs` passes of the
+ * nsamples DEVICE samples X (nsamples,3,H,W), A (nsamples,4,H,W) in shuffled
+ * batches of `batch` (a trailing partial batch is skipped); the order comes from
+ * seed.  loss_per_epoch (HOST, epochs doubles, may be NULL) gets the mean batch
+ * loss of each epoch. */
+int hp_unet_train(hp_unet *U, const float *X, const float *A, int nsamples, int epochs, int batch, double lr,
+                  unsigned long long seed, double *loss_per_epoch);
+
+/* The network's view of a 2D problem: grid H = W = the node count per axis
+ * rounded up to a multiple of 8; node (ix, iy) sits at row iy, column ix.  For a
+ * solve K x = b (b zero on the Dirichlet faces iy = 0, N): z = D^-1 b with D the
+ * diagonal of K, c = |z| / sqrt(nfree) its RMS over the nfree free nodes.  Input
+ * channels: m; z / c; the 0/1 mask of the free nodes.  The output y is the
+ * solution in the same scaling, so the initial guess is x0 = c y on the free
+ * nodes, 0 elsewhere.  HP_ERR_INVALID for a 3D problem. */
+int hp_warmstart_grid(const hp_problem *P, int *H, int *W);
+/* Attaches a network (not owned; NULL detaches) of the problem's grid.  While
+ * attached and enabled, every stiffness solve (state, adjoint, incremental
+ * forward and adjoint) starts from the network's guess instead of zero; a
+ * column whose guess has a residual no smaller than |b| (or non-finite) starts
+ * from zero instead.  Every solve still runs to the same relative tolerance. */
+int hp_warmstart_attach(hp_problem *P, hp_unet *U);
+int hp_warmstart_enable(hp_problem *P, int on);
+/* Records the problem's stiffness solves as training samples: after each solve,
+ * column j appends its network input to X (capacity,3,H,W), its loss data
+ * (b / c, diag, cx, cy) of the current level-0 stiffness stencil to A
+ * (capacity,4,H,W) and, if T is not NULL, its solution x / c to T
+ * (capacity,1,H,W) (DEVICE arrays) until capacity is reached.  X = NULL stops
+ * recording (the count of the last recording stays readable); a new recording
+ * starts the count from zero. */
+int hp_warmstart_record(hp_problem *P, float *X, float *A, float *T, int capacity);
+/* Samples recorded, columns that started from a guess, columns that fell back
+ * to zero (HOST, each may be NULL); since attach / record. */
+int hp_warmstart_counts(const hp_problem *P, long long *recorded, long long *guesses, long long *fallbacks);
+
 /* ---- measurement ---------------------------------------------------------- */
 
 /* Kernel families timed when profiling is on (CUDA events on the problem's

@@ -4,8 +4,11 @@ Poisson inverse problem (hIPPYlib, Part I).
 The engine is the C-ABI library ``libhp.so`` (declared in include/hp.h, built
 from ``csrc/`` by ``build.py``); ``hp`` is its ctypes binding.  Importing the
 package does not load the library; the first call does, and raises if it is
-missing.
+missing.  ``warmstart`` generates training data for, and trains, the learned
+initial guess of the 2D stiffness solves (``UNet``).
 """
-from .hp import Batch, Problem, HPError, lib, kernel_launches, philox_normals, EXPORTED, LIB_PATH  # noqa: F401
+from .hp import (Batch, Problem, UNet, HPError, lib, kernel_launches, philox_normals,  # noqa: F401
+                 EXPORTED, LIB_PATH)
 
-__all__ = ["Batch", "Problem", "HPError", "lib", "kernel_launches", "philox_normals", "EXPORTED", "LIB_PATH"]
+__all__ = ["Batch", "Problem", "UNet", "HPError", "lib", "kernel_launches", "philox_normals", "EXPORTED",
+           "LIB_PATH"]

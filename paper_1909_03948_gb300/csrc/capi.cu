@@ -478,7 +478,9 @@ void hp_problem_destroy(hp_problem *P) {
   ScalarWS &S = P->sc;
   for (DBuf *b : {&S.iter, &S.rz, &S.pq, &S.rr, &S.bb, &S.alpha, &S.beta, &S.scale, &S.iscale, &S.tol2col, &S.tmp, &S.active, &S.partial, &S.counter})
     b->release();
-  for (DBuf *b : {&P->r64, &P->b64, &P->t64a, &P->t64b, &P->t64c, &P->obsbuf, &P->small, &P->etabuf}) b->release();
+  for (DBuf *b : {&P->r64, &P->b64, &P->t64a, &P->t64b, &P->t64c, &P->obsbuf, &P->small, &P->etabuf, &P->ws_flag,
+                  &P->ws_bb, &P->ws_z})
+    b->release();
   for (int i = 0; i < 6; ++i) P->vtmp[i].release();
   for (cudaEvent_t e : P->prof_ev) cudaEventDestroy(e);
   delete P;

@@ -131,6 +131,14 @@ struct hp_problem {
   bool prof_failed = false;            // graph-recorded event timing unavailable
   long prof_cnt[16] = {};              // harvested totals per family
   double prof_ms[16] = {};
+
+  // learned warm start of the stiffness solves (warm.cu)
+  hp_unet *ws_net = nullptr;
+  bool ws_on = false;
+  float *ws_rx = nullptr, *ws_ra = nullptr, *ws_rt = nullptr;  // recorder targets (caller's)
+  long ws_rcap = 0, ws_rcount = 0;
+  long long ws_guesses = 0, ws_fallbacks = 0;
+  hp::DBuf ws_flag, ws_bb, ws_z;
 };
 
 namespace hp {
@@ -193,6 +201,21 @@ void launch_ew_exp(const double *m, double *E, long n, cudaStream_t st);
 // per-column deterministic dots: out[j] = sum_i X_ij Y_ij (FP64)
 int block_dot(hp_problem *P, const double *X, long ldx, const double *Y, long ldy, long n, int s,
               double *out_dev);
+
+// ---- unet.cu / warm.cu -------------------------------------------------------
+float *unet_input(hp_unet *U);          // (cap,3,H,W) input buffer of the network
+const float *unet_output(const hp_unet *U);  // (cap,1,H,W) output of the last unet_run
+int unet_cap(const hp_unet *U);
+void unet_dims(const hp_unet *U, int *H, int *W);
+void unet_run(hp_unet *U, int N, cudaStream_t st);  // forward of the first N inputs, enqueued on st
+// Stiffness solves: X (n x s) = initial guesses for the Dirichlet-zeroed right-hand
+// sides B when a network is attached and enabled; returns 1 if X was written, 0 if not.
+int warm_guess(hp_problem *P, const double *B, long ldb, double *X, long ldx, int s);
+// Columns j with flag[j] != 0 restart from zero: X_j = 0, R_j = B_j.
+void warm_fallback(hp_problem *P, const int *flag_host, int s, const double *B, long ldb, double *X, long ldx,
+                   double *R, long ldr);
+// Appends the finished solves (B_j, X_j) to the recorder, if one is set.
+void warm_record(hp_problem *P, const double *B, long ldb, const double *X, long ldx, int s);
 
 // ---- solver.cu --------------------------------------------------------------
 int ensure_scalars(hp_problem *P, int s);

@@ -1018,10 +1018,16 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
   double *r64 = P->r64.as<double>(), *b64 = P->b64.as<double>();
   launch_copy(B, ldb, b64, ld64, n, s, st);
   if (op == OP_K) launch_zero_dirichlet(P, b64, ld64, s);
-  launch_fill(X, ldx, n, s, 0.0, st);
   HP_TRY(block_dot(P, b64, ld64, b64, ld64, n, s, P->sc.bb.as<double>()));
-  launch_copy(b64, ld64, r64, ld64, n, s, st);
-  HP_TRY(block_dot(P, r64, ld64, r64, ld64, n, s, P->sc.rr.as<double>()));
+  // start from the learned guess (stiffness solves with a network attached) or from zero
+  const bool warm = op == OP_K && warm_guess(P, b64, ld64, X, ldx, s);
+  if (warm) {
+    HP_TRY(residual64(P, op, b64, ld64, X, ldx, r64, ld64, s));
+  } else {
+    launch_fill(X, ldx, n, s, 0.0, st);
+    launch_copy(b64, ld64, r64, ld64, n, s, st);
+    HP_TRY(block_dot(P, r64, ld64, r64, ld64, n, s, P->sc.rr.as<double>()));
+  }
   double *hrr = P->sc.h_rr, *hbb = P->sc.h_bb;
   HP_CUDA(cudaMemcpyAsync(hbb, P->sc.bb.p, sizeof(double) * s, cudaMemcpyDeviceToHost, st));
   std::vector<double> hscale(s), hiscale(s), htol2(s);
@@ -1030,6 +1036,15 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
   for (outer = 0; outer <= P->max_outer; ++outer) {
     HP_CUDA(cudaMemcpyAsync(hrr, P->sc.rr.p, sizeof(double) * s, cudaMemcpyDeviceToHost, st));
     HP_CUDA(cudaStreamSynchronize(st));
+    if (warm && outer == 0) {
+      // a guess whose residual is no smaller than |b| (or non-finite) is dropped for zero
+      std::vector<int> flag(s);
+      for (int j = 0; j < s; ++j) {
+        flag[j] = hbb[j] > 0.0 && !(hrr[j] < hbb[j]);
+        if (flag[j]) hrr[j] = hbb[j];
+      }
+      warm_fallback(P, flag.data(), s, b64, ld64, X, ldx, r64, ld64);
+    }
     int nact = 0;
     worst = 0.0;
     for (int j = 0; j < s; ++j) {
@@ -1073,6 +1088,7 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
     stats->rel_res = std::max(stats->rel_res, worst);
   }
   if (rc) return set_error(rc, "PDE solve did not reach the requested tolerance");
+  if (op == OP_K) warm_record(P, b64, ld64, X, ldx, s);
   return cuda_check(cudaGetLastError(), "ir_solve");
 }
 

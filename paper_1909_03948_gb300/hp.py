@@ -127,6 +127,20 @@ _SIGS = {
     "hp_set_tuning": (_I, [_P, C.POINTER(Tuning)]),
     "hp_get_tuning": (_I, [_P, C.POINTER(Tuning)]),
     "hp_autotune": (_I, [_P, _I, _I, C.POINTER(Tuning), C.POINTER(C.c_double)]),
+    "hp_unet_create": (_I, [_I, _I, _I, C.POINTER(C.c_void_p)]),
+    "hp_unet_destroy": (None, [C.c_void_p]),
+    "hp_unet_num_params": (C.c_long, [C.c_void_p]),
+    "hp_unet_set_params": (_I, [C.c_void_p, C.POINTER(C.c_float)]),
+    "hp_unet_get_params": (_I, [C.c_void_p, C.POINTER(C.c_float)]),
+    "hp_unet_forward": (_I, [C.c_void_p, _D, _I, _D]),
+    "hp_unet_loss_grad": (_I, [C.c_void_p, _D, _D, _I, C.POINTER(C.c_double), C.POINTER(C.c_float)]),
+    "hp_unet_train": (_I, [C.c_void_p, _D, _D, _I, _I, _I, C.c_double, C.c_ulonglong, C.POINTER(C.c_double)]),
+    "hp_warmstart_grid": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "hp_warmstart_attach": (_I, [_P, C.c_void_p]),
+    "hp_warmstart_enable": (_I, [_P, _I]),
+    "hp_warmstart_record": (_I, [_P, _D, _D, _D, _I]),
+    "hp_warmstart_counts": (_I, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                 C.POINTER(C.c_longlong)]),
     "hp_status_string": (C.c_char_p, [_I]),
     "hp_last_error": (C.c_char_p, []),
     "hp_kernel_launches": (C.c_ulonglong, []),
@@ -290,6 +304,45 @@ class Problem:
         _check(lib().hp_gradient(self._h, _dptr(m), _dptr(g), J), "hp_gradient")
         return g, tuple(J)
 
+    # ---- learned warm start (2D) ------------------------------------------------
+    def warmstart_grid(self):
+        H, W = C.c_int(), C.c_int()
+        _check(lib().hp_warmstart_grid(self._h, C.byref(H), C.byref(W)), "hp_warmstart_grid")
+        return H.value, W.value
+
+    def warmstart_attach(self, net):
+        """Start every stiffness solve from `net`'s guess (None detaches)."""
+        _check(lib().hp_warmstart_attach(self._h, net._h if net is not None else None), "hp_warmstart_attach")
+        self._ws_net = net   # keeps the network alive while attached
+
+    def warmstart_enable(self, on: bool = True):
+        _check(lib().hp_warmstart_enable(self._h, 1 if on else 0), "hp_warmstart_enable")
+
+    def warmstart_record(self, X=None, A=None, T=None):
+        """Record the following stiffness solves: inputs into X (cap,3,H,W), loss data into
+        A (cap,4,H,W), solutions (optional) into T (cap,1,H,W), CUDA float32; no arguments
+        stops recording."""
+        if X is None:
+            _check(lib().hp_warmstart_record(self._h, None, None, None, 0), "hp_warmstart_record")
+            self._ws_rec = None
+            return
+        H, W = self.warmstart_grid()
+        cap = X.shape[0]
+        for t, c, nm in ((X, 3, "X"), (A, 4, "A"), (T, 1, "T")):
+            if nm == "T" and t is None:
+                continue
+            if (not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous()
+                    or tuple(t.shape) != (cap, c, H, W)):
+                raise ValueError(f"{nm}: expected a contiguous CUDA float32 tensor of shape {(cap, c, H, W)}")
+        _check(lib().hp_warmstart_record(self._h, _dptr(X), _dptr(A), _dptr(T) if T is not None else None, cap),
+               "hp_warmstart_record")
+        self._ws_rec = (X, A, T)
+
+    def warmstart_counts(self):
+        r, g, f = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        _check(lib().hp_warmstart_counts(self._h, C.byref(r), C.byref(g), C.byref(f)), "hp_warmstart_counts")
+        return {"recorded": r.value, "guesses": g.value, "fallbacks": f.value}
+
     # ---- Hessian / operators --------------------------------------------------
     def hessian_apply(self, X, with_prior: bool = False, out=None):
         X2, s, n = _block(X, self.n, "X")
@@ -440,6 +493,69 @@ def philox_normals(seed: int, first_sample: int, nsamples: int, nper: int, raw: 
     _check(lib().hp_philox_normals(seed, first_sample, nsamples, nper, _dptr(out), nper, 1 if raw else 0, None),
            "hp_philox_normals")
     return out
+
+
+class UNet:
+    """The warm-start network (owns an hp_unet handle).  Parameters travel as one
+    packed float32 numpy vector (per layer: weights (co, ci, k, k), then biases)."""
+
+    def __init__(self, H: int, W: int, batch_cap: int = 16):
+        h = C.c_void_p()
+        _check(lib().hp_unet_create(H, W, batch_cap, C.byref(h)), "hp_unet_create")
+        self._h, self.H, self.W, self.cap = h, H, W, batch_cap
+        self.nparam = int(lib().hp_unet_num_params(h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().hp_unet_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        if p.size != self.nparam:
+            raise ValueError(f"expected {self.nparam} parameters, got {p.size}")
+        _check(lib().hp_unet_set_params(self._h, p.ctypes.data_as(C.POINTER(C.c_float))), "hp_unet_set_params")
+
+    def get_params(self):
+        p = np.empty(self.nparam, dtype=np.float32)
+        _check(lib().hp_unet_get_params(self._h, p.ctypes.data_as(C.POINTER(C.c_float))), "hp_unet_get_params")
+        return p
+
+    def _chk(self, t, c, name, N=None):
+        if (not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous()
+                or t.dim() != 4 or tuple(t.shape[1:]) != (c, self.H, self.W) or (N is not None and t.shape[0] != N)):
+            raise ValueError(f"{name}: expected a contiguous CUDA float32 tensor (N, {c}, {self.H}, {self.W})")
+        return t.shape[0]
+
+    def forward(self, x):
+        N = self._chk(x, 3, "x")
+        y = torch.empty((N, 1, self.H, self.W), dtype=torch.float32, device=x.device)
+        _check(lib().hp_unet_forward(self._h, _dptr(x), N, _dptr(y)), "hp_unet_forward")
+        return y
+
+    def loss_grad(self, x, aux):
+        """(loss, packed gradient) of the relative-residual loss for x (N,3,H,W), aux (N,4,H,W)."""
+        N = self._chk(x, 3, "x")
+        self._chk(aux, 4, "aux", N)
+        L = C.c_double()
+        g = np.empty(self.nparam, dtype=np.float32)
+        _check(lib().hp_unet_loss_grad(self._h, _dptr(x), _dptr(aux), N, C.byref(L),
+                                       g.ctypes.data_as(C.POINTER(C.c_float))), "hp_unet_loss_grad")
+        return L.value, g
+
+    def train(self, X, A, epochs: int, batch: int, lr: float = 1e-3, seed: int = 0):
+        ns = self._chk(X, 3, "X")
+        self._chk(A, 4, "A", ns)
+        losses = np.zeros(epochs)
+        _check(lib().hp_unet_train(self._h, _dptr(X), _dptr(A), ns, epochs, batch, lr, seed,
+                                   losses.ctypes.data_as(C.POINTER(C.c_double))), "hp_unet_train")
+        return losses
 
 
 def _ptrs(ts):
