@@ -361,6 +361,18 @@ int hp_profile_enable(hp_problem *P, int on);
  * iteration is headed by a short bounded clock-spin kernel, so the iteration's
  * kernels run back to back and each event pair times its kernel alone. */
 int hp_profile_read(hp_problem *P, int nids, int *counts, double *total_ms);
+/* Replays one level-0 kernel of the last FP32 block solve on its live workspace
+ * (same columns, launch configuration and tuning), reps times back to back on the
+ * problem's stream, with CUDA events around the burst: family 0 damped-Jacobi
+ * sweep, 1 V-cycle residual, 2 fused two-sweep pre-smoothing.  The kernels read
+ * the workspace and write a scratch level vector, so the solver state is kept.
+ * us_warm (HOST, may be NULL): mean microseconds per launch back to back (data
+ * largely L2-resident).  us_cold (HOST, may be NULL): each launch preceded by a
+ * read of the DEVICE buffer `flush` (>= 64 MB; pass one larger than L2), minus
+ * the same reads timed alone -- the launch with its data in HBM.  Needs a prior
+ * FP32 solve with at least 4 columns on a multilevel hierarchy (HP_ERR_STATE). */
+int hp_replay_kernel(hp_problem *P, int family, int reps, void *flush, size_t flush_bytes, double *us_warm,
+                     double *us_cold);
 
 /* ---- status --------------------------------------------------------------- */
 const char *hp_status_string(int status);

@@ -1118,3 +1118,84 @@ int solve_block(hp_problem *P, OpKind op, const double *B, long ldb, double *X, 
 }
 
 }  // namespace hp
+
+// ---------------------------------------------------------------------------
+// kernel replay for the roofline (hp_replay_kernel)
+// ---------------------------------------------------------------------------
+namespace hp {
+
+// reads a buffer larger than L2 so that the next kernel finds its data in HBM
+__global__ void k_flush_read(const float4 *__restrict__ a, long n4, float *__restrict__ sink) {
+  float acc = 0.f;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n4; i += (long)gridDim.x * blockDim.x) {
+    const float4 v = a[i];
+    acc += v.x + v.y + v.z + v.w;
+  }
+  if (acc == -1.2345e30f) *sink = acc;  // keeps the loads; never taken for finite data
+}
+
+}  // namespace hp
+
+extern "C" int hp_replay_kernel(hp_problem *P, int family, int reps, void *flush, size_t flush_bytes,
+                                double *us_warm, double *us_cold) {
+  using namespace hp;
+  if (!P || reps < 1 || family < 0 || family > 2 || (us_cold && (!flush || flush_bytes < (64u << 20))))
+    return set_error(HP_ERR_INVALID, "hp_replay_kernel: family 0..2, reps >= 1, flush buffer >= 64 MB");
+  BlockWS<float> &W = P->w32;
+  if (W.scap < 4 || P->L < 2 || !P->have_point)
+    return set_error(HP_ERR_STATE, "hp_replay_kernel: needs an FP32 multi-column solve at a point first");
+  const int s = W.scap, VW = 4;
+  const long gs = W.ldn * VW;
+  tl_max_blocks = P->max_blocks;
+  const GridDesc &g = P->lv[0].g;
+  const Stencil<float> &S = P->lv[0].K32;
+  const float om = (float)P->omega;
+  float *z = W.z.as<float>(), *r = W.r.as<float>(), *y = W.lb[0].as<float>();
+  auto launch = [&]() {
+    if (family == 0)
+      st_launch<float, 4, M_JACOBI>(g, S, z, gs, r, gs, y, gs, s, om, Fin{}, P->st);
+    else if (family == 1)
+      st_launch<float, 4, M_RESID>(g, S, z, gs, r, gs, y, gs, s, om, Fin{}, P->st);
+    else
+      st_launch<float, 4, M_JAC2>(g, S, r, gs, nullptr, 0, y, gs, s, om, Fin{}, P->st);
+  };
+  const long n4 = (long)(flush_bytes / sizeof(float4));
+  HP_TRY(P->sc.tmp.ensure(64));
+  float *sink = P->sc.tmp.as<float>();
+  auto flush_read = [&]() {
+    k_flush_read<<<4 * 152, 512, 0, P->st>>>(reinterpret_cast<const float4 *>(flush), n4, sink);
+    count_launch();
+  };
+  cudaEvent_t e[6];
+  for (auto &x : e) HP_CUDA(cudaEventCreate(&x));
+  launch();  // warm-up
+  cudaEventRecord(e[0], P->st);
+  for (int k = 0; k < reps; ++k) launch();
+  cudaEventRecord(e[1], P->st);
+  if (us_cold) {
+    cudaEventRecord(e[2], P->st);
+    for (int k = 0; k < reps; ++k) {
+      flush_read();
+      launch();
+    }
+    cudaEventRecord(e[3], P->st);
+    cudaEventRecord(e[4], P->st);
+    for (int k = 0; k < reps; ++k) flush_read();
+    cudaEventRecord(e[5], P->st);
+  }
+  const int rc = cuda_check(cudaEventSynchronize(us_cold ? e[5] : e[1]), "hp_replay_kernel");
+  float t01 = 0.f, t23 = 0.f, t45 = 0.f;
+  if (!rc) {
+    cudaEventElapsedTime(&t01, e[0], e[1]);
+    if (us_cold) {
+      cudaEventElapsedTime(&t23, e[2], e[3]);
+      cudaEventElapsedTime(&t45, e[4], e[5]);
+    }
+  }
+  for (auto &x : e) cudaEventDestroy(x);
+  if (rc) return rc;
+  if (us_warm) *us_warm = 1e3 * t01 / reps;
+  if (us_cold) *us_cold = 1e3 * (t23 - t45) / reps;
+  return HP_OK;
+}
+

@@ -115,6 +115,7 @@ _SIGS = {
     "hp_philox_normals": (_I, [C.c_ulonglong, C.c_longlong, _I, _I, _D, _I, _I, C.c_void_p]),
     "hp_profile_enable": (_I, [_P, _I]),
     "hp_profile_read": (_I, [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "hp_replay_kernel": (_I, [_P, _I, _I, C.c_void_p, C.c_size_t, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "hp_batch_create": (_I, [C.POINTER(C.c_void_p), _I, _I, C.POINTER(C.c_void_p)]),
     "hp_batch_destroy": (None, [C.c_void_p]),
     "hp_batch_set_point": (_I, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int)]),
@@ -440,6 +441,21 @@ class Problem:
         ms = (C.c_double * k)()
         _check(lib().hp_profile_read(self._h, k, cnt, ms), "hp_profile_read")
         return {name: (cnt[i], ms[i]) for i, name in enumerate(self.PROF_NAMES)}
+
+    REPLAY_FAMILIES = ("smooth", "resid_mg", "presmooth")
+
+    def replay_kernel(self, family: str, reps: int, flush=None):
+        """(us per launch back to back, us per launch from HBM or None) of a level-0
+        kernel of the last FP32 block solve, replayed on its live workspace; `flush` is a
+        CUDA tensor larger than L2 read before each cold launch."""
+        w, c = C.c_double(), C.c_double()
+        fam = self.REPLAY_FAMILIES.index(family)
+        if flush is not None:
+            _check(lib().hp_replay_kernel(self._h, fam, reps, _dptr(flush), flush.numel() * flush.element_size(),
+                                          C.byref(w), C.byref(c)), "hp_replay_kernel")
+            return w.value, c.value
+        _check(lib().hp_replay_kernel(self._h, fam, reps, None, 0, C.byref(w), None), "hp_replay_kernel")
+        return w.value, None
 
     # ---- algorithms --------------------------------------------------------------
     def newton_cg_map(self, m0=None, rel_tol=1e-6, abs_tol=0.0, max_iter=50, max_backtrack=10,
