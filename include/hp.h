@@ -259,13 +259,18 @@ int hp_philox_normals(unsigned long long seed, long long first_sample, int nsamp
  * Knobs of the PDE solver (no counterpart in the paper): nu damped-Jacobi sweeps
  * before and after each coarse correction and damping omega, the number of RHS
  * columns solved together (0 = all), and the grid-size cap of the node kernels.
- * Defaults: nu 2, omega 0.7, col_chunk 0, max_blocks 2048.  Every setting
- * solves to the same tolerance; only speed changes. */
+ * Defaults: nu 2, omega 0.7, col_chunk 0, max_blocks 2048, fuse_from 0.  Every
+ * setting solves to the same tolerance; only speed changes. */
 typedef struct {
   int nu;          /* 1..4 */
   double omega;    /* (0, 1) */
   int col_chunk;   /* >= 0 */
   int max_blocks;  /* >= 64 */
+  int fuse_from;   /* 0 = off, else the first multigrid level (>= 1) whose whole
+                      coarse tail of the V-cycle runs as one launch: one thread-block
+                      cluster of 8 CTAs per column group, steps separated by the
+                      hardware cluster barrier (ignored when fewer than 2 levels
+                      remain below it) */
 } hp_tuning;
 int hp_set_tuning(hp_problem *P, const hp_tuning *t);
 int hp_get_tuning(const hp_problem *P, hp_tuning *t);

@@ -93,6 +93,7 @@ struct hp_problem {
   double omega = 0.7;           // Jacobi damping                     (tuning)
   int col_chunk = 0;            // RHS columns per solve, 0 = all     (tuning)
   long max_blocks = 2048;       // grid cap of the node kernels       (tuning)
+  int fuse_from = 0;            // first multigrid level of the fused coarse tail, 0 = none (tuning)
   cudaStream_t st = nullptr;
   cudaStream_t cap = nullptr;   // private stream used to capture CUDA graphs
   bool use_graphs = true;       // inner PCG loops as graphs with a device-side while node

@@ -1,10 +1,11 @@
 // tune.cu -- solver tuning knobs and the autotuner.
 //
 // Knobs: Jacobi sweeps nu and damping omega of the V-cycle, the RHS column
-// chunk processed per solve (0 = all columns at once) and the grid-size cap of
-// the node kernels.  hp_autotune times one block of Gauss-Newton Hessian
+// chunk processed per solve (0 = all columns at once), the level from which the
+// coarse tail of the V-cycle runs as one cluster launch, and the grid-size cap
+// of the node kernels.  hp_autotune times one block of Gauss-Newton Hessian
 // actions at the current linearisation point (CUDA events on the problem's
-// stream) for each candidate, by coordinate descent over the three groups of
+// stream) for each candidate, by coordinate descent over the four groups of
 // knobs, and keeps the fastest.  Every candidate solves to the same tolerance,
 // so tuning changes speed, not the stopping rule.
 #include <algorithm>
@@ -19,10 +20,13 @@ extern "C" {
 int hp_set_tuning(hp_problem *P, const hp_tuning *t) {
   if (!P || !t) return set_error(HP_ERR_INVALID, "hp_set_tuning: null");
   if (t->nu < 1 || t->nu > 4 || !(t->omega > 0.0 && t->omega < 1.0) || t->col_chunk < 0 || t->max_blocks < 64 ||
-      t->max_blocks > (1 << 20))
-    return set_error(HP_ERR_INVALID, "hp_set_tuning: nu in [1,4], omega in (0,1), col_chunk >= 0, max_blocks >= 64");
+      t->max_blocks > (1 << 20) || t->fuse_from < 0 || t->fuse_from >= HP_MAXL)
+    return set_error(HP_ERR_INVALID, "hp_set_tuning: nu in [1,4], omega in (0,1), col_chunk >= 0, max_blocks >= 64, "
+                                     "fuse_from in [0, 15]");
   HP_CUDA(cudaStreamSynchronize(P->st));
-  if (t->nu != P->nu || t->omega != P->omega || t->max_blocks != P->max_blocks) drop_graphs(P);
+  if (t->nu != P->nu || t->omega != P->omega || t->max_blocks != P->max_blocks || t->fuse_from != P->fuse_from)
+    drop_graphs(P);
+  P->fuse_from = t->fuse_from;
   P->nu = t->nu;
   P->omega = t->omega;
   P->col_chunk = t->col_chunk;
@@ -36,6 +40,7 @@ int hp_get_tuning(const hp_problem *P, hp_tuning *t) {
   t->omega = P->omega;
   t->col_chunk = P->col_chunk;
   t->max_blocks = (int)P->max_blocks;
+  t->fuse_from = P->fuse_from;
   return HP_OK;
 }
 
@@ -104,6 +109,17 @@ int hp_autotune(hp_problem *P, int nrhs, int reps, hp_tuning *best, double *best
     if (w >= nrhs) continue;
     hp_tuning t = cur;
     t.col_chunk = w;
+    double ms;
+    if ((rc = time_it(t, &ms))) return cleanup(rc);
+    if (ms < cur_ms) {
+      cur = t;
+      cur_ms = ms;
+    }
+  }
+  for (int ff : {1, 2}) {
+    if (ff + 2 > P->L) continue;
+    hp_tuning t = cur;
+    t.fuse_from = ff;
     double ms;
     if ((rc = time_it(t, &ms))) return cleanup(rc);
     if (ms < cur_ms) {

@@ -221,3 +221,28 @@ def test_autotune_keeps_results(small2d):
     Y1, _ = P.hessian_apply(X)
     assert float((Y1 - Y0).norm() / Y0.norm()) < 1e-7
     P.set_tuning()  # back to the defaults for the other tests
+
+
+@pytest.mark.parametrize("dim,N,precision", [(2, 64, "fp32_ir"), (2, 64, "fp64"), (3, 16, "fp32_ir"),
+                                             (2, 48, "fp32_ir")])
+def test_fused_coarse_tail_matches_separate_launches(dim, N, precision):
+    """The coarse tail of the V-cycle in one cluster launch (fuse_from = 1, 2) gives the
+    same Hessian actions as the per-level launches, to the solve tolerance, and the
+    same iteration counts give or take one."""
+    from paper_1909_03948_gb300 import Problem
+    w = W.make_workload(dim, N, 30, seed=77)
+    dr = W.draws(w)
+    P = Problem(dim, N, w.gamma, w.delta, 0.01, dr.obs_xyz, rtol=1e-10, precision=precision)
+    m = 0.3 * torch.tensor(np.random.default_rng(5).standard_normal(P.n), device=DEV)
+    X = torch.tensor(np.random.default_rng(6).standard_normal((9, P.n)), device=DEV)
+    P.set_point(m)
+    Y0, st0 = P.hessian_apply(X)
+    for ff in (1, 2):
+        P.set_tuning(fuse_from=ff)
+        P.set_point(m)
+        Y1, st1 = P.hessian_apply(X)
+        rel = float(torch.linalg.norm(Y1 - Y0) / torch.linalg.norm(Y0))
+        assert rel <= 1e-8, (ff, rel)
+        assert abs(st1["iterations"] - st0["iterations"]) <= 2, (ff, st0, st1)
+    P.set_tuning()
+    P.close()
