@@ -217,19 +217,28 @@ def family_bytes(fam, n, s, dim, fp32):
     return None
 
 
+def stencil_kernel_sha256():
+    """sha256 of the stencil kernel's source: the Pack / reduction / k_st block of
+    csrc/solver.cu and csrc/common.cuh (the code an ncu traffic record belongs to)."""
+    csrc = os.path.join(ROOT, "paper_1909_03948_gb300", "csrc")
+    src = open(os.path.join(csrc, "solver.cu")).read()
+    a = src.index("template <typename T, int VW> struct Pack {")
+    b = src.index("// grid transfer, coarse solve")
+    h = hashlib.sha256(src[a:b].encode())
+    h.update(open(os.path.join(csrc, "common.cuh"), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_record(fam, workload):
     """ncu DRAM bytes per launch recorded in profiles/traffic.json, valid only while
-    the kernel sources are unchanged (sha256 of csrc/solver.cu + common.cuh)."""
+    the stencil kernel's source is unchanged (stencil_kernel_sha256)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     try:
         d = json.load(open(p))
-        h = hashlib.sha256()
-        for f in ("solver.cu", "common.cuh"):
-            h.update(open(os.path.join(ROOT, "paper_1909_03948_gb300", "csrc", f), "rb").read())
         rec = d.get(workload, {}).get(fam)
-        if rec and rec.get("src_sha256") == h.hexdigest():
+        if rec and rec.get("src_sha256") == stencil_kernel_sha256():
             return rec.get("dram_bytes_per_launch")
     except Exception:
         return None
