@@ -230,7 +230,10 @@ int hp_newton_cg_map(hp_problem *P, double *m_dev_inout, const hp_newton_opts *o
  * Algorithm 4) for H_misfit v = lambda R v at m_map_dev.  Omega_dev: n x (k+p)
  * Gaussian test matrix (caller-drawn), ld ldo.  Outputs: lambda_dev (k values,
  * descending), V_dev (n x k, ld ldv, R-orthonormal, sign: largest-magnitude
- * entry positive).  single_pass != 0 selects Algorithm 3 instead. */
+ * entry positive).  single_pass != 0 selects Algorithm 3 instead: one block of
+ * k+p Hessian actions, T the least-squares fit of eq. (Tsinglepass) over
+ * symmetric matrices (solved exactly as the Lyapunov equation X M + M X = C,
+ * M = W W^T, C = Zs W^T + W Zs^T, W = Qb^T Omega, Zs = Qb^T Y, Qb = R Q). */
 int hp_lowrank_eig(hp_problem *P, const double *m_map_dev, int k, int p, const double *Omega_dev,
                    int ldo, double *lambda_dev, double *V_dev, int ldv, int single_pass,
                    hp_solve_stats *st);
@@ -254,6 +257,23 @@ int hp_laplace_sample(hp_problem *P, const double *m_map_dev, const double *lamb
  * enqueued on stream (cudaStream_t; NULL = legacy) and synchronised. */
 int hp_philox_normals(unsigned long long seed, long long first_sample, int nsamples, int nper,
                       double *out, int ld, int raw, void *stream);
+
+/* Pointwise variance (Section 4.4).  The prior part, diag(R^-1), by
+ *   HP_VAR_RANDOMIZED: Algorithm 2 with A = R^-1, B = I on the r columns of Z
+ *     (Gaussian, caller-drawn): diag(R^-1) ~ sum_i mu_i vbar_i (.) vbar_i
+ *     (eq. (prior_mvar)); or
+ *   HP_VAR_STOCHASTIC: diag(R^-1) ~ [sum_j z_j (.) w_j] / [sum_j z_j (.) z_j] with
+ *     R w_j = z_j for the r probe columns of Z (eq. (stoc_diag_estimator)).
+ * prior_var_dev (n) receives it.  With k > 0 eigenpairs (lambda_dev, V_dev) of
+ * the prior-preconditioned misfit Hessian, post_var_dev (n) receives
+ * prior_var - sum_i lambda_i / (1 + lambda_i) v_i (.) v_i (eq. (post_mvar));
+ * post_var_dev may be NULL.  Z_dev: n x r, ld ldz; r <= min(n, 1024) for the
+ * randomized method.  Needs no linearisation point (R does not depend on m). */
+#define HP_VAR_RANDOMIZED 0
+#define HP_VAR_STOCHASTIC 1
+int hp_pointwise_variance(hp_problem *P, int method, const double *Z_dev, int ldz, int r,
+                          const double *lambda_dev, const double *V_dev, int ldv, int k,
+                          double *prior_var_dev, double *post_var_dev, hp_solve_stats *st);
 
 /* ---- tuning ----------------------------------------------------------------
  * Knobs of the PDE solver (no counterpart in the paper): nu damped-Jacobi sweeps

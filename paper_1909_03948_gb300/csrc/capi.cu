@@ -804,13 +804,86 @@ int hp_newton_cg_map(hp_problem *P, double *m, const hp_newton_opts *opts_in, hp
 // ---------------------------------------------------------------------------
 // Algorithms 2 and 4: double-pass randomized generalized eigensolver
 // ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace hp {
+
+// C (s x s) = op(A) op(B) for s x s column-major matrices (ta, tb: transpose flags)
+__global__ void k_small_gemm(int s, int ta, int tb, const double *__restrict__ A, const double *__restrict__ B,
+                             double *__restrict__ C) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= s * s) return;
+  const int i = t % s, j = t / s;
+  double acc = 0.0;
+  for (int k = 0; k < s; ++k) {
+    const double a = ta ? A[k + (long)s * i] : A[i + (long)s * k];
+    const double b = tb ? B[j + (long)s * k] : B[k + (long)s * j];
+    acc += a * b;
+  }
+  C[t] = acc;
+}
+
+static void small_gemm(hp_problem *P, int s, int ta, int tb, const double *A, const double *B, double *C) {
+  k_small_gemm<<<(s * s + 255) / 256, 256, 0, P->st>>>(s, ta, tb, A, B, C);
+  count_launch();
+}
+
+// C = E + E^T
+__global__ void k_sym_sum(const double *__restrict__ E, double *__restrict__ C, int s) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= s * s) return;
+  const int i = t % s, j = t / s;
+  C[t] = E[i + (long)s * j] + E[j + (long)s * i];
+}
+
+// Lyapunov solve in the eigenbasis of M: Ct_ij /= (d_i + d_j); pairs with d_i + d_j below
+// 1e-14 d_max (a rank-deficient M) get the minimum-norm value 0
+__global__ void k_lyap_div(double *__restrict__ Ct, const double *__restrict__ d, int s) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= s * s) return;
+  const int i = t % s, j = t / s;
+  const double den = d[i] + d[j], dmax = fmax(fabs(d[0]), fabs(d[s - 1]));
+  Ct[t] = den > 1e-14 * dmax ? Ct[t] / den : 0.0;
+}
+
+// out_i = base_i + sgn sum_j w_j V_ij^2 with w_j = mu_j (xf = 0) or mu_j / (1 + mu_j) (xf = 1)
+__global__ void k_diag_lowrank(const double *__restrict__ V, long ldv, long n, int k, const double *__restrict__ mu,
+                               int xf, double sgn, const double *__restrict__ base, double *__restrict__ out) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) {
+      const double v = V[ldv * j + i];
+      const double w = xf ? mu[j] / (1.0 + mu[j]) : mu[j];
+      acc += w * v * v;
+    }
+    out[i] = (base ? base[i] : 0.0) + sgn * acc;
+  }
+}
+
+// stochastic diagonal estimator: out_i = sum_j Z_ij W_ij / sum_j Z_ij^2
+__global__ void k_stoch_diag(const double *__restrict__ Z, long ldz, const double *__restrict__ Wm, long ldw, long n,
+                             int r, double *__restrict__ out) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    double num = 0.0, den = 0.0;
+    for (int j = 0; j < r; ++j) {
+      const double z = Z[ldz * j + i];
+      num += z * Wm[ldw * j + i];
+      den += z * z;
+    }
+    out[i] = den > 0.0 ? num / den : 0.0;
+  }
+}
+
+}  // namespace hp
+
+extern "C" {
+
 int hp_lowrank_eig(hp_problem *P, const double *m_map, int k, int p, const double *Omega, int ldo, double *lambda,
                    double *V, int ldv, int single_pass, hp_solve_stats *st) {
   if (!P || !m_map || !Omega || !lambda || !V || k < 1 || p < 0 || ldo < P->n || ldv < P->n)
     return set_error(HP_ERR_INVALID, "arguments");
   const int s = k + p;
   if (s > P->n || s > 1024) return set_error(HP_ERR_INVALID, "k + p too large");
-  if (single_pass) return set_error(HP_ERR_INVALID, "single-pass variant not built");
   if (st) *st = hp_solve_stats{};
   int rc = 0;
   const long n = P->n, ld = padded(n);
@@ -821,13 +894,22 @@ int hp_lowrank_eig(hp_problem *P, const double *m_map, int k, int p, const doubl
   HP_TRY(rc);
   double *H = col64(P->vtmp[2], P, s, &rc);
   HP_TRY(rc);
-  HP_TRY(P->small.ensure(sizeof(double) * (4 * (size_t)s * s + 2 * s + 64)));
-  double *G = P->small.as<double>(), *T = G + (size_t)s * s, *Sm = T + (size_t)s * s, *Ts = Sm + (size_t)s * s;
-  double *lam = Ts + (size_t)s * s;
+  const size_t s2 = (size_t)s * s;
+  HP_TRY(P->small.ensure(sizeof(double) * (12 * s2 + 4 * s + 64)));
+  double *G = P->small.as<double>(), *T = G + s2, *Sm = T + s2, *Ts = Sm + s2;
+  double *lam = Ts + s2;
+  double *Wm = lam + 2 * s, *Zs = Wm + s2, *M = Zs + s2, *Cm = M + s2, *E = Cm + s2, *U = E + s2, *tmp = U + s2,
+         *d = tmp + s2;
   // Ybar = A Omega ; Y = B^{-1} Ybar
   HP_TRY(hessian_block(P, Omega, ldo, H, ld, s, HP_MISFIT_ONLY, st));
   HP_TRY(Rinv_apply(P, H, ld, Y, ld, s));
-  // PreCholQR: Z = qr(Y); Zb = B Z; R_Z = chol(Z^T Zb); Q = Z R_Z^{-1}
+  double *Ysave = nullptr;
+  if (single_pass) {  // Y is needed again after the QR overwrites it
+    Ysave = col64(P->t64c, P, s, &rc);
+    HP_TRY(rc);
+    launch_copy(Y, ld, Ysave, ld, n, s, P->st);
+  }
+  // PreCholQR: Z = qr(Y); Zb = B Z; R_Z = chol(Z^T Zb); Q = Z R_Z^{-1} (and Qb = Zb R_Z^{-1})
   HP_TRY(cgs2_qr(P, Y, ld, n, s));
   HP_TRY(R_apply(P, Y, ld, Zb, ld, s));
   HP_TRY(gram(P, Y, ld, s, Zb, ld, s, G, s, n));
@@ -835,9 +917,31 @@ int hp_lowrank_eig(hp_problem *P, const double *m_map, int k, int p, const doubl
   count_launch();
   HP_TRY(small_cholesky(P, Ts, s));
   launch_trsm_right_upper(Y, ld, n, s, Ts, P->st);
-  // T = Q^T A Q
-  HP_TRY(hessian_block(P, Y, ld, H, ld, s, HP_MISFIT_ONLY, st));
-  HP_TRY(gram(P, Y, ld, s, H, ld, s, T, s, n));
+  if (!single_pass) {
+    // Algorithm 2: T = Q^T A Q (the second pass)
+    HP_TRY(hessian_block(P, Y, ld, H, ld, s, HP_MISFIT_ONLY, st));
+    HP_TRY(gram(P, Y, ld, s, H, ld, s, T, s, n));
+  } else {
+    // Algorithm 3, eq. (Tsinglepass): T = argmin over symmetric X of |X W - Zs|_F with
+    // W = Qb^T Omega, Zs = Qb^T Y.  Its normal equations restricted to symmetric X are the
+    // Lyapunov equation X M + M X = C, M = W W^T, C = Zs W^T + W Zs^T, solved in the
+    // eigenbasis of M: with M = U D U^T, (U^T X U)_ij = (U^T C U)_ij / (d_i + d_j).
+    launch_trsm_right_upper(Zb, ld, n, s, Ts, P->st);
+    HP_TRY(gram(P, Zb, ld, s, Omega, ldo, s, Wm, s, n));
+    HP_TRY(gram(P, Zb, ld, s, Ysave, ld, s, Zs, s, n));
+    small_gemm(P, s, 0, 1, Wm, Wm, M);   // M = W W^T
+    small_gemm(P, s, 0, 1, Zs, Wm, E);   // E = Zs W^T
+    k_sym_sum<<<(s * s + 255) / 256, 256, 0, P->st>>>(E, Cm, s);
+    k_symmetrize<<<(s * s + 255) / 256, 256, 0, P->st>>>(M, E, s);
+    count_launch(2);
+    HP_TRY(small_symeig(P, E, s, d, U));
+    small_gemm(P, s, 1, 0, U, Cm, tmp);  // U^T C
+    small_gemm(P, s, 0, 0, tmp, U, E);   // U^T C U
+    k_lyap_div<<<(s * s + 255) / 256, 256, 0, P->st>>>(E, d, s);
+    count_launch();
+    small_gemm(P, s, 0, 0, U, E, tmp);   // U Xt
+    small_gemm(P, s, 0, 1, tmp, U, T);   // X = U Xt U^T
+  }
   k_symmetrize<<<(s * s + 255) / 256, 256, 0, P->st>>>(T, Ts, s);
   count_launch();
   HP_TRY(small_symeig(P, Ts, s, lam, Sm));
@@ -846,6 +950,60 @@ int hp_lowrank_eig(hp_problem *P, const double *m_map, int k, int p, const doubl
   k_sign_normalise<<<k, NT, 0, P->st>>>(V, ldv, n);
   count_launch();
   HP_CUDA(cudaMemcpyAsync(lambda, lam, sizeof(double) * k, cudaMemcpyDeviceToDevice, P->st));
+  return sync(P);
+}
+
+// ---------------------------------------------------------------------------
+// Section 4.4: pointwise variance
+// ---------------------------------------------------------------------------
+int hp_pointwise_variance(hp_problem *P, int method, const double *Z, int ldz, int r, const double *lambda,
+                          const double *V, int ldv, int k, double *prior_var, double *post_var,
+                          hp_solve_stats *st) {
+  if (!P || !Z || !prior_var || r < 1 || ldz < P->n || (method != HP_VAR_RANDOMIZED && method != HP_VAR_STOCHASTIC))
+    return set_error(HP_ERR_INVALID, "hp_pointwise_variance: arguments");
+  if (k < 0 || (k > 0 && (!lambda || !V || ldv < P->n)))
+    return set_error(HP_ERR_INVALID, "hp_pointwise_variance: eigenpair arguments");
+  if (method == HP_VAR_RANDOMIZED && (r > P->n || r > 1024))
+    return set_error(HP_ERR_INVALID, "hp_pointwise_variance: r <= min(n, 1024)");
+  if (st) *st = hp_solve_stats{};
+  int rc = 0;
+  const long n = P->n, ld = padded(n);
+  double *Y = col64(P->vtmp[0], P, r, &rc);
+  HP_TRY(rc);
+  const unsigned nb = (unsigned)blocks_for(n, 1);
+  if (method == HP_VAR_STOCHASTIC) {
+    HP_TRY(Rinv_apply(P, Z, ldz, Y, ld, r));
+    k_stoch_diag<<<nb, NT, 0, P->st>>>(Z, ldz, Y, ld, n, r, prior_var);
+    count_launch();
+  } else {
+    // Algorithm 2 with A = R^-1, B = I: Q = qr(R^-1 Z) (PreCholQR with B = I is a plain QR),
+    // T = Q^T R^-1 Q = S diag(mu) S^T, vbar = Q S
+    double *AQ = col64(P->vtmp[1], P, r, &rc);
+    HP_TRY(rc);
+    double *Vb = col64(P->vtmp[2], P, r, &rc);
+    HP_TRY(rc);
+    const size_t r2 = (size_t)r * r;
+    HP_TRY(P->small.ensure(sizeof(double) * (3 * r2 + 2 * r + 64)));
+    double *T = P->small.as<double>(), *Ts = T + r2, *Sm = Ts + r2, *mu = Sm + r2;
+    HP_TRY(Rinv_apply(P, Z, ldz, Y, ld, r));
+    HP_TRY(cgs2_qr(P, Y, ld, n, r));
+    HP_TRY(Rinv_apply(P, Y, ld, AQ, ld, r));
+    HP_TRY(gram(P, Y, ld, r, AQ, ld, r, T, r, n));
+    k_symmetrize<<<(unsigned)((r2 + 255) / 256), 256, 0, P->st>>>(T, Ts, r);
+    count_launch();
+    HP_TRY(small_symeig(P, Ts, r, mu, Sm));
+    launch_gemm_nn(Y, ld, r, Sm, r, r, Vb, ld, n, 1.0, 0.0, P->st);
+    k_diag_lowrank<<<nb, NT, 0, P->st>>>(Vb, ld, n, r, mu, 0, 1.0, nullptr, prior_var);
+    count_launch();
+  }
+  if (post_var) {
+    if (k > 0) {
+      k_diag_lowrank<<<nb, NT, 0, P->st>>>(V, ldv, n, k, lambda, 1, -1.0, prior_var, post_var);
+      count_launch();
+    } else {
+      HP_CUDA(cudaMemcpyAsync(post_var, prior_var, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->st));
+    }
+  }
   return sync(P);
 }
 

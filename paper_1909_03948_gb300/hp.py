@@ -114,6 +114,7 @@ _SIGS = {
     "hp_laplace_sample": (_I, [_P, _D, _D, _D, _I, _I, _D, _I, C.c_ulonglong, _I, _D, _D, _I,
                                C.POINTER(SolveStats)]),
     "hp_philox_normals": (_I, [C.c_ulonglong, C.c_longlong, _I, _I, _D, _I, _I, C.c_void_p]),
+    "hp_pointwise_variance": (_I, [_P, _I, _D, _I, _I, _D, _D, _I, _I, _D, _D, C.POINTER(SolveStats)]),
     "hp_profile_enable": (_I, [_P, _I]),
     "hp_profile_read": (_I, [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "hp_replay_kernel": (_I, [_P, _I, _I, C.c_void_p, C.c_size_t, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -480,6 +481,29 @@ class Problem:
         _check(lib().hp_lowrank_eig(self._h, _dptr(m_map), k, p, _dptr(O2), n, _dptr(lam), _dptr(V), n,
                                     1 if single_pass else 0, C.byref(st)), "hp_lowrank_eig")
         return lam, V, st.as_dict()
+
+    VARIANCE_METHODS = ("randomized", "stochastic")
+
+    def pointwise_variance(self, Z, method: str = "randomized", lam=None, V=None):
+        """Section 4.4: (prior_var, post_var or None) as (n,) float64 tensors.  Z: (r, n)
+        Gaussian columns (randomized eig of R^-1, eq. prior_mvar) or probe vectors
+        (stochastic estimator); lam (k,), V (k, n): Hessian eigenpairs for eq. post_mvar."""
+        Z2, r, n = _block(Z, self.n, "Z")
+        prior = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        post = None
+        k, lp, vp = 0, None, None
+        if V is not None:
+            V2, k, _ = _block(V, self.n, "V")
+            lam = lam.contiguous()
+            if lam.numel() != k or not lam.is_cuda or lam.dtype != torch.float64:
+                raise ValueError("lam: k CUDA float64 values")
+            post = torch.empty_like(prior)
+            lp, vp = _dptr(lam), _dptr(V2)
+        st = SolveStats()
+        _check(lib().hp_pointwise_variance(self._h, self.VARIANCE_METHODS.index(method), _dptr(Z2), n, r, lp, vp,
+                                           n, k, _dptr(prior), _dptr(post) if post is not None else None,
+                                           C.byref(st)), "hp_pointwise_variance")
+        return prior, post
 
     def laplace_sample(self, m_map, lam, V, eta=None, want_prior=True, want_post=True, seed=0, nsamples=None):
         """Prior and Laplace-posterior samples.  eta: (N, (dim+1)*nelems) normals, or None

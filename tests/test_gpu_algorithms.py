@@ -246,3 +246,81 @@ def test_fused_coarse_tail_matches_separate_launches(dim, N, precision):
         assert abs(st1["iterations"] - st0["iterations"]) <= 2, (ff, st0, st1)
     P.set_tuning()
     P.close()
+
+
+def test_single_pass_matches_oracle(small2d):
+    """Algorithm 3 with the same Omega: eigenvalues > 0.1 to relative 1e-5, V R-orthonormal,
+    well-separated eigenvectors aligned with the oracle's."""
+    orc, w, P = small2d["orc"], small2d["w"], small2d["P"]
+    m_map = small2d["m_map"]
+    Om = W.omega(w)
+    lam_ref, V_ref = A.lowrank_eig(orc, m_map, Om, w.k, single=True)
+    lam, V, st = P.lowrank_eig(torch.tensor(m_map, device=DEV), w.k, w.p,
+                               torch.tensor(np.ascontiguousarray(Om.T), device=DEV), single_pass=True)
+    lam, V = lam.cpu().numpy(), V.cpu().numpy().T
+    big = lam_ref > 0.1
+    assert np.all(np.abs(lam[big] - lam_ref[big]) <= 1e-5 * lam_ref[big]), (lam[:8], lam_ref[:8])
+    VtRV = V.T @ orc.R_apply(V)
+    assert np.allclose(VtRV, np.eye(w.k), atol=1e-7)
+    gap = np.ones(w.k, dtype=bool)
+    gap[1:] &= lam_ref[1:] < 0.9 * lam_ref[:-1]
+    gap[:-1] &= lam_ref[1:] < 0.9 * lam_ref[:-1]
+    sel = big & gap
+    c = np.abs(np.einsum("ij,ij->j", V[:, sel], orc.R_apply(V_ref[:, sel])))
+    assert np.all(np.abs(c - 1) < 1e-4), c
+
+
+def test_single_pass_is_exact_at_low_rank():
+    """With rank(H_misfit) <= q = 8 < k + p both algorithms are exact: the GPU's single pass
+    equals its double pass."""
+    from paper_1909_03948_gb300 import Problem
+    w = W.make_workload(2, 32, 8, seed=99)
+    orc, _, _ = make_problem(w, W.draws(w))
+    P = _gpu_problem(orc, w)
+    m = torch.tensor(0.2 * np.random.default_rng(3).standard_normal(P.n), device=DEV)
+    Om = torch.tensor(np.random.default_rng(4).standard_normal((14, P.n)), device=DEV)
+    l2, V2, _ = P.lowrank_eig(m, 6, 8, Om)
+    l1, V1, _ = P.lowrank_eig(m, 6, 8, Om, single_pass=True)
+    l1, l2 = l1.cpu().numpy(), l2.cpu().numpy()
+    keep = l2 > 1e-6 * l2[0]
+    assert np.all(np.abs(l1[keep] - l2[keep]) <= 1e-6 * l2[keep]), (l1, l2)
+    P.close()
+
+
+def test_pointwise_variance_matches_oracle(small2d):
+    """Section 4.4 with the same random columns: randomized prior variance (eq. prior_mvar)
+    relative 1e-6, stochastic estimator (eq. stoc_diag_estimator) 1e-8, posterior
+    correction (eq. post_mvar) with the oracle's eigenpairs 1e-8."""
+    orc, w, P = small2d["orc"], small2d["w"], small2d["P"]
+    Z = W.omega(w, ncols=30, seed_offset=5)
+    Zt = torch.tensor(np.ascontiguousarray(Z.T), device=DEV)
+    ref_r = A.prior_variance_randomized(orc, Z, 30)
+    ref_s = A.stochastic_diag_estimator(orc, Z)
+    lam_ref, V_ref = A.lowrank_eig(orc, small2d["m_map"], W.omega(w), w.k)
+    pr, po = P.pointwise_variance(Zt, "randomized", torch.tensor(lam_ref, device=DEV),
+                                  torch.tensor(np.ascontiguousarray(V_ref.T), device=DEV))
+    pr, po = pr.cpu().numpy(), po.cpu().numpy()
+    assert np.abs(pr - ref_r).max() <= 1e-6 * np.abs(ref_r).max()
+    post_ref = ref_r - (V_ref ** 2) @ (lam_ref / (1 + lam_ref))
+    assert np.abs(po - (pr - (V_ref ** 2) @ (lam_ref / (1 + lam_ref)))).max() <= 1e-10 * np.abs(pr).max()
+    assert np.abs(po - post_ref).max() <= 1e-6 * np.abs(post_ref).max()
+    ps, none = P.pointwise_variance(Zt, "stochastic")
+    assert none is None
+    assert np.abs(ps.cpu().numpy() - ref_s).max() <= 1e-8 * np.abs(ref_s).max()
+
+
+@pytest.mark.parametrize("dim,N", [(2, 6), (3, 3)])
+def test_randomized_prior_variance_is_exact_with_full_rank(dim, N):
+    """r = n columns: Algorithm 2 on R^-1 is exact, so the estimate equals diag(R^-1) =
+    diag(A^-1 M A^-1) computed by the oracle's sparse direct solves at every node."""
+    from paper_1909_03948_gb300 import Problem
+    w = W.make_workload(dim, N, 3, seed=17)
+    orc, _, _ = make_problem(w, W.draws(w))
+    P = Problem(dim, N, w.gamma, w.delta, orc.sigma, orc.obs_xyz, rtol=1e-12)
+    Z = torch.tensor(np.random.default_rng(8).standard_normal((P.n, P.n)), device=DEV)
+    pr, _ = P.pointwise_variance(Z, "randomized")
+    exact = A.prior_variance_exact(orc, np.arange(P.n))
+    assert np.abs(pr.cpu().numpy() - exact).max() <= 1e-8 * exact.max()
+    with pytest.raises(Exception):
+        P.pointwise_variance(Z[:, :3], "randomized")          # wrong block shape
+    P.close()
