@@ -10,6 +10,9 @@ All quantities FP64.  Readings of the paper where it is silent:
   most 10 backtracks; at most 50 Newton iterations; Steihaug exit on
   non-positive curvature (with the preconditioned steepest-descent direction
   if it happens at the first CG iteration).
+* Newton-CG uses the Gauss-Newton Hessian by default; full=True uses the
+  Hessian with the adjoint terms (Appendix A), which may be indefinite away
+  from the MAP point -- the Steihaug exit handles that.
 * Double pass (Algorithm 2) with PreCholQR (Algorithm 4), A = H_misfit,
   B = R; the eigenvector sign is normalised so that the entry of largest
   magnitude is positive.
@@ -68,7 +71,7 @@ def cg_steihaug(apply_H, apply_P, b, rtol, max_iter=200, min_iter=1):
 
 
 def newton_cg(prob, m0=None, rel_tol=1e-6, abs_tol=0.0, max_iter=50, max_backtrack=10,
-              c_armijo=1e-4, cg_max_iter=200):
+              c_armijo=1e-4, cg_max_iter=200, full=False):
     m = prob.m_prior.copy() if m0 is None else np.array(m0, dtype=float)
     u = prob.forward(m)
     J = prob.cost(m, u)[0]
@@ -85,8 +88,11 @@ def newton_cg(prob, m0=None, rel_tol=1e-6, abs_tol=0.0, max_iter=50, max_backtra
             res.converged = True
             break
         eta = min(0.5, np.sqrt(gnorm / g0norm))
-        mhat, ncg, _ = cg_steihaug(lambda v: prob.hessian(m, u, v), prob.Rinv_apply, -g, eta,
-                                   max_iter=cg_max_iter)
+        if full:
+            H = lambda v, m=m, u=u, p=p: prob.hessian_full(m, u, p, v)
+        else:
+            H = lambda v, m=m, u=u: prob.hessian(m, u, v)
+        mhat, ncg, _ = cg_steihaug(H, prob.Rinv_apply, -g, eta, max_iter=cg_max_iter)
         res.cg_iterations.append(ncg)
         gdm = float(g @ mhat)
         alpha = 1.0

@@ -172,6 +172,27 @@ class Problem:
     def hessian(self, m: np.ndarray, u: np.ndarray, X: np.ndarray) -> np.ndarray:
         return self.hessian_misfit(m, u, X) + self.R_apply(X)
 
+    # ---- full Newton Hessian action (Appendix A with the adjoint terms) -------
+    def hessian_full_misfit(self, m: np.ndarray, u: np.ndarray, p: np.ndarray, X: np.ndarray) -> np.ndarray:
+        """Misfit part of the Hessian action with every term of eqs. incrementals1-3:
+
+            K uhat = -C(u) X                               (incrementals1)
+            K phat = -B^T B uhat / sigma^2 - C(p) X         (incrementals2)
+            H X    = C(u)^T phat + C(p)^T uhat + X (.) C(u)^T p   (incrementals3)
+
+        C(w) X = K(kappa_hat) w is the derivative of K(m) w in direction X; the last term
+        is the second derivative of p^T K(m) u, diagonal because each element coefficient
+        is linear in e^m."""
+        uhat = self.solve_state(m, -self.C_apply(m, u, X))
+        rhs = -(self.B.T @ (self.B @ uhat)) / self.sigma ** 2 - self.C_apply(m, p, X)
+        phat = self.solve_state(m, rhs)
+        wmm = self.Ct_apply(m, u, p)
+        diag = wmm[:, None] * X if X.ndim == 2 else wmm * X
+        return self.Ct_apply(m, u, phat) + self.Ct_apply(m, p, uhat) + diag
+
+    def hessian_full(self, m: np.ndarray, u: np.ndarray, p: np.ndarray, X: np.ndarray) -> np.ndarray:
+        return self.hessian_full_misfit(m, u, p, X) + self.R_apply(X)
+
     def parameter_to_observable(self, m: np.ndarray) -> np.ndarray:
         return self.observe(self.forward(m))
 

@@ -35,6 +35,17 @@ def test_newton_matches_independent_optimizer():
     assert f(res.m) <= f(ref.x) + 1e-9
 
 
+def test_full_newton_reaches_the_same_map_in_fewer_iterations():
+    """Newton-CG with the full Hessian minimises the same cost: same MAP as the
+    Gauss-Newton run, and no more Newton iterations."""
+    prob, _ = _problem(2, 6, 12, seed=11)
+    gn = A.newton_cg(prob, rel_tol=1e-10)
+    fn = A.newton_cg(prob, rel_tol=1e-10, full=True)
+    assert gn.converged and fn.converged
+    assert np.linalg.norm(fn.m - gn.m) <= 1e-7 * np.linalg.norm(gn.m)
+    assert fn.iterations <= gn.iterations
+
+
 def test_cg_steihaug_solves_spd_system():
     rng = np.random.default_rng(0)
     Q = rng.standard_normal((20, 20))

@@ -1,5 +1,6 @@
 """Pins for oracle/inverse.py: exact solutions, O(h^2) convergence, finite-difference
-derivative checks and symmetry of the Gauss-Newton Hessian."""
+derivative checks, symmetry of the Gauss-Newton Hessian, and the full Hessian (with
+the adjoint terms) against finite differences of the gradient at a nonzero residual."""
 import numpy as np
 import pytest
 
@@ -129,6 +130,38 @@ def test_gn_hessian_is_full_hessian_at_zero_residual():
     fd = (prob.gradient(m + eps * v)[0] - prob.gradient(m - eps * v)[0]) / (2 * eps)
     Hv = prob.hessian(m, u, v)
     assert np.linalg.norm(fd - Hv) <= 1e-6 * np.linalg.norm(Hv)
+
+
+@pytest.mark.parametrize("dim,N", [(2, 6), (3, 2)])
+def test_full_hessian_is_the_derivative_of_the_gradient(dim, N):
+    """At a nonzero data residual (the adjoint p is not 0) the full Hessian action of
+    eqs. incrementals1-3 equals central differences of the gradient, while the
+    Gauss-Newton Hessian does not."""
+    prob = _problem(dim, N, 8, seed=11)
+    m = _smooth_m(prob.mesh)
+    g, _, u, p = prob.gradient(m)
+    assert np.linalg.norm(p) > 1e-3 * np.linalg.norm(u)
+    rng = np.random.default_rng(12)
+    for _ in range(2):
+        v = rng.standard_normal(prob.n)
+        eps = 1e-5
+        fd = (prob.gradient(m + eps * v)[0] - prob.gradient(m - eps * v)[0]) / (2 * eps)
+        Hv = prob.hessian_full(m, u, p, v)
+        assert np.linalg.norm(fd - Hv) <= 1e-6 * np.linalg.norm(Hv)
+        gn = prob.hessian(m, u, v)
+        assert np.linalg.norm(fd - gn) > 1e-3 * np.linalg.norm(Hv)
+    # blocks act column by column
+    V = rng.standard_normal((prob.n, 3))
+    HV = prob.hessian_full(m, u, p, V)
+    assert np.allclose(HV[:, 1], prob.hessian_full(m, u, p, V[:, 1]), rtol=1e-12, atol=1e-12)
+
+
+def test_full_hessian_is_symmetric():
+    prob = _problem(2, 5, 6, seed=13)
+    m = _smooth_m(prob.mesh)
+    _, _, u, p = prob.gradient(m)
+    H = prob.hessian_full_misfit(m, u, p, np.eye(prob.n))
+    assert np.abs(H - H.T).max() <= 1e-10 * np.abs(H).max()
 
 
 def test_hessian_symmetry_and_rank():
