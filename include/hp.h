@@ -54,6 +54,7 @@ extern "C" {
 /* flags of hp_hessian_apply */
 #define HP_MISFIT_ONLY 0 /* Y = H_misfit X                                 */
 #define HP_WITH_PRIOR 1  /* Y = (H_misfit + R) X                           */
+#define HP_FULL_NEWTON 2 /* add the adjoint terms (full Hessian, see below)  */
 
 typedef struct hp_problem hp_problem;
 
@@ -87,6 +88,8 @@ typedef struct {
   int max_backtrack;     /* Armijo backtracks (Algorithm 1: max_backtracking_iter)        */
   double c_armijo;       /* Armijo constant (Section 4.1: 1e-5 .. 1e-4)                   */
   int cg_max_iter;       /* inner CG cap                                                  */
+  int full_newton;       /* 0: Gauss-Newton Hessian; 1: full Hessian (HP_FULL_NEWTON); the
+                            CG stops on non-positive curvature (Steihaug) either way       */
 } hp_newton_opts;
 
 typedef struct {
@@ -136,7 +139,12 @@ int hp_gradient(hp_problem *P, const double *m_dev, double *g_dev, double *J_out
 
 /* Gauss-Newton Hessian action at the current linearisation point on a block
  * of nrhs columns:  K Uh = -C X,  K Ph = -B^T B Uh / sigma^2,  Y = C^T Ph
- * (+ R X if flags & HP_WITH_PRIOR).  X and Y may not alias. */
+ * (+ R X if flags & HP_WITH_PRIOR).  With flags & HP_FULL_NEWTON the adjoint
+ * terms of the same equations are kept (the full Hessian):
+ *   K Ph = -B^T B Uh / sigma^2 - C(p) X,  Y = C^T Ph + C(p)^T Uh + X (.) C^T p,
+ * where p is the adjoint at the point (solved on first use after hp_set_point /
+ * hp_set_data and kept) and C(p) is C built from p instead of u.  X and Y may
+ * not alias. */
 int hp_hessian_apply(hp_problem *P, const double *X_dev, int ldx, double *Y_dev, int ldy,
                      int nrhs, int flags, hp_solve_stats *st);
 

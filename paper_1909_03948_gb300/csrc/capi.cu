@@ -260,15 +260,15 @@ static int set_point(hp_problem *P, const double *m_dev, double *J3, hp_solve_st
   return sync(P);
 }
 
-// g = R (m - m_pr) + C^T p at the current point
-static int gradient_at_point(hp_problem *P, double *g, double *J3) {
+// adjoint p at the current point into P->padj (one stiffness solve, kept until the point
+// or the data change): K p = -B^T (B u - d) / sigma^2
+static int adjoint_at_point(hp_problem *P) {
+  if (P->have_p) return 0;
   int rc = 0;
   const long n = P->n;
+  if (!P->padj && cudaMalloc(&P->padj, sizeof(double) * n) != cudaSuccess)
+    return set_error(HP_ERR_NOMEM, "adjoint");
   double *rhs = col64(P->t64a, P, 1, &rc);
-  HP_TRY(rc);
-  double *p = col64(P->vtmp[1], P, 1, &rc);
-  HP_TRY(rc);
-  double *Rdm = col64(P->vtmp[2], P, 1, &rc);
   HP_TRY(rc);
   HP_TRY(P->obsbuf.ensure(sizeof(double) * (2 * (size_t)std::max(P->nobs, 1) + 8)));
   double *yq = P->obsbuf.as<double>();
@@ -278,10 +278,44 @@ static int gradient_at_point(hp_problem *P, double *g, double *J3) {
     count_launch();
   }
   launch_obs_scatter(P, yq, rhs, n, 1, -1.0 / (P->sigma * P->sigma));
-  HP_TRY(solve_block(P, OP_K, rhs, n, p, n, 1, P->rtol, nullptr));
+  HP_TRY(solve_block(P, OP_K, rhs, n, P->padj, n, 1, P->rtol, nullptr));
+  P->have_p = true;
+  return 0;
+}
+
+// the adjoint terms of the full Hessian at the current point: C(p) and C(u)^T p
+static int full_terms_at_point(hp_problem *P) {
+  if (P->have_full) return 0;
+  HP_TRY(adjoint_at_point(P));
+  const long n = P->n;
+  const int nC = (1 << (P->dim + 1)) - 1;
+  if (!P->Cbeta_p && cudaMalloc(&P->Cbeta_p, sizeof(double) * n * nC) != cudaSuccess)
+    return set_error(HP_ERR_NOMEM, "full Hessian terms");
+  if (!P->wmm && cudaMalloc(&P->wmm, sizeof(double) * n) != cudaSuccess)
+    return set_error(HP_ERR_NOMEM, "full Hessian terms");
+  launch_build_C_from(P, P->padj, P->Cbeta_p);
+  launch_Ct_apply(P, P->padj, n, P->wmm, n, 1, 1.0, 0.0);
+  P->have_full = true;
+  return 0;
+}
+
+__global__ void k_add_diag_cols(const double *__restrict__ w, const double *__restrict__ X, long ldx,
+                                double *__restrict__ Y, long ldy, long n) {
+  const int j = blockIdx.y;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    Y[ldy * j + i] += w[i] * X[ldx * j + i];
+}
+
+// g = R (m - m_pr) + C^T p at the current point
+static int gradient_at_point(hp_problem *P, double *g, double *J3) {
+  int rc = 0;
+  const long n = P->n;
+  double *Rdm = col64(P->vtmp[2], P, 1, &rc);
+  HP_TRY(rc);
+  HP_TRY(adjoint_at_point(P));
   double J3l[3];
   HP_TRY(cost_at_point(P, J3 ? J3 : J3l, Rdm));
-  launch_Ct_apply(P, p, n, g, n, 1, 1.0, 0.0);
+  launch_Ct_apply(P, P->padj, n, g, n, 1, 1.0, 0.0);
   launch_axpby(1.0, Rdm, n, 1.0, g, n, n, 1, P->st);
   return sync(P);
 }
@@ -297,15 +331,31 @@ static int hessian_block(hp_problem *P, const double *X, long ldx, double *Y, lo
   HP_TRY(rc);
   HP_TRY(P->obsbuf.ensure(sizeof(double) * ((size_t)std::max(P->nobs, 1) * s + 8)));
   double *yq = P->obsbuf.as<double>();
-  // incremental forward: K Uh = -C X
+  const bool full = (flags & HP_FULL_NEWTON) != 0;
+  double *uh = nullptr;
+  if (full) {
+    HP_TRY(full_terms_at_point(P));
+    uh = col64(P->t64c, P, s, &rc);
+    HP_TRY(rc);
+  }
+  // incremental forward (eq. incrementals1): K Uh = -C X
   launch_C_apply(P, X, ldx, t1, ld, s, -1.0);
   HP_TRY(solve_block(P, OP_K, t1, ld, t2, ld, s, P->rtol, st));
-  // incremental adjoint: K Ph = -B^T B Uh / sigma^2
+  // incremental adjoint (eq. incrementals2): K Ph = -B^T B Uh / sigma^2 [- C(p) X]
   launch_obs_gather(P, t2, ld, yq, s);
   launch_obs_scatter(P, yq, t1, ld, s, -1.0 / (P->sigma * P->sigma));
+  if (full) {
+    launch_copy(t2, ld, uh, ld, n, s, P->st);
+    launch_C_apply_beta(P, P->Cbeta_p, X, ldx, t1, ld, s, -1.0, 1.0);
+  }
   HP_TRY(solve_block(P, OP_K, t1, ld, t2, ld, s, P->rtol, st));
-  // Y = C^T Ph
+  // eq. incrementals3: Y = C^T Ph [+ C(p)^T Uh + X (.) C^T p]
   launch_Ct_apply(P, t2, ld, Y, ldy, s, 1.0, 0.0);
+  if (full) {
+    launch_Ct_apply_beta(P, P->Cbeta_p, uh, ld, Y, ldy, s, 1.0, 1.0);
+    k_add_diag_cols<<<dim3(blocks_for(n, s), s), NT, 0, P->st>>>(P->wmm, X, ldx, Y, ldy, n);
+    count_launch();
+  }
   if (flags & HP_WITH_PRIOR) {
     double *t3 = col64(P->t64c, P, s, &rc);
     HP_TRY(rc);
@@ -452,7 +502,7 @@ void hp_problem_destroy(hp_problem *P) {
       if (p) cudaFree(p);
   for (void *p : {(void *)P->M64.diag, (void *)P->M64.invdiag, (void *)P->M64.c, (void *)P->M32.diag,
                   (void *)P->M32.invdiag, (void *)P->M32.c, (void *)P->m, (void *)P->E, (void *)P->u,
-                  (void *)P->lift, (void *)P->Cbeta, (void *)P->m_prior, (void *)P->f_load, (void *)P->d_obs, (void *)P->obs_node,
+                  (void *)P->lift, (void *)P->Cbeta, (void *)P->padj, (void *)P->Cbeta_p, (void *)P->wmm, (void *)P->m_prior, (void *)P->f_load, (void *)P->d_obs, (void *)P->obs_node,
                   (void *)P->obs_w, (void *)P->bt_row, (void *)P->bt_ptr, (void *)P->bt_ent})
     if (p) cudaFree(p);
   for (BlockWS<float> *W = &P->w32; W; W = nullptr) {
@@ -509,6 +559,7 @@ int hp_set_data(hp_problem *P, const double *d_obs_host, double sigma) {
   if (!P || !(sigma > 0)) return set_error(HP_ERR_INVALID, "sigma");
   P->sigma = sigma;
   if (d_obs_host && P->nobs) HP_CUDA(cudaMemcpy(P->d_obs, d_obs_host, sizeof(double) * P->nobs, cudaMemcpyHostToDevice));
+  P->have_p = P->have_full = false;  // the adjoint depends on the data
   return HP_OK;
 }
 
@@ -697,7 +748,7 @@ int hp_mass_factor_apply(hp_problem *P, const double *eta, int ldeta, double *W,
 // ---------------------------------------------------------------------------
 int hp_newton_cg_map(hp_problem *P, double *m, const hp_newton_opts *opts_in, hp_newton_stats *out) {
   if (!P || !m) return set_error(HP_ERR_INVALID, "null");
-  hp_newton_opts o{1e-6, 0.0, 50, 10, 1e-4, 200};
+  hp_newton_opts o{1e-6, 0.0, 50, 10, 1e-4, 200, 0};
   if (opts_in) o = *opts_in;
   hp_newton_stats S{};
   const long n = P->n;
@@ -750,7 +801,8 @@ int hp_newton_cg_map(hp_problem *P, double *m, const hp_newton_opts *opts_in, hp
     int k = 0;
     for (k = 1; k <= o.cg_max_iter; ++k) {
       hp_solve_stats hs{};
-      if ((rc = hessian_block(P, d, n, Hd, n, 1, HP_WITH_PRIOR, &hs))) return cleanup(rc);
+      if ((rc = hessian_block(P, d, n, Hd, n, 1, HP_WITH_PRIOR | (o.full_newton ? HP_FULL_NEWTON : 0), &hs)))
+        return cleanup(rc);
       solves += hs.solves;
       double dHd = 0.0;
       if ((rc = dot1(P, d, Hd, &dHd))) return cleanup(rc);

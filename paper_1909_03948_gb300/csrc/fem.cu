@@ -410,6 +410,7 @@ int build_hierarchy_geometry(hp_problem *P) {
 
 int build_point(hp_problem *P, const double *m_dev) {
   const long n = P->n;
+  P->have_p = P->have_full = false;
   HP_CUDA(cudaMemcpyAsync(P->m, m_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->st));
   launch_ew_exp(P->m, P->E, n, P->st);
   const int D = P->dim;
@@ -514,10 +515,11 @@ __device__ __forceinline__ bool shift_ok(const GridDesc &g, const int v[3], int 
   return ok;
 }
 
-// Y = scale * S_C (E (.) X)
+// Y = scale * S_C (E (.) X) + yb * Y
 template <int D>
 __global__ void k_C_apply(GridDesc g, const double *__restrict__ E, const double *__restrict__ beta,
-                          const double *__restrict__ X, long ldx, double *__restrict__ Y, long ldy, double scale) {
+                          const double *__restrict__ X, long ldx, double *__restrict__ Y, long ldy, double scale,
+                          double yb) {
   constexpr int NC = (1 << (D + 1)) - 1;
   const int j = blockIdx.y;
   const double *x = X + ldx * j;
@@ -533,7 +535,7 @@ __global__ void k_C_apply(GridDesc g, const double *__restrict__ E, const double
       const long w = i + sg * mask_offset(g, m);
       acc += beta[(long)q * g.n + i] * E[w] * x[w];
     }
-    Y[ldy * j + i] = scale * acc;
+    Y[ldy * j + i] = yb == 0.0 ? scale * acc : scale * acc + yb * Y[ldy * j + i];
   }
 }
 
@@ -563,31 +565,43 @@ __global__ void k_Ct_apply(GridDesc g, const double *__restrict__ E, const doubl
   }
 }
 
-void launch_build_C(hp_problem *P) {
+void launch_build_C_from(hp_problem *P, const double *w, double *beta) {
   if (P->dim == 2)
-    k_build_C<2><<<grid_blocks(P->n), 256, 0, P->st>>>(P->lv[0].g, P->u, P->Cbeta);
+    k_build_C<2><<<grid_blocks(P->n), 256, 0, P->st>>>(P->lv[0].g, w, beta);
   else
-    k_build_C<3><<<grid_blocks(P->n), 256, 0, P->st>>>(P->lv[0].g, P->u, P->Cbeta);
+    k_build_C<3><<<grid_blocks(P->n), 256, 0, P->st>>>(P->lv[0].g, w, beta);
+  count_launch();
+}
+
+void launch_build_C(hp_problem *P) { launch_build_C_from(P, P->u, P->Cbeta); }
+
+void launch_C_apply_beta(hp_problem *P, const double *beta, const double *X, long ldx, double *Y, long ldy, int s,
+                         double scale, double yb) {
+  dim3 grid(blocks_for(P->n, s), s);
+  if (P->dim == 2)
+    k_C_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, beta, X, ldx, Y, ldy, scale, yb);
+  else
+    k_C_apply<3><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, beta, X, ldx, Y, ldy, scale, yb);
   count_launch();
 }
 
 void launch_C_apply(hp_problem *P, const double *X, long ldx, double *Y, long ldy, int s, double scale) {
+  launch_C_apply_beta(P, P->Cbeta, X, ldx, Y, ldy, s, scale, 0.0);
+}
+
+void launch_Ct_apply_beta(hp_problem *P, const double *beta_c, const double *W, long ldw, double *Y, long ldy, int s,
+                          double scale, double beta) {
   dim3 grid(blocks_for(P->n, s), s);
   if (P->dim == 2)
-    k_C_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, P->Cbeta, X, ldx, Y, ldy, scale);
+    k_Ct_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, beta_c, W, ldw, Y, ldy, scale, beta);
   else
-    k_C_apply<3><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, P->Cbeta, X, ldx, Y, ldy, scale);
+    k_Ct_apply<3><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, beta_c, W, ldw, Y, ldy, scale, beta);
   count_launch();
 }
 
 void launch_Ct_apply(hp_problem *P, const double *W, long ldw, double *Y, long ldy, int s, double scale,
                      double beta) {
-  dim3 grid(blocks_for(P->n, s), s);
-  if (P->dim == 2)
-    k_Ct_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, P->Cbeta, W, ldw, Y, ldy, scale, beta);
-  else
-    k_Ct_apply<3><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, P->Cbeta, W, ldw, Y, ldy, scale, beta);
-  count_launch();
+  launch_Ct_apply_beta(P, P->Cbeta, W, ldw, Y, ldy, s, scale, beta);
 }
 
 // ---------------------------------------------------------------------------

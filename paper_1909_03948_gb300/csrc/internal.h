@@ -108,6 +108,11 @@ struct hp_problem {
   bool have_point = false;
   double *m = nullptr, *E = nullptr, *u = nullptr, *lift = nullptr;
   double *Cbeta = nullptr;      // C as a stencil on e^m (.) X: (2^{D+1}-1) x n, built from u
+  // adjoint terms of the full Newton Hessian (built on demand at the current point)
+  double *padj = nullptr;       // adjoint p
+  double *Cbeta_p = nullptr;    // C(p): the same stencil built from p
+  double *wmm = nullptr;        // C(u)^T p: weights of the diagonal second-derivative term
+  bool have_p = false, have_full = false;
   // data
   double *m_prior = nullptr, *f_load = nullptr, *d_obs = nullptr;
   int nobs = 0;
@@ -177,6 +182,11 @@ void prof_spin(hp_problem *P);  // profiling only: keep the GPU busy while the h
 int build_hierarchy_geometry(hp_problem *P);  // levels, allocs, prior/mass stencils, coarse A inverse
 int build_point(hp_problem *P, const double *m_dev);  // E, kappa hierarchy, K stencils, lift, coarse K inverse
 void launch_build_C(hp_problem *P);  // after the state solve
+void launch_build_C_from(hp_problem *P, const double *w, double *beta);  // C(w) stencil of any nodal w
+void launch_C_apply_beta(hp_problem *P, const double *beta, const double *X, long ldx, double *Y, long ldy, int s,
+                         double scale, double yb);
+void launch_Ct_apply_beta(hp_problem *P, const double *beta_c, const double *W, long ldw, double *Y, long ldy, int s,
+                          double scale, double beta);
 void launch_C_apply(hp_problem *P, const double *X, long ldx, double *Y, long ldy, int s, double scale);
 void launch_Ct_apply(hp_problem *P, const double *W, long ldw, double *Y, long ldy, int s, double scale,
                      double beta);

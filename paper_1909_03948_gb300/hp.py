@@ -32,6 +32,7 @@ HP_FP64_PLAIN = 0
 HP_FP32_IR = 1
 HP_MISFIT_ONLY = 0
 HP_WITH_PRIOR = 1
+HP_FULL_NEWTON = 2
 
 
 class HPError(RuntimeError):
@@ -65,7 +66,8 @@ class Tuning(C.Structure):
 
 class NewtonOpts(C.Structure):
     _fields_ = [("rel_tol", C.c_double), ("abs_tol", C.c_double), ("max_iter", C.c_int),
-                ("max_backtrack", C.c_int), ("c_armijo", C.c_double), ("cg_max_iter", C.c_int)]
+                ("max_backtrack", C.c_int), ("c_armijo", C.c_double), ("cg_max_iter", C.c_int),
+                ("full_newton", C.c_int)]
 
 
 class NewtonStats(C.Structure):
@@ -347,12 +349,13 @@ class Problem:
         return {"recorded": r.value, "guesses": g.value, "fallbacks": f.value}
 
     # ---- Hessian / operators --------------------------------------------------
-    def hessian_apply(self, X, with_prior: bool = False, out=None):
+    def hessian_apply(self, X, with_prior: bool = False, out=None, full: bool = False):
+        """Gauss-Newton (default) or full (full=True: with the adjoint terms) Hessian action."""
         X2, s, n = _block(X, self.n, "X")
         Y = torch.empty_like(X2) if out is None else _block(out, self.n, "out")[0]
         st = SolveStats()
-        _check(lib().hp_hessian_apply(self._h, _dptr(X2), n, _dptr(Y), n, s,
-                                      HP_WITH_PRIOR if with_prior else HP_MISFIT_ONLY, C.byref(st)),
+        flags = (HP_WITH_PRIOR if with_prior else HP_MISFIT_ONLY) | (HP_FULL_NEWTON if full else 0)
+        _check(lib().hp_hessian_apply(self._h, _dptr(X2), n, _dptr(Y), n, s, flags, C.byref(st)),
                "hp_hessian_apply")
         return (Y.reshape(X.shape) if out is None else out), st.as_dict()
 
@@ -461,9 +464,9 @@ class Problem:
 
     # ---- algorithms --------------------------------------------------------------
     def newton_cg_map(self, m0=None, rel_tol=1e-6, abs_tol=0.0, max_iter=50, max_backtrack=10,
-                      c_armijo=1e-4, cg_max_iter=200):
+                      c_armijo=1e-4, cg_max_iter=200, full=False):
         m = self.zeros() if m0 is None else self._vec(m0, "m0").clone().reshape(-1)
-        o = NewtonOpts(rel_tol, abs_tol, max_iter, max_backtrack, c_armijo, cg_max_iter)
+        o = NewtonOpts(rel_tol, abs_tol, max_iter, max_backtrack, c_armijo, cg_max_iter, 1 if full else 0)
         st = NewtonStats()
         rc = lib().hp_newton_cg_map(self._h, _dptr(m), C.byref(o), C.byref(st))
         if rc not in (HP_OK, HP_ERR_NOT_CONVERGED):

@@ -47,6 +47,19 @@ def test_newton_map_matches_oracle(small2d, precision):
     assert abs(st["J"] - orc.cost(ref)[0]) <= 1e-8 * abs(st["J"])
 
 
+def test_full_newton_map_matches_oracle(small2d):
+    """Newton-CG with the full Hessian (Steihaug exit on negative curvature) reaches the
+    oracle's MAP point to relative 1e-6, in no more Newton iterations than Gauss-Newton."""
+    orc, w, P = small2d["orc"], small2d["w"], small2d["P"]
+    ref = small2d["res"]
+    m, st = P.newton_cg_map(rel_tol=1e-9, full=True)
+    assert st["converged"]
+    assert np.linalg.norm(m.cpu().numpy() - ref.m) <= 1e-6 * np.linalg.norm(ref.m)
+    ref_full = A.newton_cg(orc, rel_tol=1e-9, full=True)
+    assert ref_full.converged and st["iterations"] <= ref.iterations + 1
+    assert abs(st["iterations"] - ref_full.iterations) <= 1
+
+
 def test_newton_baseline_tolerance(small2d):
     """At the workload's relative gradient tolerance 1e-6 the GPU and the oracle take the
     same Newton path (same eta_i, same CG) to within one iteration."""

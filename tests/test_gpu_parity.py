@@ -163,6 +163,46 @@ def test_hessian_block(case, s, precision):
         P.set_point(torch.tensor(m, device=dev))
 
 
+@pytest.mark.parametrize("s", [1, 5])
+@pytest.mark.parametrize("precision", ["fp32_ir", "fp64"])
+def test_full_hessian_block(case, s, precision):
+    """Full Hessian (the adjoint terms of eqs. incrementals1-3) at a point with a nonzero
+    data residual, against the oracle, to the same 1e-7 as the Gauss-Newton action."""
+    P, orc, m, dev = case["P"], case["orc"], case["m"], case["dev"]
+    P.set_precision(precision)
+    try:
+        P.set_point(torch.tensor(m, device=dev))
+        u = case["u_ref"]
+        p = orc.adjoint(m, u)
+        X = W.random_block(orc.n, s, 50 + s)
+        Y, _ = P.hessian_apply(T(X, dev), full=True)
+        ref = orc.hessian_full_misfit(m, u, p, X)
+        assert _colrel(N_(Y).reshape(orc.n, s), ref) < 1e-7
+        Yp, _ = P.hessian_apply(T(X, dev), with_prior=True, full=True)
+        assert _colrel(N_(Yp).reshape(orc.n, s), ref + orc.R_apply(X)) < 1e-7
+    finally:
+        P.set_precision("fp32_ir")
+        P.set_point(torch.tensor(m, device=dev))
+
+
+def test_full_hessian_follows_new_data(case):
+    """The adjoint behind the full Hessian is recomputed after hp_set_data."""
+    P, orc, m, dev = case["P"], case["orc"], case["m"], case["dev"]
+    X = W.random_block(orc.n, 2, 61)
+    P.hessian_apply(T(X, dev), full=True)
+    d_old = orc.d_obs.copy()
+    d_new = d_old + 3.0 * orc.sigma * np.random.default_rng(62).standard_normal(d_old.shape)
+    try:
+        orc.d_obs = d_new
+        P.set_data(d_new, orc.sigma)
+        u = case["u_ref"]
+        Y, _ = P.hessian_apply(T(X, dev), full=True)
+        assert _colrel(N_(Y).reshape(orc.n, 2), orc.hessian_full_misfit(m, u, orc.adjoint(m, u), X)) < 1e-7
+    finally:
+        orc.d_obs = d_old
+        P.set_data(d_old, orc.sigma)
+
+
 def test_hessian_block_equals_single_columns(case):
     """A block of s actions equals s one-column actions (to solver tolerance)."""
     P, orc, dev = case["P"], case["orc"], case["dev"]
