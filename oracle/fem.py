@@ -100,6 +100,45 @@ class Mesh:
         vol, G = self.geometry
         return vol[:, None, None] * np.einsum("eak,ebk->eab", G, G)
 
+    def local_stiffness_tensor(self, Theta) -> np.ndarray:
+        """Element stiffness of -div(Theta grad): |e| G Theta G^T, shape (ne, d+1, d+1)."""
+        vol, G = self.geometry
+        Th = np.asarray(Theta, dtype=float).reshape(self.dim, self.dim)
+        return vol[:, None, None] * np.einsum("eak,kl,ebl->eab", G, Th, G)
+
+    def stiffness_tensor(self, Theta) -> sp.csr_matrix:
+        return self.assemble(self.local_stiffness_tensor(Theta))
+
+    @cached_property
+    def boundary_mass(self) -> sp.csr_matrix:
+        """P1 mass matrix of the boundary: sum over the element facets that lie on a face of
+        the unit square / cube of |f| (1 + delta_ab) / (d (d + 1)) (the facets are segments
+        in 2D and triangles in 3D)."""
+        el, X = self.elements, self.coords
+        d = self.dim
+        rows, cols, vals = [], [], []
+        base = (np.ones((d, d)) + np.eye(d)) / (d * (d + 1))
+        for drop in range(d + 1):
+            fv = np.delete(el, drop, axis=1)                     # (ne, d) facet vertices
+            P = X[fv]                                            # (ne, d, d)
+            on = np.zeros(len(fv), dtype=bool)
+            for a in range(d):
+                for side in (0.0, 1.0):
+                    on |= np.all(np.abs(P[:, :, a] - side) < 1e-12, axis=1)
+            if not on.any():
+                continue
+            Pf = P[on]
+            if d == 2:
+                meas = np.linalg.norm(Pf[:, 1] - Pf[:, 0], axis=1)
+            else:
+                meas = 0.5 * np.linalg.norm(np.cross(Pf[:, 1] - Pf[:, 0], Pf[:, 2] - Pf[:, 0]), axis=1)
+            f = fv[on]
+            rows.append(np.repeat(f, d, axis=1).ravel())
+            cols.append(np.tile(f, (1, d)).ravel())
+            vals.append((meas[:, None, None] * base[None]).ravel())
+        return sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                             shape=(self.n, self.n)).tocsr()
+
     def local_mass(self) -> np.ndarray:
         """Consistent element mass |e| (1 + delta_ab) / ((d+1)(d+2))."""
         vol, _ = self.geometry
@@ -207,3 +246,13 @@ class Mesh:
         """C_M as a dense (n, nelems*(d+1)) matrix (tiny meshes only)."""
         I = np.eye(self.nelems * (self.dim + 1))
         return self.mass_factor_apply(I)
+
+
+def rotated_theta(theta1: float, theta2: float, alpha: float) -> np.ndarray:
+    """2D anisotropy tensor with eigenvalues theta1, theta2 and the theta1-axis at angle alpha
+    from the x axis: R(alpha) diag(theta1, theta2) R(alpha)^T (the s.p.d. reading of the
+    printed tensor of Section 5.1.1)."""
+    c, s = np.cos(alpha), np.sin(alpha)
+    Rm = np.array([[c, -s], [s, c]])
+    return Rm @ np.diag([theta1, theta2]) @ Rm.T
+

@@ -6,8 +6,10 @@ mean of the nodal field E = e^m, kappa_e = (1/(d+1)) sum_{v in e} E_v, i.e. the
 exact integral of the P1 interpolant of e^m; this makes the discrete map
 exactly differentiable, with d kappa_e / d m_v = E_v / (d+1).
 
-Prior (Section 5.1.1, eq. (PoissonPrior); Section 2.3): C = A^{-2}, A = gamma*K(1) + delta*M with zero
-Neumann (Robin beta = 0) and Theta = I; discrete precision R = A M^{-1} A.
+Prior (Section 5.1.1, eq. (PoissonPrior); Section 2.3): C = A^{-2}, A = gamma*K(Theta) + delta*M
++ gamma*beta*M_boundary: the weak form of -gamma div(Theta grad m) + delta m with the Robin
+condition Theta grad m . n + beta m = 0.  Defaults Theta = I, beta = 0 (zero Neumann);
+discrete precision R = A M^{-1} A.
 
 Misfit (Section 5.1.1): B = P1 interpolation at q points, Gamma_noise = sigma^2 I.
 
@@ -33,7 +35,8 @@ class Problem:
     def __init__(self, mesh: Mesh, gamma: float, delta: float, obs_xyz: np.ndarray,
                  d_obs: np.ndarray | None, sigma: float, m_prior: np.ndarray | None = None,
                  f: np.ndarray | None = None, u_top: float = 1.0, u_bottom: float = 0.0,
-                 dirichlet_mask: np.ndarray | None = None, dirichlet_values: np.ndarray | None = None):
+                 dirichlet_mask: np.ndarray | None = None, dirichlet_values: np.ndarray | None = None,
+                 theta=None, robin_beta: float = 0.0):
         self.mesh = mesh
         self.n = mesh.n
         self.gamma, self.delta, self.sigma = float(gamma), float(delta), float(sigma)
@@ -48,10 +51,15 @@ class Problem:
         self.dmask = np.asarray(dirichlet_mask, dtype=bool)
         self.gD = np.where(self.dmask, dirichlet_values, 0.0)
         self.free = np.flatnonzero(~self.dmask)
-        # prior operator A = gamma K(1) + delta M (all nodes, zero Neumann)
-        self.K1 = mesh.stiffness(np.ones(mesh.nelems))
+        # prior operator A = gamma K(Theta) + delta M + gamma beta M_boundary (all nodes)
+        self.theta = np.eye(mesh.dim) if theta is None else np.asarray(theta, dtype=float)
+        self.robin_beta = float(robin_beta)
+        self.K1 = mesh.stiffness_tensor(self.theta)
         self.M = mesh.mass
-        self.A = (self.gamma * self.K1 + self.delta * self.M).tocsc()
+        A = self.gamma * self.K1 + self.delta * self.M
+        if self.robin_beta != 0.0:
+            A = A + self.gamma * self.robin_beta * mesh.boundary_mass
+        self.A = A.tocsc()
         self._A_lu = spla.splu(self.A)
         self._M_lu = spla.splu(self.M.tocsc())
         self._cache_key = None

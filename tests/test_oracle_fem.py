@@ -135,3 +135,41 @@ def test_observation_reproduces_linear_functions(dim):
     assert np.allclose(B @ f, coef[0] + pts @ coef[1:], atol=1e-13)
     assert np.allclose(np.asarray(B.sum(axis=1)).ravel(), 1.0)
     assert (B.data >= -1e-12).all()
+
+
+# ---- anisotropic stiffness and boundary mass (prior variants, Section 5.1.1) ----------
+@pytest.mark.parametrize("dim,N", [(2, 5), (3, 3)])
+def test_tensor_stiffness_reduces_to_unit_and_integrates_linear_energy(dim, N):
+    mesh = Mesh(dim, N)
+    assert abs(mesh.stiffness_tensor(np.eye(dim)) - mesh.stiffness(np.ones(mesh.nelems))).max() < 1e-15
+    rng = np.random.default_rng(dim)
+    L = rng.standard_normal((dim, dim))
+    Th = L @ L.T + 0.1 * np.eye(dim)                       # any s.p.d. tensor
+    K = mesh.stiffness_tensor(Th)
+    assert abs(K - K.T).max() < 1e-14
+    assert np.abs(K @ np.ones(mesh.n)).max() < 1e-13      # constants in the kernel
+    a = rng.standard_normal(dim)
+    x = mesh.coords @ a                                   # linear field: energy a^T Theta a |D|
+    assert np.isclose(x @ (K @ x), a @ Th @ a, rtol=1e-12)
+
+
+@pytest.mark.parametrize("dim,N,area,x2", [(2, 4, 4.0, 5.0 / 3.0), (3, 3, 6.0, 7.0 / 3.0)])
+def test_boundary_mass_closed_forms(dim, N, area, x2):
+    """1^T Mb 1 = |boundary|; x^T Mb x = integral of x^2 over the boundary (P1 exact for
+    products of linear functions): 2D 0 + 1 + 1/3 + 1/3, 3D 0 + 1 + 4/3."""
+    mesh = Mesh(dim, N)
+    Mb = mesh.boundary_mass
+    one = np.ones(mesh.n)
+    assert np.isclose(one @ (Mb @ one), area, rtol=1e-13)
+    x = mesh.coords[:, 0]
+    assert np.isclose(x @ (Mb @ x), x2, rtol=1e-13)
+    interior = np.all((mesh.coords > 1e-12) & (mesh.coords < 1 - 1e-12), axis=1)
+    assert abs(Mb[interior]).max() == 0.0
+
+
+def test_rotated_theta_is_spd_with_given_eigenpairs():
+    from oracle.fem import rotated_theta
+    Th = rotated_theta(2.0, 0.5, 0.3)
+    ev, V = np.linalg.eigh(Th)
+    assert np.allclose(ev, [0.5, 2.0])
+    assert np.isclose(abs(V[:, 1] @ np.array([np.cos(0.3), np.sin(0.3)])), 1.0)
