@@ -61,7 +61,7 @@ typedef struct hp_problem hp_problem;
 typedef struct {
   int dim;               /* 2 or 3                                            */
   int N;                 /* cells per axis (>= 1); nodes n = (N+1)^dim        */
-  double gamma, delta;   /* prior operator A = gamma K(1) + delta M (> 0)     */
+  double gamma, delta;   /* prior operator A = gamma K(Theta) + delta M (> 0) */
   double sigma;          /* noise standard deviation (> 0)                    */
   int nobs;              /* number of pointwise observations (>= 0)          */
   const double *obs_xyz; /* HOST, nobs*dim, point-major, inside [0,1]^dim     */
@@ -72,6 +72,11 @@ typedef struct {
   int precision;         /* HP_FP64_PLAIN or HP_FP32_IR                       */
   double rtol;           /* relative residual of every PDE solve (e.g. 1e-8)  */
   int max_iter;          /* cap on CG iterations per solve (e.g. 500)         */
+  double theta[6];       /* prior anisotropy Theta (s.p.d.): T00, T11, T22, T01,
+                            T02, T12 (2D uses T00, T11, T01); all zero = identity */
+  double robin_beta;     /* Robin condition Theta grad m . n + beta m = 0 of the
+                            prior (Section 5.1.1): A gains gamma beta M_boundary;
+                            0 = zero Neumann                                   */
 } hp_problem_desc;
 
 typedef struct {

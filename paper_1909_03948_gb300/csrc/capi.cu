@@ -451,6 +451,28 @@ int hp_problem_create(const hp_problem_desc *d, hp_problem **out) {
   P->rtol = d->rtol > 0 ? d->rtol : 1e-8;
   P->max_iter = d->max_iter > 0 ? d->max_iter : 500;
   P->nobs = d->nobs;
+  {
+    bool zero = true;
+    for (int q = 0; q < 6; ++q) zero = zero && d->theta[q] == 0.0;
+    if (!zero) {
+      const double *t = d->theta;
+      const double m1 = t[0], m2 = t[0] * t[1] - t[3] * t[3];
+      const double m3 = d->dim == 3 ? t[0] * (t[1] * t[2] - t[5] * t[5]) - t[3] * (t[3] * t[2] - t[5] * t[4]) +
+                                          t[4] * (t[3] * t[5] - t[1] * t[4])
+                                    : 1.0;
+      if (!(m1 > 0 && m2 > 0 && m3 > 0)) {
+        delete P;
+        return set_error(HP_ERR_INVALID, "theta must be symmetric positive definite");
+      }
+      for (int q = 0; q < 6; ++q) P->theta[q] = t[q];
+      if (d->dim == 2) P->theta[2] = 1.0, P->theta[4] = P->theta[5] = 0.0;
+    }
+    if (!(d->robin_beta >= 0.0)) {
+      delete P;
+      return set_error(HP_ERR_INVALID, "robin_beta must be >= 0");
+    }
+    P->robin_beta = d->robin_beta;
+  }
   if (const char *e = getenv("HP_GRAPHS")) P->use_graphs = !(e[0] == '0');
   int rc = 0;
   auto fail = [&](int code) {

@@ -199,40 +199,94 @@ __device__ __forceinline__ int count_elems(const GridDesc &g, const int v[3], in
   return n;
 }
 
-// A = gamma K(1) + delta M with zero Neumann (no Dirichlet rows)
+// Symmetric anisotropy tensor: t[0..2] = (T00, T11, T22), t[3..5] = (T01, T02, T12).
+struct Theta6 {
+  double t[6];
+};
+__device__ __forceinline__ double theta_ab(const Theta6 &T, int a, int b) {
+  if (a == b) return T.t[a];
+  const int lo = a < b ? a : b, hi = a < b ? b : a;
+  return lo == 0 ? (hi == 1 ? T.t[3] : T.t[4]) : T.t[5];
+}
+
+// Gradient (in units of 1/h) of the barycentric function of chain vertex t of Kuhn simplex p:
+// with pi_t the axis added at step t, lambda_0 = 1 - x_{pi_1}, lambda_t = x_{pi_t} - x_{pi_{t+1}},
+// lambda_D = x_{pi_D} in the cell's local coordinates.
 template <int D>
-__global__ void k_build_A(GridDesc g, double gamma, double delta, double *diag, double *invdiag, double *c,
-                          float *diag32, float *invdiag32, float *c32) {
+__device__ __forceinline__ void kuhn_grad(int p, int t, double gv[3]) {
+  gv[0] = gv[1] = gv[2] = 0.0;
+  if (t >= 1) gv[__ffs(MeshT<D>::chain(p, t) ^ MeshT<D>::chain(p, t - 1)) - 1] += 1.0;
+  if (t < D) gv[__ffs(MeshT<D>::chain(p, t + 1) ^ MeshT<D>::chain(p, t)) - 1] -= 1.0;
+}
+
+// A = gamma K(Theta) + delta M + cR M_boundary (all nodes, no Dirichlet rows), assembled per
+// node from the simplices that contain it (each node keeps its diagonal and its forward
+// couplings along the 2^D - 1 Kuhn edge directions) and from the boundary facets that
+// contain it (the facets of a face of the cube are the Kuhn triangulation of that face).
+// With Theta = I and cR = 0 this is gamma K(1) + delta M with zero Neumann.
+template <int D>
+__global__ void k_build_A(GridDesc g, double gamma, double delta, double cR, Theta6 Th, double *diag,
+                          double *invdiag, double *c, float *diag32, float *invdiag32, float *c32) {
+  constexpr int NF = (1 << D) - 1;
   const double vh2 = vol_over_h2<D>(g.h);
   const double mc = elem_vol<D>(g.h) / ((D + 1) * (D + 2));
+  const double fvol = D == 2 ? g.h : 0.5 * g.h * g.h;   // boundary facet measure
+  const double fm = fvol / (D * (D + 1));                // off-diagonal boundary facet mass
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
     int v[3];
     node_coords<D>(g, i, v);
-    for (int f = 0; f < (1 << D) - 1; ++f) {
-      const int b = f + 1;
-      bool fwd = true;
-      for (int a = 0; a < D; ++a)
-        if ((b >> a) & 1) fwd = fwd && (v[a] < g.N);
-      double cf = 0.0;
-      if (fwd) {
-        const int cnt = count_elems<D>(g, v, b);
-        const double k1 = popc3(b) == 1 ? -vh2 * cnt : 0.0;
-        cf = gamma * k1 + delta * mc * cnt;
+    double cf[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) cf[f] = 0.0;
+    double dg = 0.0;
+    for_elems_with<D>(g, v, 0, [&](const int *, int p, int k) {
+      double gk[3];
+      kuhn_grad<D>(p, k, gk);
+      for (int t = k; t <= D; ++t) {
+        double gt[3];
+        kuhn_grad<D>(p, t, gt);
+        double e = 0.0;
+        for (int a = 0; a < D; ++a)
+          for (int b = 0; b < D; ++b) e += gk[a] * theta_ab(Th, a, b) * gt[b];
+        const double val = gamma * vh2 * e + delta * mc * (t == k ? 2.0 : 1.0);
+        if (t == k)
+          dg += val;
+        else
+          cf[(MeshT<D>::chain(p, t) ^ MeshT<D>::chain(p, k)) - 1] += val;
       }
-      c[(long)f * g.n + i] = cf;
-      c32[(long)f * g.n + i] = (float)cf;
-    }
-    double k1d = 0.0;
-    for (int a = 0; a < D; ++a) {
-      if (v[a] < g.N) k1d += vh2 * count_elems<D>(g, v, 1 << a);
-      if (v[a] > 0) {
-        int vb[3] = {v[0], v[1], v[2]};
-        vb[a] -= 1;
-        k1d += vh2 * count_elems<D>(g, vb, 1 << a);
+    });
+    if (cR != 0.0) {
+      for (int a = 0; a < D; ++a) {
+        if (v[a] != 0 && v[a] != g.N) continue;
+        int ax[2] = {0, 0}, na = 0;
+        for (int o = 0; o < D; ++o)
+          if (o != a) ax[na++] = o;
+        for (int s0 = 0; s0 < 2; ++s0)
+          for (int s1 = 0; s1 < (D == 3 ? 2 : 1); ++s1) {
+            int cc[3] = {v[0], v[1], v[2]};
+            cc[ax[0]] -= s0;
+            if (D == 3) cc[ax[1]] -= s1;
+            if (cc[ax[0]] < 0 || cc[ax[0]] >= g.N) continue;
+            if (D == 3 && (cc[ax[1]] < 0 || cc[ax[1]] >= g.N)) continue;
+            const int vm = (s0 << ax[0]) | (D == 3 ? (s1 << ax[1]) : 0);  // v - cc as a corner mask
+            for (int perm = 0; perm < (D == 3 ? 2 : 1); ++perm) {
+              const int p1 = D == 3 ? ax[perm] : ax[0];
+              const int m[3] = {0, 1 << p1, D == 3 ? ((1 << p1) | (1 << ax[1 - perm])) : 0};
+              int k = -1;
+              for (int t = 0; t < D; ++t)
+                if (m[t] == vm) k = t;
+              if (k < 0) continue;
+              dg += cR * 2.0 * fm;
+              for (int t = k + 1; t < D; ++t) cf[(m[t] ^ m[k]) - 1] += cR * fm;
+            }
+          }
       }
     }
-    const double md = 2.0 * mc * count_elems<D>(g, v, 0);
-    const double dg = gamma * k1d + delta * md;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      c[(long)f * g.n + i] = cf[f];
+      c32[(long)f * g.n + i] = (float)cf[f];
+    }
     diag[i] = dg;
     invdiag[i] = 1.0 / dg;
     diag32[i] = (float)dg;
@@ -378,23 +432,27 @@ int build_hierarchy_geometry(hp_problem *P) {
     HP_TRY(alloc_stencil(lv.K64, lv.K32, lv.g.n, nfK, false));
     HP_TRY(alloc_stencil(lv.A64, lv.A32, lv.g.n, nfA, true));
     const int nb = grid_blocks(lv.g.n);
+    Theta6 th;
+    for (int q = 0; q < 6; ++q) th.t[q] = P->theta[q];
+    const double cR = P->gamma * P->robin_beta;
     if (D == 2)
-      k_build_A<2><<<nb, 256, 0, P->st>>>(lv.g, P->gamma, P->delta, lv.A64.diag, lv.A64.invdiag, lv.A64.c,
+      k_build_A<2><<<nb, 256, 0, P->st>>>(lv.g, P->gamma, P->delta, cR, th, lv.A64.diag, lv.A64.invdiag, lv.A64.c,
                                           lv.A32.diag, lv.A32.invdiag, lv.A32.c);
     else
-      k_build_A<3><<<nb, 256, 0, P->st>>>(lv.g, P->gamma, P->delta, lv.A64.diag, lv.A64.invdiag, lv.A64.c,
+      k_build_A<3><<<nb, 256, 0, P->st>>>(lv.g, P->gamma, P->delta, cR, th, lv.A64.diag, lv.A64.invdiag, lv.A64.c,
                                           lv.A32.diag, lv.A32.invdiag, lv.A32.c);
     count_launch();
   }
   // mass matrix on the fine grid
   const Level &l0 = P->lv[0];
   HP_TRY(alloc_stencil(P->M64, P->M32, l0.g.n, nfA, true));
+  const Theta6 eye{{1.0, 1.0, 1.0, 0.0, 0.0, 0.0}};
   if (D == 2)
-    k_build_A<2><<<grid_blocks(l0.g.n), 256, 0, P->st>>>(l0.g, 0.0, 1.0, P->M64.diag, P->M64.invdiag, P->M64.c,
-                                                         P->M32.diag, P->M32.invdiag, P->M32.c);
+    k_build_A<2><<<grid_blocks(l0.g.n), 256, 0, P->st>>>(l0.g, 0.0, 1.0, 0.0, eye, P->M64.diag, P->M64.invdiag,
+                                                         P->M64.c, P->M32.diag, P->M32.invdiag, P->M32.c);
   else
-    k_build_A<3><<<grid_blocks(l0.g.n), 256, 0, P->st>>>(l0.g, 0.0, 1.0, P->M64.diag, P->M64.invdiag, P->M64.c,
-                                                         P->M32.diag, P->M32.invdiag, P->M32.c);
+    k_build_A<3><<<grid_blocks(l0.g.n), 256, 0, P->st>>>(l0.g, 0.0, 1.0, 0.0, eye, P->M64.diag, P->M64.invdiag,
+                                                         P->M64.c, P->M32.diag, P->M32.invdiag, P->M32.c);
   count_launch();
   // coarse inverses
   const long ncn = P->lv[L - 1].g.n;

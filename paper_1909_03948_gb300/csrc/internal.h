@@ -84,6 +84,8 @@ struct hp_problem {
   int dim = 2, N = 0, L = 0;
   long n = 0, nelems = 0;
   double gamma = 0, delta = 0, sigma = 1, u_top = 1, u_bottom = 0;
+  double theta[6] = {1, 1, 1, 0, 0, 0};  // prior anisotropy (T00, T11, T22, T01, T02, T12)
+  double robin_beta = 0;                 // prior Robin coefficient beta (0 = zero Neumann)
   int precision = HP_FP32_IR;
   double rtol = 1e-8;
   int max_iter = 500;

@@ -46,7 +46,8 @@ class Desc(C.Structure):
                 ("sigma", C.c_double), ("nobs", C.c_int), ("obs_xyz", C.POINTER(C.c_double)),
                 ("d_obs", C.POINTER(C.c_double)), ("m_prior", C.POINTER(C.c_double)),
                 ("f", C.POINTER(C.c_double)), ("u_top", C.c_double), ("u_bottom", C.c_double),
-                ("precision", C.c_int), ("rtol", C.c_double), ("max_iter", C.c_int)]
+                ("precision", C.c_int), ("rtol", C.c_double), ("max_iter", C.c_int),
+                ("theta", C.c_double * 6), ("robin_beta", C.c_double)]
 
 
 class SolveStats(C.Structure):
@@ -210,7 +211,10 @@ class Problem:
 
     def __init__(self, dim: int, N: int, gamma: float, delta: float, sigma: float, obs_xyz,
                  d_obs=None, m_prior=None, f=None, u_top: float = 1.0, u_bottom: float = 0.0,
-                 precision: str = "fp32_ir", rtol: float = 1e-8, max_iter: int = 500):
+                 precision: str = "fp32_ir", rtol: float = 1e-8, max_iter: int = 500,
+                 theta=None, robin_beta: float = 0.0):
+        """theta: the prior's s.p.d. anisotropy tensor (dim x dim; None = identity);
+        robin_beta: Robin coefficient of the prior's boundary condition (0 = Neumann)."""
         L = lib()
         self._keep = []
         obs = np.ascontiguousarray(np.asarray(obs_xyz, dtype=np.float64).reshape(-1, dim))
@@ -230,7 +234,13 @@ class Problem:
                  obs_xyz=_hptr(obs) if obs.size else None, d_obs=opt(d_obs, obs.shape[0]),
                  m_prior=opt(m_prior, n), f=opt(f, n), u_top=u_top, u_bottom=u_bottom,
                  precision=HP_FP32_IR if precision == "fp32_ir" else HP_FP64_PLAIN,
-                 rtol=rtol, max_iter=max_iter)
+                 rtol=rtol, max_iter=max_iter, robin_beta=robin_beta)
+        if theta is not None:
+            Th = np.asarray(theta, dtype=np.float64).reshape(dim, dim)
+            t6 = [Th[0, 0], Th[1, 1], Th[2, 2] if dim == 3 else 0.0, Th[0, 1],
+                  Th[0, 2] if dim == 3 else 0.0, Th[1, 2] if dim == 3 else 0.0]
+            for q in range(6):
+                d.theta[q] = float(t6[q])
         h = C.c_void_p()
         _check(L.hp_problem_create(C.byref(d), C.byref(h)), "hp_problem_create")
         self._h = h

@@ -49,15 +49,18 @@ def test_newton_map_matches_oracle(small2d, precision):
 
 def test_full_newton_map_matches_oracle(small2d):
     """Newton-CG with the full Hessian (Steihaug exit on negative curvature) reaches the
-    oracle's MAP point to relative 1e-6, in no more Newton iterations than Gauss-Newton."""
+    oracle's full-Newton MAP point to relative 1e-6 in the same number of Newton iterations
+    (give or take one), fewer than Gauss-Newton needs.  The reference is the oracle's
+    full-Newton run: it converges quadratically, so at relative gradient 1e-9 it is within
+    ~1e-8 of the exact MAP, while the Gauss-Newton run stops ~1.6e-6 away from it."""
     orc, w, P = small2d["orc"], small2d["w"], small2d["P"]
-    ref = small2d["res"]
     m, st = P.newton_cg_map(rel_tol=1e-9, full=True)
     assert st["converged"]
-    assert np.linalg.norm(m.cpu().numpy() - ref.m) <= 1e-6 * np.linalg.norm(ref.m)
     ref_full = A.newton_cg(orc, rel_tol=1e-9, full=True)
-    assert ref_full.converged and st["iterations"] <= ref.iterations + 1
+    assert ref_full.converged
+    assert np.linalg.norm(m.cpu().numpy() - ref_full.m) <= 1e-6 * np.linalg.norm(ref_full.m)
     assert abs(st["iterations"] - ref_full.iterations) <= 1
+    assert st["iterations"] < small2d["res"].iterations
 
 
 def test_newton_baseline_tolerance(small2d):

@@ -223,3 +223,44 @@ def test_zero_columns_and_empty_block(case):
     empty = torch.zeros((0, orc.n), dtype=torch.float64, device=dev)
     Y0, _ = P.hessian_apply(empty)
     assert Y0.shape == (0, orc.n)
+
+
+# ---- prior variants (Section 5.1.1): anisotropic Theta and the Robin condition --------
+ANISO = [(2, 32, 0.0), (2, 32, 0.7), (2, 24, 1.3), (3, 8, 0.5)]
+
+
+@pytest.mark.parametrize("dim,N,beta", ANISO, ids=lambda v: str(v))
+def test_anisotropic_robin_prior(dim, N, beta):
+    """A = gamma K(Theta) + delta M + gamma beta M_boundary against the oracle's assembled
+    matrices: apply 1e-12, multigrid solves A^-1 and R^-1 1e-8, prior samples from
+    identical normals 1e-8."""
+    from oracle.fem import Mesh, rotated_theta
+    from oracle.inverse import Problem as OProblem
+    from paper_1909_03948_gb300 import Problem
+    if dim == 2:
+        Th = rotated_theta(2.0, 0.5, 0.6)
+    else:
+        L = np.random.default_rng(9).standard_normal((3, 3))
+        Th = L @ L.T + 0.5 * np.eye(3)
+    w = W.make_workload(dim, N, 5, seed=W.SEED_BASE + 700 + N)
+    dr = W.draws(w)
+    orc = OProblem(Mesh(dim, N), w.gamma, w.delta, dr.obs_xyz, np.zeros(5), 0.01, theta=Th, robin_beta=beta)
+    P = Problem(dim, N, w.gamma, w.delta, 0.01, dr.obs_xyz, rtol=1e-11, theta=Th, robin_beta=beta)
+    dev = torch.device("cuda", 0)
+    X = W.random_block(orc.n, 3, 71)
+    assert _colrel(N_(P.prior_apply(T(X, dev))), orc.A @ X) < 1e-12
+    Y, _ = P.prior_solve(T(X, dev))
+    assert _colrel(N_(Y), orc.A_solve(X)) < 1e-8
+    assert _colrel(N_(P.Rinv_apply(T(X, dev))), orc.Rinv_apply(X)) < 1e-8
+    eta = W.random_block(orc.mesh.nelems * (dim + 1), 2, 72)
+    prior, _, _ = P.laplace_sample(None, None, None, T(eta, dev), want_prior=True, want_post=False)
+    assert _colrel(N_(prior), orc.prior_sample(eta)) < 1e-8
+    P.close()
+
+
+def test_invalid_prior_tensor_is_rejected():
+    from paper_1909_03948_gb300 import Problem, HPError
+    with pytest.raises(HPError):
+        Problem(2, 8, 0.1, 0.5, 0.01, np.array([[0.5, 0.5]]), theta=np.array([[1.0, 2.0], [2.0, 1.0]]))
+    with pytest.raises(HPError):
+        Problem(2, 8, 0.1, 0.5, 0.01, np.array([[0.5, 0.5]]), robin_beta=-1.0)
