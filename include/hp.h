@@ -292,13 +292,19 @@ int hp_pointwise_variance(hp_problem *P, int method, const double *Z_dev, int ld
  * Knobs of the PDE solver (no counterpart in the paper): nu damped-Jacobi sweeps
  * before and after each coarse correction and damping omega, the number of RHS
  * columns solved together (0 = all), and the grid-size cap of the node kernels.
- * Defaults: nu 2, omega 0.7, col_chunk 0, max_blocks 2048, fuse_from 0.  Every
- * setting solves to the same tolerance; only speed changes. */
+ * Defaults: nu 3, omega 0.7, col_chunk 0, max_blocks 2048, smoother 1
+ * (Chebyshev), cheb_alpha 10, fuse_from 0.  Every setting solves to the same
+ * tolerance; only speed changes. */
 typedef struct {
   int nu;          /* 1..4 */
   double omega;    /* (0, 1) */
   int col_chunk;   /* >= 0 */
   int max_blocks;  /* >= 64 */
+  int smoother;    /* 0 damped Jacobi with omega; 1 Chebyshev: sweep k uses the
+                      reciprocal of root k of the degree-nu Chebyshev polynomial on
+                      [lmax / cheb_alpha, lmax] (lmax: Gershgorin bound of D^-1 S on
+                      each level), post-smoothing in reverse order */
+  double cheb_alpha; /* > 1 */
   int fuse_from;   /* 0 = off, else the first multigrid level (>= 1) whose whole
                       coarse tail of the V-cycle runs as one launch: one thread-block
                       cluster of 8 CTAs per column group, steps separated by the

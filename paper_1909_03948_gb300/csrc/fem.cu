@@ -294,6 +294,53 @@ __global__ void k_build_A(GridDesc g, double gamma, double delta, double cR, The
   }
 }
 
+// max over nodes of (diag_i + sum_j |s_ij|) / diag_i: a bound of the spectrum of diag^-1 S
+template <int D>
+__global__ void k_gersh(GridDesc g, const double *__restrict__ diag, const double *__restrict__ c, int nf, bool full,
+                        unsigned long long *out) {
+  double mx = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
+    int v[3];
+    node_coords<D>(g, i, v);
+    double sum = fabs(diag[i]);
+    for (int f = 0; f < nf; ++f) {
+      const int b = full ? f + 1 : (1 << f);
+      bool fw = true, bw = true;
+      for (int a = 0; a < D; ++a)
+        if ((b >> a) & 1) {
+          fw = fw && (v[a] < g.N);
+          bw = bw && (v[a] > 0);
+        }
+      const long off = mask_offset(g, b);
+      if (fw) sum += fabs(c[(long)f * g.n + i]);
+      if (bw) sum += fabs(c[(long)f * g.n + i - off]);
+    }
+    mx = fmax(mx, sum / diag[i]);
+  }
+  // positive doubles order like their bit patterns
+  atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
+int gershgorin_bound(hp_problem *P, const GridDesc &g, const Stencil<double> &S, double *out) {
+  unsigned long long *d = reinterpret_cast<unsigned long long *>(P->sc.tmp.p);
+  HP_TRY(P->sc.tmp.ensure(64));
+  d = reinterpret_cast<unsigned long long *>(P->sc.tmp.p);
+  HP_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long), P->st));
+  const int nb = (int)std::min<long>((g.n + 255) / 256, 1024);
+  if (g.dim == 2)
+    k_gersh<2><<<nb, 256, 0, P->st>>>(g, S.diag, S.c, S.nf, S.full, d);
+  else
+    k_gersh<3><<<nb, 256, 0, P->st>>>(g, S.diag, S.c, S.nf, S.full, d);
+  count_launch();
+  unsigned long long h = 0;
+  HP_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, P->st));
+  HP_CUDA(cudaStreamSynchronize(P->st));
+  double v;
+  std::memcpy(&v, &h, sizeof(v));
+  *out = v;
+  return 0;
+}
+
 // ---------------------------------------------------------------------------
 // dense coarse-grid inverse
 // ---------------------------------------------------------------------------
@@ -463,6 +510,11 @@ int build_hierarchy_geometry(hp_problem *P) {
     HP_CUDA(cudaMalloc(&C->inv32, sizeof(float) * ncn * ncn));
   }
   HP_TRY(coarse_setup(P, OP_A));
+  for (int l = 0; l < L; ++l) {
+    double b = 2.0;
+    HP_TRY(gershgorin_bound(P, P->lv[l].g, P->lv[l].A64, &b));
+    P->lv[l].A64.lmax = P->lv[l].A32.lmax = b;
+  }
   return 0;
 }
 

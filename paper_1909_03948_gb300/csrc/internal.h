@@ -23,6 +23,7 @@ template <typename T> struct Stencil {
   T *c = nullptr;
   int nf = 0;
   bool full = false;
+  double lmax = 2.0;  // upper bound of the spectrum of diag^-1 S (Gershgorin)
 };
 
 struct Level {
@@ -91,11 +92,13 @@ struct hp_problem {
   int max_iter = 500;
   double inner_rtol = 1e-5;     // FP32 inner tolerance of the refinement
   int max_outer = 12;
-  int nu = 2;                   // pre/post Jacobi sweeps            (tuning)
+  int nu = 3;                   // pre/post smoothing sweeps         (tuning)
   double omega = 0.7;           // Jacobi damping                     (tuning)
   int col_chunk = 0;            // RHS columns per solve, 0 = all     (tuning)
   long max_blocks = 2048;       // grid cap of the node kernels       (tuning)
   int fuse_from = 0;            // first multigrid level of the fused coarse tail, 0 = none (tuning)
+  int smoother = 1;             // 0 damped Jacobi (omega), 1 Chebyshev (cheb_alpha)   (tuning)
+  double cheb_alpha = 10.0;     // Chebyshev interval [lmax / alpha, lmax]             (tuning)
   cudaStream_t st = nullptr;
   cudaStream_t cap = nullptr;   // private stream used to capture CUDA graphs
   bool use_graphs = true;       // inner PCG loops as graphs with a device-side while node
@@ -204,6 +207,8 @@ template <typename T>
 void launch_stencil_apply(const hp_problem *P, const GridDesc &g, const Stencil<T> &S, const T *X, long ldx,
                           T *Y, long ldy, int s, cudaStream_t st);
 int coarse_setup(hp_problem *P, hp::OpKind op);
+// Gershgorin bound of the spectrum of diag^-1 S for a level stencil (host value, synchronises)
+int gershgorin_bound(hp_problem *P, const GridDesc &g, const Stencil<double> &S, double *out);
 
 // ---- vec.cu ---------------------------------------------------------------
 void launch_copy(const double *X, long ldx, double *Y, long ldy, long n, int s, cudaStream_t st);

@@ -4,7 +4,8 @@
 // Every PDE solve of the method (state, adjoint, incremental forward /
 // adjoint, prior A, mass M) goes through solve_block(): s columns at once.
 //   * Inner solver: PCG in T (float for HP_FP32_IR, double for HP_FP64_PLAIN)
-//     with a symmetric V-cycle preconditioner (damped Jacobi smoothing, P1
+//     with a symmetric V-cycle preconditioner (polynomial smoothing: Chebyshev
+//     weights on [lmax / alpha, lmax] by default, or damped Jacobi; P1
 //     interpolation / its transpose, Galerkin coarse operators, dense coarse
 //     inverse) -- or diagonal scaling for the mass matrix.  alpha, beta and
 //     the per-column convergence flags live on the device; converged columns
@@ -160,7 +161,7 @@ template <typename T, int VW, int D, bool FULL, int MODE>
 __global__ void __launch_bounds__(NB) k_st(GridDesc g, const T *__restrict__ diag, const T *__restrict__ invdiag,
                                            const T *__restrict__ c, const T *__restrict__ X, long gx,
                                            const T *__restrict__ B, long gb, T *__restrict__ Y, long gy, int s,
-                                           T omega, Fin fin) {
+                                           T omega, T omega2, Fin fin) {
   using PK = Pack<T, VW>;
   const int lane = threadIdx.x & 31;
   const int i0 = blockIdx.x * 32 + lane;
@@ -176,8 +177,8 @@ __global__ void __launch_bounds__(NB) k_st(GridDesc g, const T *__restrict__ dia
     constexpr int NF = FULL ? (1 << D) - 1 : D;
     PK out;
     if (MODE == M_JAC2) {
-      // two damped-Jacobi sweeps from zero: e1 = w D^-1 r, e2 = e1 + w D^-1 (r - S e1)
-      const T wi = omega * invdiag[id];
+      // two damped-Jacobi sweeps from zero: e1 = w1 D^-1 r, e2 = e1 + w2 D^-1 (r - S e1)
+      const T wi = omega * invdiag[id], wi2 = omega2 * invdiag[id];
       const PK r = PK::ld(x + id * VW);
       PK e1c;
 #pragma unroll
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(NB) k_st(GridDesc g, const T *__restrict__ dia
         if (bw) sx.axpy(c[(long)f * g.n + id - off] * omega * invdiag[id - off], PK::ld(x + (id - off) * VW));
       }
 #pragma unroll
-      for (int q = 0; q < VW; ++q) out.v[q] = e1c.v[q] + wi * (r.v[q] - sx.v[q]);
+      for (int q = 0; q < VW; ++q) out.v[q] = e1c.v[q] + wi2 * (r.v[q] - sx.v[q]);
     } else {
       const PK xc = PK::ld(x + id * VW);
       PK sx;
@@ -577,19 +578,23 @@ static long rowgrid_blocks(const GridDesc &g) {
 
 template <typename T, int VW, int MODE>
 static void st_launch(const GridDesc &g, const Stencil<T> &S, const T *X, long gx, const T *B, long gb, T *Y, long gy,
-                      int s, T omega, const Fin &fin, cudaStream_t st) {
+                      int s, T omega, const Fin &fin, cudaStream_t st, T omega2 = T(0)) {
   const int ng = (s + VW - 1) / VW;
   const dim3 grid = rowgrid_capped(g, ng);
   if (g.dim == 2) {
     if (S.full)
-      k_st<T, VW, 2, true, MODE><<<grid, NB, 0, st>>>(g, S.diag, S.invdiag, S.c, X, gx, B, gb, Y, gy, s, omega, fin);
+      k_st<T, VW, 2, true, MODE><<<grid, NB, 0, st>>>(g, S.diag, S.invdiag, S.c, X, gx, B, gb, Y, gy, s, omega,
+                                                     omega2, fin);
     else
-      k_st<T, VW, 2, false, MODE><<<grid, NB, 0, st>>>(g, S.diag, S.invdiag, S.c, X, gx, B, gb, Y, gy, s, omega, fin);
+      k_st<T, VW, 2, false, MODE><<<grid, NB, 0, st>>>(g, S.diag, S.invdiag, S.c, X, gx, B, gb, Y, gy, s, omega,
+                                                     omega2, fin);
   } else {
     if (S.full)
-      k_st<T, VW, 3, true, MODE><<<grid, NB, 0, st>>>(g, S.diag, S.invdiag, S.c, X, gx, B, gb, Y, gy, s, omega, fin);
+      k_st<T, VW, 3, true, MODE><<<grid, NB, 0, st>>>(g, S.diag, S.invdiag, S.c, X, gx, B, gb, Y, gy, s, omega,
+                                                     omega2, fin);
     else
-      k_st<T, VW, 3, false, MODE><<<grid, NB, 0, st>>>(g, S.diag, S.invdiag, S.c, X, gx, B, gb, Y, gy, s, omega, fin);
+      k_st<T, VW, 3, false, MODE><<<grid, NB, 0, st>>>(g, S.diag, S.invdiag, S.c, X, gx, B, gb, Y, gy, s, omega,
+                                                     omega2, fin);
   }
   count_launch();
   if (MODE == M_APPLY_DOT || MODE == M_JACOBI_DOT) dot_finalize(fin, grid.x * grid.y, s, st);
@@ -724,6 +729,7 @@ constexpr int VC_NT = 512;   // threads per CTA
 template <typename T> struct VTail {
   int l0, L, nu, full, zero_dirichlet, nc;
   T omega;
+  T w[HP_MAXL][4];  // smoothing weights per level and sweep
   GridDesc g[HP_MAXL];
   const T *diag[HP_MAXL], *invdiag[HP_MAXL], *c[HP_MAXL];
   T *rl[HP_MAXL], *ea[HP_MAXL], *eb[HP_MAXL];
@@ -789,12 +795,11 @@ __global__ void __launch_bounds__(VC_NT) k_vcycle_tail(VTail<T> vt) {
   asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
   const int grp = blockIdx.y;
   const long gt = (long)rank * VC_NT + threadIdx.x, gstride = (long)ncta * VC_NT;
-  const T om = vt.omega;
   T *cur[HP_MAXL], *oth[HP_MAXL];
 
-  // one damped-Jacobi-type node step over level l: mode 0 two sweeps from zero (rhs in),
-  // 1 one sweep from zero, 2 sweep (x in, rhs b), 3 residual b - S x
-  auto sweep = [&](int l, int mode, const T *x, const T *b, T *y) {
+  // one damped-Jacobi-type node step over level l: mode 0 two sweeps from zero (rhs in,
+  // weights w1, w2), 1 one sweep from zero (w1), 2 sweep (x in, rhs b, w1), 3 residual b - S x
+  auto sweep = [&](int l, int mode, const T *x, const T *b, T *y, T w1, T w2) {
     const GridDesc &g = vt.g[l];
     const long gs = vt.gs[l];
     const T *xg = x + grp * gs, *bg = b ? b + grp * gs : nullptr;
@@ -804,29 +809,29 @@ __global__ void __launch_bounds__(VC_NT) k_vcycle_tail(VTail<T> vt) {
       vt_coords<D>(g, id, v);
       PK out;
       if (mode == 0) {
-        // two sweeps from zero: e1 = w D^-1 r, e2 = e1 + w D^-1 (r - S e1)
-        const T wi = om * vt.invdiag[l][id];
+        // two sweeps from zero: e1 = w1 D^-1 r, e2 = e1 + w2 D^-1 (r - S e1)
+        const T wi = w1 * vt.invdiag[l][id], wi2 = w2 * vt.invdiag[l][id];
         const PK r = PK::ld(xg + id * VW);
         PK e1c;
 #pragma unroll
         for (int q = 0; q < VW; ++q) e1c.v[q] = wi * r.v[q];
-        const PK sx = vt_apply<T, VW, D, FULL, true>(g, vt.diag[l], vt.invdiag[l], vt.c[l], xg, id, v, om, e1c);
+        const PK sx = vt_apply<T, VW, D, FULL, true>(g, vt.diag[l], vt.invdiag[l], vt.c[l], xg, id, v, w1, e1c);
 #pragma unroll
-        for (int q = 0; q < VW; ++q) out.v[q] = e1c.v[q] + wi * (r.v[q] - sx.v[q]);
+        for (int q = 0; q < VW; ++q) out.v[q] = e1c.v[q] + wi2 * (r.v[q] - sx.v[q]);
       } else if (mode == 1) {
-        const T wi = om * vt.invdiag[l][id];
+        const T wi = w1 * vt.invdiag[l][id];
         const PK r = PK::ld(xg + id * VW);
 #pragma unroll
         for (int q = 0; q < VW; ++q) out.v[q] = wi * r.v[q];
       } else {
         const PK xc = PK::ld(xg + id * VW);
-        const PK sx = vt_apply<T, VW, D, FULL, false>(g, vt.diag[l], vt.invdiag[l], vt.c[l], xg, id, v, om, xc);
+        const PK sx = vt_apply<T, VW, D, FULL, false>(g, vt.diag[l], vt.invdiag[l], vt.c[l], xg, id, v, T(0), xc);
         const PK bb = PK::ld(bg + id * VW);
         if (mode == 3) {
 #pragma unroll
           for (int q = 0; q < VW; ++q) out.v[q] = bb.v[q] - sx.v[q];
         } else {
-          const T wi = om * vt.invdiag[l][id];
+          const T wi = w1 * vt.invdiag[l][id];
 #pragma unroll
           for (int q = 0; q < VW; ++q) out.v[q] = xc.v[q] + wi * (bb.v[q] - sx.v[q]);
         }
@@ -837,14 +842,14 @@ __global__ void __launch_bounds__(VC_NT) k_vcycle_tail(VTail<T> vt) {
 
   for (int l = vt.l0; l + 1 < vt.L; ++l) {
     T *c = vt.nu >= 2 ? vt.ea[l] : vt.eb[l], *o = vt.nu >= 2 ? vt.eb[l] : vt.ea[l];
-    sweep(l, vt.nu >= 2 ? 0 : 1, vt.rl[l], nullptr, c);
+    sweep(l, vt.nu >= 2 ? 0 : 1, vt.rl[l], nullptr, c, vt.w[l][0], vt.w[l][1]);
     cluster_barrier();
     for (int k = 2; k < vt.nu; ++k) {
-      sweep(l, 2, c, vt.rl[l], o);
+      sweep(l, 2, c, vt.rl[l], o, vt.w[l][k], T(0));
       cluster_barrier();
       T *t = c; c = o; o = t;
     }
-    sweep(l, 3, c, vt.rl[l], o);
+    sweep(l, 3, c, vt.rl[l], o, T(0), T(0));
     cluster_barrier();
     // restriction to level l + 1 (transpose of the P1 prolongation)
     {
@@ -940,12 +945,31 @@ __global__ void __launch_bounds__(VC_NT) k_vcycle_tail(VTail<T> vt) {
     cluster_barrier();
     T *c = cur[l], *o = oth[l];
     for (int k = 0; k < vt.nu; ++k) {
-      sweep(l, 2, c, vt.rl[l], o);
+      sweep(l, 2, c, vt.rl[l], o, vt.w[l][vt.nu - 1 - k], T(0));
       cluster_barrier();
       T *t = c; c = o; o = t;
     }
     cur[l] = c;
   }
+}
+
+// Smoothing weights of level l, sweep k = 0 .. nu-1 (pre-smoothing applies them in this
+// order, post-smoothing in reverse, so the V-cycle stays symmetric).  Damped Jacobi: omega
+// every sweep.  Chebyshev: the reciprocals of the roots of the degree-nu Chebyshev
+// polynomial on [lmax / alpha, lmax], lmax the Gershgorin bound of diag^-1 S, so that the
+// smoother damps that interval optimally and every |1 - w lambda| product stays below 1 on
+// (0, lmax].
+template <typename T>
+static void smooth_weights(const hp_problem *P, OpKind op, int l, T w[4]) {
+  const int nu = P->nu;
+  if (P->smoother != 1) {
+    for (int k = 0; k < 4; ++k) w[k] = (T)P->omega;
+    return;
+  }
+  const double b = stencil_of<double>(P, op, l).lmax, a = b / P->cheb_alpha;
+  const double c = 0.5 * (a + b), d = 0.5 * (b - a);
+  for (int k = 0; k < 4; ++k)
+    w[k] = k < nu ? (T)(1.0 / (c - d * std::cos(M_PI * (2.0 * k + 1.0) / (2.0 * nu)))) : T(0);
 }
 
 // first level of the fused coarse tail for this solve, or L (no fusion)
@@ -966,6 +990,7 @@ static void launch_vtail(hp_problem *P, OpKind op, int s, int l0, const T *const
   vt.nc = (int)P->lv[L - 1].g.n;
   vt.omega = (T)P->omega;
   for (int l = 0; l < L; ++l) {
+    smooth_weights<T>(P, op, l, vt.w[l]);
     const Stencil<T> &S = stencil_of<T>(P, op, l);
     vt.g[l] = P->lv[l].g;
     vt.diag[l] = S.diag;
@@ -1056,21 +1081,23 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
     }
     const GridDesc &g = P->lv[l].g;
     const Stencil<T> &S = stencil_of<T>(P, op, l);
+    T w[4];
+    smooth_weights<T>(P, op, l, w);
     // Pre-smoothing from zero.  Each later sweep flips buffers (nu - 2 more pre, nu post), so the
     // fused two-sweep kernel writes ea[l] and the single sweep (nu = 1) writes eb[l]: either way the
     // level's final correction lands in ea[l] (z0 at level 0).
     T *c = nu >= 2 ? ea[l] : eb[l], *o = nu >= 2 ? eb[l] : ea[l];
     int pr = prof_start(P, l == 0 ? (nu >= 2 ? PROF_PRESMOOTH : PROF_SMOOTH) : -1);
     if (nu >= 2) {
-      st_launch<T, VW, M_JAC2>(g, S, rl[l], gsl[l], nullptr, 0, c, gsl[l], s, om, nofin, st);
+      st_launch<T, VW, M_JAC2>(g, S, rl[l], gsl[l], nullptr, 0, c, gsl[l], s, w[0], nofin, st, w[1]);
     } else {
-      k_jacobi0<T, VW><<<nodegrid(g.n, ng), NB, 0, st>>>(g.n, S.invdiag, rl[l], gsl[l], c, om, s, nofin, 0);
+      k_jacobi0<T, VW><<<nodegrid(g.n, ng), NB, 0, st>>>(g.n, S.invdiag, rl[l], gsl[l], c, w[0], s, nofin, 0);
       count_launch();
     }
     prof_stop(P, pr);
     for (int k = 2; k < nu; ++k) {
       pr = prof_start(P, l == 0 ? PROF_SMOOTH : -1);
-      st_launch<T, VW, M_JACOBI>(g, S, c, gsl[l], rl[l], gsl[l], o, gsl[l], s, om, nofin, st);
+      st_launch<T, VW, M_JACOBI>(g, S, c, gsl[l], rl[l], gsl[l], o, gsl[l], s, w[k], nofin, st);
       prof_stop(P, pr);
       std::swap(c, o);
     }
@@ -1112,12 +1139,14 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
       k_prolong_add<T, VW, 3><<<rowgrid(g, ng), NB, 0, st>>>(g, gc, cur[l + 1], gsl[l + 1], cur[l], gsl[l]);
     count_launch();
     T *c = cur[l], *o = oth[l];
+    T w[4];
+    smooth_weights<T>(P, op, l, w);
     for (int k = 0; k < nu; ++k) {
       const int pr = prof_start(P, l == 0 ? PROF_SMOOTH : -1);
       if (l == 0 && k == nu - 1)
-        st_launch<T, VW, M_JACOBI_DOT>(g, S, c, gsl[l], rl[l], gsl[l], o, gsl[l], s, om, fin, st);
+        st_launch<T, VW, M_JACOBI_DOT>(g, S, c, gsl[l], rl[l], gsl[l], o, gsl[l], s, w[nu - 1 - k], fin, st);
       else
-        st_launch<T, VW, M_JACOBI>(g, S, c, gsl[l], rl[l], gsl[l], o, gsl[l], s, om, nofin, st);
+        st_launch<T, VW, M_JACOBI>(g, S, c, gsl[l], rl[l], gsl[l], o, gsl[l], s, w[nu - 1 - k], nofin, st);
       prof_stop(P, pr);
       std::swap(c, o);
     }
@@ -1474,7 +1503,7 @@ extern "C" int hp_replay_kernel(hp_problem *P, int family, int reps, void *flush
     else if (family == 1)
       st_launch<float, 4, M_RESID>(g, S, z, gs, r, gs, y, gs, s, om, Fin{}, P->st);
     else
-      st_launch<float, 4, M_JAC2>(g, S, r, gs, nullptr, 0, y, gs, s, om, Fin{}, P->st);
+      st_launch<float, 4, M_JAC2>(g, S, r, gs, nullptr, 0, y, gs, s, om, Fin{}, P->st, om);
   };
   const long n4 = (long)(flush_bytes / sizeof(float4));
   HP_TRY(P->sc.tmp.ensure(64));

@@ -1,6 +1,7 @@
 // tune.cu -- solver tuning knobs and the autotuner.
 //
-// Knobs: Jacobi sweeps nu and damping omega of the V-cycle, the RHS column
+// Knobs: the V-cycle's smoother (nu sweeps, damped Jacobi with omega or Chebyshev
+// weights on [lmax / alpha, lmax]), the RHS column
 // chunk processed per solve (0 = all columns at once), the level from which the
 // coarse tail of the V-cycle runs as one cluster launch, and the grid-size cap
 // of the node kernels.  hp_autotune times one block of Gauss-Newton Hessian
@@ -20,13 +21,17 @@ extern "C" {
 int hp_set_tuning(hp_problem *P, const hp_tuning *t) {
   if (!P || !t) return set_error(HP_ERR_INVALID, "hp_set_tuning: null");
   if (t->nu < 1 || t->nu > 4 || !(t->omega > 0.0 && t->omega < 1.0) || t->col_chunk < 0 || t->max_blocks < 64 ||
-      t->max_blocks > (1 << 20) || t->fuse_from < 0 || t->fuse_from >= HP_MAXL)
+      t->max_blocks > (1 << 20) || t->fuse_from < 0 || t->fuse_from >= HP_MAXL || t->smoother < 0 ||
+      t->smoother > 1 || (t->smoother == 1 && !(t->cheb_alpha > 1.0 && t->cheb_alpha < 1e6)))
     return set_error(HP_ERR_INVALID, "hp_set_tuning: nu in [1,4], omega in (0,1), col_chunk >= 0, max_blocks >= 64, "
-                                     "fuse_from in [0, 15]");
+                                     "fuse_from in [0, 15], smoother 0/1, cheb_alpha > 1");
   HP_CUDA(cudaStreamSynchronize(P->st));
-  if (t->nu != P->nu || t->omega != P->omega || t->max_blocks != P->max_blocks || t->fuse_from != P->fuse_from)
+  if (t->nu != P->nu || t->omega != P->omega || t->max_blocks != P->max_blocks || t->fuse_from != P->fuse_from ||
+      t->smoother != P->smoother || (t->smoother == 1 && t->cheb_alpha != P->cheb_alpha))
     drop_graphs(P);
   P->fuse_from = t->fuse_from;
+  P->smoother = t->smoother;
+  if (t->smoother == 1) P->cheb_alpha = t->cheb_alpha;
   P->nu = t->nu;
   P->omega = t->omega;
   P->col_chunk = t->col_chunk;
@@ -41,6 +46,8 @@ int hp_get_tuning(const hp_problem *P, hp_tuning *t) {
   t->col_chunk = P->col_chunk;
   t->max_blocks = (int)P->max_blocks;
   t->fuse_from = P->fuse_from;
+  t->smoother = P->smoother;
+  t->cheb_alpha = P->cheb_alpha;
   return HP_OK;
 }
 
@@ -89,15 +96,18 @@ int hp_autotune(hp_problem *P, int nrhs, int reps, hp_tuning *best, double *best
   double cur_ms = 0.0;
   int rc = time_it(cur, &cur_ms);
   if (rc) return cleanup(rc);
-  struct Smooth {
-    int nu;
-    double omega;
+  struct SmoothC {
+    int nu, kind;
+    double omega, alpha;
   };
-  const Smooth smooth[] = {{1, 0.8}, {2, 0.7}, {2, 0.8}, {3, 0.7}};
-  for (const Smooth &sm : smooth) {
+  const SmoothC smooth[] = {{2, 0, 0.8, 10.0}, {2, 1, 0.7, 5.0}, {3, 1, 0.7, 8.0}, {3, 1, 0.7, 12.0},
+                            {4, 1, 0.7, 12.0}};
+  for (const SmoothC &sm : smooth) {
     hp_tuning t = cur;
     t.nu = sm.nu;
     t.omega = sm.omega;
+    t.smoother = sm.kind;
+    t.cheb_alpha = sm.alpha;
     double ms;
     if ((rc = time_it(t, &ms))) return cleanup(rc);
     if (ms < cur_ms) {

@@ -340,3 +340,30 @@ def test_randomized_prior_variance_is_exact_with_full_rank(dim, N):
     with pytest.raises(Exception):
         P.pointwise_variance(Z[:, :3], "randomized")          # wrong block shape
     P.close()
+
+
+@pytest.mark.parametrize("dim,N,precision", [(2, 64, "fp32_ir"), (2, 48, "fp64"), (3, 16, "fp32_ir")])
+def test_chebyshev_smoother_keeps_results(dim, N, precision):
+    """Chebyshev smoothing weights change only the speed: Hessian actions and prior solves
+    agree with the damped-Jacobi runs to the solve tolerance, also with the fused coarse
+    tail."""
+    from paper_1909_03948_gb300 import Problem
+    w = W.make_workload(dim, N, 30, seed=78)
+    dr = W.draws(w)
+    P = Problem(dim, N, w.gamma, w.delta, 0.01, dr.obs_xyz, rtol=1e-10, precision=precision)
+    m = 0.3 * torch.tensor(np.random.default_rng(5).standard_normal(P.n), device=DEV)
+    X = torch.tensor(np.random.default_rng(6).standard_normal((9, P.n)), device=DEV)
+    P.set_point(m)
+    Y0, _ = P.hessian_apply(X)
+    Z0, _ = P.prior_solve(X)
+    for alpha, ff in ((3.0, 0), (8.0, 0), (5.0, 2)):
+        P.set_tuning(smoother=1, cheb_alpha=alpha, fuse_from=ff)
+        P.set_point(m)
+        Y1, st1 = P.hessian_apply(X)
+        Z1, _ = P.prior_solve(X)
+        assert float(torch.linalg.norm(Y1 - Y0) / torch.linalg.norm(Y0)) <= 1e-8, alpha
+        assert float(torch.linalg.norm(Z1 - Z0) / torch.linalg.norm(Z0)) <= 1e-8, alpha
+    with pytest.raises(Exception):
+        P.set_tuning(smoother=1, cheb_alpha=0.5)
+    P.set_tuning()
+    P.close()
