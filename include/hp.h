@@ -293,7 +293,7 @@ int hp_pointwise_variance(hp_problem *P, int method, const double *Z_dev, int ld
  * before and after each coarse correction and damping omega, the number of RHS
  * columns solved together (0 = all), and the grid-size cap of the node kernels.
  * Defaults: nu 3, omega 0.7, col_chunk 0, max_blocks 2048, smoother 1
- * (Chebyshev), cheb_alpha 10, fuse_from 0.  Every setting solves to the same
+ * (Chebyshev), cheb_alpha 10, fuse_transfer 0, fuse_from 0.  Every setting solves to the same
  * tolerance; only speed changes. */
 typedef struct {
   int nu;          /* 1..4 */
@@ -305,6 +305,9 @@ typedef struct {
                       [lmax / cheb_alpha, lmax] (lmax: Gershgorin bound of D^-1 S on
                       each level), post-smoothing in reverse order */
   double cheb_alpha; /* > 1 */
+  int fuse_transfer; /* 1: the residual and its restriction run as one kernel, and so
+                        do the prolongation and the first post-smoothing sweep (the
+                        fine residual and the prolonged iterate are never stored) */
   int fuse_from;   /* 0 = off, else the first multigrid level (>= 1) whose whole
                       coarse tail of the V-cycle runs as one launch: one thread-block
                       cluster of 8 CTAs per column group, steps separated by the

@@ -98,6 +98,7 @@ struct hp_problem {
   long max_blocks = 2048;       // grid cap of the node kernels       (tuning)
   int fuse_from = 0;            // first multigrid level of the fused coarse tail, 0 = none (tuning)
   int smoother = 1;             // 0 damped Jacobi (omega), 1 Chebyshev (cheb_alpha)   (tuning)
+  int fuse_transfer = 0;        // residual + restriction and prolongation + first post sweep fused (tuning)
   double cheb_alpha = 10.0;     // Chebyshev interval [lmax / alpha, lmax]             (tuning)
   cudaStream_t st = nullptr;
   cudaStream_t cap = nullptr;   // private stream used to capture CUDA graphs

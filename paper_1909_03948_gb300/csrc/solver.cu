@@ -314,6 +314,156 @@ __global__ void __launch_bounds__(NB) k_prolong_add(GridDesc gf, GridDesc gc, co
   cur.st(o);
 }
 
+// (S x)(id) for node id with coordinates v (level stencil, boundary-aware)
+template <typename T, int VW, int D, bool FULL>
+__device__ __forceinline__ Pack<T, VW> stencil_at(const GridDesc &g, const T *__restrict__ diag,
+                                                  const T *__restrict__ c, const T *__restrict__ x, long id,
+                                                  const int v[3]) {
+  using PK = Pack<T, VW>;
+  constexpr int NF = FULL ? (1 << D) - 1 : D;
+  const PK xc = PK::ld(x + id * VW);
+  PK sx;
+  const T dg = diag[id];
+#pragma unroll
+  for (int q = 0; q < VW; ++q) sx.v[q] = dg * xc.v[q];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int b = FULL ? f + 1 : (1 << f);
+    bool fw = true, bw = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if ((b >> a) & 1) {
+        fw = fw && (v[a] < g.N);
+        bw = bw && (v[a] > 0);
+      }
+    const long off = mask_offset(g, b);
+    if (fw) sx.axpy(c[(long)f * g.n + id], PK::ld(x + (id + off) * VW));
+    if (bw) sx.axpy(c[(long)f * g.n + id - off], PK::ld(x + (id - off) * VW));
+  }
+  return sx;
+}
+
+// Residual and restriction in one pass: r_c(J) = sum over the fine nodes j of the
+// restriction stencil of 2J (weight 1 at 2J, 1/2 at 2J +- b) of (b_f - S e)(j).  The fine
+// residual is never stored.  One coarse node per thread.
+template <typename T, int VW, int D, bool FULL>
+__global__ void __launch_bounds__(NB) k_resid_restrict(GridDesc gf, GridDesc gc, const T *__restrict__ diag,
+                                                       const T *__restrict__ c, const T *__restrict__ e,
+                                                       const T *__restrict__ bf, long gsf, T *__restrict__ rc,
+                                                       long gsc, int zero_dirichlet) {
+  using PK = Pack<T, VW>;
+  const int I0 = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int row = blockIdx.y * (NB / 32) + (threadIdx.x >> 5);
+  const int nrows = D == 2 ? gc.np : gc.np * gc.np;
+  if (I0 >= gc.np || row >= nrows) return;
+  const int J[3] = {I0, D == 2 ? row : row % gc.np, D == 2 ? 0 : row / gc.np};
+  const long I = I0 + (long)gc.np * row;
+  const T *eg = e + blockIdx.z * gsf, *bg = bf + blockIdx.z * gsf;
+  PK out = PK::zero();
+  auto resid = [&](long j, const int vj[3]) {
+    const PK sx = stencil_at<T, VW, D, FULL>(gf, diag, c, eg, j, vj);
+    PK r = PK::ld(bg + j * VW);
+#pragma unroll
+    for (int q = 0; q < VW; ++q) r.v[q] -= sx.v[q];
+    return r;
+  };
+  if (!(zero_dirichlet && (J[D - 1] == 0 || J[D - 1] == gc.N))) {
+    const int v0[3] = {2 * J[0], 2 * J[1], 2 * J[2]};
+    const long f0 = v0[0] + (long)gf.np * (v0[1] + (long)gf.np * v0[2]);
+    out = resid(f0, v0);
+#pragma unroll
+    for (int b = 1; b < (1 << D); ++b) {
+      bool fw = true, bw = true;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        if ((b >> a) & 1) {
+          fw = fw && (J[a] < gc.N);
+          bw = bw && (J[a] > 0);
+        }
+      const long off = mask_offset(gf, b);
+      if (fw) {
+        const int vf[3] = {v0[0] + (b & 1), v0[1] + ((b >> 1) & 1), v0[2] + ((b >> 2) & 1)};
+        out.axpy(T(0.5), resid(f0 + off, vf));
+      }
+      if (bw) {
+        const int vb[3] = {v0[0] - (b & 1), v0[1] - ((b >> 1) & 1), v0[2] - ((b >> 2) & 1)};
+        out.axpy(T(0.5), resid(f0 - off, vb));
+      }
+    }
+  }
+  out.st(rc + blockIdx.z * gsc + I * VW);
+}
+
+// Prolongation and the first post-smoothing sweep in one pass:
+//   x' = x + P e_c (at the node and its stencil neighbours, recomputed on the fly),
+//   y  = x' + w D^-1 (b - S x')
+// The prolonged x' is never stored.
+template <typename T, int VW, int D, bool FULL>
+__global__ void __launch_bounds__(NB) k_prolong_sweep(GridDesc gf, GridDesc gc, const T *__restrict__ diag,
+                                                      const T *__restrict__ invdiag, const T *__restrict__ c,
+                                                      const T *__restrict__ x, const T *__restrict__ ec,
+                                                      long gsc, const T *__restrict__ bf, T *__restrict__ y,
+                                                      long gsf, T omega) {
+  using PK = Pack<T, VW>;
+  constexpr int NF = FULL ? (1 << D) - 1 : D;
+  const int lane = threadIdx.x & 31;
+  const int i0 = blockIdx.x * 32 + lane;
+  const int nrows = D == 2 ? gf.np : gf.np * gf.np;
+  const T *xg = x + blockIdx.z * gsf, *bg = bf + blockIdx.z * gsf, *eg = ec + blockIdx.z * gsc;
+  // x' at fine node j with coordinates vj
+  auto xp = [&](long j, const int vj[3]) {
+    PK val = PK::ld(xg + j * VW);
+    const int bm = (vj[0] & 1) | ((vj[1] & 1) << 1) | ((vj[2] & 1) << 2);
+    const long ic = (vj[0] >> 1) + (long)gc.np * ((vj[1] >> 1) + (long)gc.np * (vj[2] >> 1));
+    const PK e0 = PK::ld(eg + ic * VW);
+    if (bm) {
+      const PK e1 = PK::ld(eg + (ic + mask_offset(gc, bm)) * VW);
+#pragma unroll
+      for (int q = 0; q < VW; ++q) val.v[q] += T(0.5) * (e0.v[q] + e1.v[q]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < VW; ++q) val.v[q] += e0.v[q];
+    }
+    return val;
+  };
+  for (int row = blockIdx.y * (NB / 32) + (threadIdx.x >> 5); row < nrows; row += gridDim.y * (NB / 32)) {
+    if (i0 >= gf.np) break;
+    const int v[3] = {i0, D == 2 ? row : row % gf.np, D == 2 ? 0 : row / gf.np};
+    const long id = i0 + (long)gf.np * row;
+    const PK xc = xp(id, v);
+    PK sx;
+    const T dg = diag[id];
+#pragma unroll
+    for (int q = 0; q < VW; ++q) sx.v[q] = dg * xc.v[q];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const int b = FULL ? f + 1 : (1 << f);
+      bool fw = true, bw = true;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        if ((b >> a) & 1) {
+          fw = fw && (v[a] < gf.N);
+          bw = bw && (v[a] > 0);
+        }
+      const long off = mask_offset(gf, b);
+      if (fw) {
+        const int vf[3] = {v[0] + (b & 1), v[1] + ((b >> 1) & 1), v[2] + ((b >> 2) & 1)};
+        sx.axpy(c[(long)f * gf.n + id], xp(id + off, vf));
+      }
+      if (bw) {
+        const int vb[3] = {v[0] - (b & 1), v[1] - ((b >> 1) & 1), v[2] - ((b >> 2) & 1)};
+        sx.axpy(c[(long)f * gf.n + id - off], xp(id - off, vb));
+      }
+    }
+    const PK bb = PK::ld(bg + id * VW);
+    const T wi = omega * invdiag[id];
+    PK out;
+#pragma unroll
+    for (int q = 0; q < VW; ++q) out.v[q] = xc.v[q] + wi * (bb.v[q] - sx.v[q]);
+    out.st(y + blockIdx.z * gsf + id * VW);
+  }
+}
+
 // dense coarse-grid inverse: e = A_c^{-1} r.  blockIdx.x = chunk of 32 rows (lanes),
 // blockIdx.y = column group; the 8 warps of a block split the k sum, then add.
 template <typename T, int VW>
@@ -1101,16 +1251,34 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
       prof_stop(P, pr);
       std::swap(c, o);
     }
-    pr = prof_start(P, l == 0 ? PROF_RESID_MG : -1);
-    st_launch<T, VW, M_RESID>(g, S, c, gsl[l], rl[l], gsl[l], o, gsl[l], s, om, nofin, st);
-    prof_stop(P, pr);
     const GridDesc &gc = P->lv[l + 1].g;
     T *rc = const_cast<T *>(rl[l + 1]);
-    if (g.dim == 2)
-      k_restrict<T, VW, 2><<<rowgrid(gc, ng), NB, 0, st>>>(g, gc, o, gsl[l], rc, gsl[l + 1], op == OP_K);
-    else
-      k_restrict<T, VW, 3><<<rowgrid(gc, ng), NB, 0, st>>>(g, gc, o, gsl[l], rc, gsl[l + 1], op == OP_K);
-    count_launch();
+    if (P->fuse_transfer) {
+      // residual and restriction in one pass (the fine residual is not stored)
+      const dim3 gr = rowgrid(gc, ng);
+      const int zd = op == OP_K;
+      if (g.dim == 2) {
+        if (S.full)
+          k_resid_restrict<T, VW, 2, true><<<gr, NB, 0, st>>>(g, gc, S.diag, S.c, c, rl[l], gsl[l], rc, gsl[l + 1], zd);
+        else
+          k_resid_restrict<T, VW, 2, false><<<gr, NB, 0, st>>>(g, gc, S.diag, S.c, c, rl[l], gsl[l], rc, gsl[l + 1], zd);
+      } else {
+        if (S.full)
+          k_resid_restrict<T, VW, 3, true><<<gr, NB, 0, st>>>(g, gc, S.diag, S.c, c, rl[l], gsl[l], rc, gsl[l + 1], zd);
+        else
+          k_resid_restrict<T, VW, 3, false><<<gr, NB, 0, st>>>(g, gc, S.diag, S.c, c, rl[l], gsl[l], rc, gsl[l + 1], zd);
+      }
+      count_launch();
+    } else {
+      pr = prof_start(P, l == 0 ? PROF_RESID_MG : -1);
+      st_launch<T, VW, M_RESID>(g, S, c, gsl[l], rl[l], gsl[l], o, gsl[l], s, om, nofin, st);
+      prof_stop(P, pr);
+      if (g.dim == 2)
+        k_restrict<T, VW, 2><<<rowgrid(gc, ng), NB, 0, st>>>(g, gc, o, gsl[l], rc, gsl[l + 1], op == OP_K);
+      else
+        k_restrict<T, VW, 3><<<rowgrid(gc, ng), NB, 0, st>>>(g, gc, o, gsl[l], rc, gsl[l + 1], op == OP_K);
+      count_launch();
+    }
     cur[l] = c;
     oth[l] = o;
   }
@@ -1133,15 +1301,40 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
   for (int l = std::min(L, l0) - 2 + (l0 < L ? 1 : 0); l >= 0; --l) {
     const GridDesc &g = P->lv[l].g, &gc = P->lv[l + 1].g;
     const Stencil<T> &S = stencil_of<T>(P, op, l);
-    if (g.dim == 2)
-      k_prolong_add<T, VW, 2><<<rowgrid(g, ng), NB, 0, st>>>(g, gc, cur[l + 1], gsl[l + 1], cur[l], gsl[l]);
-    else
-      k_prolong_add<T, VW, 3><<<rowgrid(g, ng), NB, 0, st>>>(g, gc, cur[l + 1], gsl[l + 1], cur[l], gsl[l]);
-    count_launch();
     T *c = cur[l], *o = oth[l];
     T w[4];
     smooth_weights<T>(P, op, l, w);
-    for (int k = 0; k < nu; ++k) {
+    int k0 = 0;
+    if (P->fuse_transfer && nu >= 2) {
+      // prolongation and the first post-smoothing sweep in one pass (x + P e_c is not stored)
+      const dim3 gr = rowgrid_capped(g, ng);
+      const T *ec = cur[l + 1];
+      if (g.dim == 2) {
+        if (S.full)
+          k_prolong_sweep<T, VW, 2, true><<<gr, NB, 0, st>>>(g, gc, S.diag, S.invdiag, S.c, c, ec, gsl[l + 1], rl[l],
+                                                             o, gsl[l], w[nu - 1]);
+        else
+          k_prolong_sweep<T, VW, 2, false><<<gr, NB, 0, st>>>(g, gc, S.diag, S.invdiag, S.c, c, ec, gsl[l + 1], rl[l],
+                                                              o, gsl[l], w[nu - 1]);
+      } else {
+        if (S.full)
+          k_prolong_sweep<T, VW, 3, true><<<gr, NB, 0, st>>>(g, gc, S.diag, S.invdiag, S.c, c, ec, gsl[l + 1], rl[l],
+                                                             o, gsl[l], w[nu - 1]);
+        else
+          k_prolong_sweep<T, VW, 3, false><<<gr, NB, 0, st>>>(g, gc, S.diag, S.invdiag, S.c, c, ec, gsl[l + 1], rl[l],
+                                                              o, gsl[l], w[nu - 1]);
+      }
+      count_launch();
+      std::swap(c, o);
+      k0 = 1;
+    } else {
+      if (g.dim == 2)
+        k_prolong_add<T, VW, 2><<<rowgrid(g, ng), NB, 0, st>>>(g, gc, cur[l + 1], gsl[l + 1], cur[l], gsl[l]);
+      else
+        k_prolong_add<T, VW, 3><<<rowgrid(g, ng), NB, 0, st>>>(g, gc, cur[l + 1], gsl[l + 1], cur[l], gsl[l]);
+      count_launch();
+    }
+    for (int k = k0; k < nu; ++k) {
       const int pr = prof_start(P, l == 0 ? PROF_SMOOTH : -1);
       if (l == 0 && k == nu - 1)
         st_launch<T, VW, M_JACOBI_DOT>(g, S, c, gsl[l], rl[l], gsl[l], o, gsl[l], s, w[nu - 1 - k], fin, st);
@@ -1284,7 +1477,8 @@ static int kernels_per_iteration(const hp_problem *P, OpKind op) {
   // V-cycle: per non-coarsest level pre (1 + nu - 2), resid, restrict, prolong, nu post; coarse 1
   // (or one fused launch for the levels from tail_level on); plus p update, matvec, cg update,
   // condition and three dot finalisations
-  const int per_level = (P->nu >= 2 ? P->nu - 1 : 1) + 3 + P->nu;
+  const int per_level = (P->nu >= 2 ? P->nu - 1 : 1) + P->nu +
+                        (P->fuse_transfer ? (P->nu >= 2 ? 1 : 2) : 3);
   const int separate = std::min(P->L, tail_level(P)) - 1 + (tail_level(P) < P->L ? 1 : 0);
   return 7 + separate * per_level + 1 + 2 * (P->L == 1);
 }

@@ -22,13 +22,16 @@ int hp_set_tuning(hp_problem *P, const hp_tuning *t) {
   if (!P || !t) return set_error(HP_ERR_INVALID, "hp_set_tuning: null");
   if (t->nu < 1 || t->nu > 4 || !(t->omega > 0.0 && t->omega < 1.0) || t->col_chunk < 0 || t->max_blocks < 64 ||
       t->max_blocks > (1 << 20) || t->fuse_from < 0 || t->fuse_from >= HP_MAXL || t->smoother < 0 ||
-      t->smoother > 1 || (t->smoother == 1 && !(t->cheb_alpha > 1.0 && t->cheb_alpha < 1e6)))
+      t->smoother > 1 || (t->smoother == 1 && !(t->cheb_alpha > 1.0 && t->cheb_alpha < 1e6)) ||
+      t->fuse_transfer < 0 || t->fuse_transfer > 1)
     return set_error(HP_ERR_INVALID, "hp_set_tuning: nu in [1,4], omega in (0,1), col_chunk >= 0, max_blocks >= 64, "
                                      "fuse_from in [0, 15], smoother 0/1, cheb_alpha > 1");
   HP_CUDA(cudaStreamSynchronize(P->st));
   if (t->nu != P->nu || t->omega != P->omega || t->max_blocks != P->max_blocks || t->fuse_from != P->fuse_from ||
-      t->smoother != P->smoother || (t->smoother == 1 && t->cheb_alpha != P->cheb_alpha))
+      t->smoother != P->smoother || (t->smoother == 1 && t->cheb_alpha != P->cheb_alpha) ||
+      t->fuse_transfer != P->fuse_transfer)
     drop_graphs(P);
+  P->fuse_transfer = t->fuse_transfer;
   P->fuse_from = t->fuse_from;
   P->smoother = t->smoother;
   if (t->smoother == 1) P->cheb_alpha = t->cheb_alpha;
@@ -48,6 +51,7 @@ int hp_get_tuning(const hp_problem *P, hp_tuning *t) {
   t->fuse_from = P->fuse_from;
   t->smoother = P->smoother;
   t->cheb_alpha = P->cheb_alpha;
+  t->fuse_transfer = P->fuse_transfer;
   return HP_OK;
 }
 
@@ -119,6 +123,16 @@ int hp_autotune(hp_problem *P, int nrhs, int reps, hp_tuning *best, double *best
     if (w >= nrhs) continue;
     hp_tuning t = cur;
     t.col_chunk = w;
+    double ms;
+    if ((rc = time_it(t, &ms))) return cleanup(rc);
+    if (ms < cur_ms) {
+      cur = t;
+      cur_ms = ms;
+    }
+  }
+  for (int ft : {1}) {
+    hp_tuning t = cur;
+    t.fuse_transfer = ft;
     double ms;
     if ((rc = time_it(t, &ms))) return cleanup(rc);
     if (ms < cur_ms) {

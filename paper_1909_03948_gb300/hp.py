@@ -59,7 +59,8 @@ class SolveStats(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("nu", C.c_int), ("omega", C.c_double), ("col_chunk", C.c_int), ("max_blocks", C.c_int),
-                ("smoother", C.c_int), ("cheb_alpha", C.c_double), ("fuse_from", C.c_int)]
+                ("smoother", C.c_int), ("cheb_alpha", C.c_double), ("fuse_transfer", C.c_int),
+                ("fuse_from", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -433,8 +434,9 @@ class Problem:
         _check(lib().hp_get_tuning(self._h, C.byref(t)), "hp_get_tuning")
         return t.as_dict()
 
-    def set_tuning(self, nu=3, omega=0.7, col_chunk=0, max_blocks=2048, smoother=1, cheb_alpha=10.0, fuse_from=0):
-        t = Tuning(nu, omega, col_chunk, max_blocks, smoother, cheb_alpha, fuse_from)
+    def set_tuning(self, nu=3, omega=0.7, col_chunk=0, max_blocks=2048, smoother=1, cheb_alpha=10.0,
+                   fuse_transfer=0, fuse_from=0):
+        t = Tuning(nu, omega, col_chunk, max_blocks, smoother, cheb_alpha, fuse_transfer, fuse_from)
         _check(lib().hp_set_tuning(self._h, C.byref(t)), "hp_set_tuning")
 
     def autotune(self, nrhs, reps=2):

@@ -367,3 +367,33 @@ def test_chebyshev_smoother_keeps_results(dim, N, precision):
         P.set_tuning(smoother=1, cheb_alpha=0.5)
     P.set_tuning()
     P.close()
+
+
+@pytest.mark.parametrize("dim,N,precision", [(2, 64, "fp32_ir"), (2, 48, "fp64"), (3, 16, "fp32_ir"),
+                                             (3, 8, "fp64")])
+@pytest.mark.parametrize("nu", [1, 2, 3])
+def test_fused_transfers_keep_results(dim, N, precision, nu):
+    """Residual + restriction and prolongation + first post sweep fused (the fine residual
+    and the prolonged iterate never stored): the same Hessian actions and prior solves to
+    the solve tolerance, for the stiffness (axis stencil) and the prior (full stencil),
+    alone and with the fused coarse tail."""
+    from paper_1909_03948_gb300 import Problem
+    w = W.make_workload(dim, N, 30, seed=79)
+    dr = W.draws(w)
+    P = Problem(dim, N, w.gamma, w.delta, 0.01, dr.obs_xyz, rtol=1e-10, precision=precision)
+    m = 0.3 * torch.tensor(np.random.default_rng(5).standard_normal(P.n), device=DEV)
+    X = torch.tensor(np.random.default_rng(6).standard_normal((5, P.n)), device=DEV)
+    P.set_tuning(nu=nu)
+    P.set_point(m)
+    Y0, st0 = P.hessian_apply(X)
+    Z0, _ = P.prior_solve(X)
+    for ff in (0, 2):
+        P.set_tuning(nu=nu, fuse_transfer=1, fuse_from=ff)
+        P.set_point(m)
+        Y1, st1 = P.hessian_apply(X)
+        Z1, _ = P.prior_solve(X)
+        assert float(torch.linalg.norm(Y1 - Y0) / torch.linalg.norm(Y0)) <= 1e-8, ff
+        assert float(torch.linalg.norm(Z1 - Z0) / torch.linalg.norm(Z0)) <= 1e-8, ff
+        assert abs(st1["iterations"] - st0["iterations"]) <= 2, (st0, st1)
+    P.set_tuning()
+    P.close()
