@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-map", action="store_true", help="linearise at the true parameter instead of the MAP")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start leg (2D)")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the plain one-vector FP64 GPU path (the speedup denominator)")
     ap.add_argument("--ws-draws", type=int, default=12, help="prior draws whose solves train the warm start")
     ap.add_argument("--ws-epochs", type=int, default=8, help="training epochs of the warm start")
     return ap.parse_args()
@@ -396,6 +398,12 @@ def run_ours(args, rank, world):
                 "families": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
     if rank != 0:
         return
+    if not args.no_plain:
+        try:
+            extra["plain_fp64_one_vector"] = plain_fp64_leg(w, wr, dev, Omega, m_lin, extra.get("time_to_map_eig_s"),
+                                                             value, args)
+        except Exception as ex:  # pragma: no cover
+            extra["plain_fp64_one_vector"] = {"failed": str(ex)}
     if w.dim == 2 and not args.no_warmstart:
         try:
             extra["warm_start"] = warmstart_leg(P, Omega, m_lin, args, dev)
@@ -440,6 +448,47 @@ def synthetic_problem(w, dev, precision="fp32_ir"):
     sigma = w.noise_level * float(u_true.abs().max())
     P.set_data(P.observe(u_true).cpu().numpy() + sigma * dr.xi_noise, sigma)
     return P
+
+
+def plain_fp64_leg(w, wr, dev, Omega, m_lin, t_me, value, args):
+    """The plain one-vector FP64 GPU path on the same GPU: the same kernels with
+    FP64 multigrid-preconditioned CG throughout (no FP32 inner solver, no refinement),
+    one right-hand side per solve, untuned.  Measures Gauss-Newton actions/s on a bounded
+    number of single columns, and time to MAP + rank-k eigenpairs."""
+    import torch
+    from paper_1909_03948_gb300 import Problem
+    dr = W.draws(wr)
+    P = Problem(w.dim, w.N, w.gamma, w.delta, 1.0, dr.obs_xyz, precision="fp64", rtol=1e-8)
+    eta = torch.tensor(dr.eta_true.reshape(1, -1), device=dev)
+    m_true = P.laplace_sample(None, None, None, eta, want_prior=True, want_post=False)[0][0].contiguous()
+    u_true, _ = P.forward(m_true)
+    sigma = w.noise_level * float(u_true.abs().max())
+    P.set_data(P.observe(u_true).cpu().numpy() + sigma * dr.xi_noise, sigma)
+    P.set_tuning(nu=2, omega=0.7, smoother=0, col_chunk=1)
+    out = {"precision": "fp64 MG-PCG, one column per solve (col_chunk 1), damped Jacobi nu 2, untuned"}
+    P.set_point(m_lin)
+    ncol = min(8, Omega.shape[0])
+    P.hessian_apply(Omega[0].contiguous())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(ncol):
+        P.hessian_apply(Omega[j].contiguous())
+    torch.cuda.synchronize()
+    t = (time.perf_counter() - t0) / ncol
+    out["actions_per_s"] = 1.0 / t
+    out["speedup_actions_per_s"] = value / out["actions_per_s"]
+    if t_me is not None and not args.no_map:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m_map, nst = P.newton_cg_map(rel_tol=1e-6)
+        # one column at a time: the double pass needs k + p actions per pass
+        lam, V, _ = P.lowrank_eig(m_map, w.k, w.p, Omega)
+        torch.cuda.synchronize()
+        out["time_to_map_eig_s"] = time.perf_counter() - t0
+        out["speedup_time_to_map_eig"] = out["time_to_map_eig_s"] / t_me
+        out["newton_iterations"] = nst["iterations"]
+    P.close()
+    return out
 
 
 def warmstart_leg(P, Omega, m_lin, args, dev):
