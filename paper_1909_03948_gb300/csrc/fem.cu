@@ -391,22 +391,25 @@ __global__ void k_dense_cholesky(double *A, int nc, int *status) {
   if (threadIdx.x == 0) *status = bad;
 }
 
-// column j of the inverse from the Cholesky factor (one thread per column)
+// Column j of the inverse from the Cholesky factor, one thread per column.  The inverse is
+// symmetric, so thread j keeps its column as row j of the output, x[i] at inv[i * nc + j]:
+// the threads of a warp then touch consecutive addresses at every step (and all read the same
+// L entry), and the substitutions start at row j (rows above it are zero in L^-1 e_j).
 __global__ void k_dense_inverse(const double *L, int nc, double *inv, float *inv32) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nc) return;
-  double *x = inv + (long)j * nc;  // column j (inverse is symmetric)
-  for (int i = 0; i < nc; ++i) {    // L y = e_j
+  for (int i = 0; i < j; ++i) inv[(long)i * nc + j] = 0.0;
+  for (int i = j; i < nc; ++i) {  // L y = e_j
     double s = (i == j) ? 1.0 : 0.0;
-    for (int k = 0; k < i; ++k) s -= L[(long)i * nc + k] * x[k];
-    x[i] = s / L[(long)i * nc + i];
+    for (int k = j; k < i; ++k) s -= L[(long)i * nc + k] * inv[(long)k * nc + j];
+    inv[(long)i * nc + j] = s / L[(long)i * nc + i];
   }
   for (int i = nc - 1; i >= 0; --i) {  // L^T x = y
-    double s = x[i];
-    for (int k = i + 1; k < nc; ++k) s -= L[(long)k * nc + i] * x[k];
-    x[i] = s / L[(long)i * nc + i];
+    double s = inv[(long)i * nc + j];
+    for (int k = i + 1; k < nc; ++k) s -= L[(long)k * nc + i] * inv[(long)k * nc + j];
+    inv[(long)i * nc + j] = s / L[(long)i * nc + i];
   }
-  for (int i = 0; i < nc; ++i) inv32[(long)j * nc + i] = (float)x[i];
+  for (int i = 0; i < nc; ++i) inv32[(long)i * nc + j] = (float)inv[(long)i * nc + j];
 }
 
 int coarse_setup(hp_problem *P, OpKind op) {
@@ -422,7 +425,7 @@ int coarse_setup(hp_problem *P, OpKind op) {
     k_dense_from_stencil<3><<<nb, 256, 0, P->st>>>(lc.g, S.diag, S.c, S.nf, S.full, C.dense);
   int *dstat = P->sc.active.as<int>();
   k_dense_cholesky<<<1, 1024, 0, P->st>>>(C.dense, (int)nc, dstat);
-  k_dense_inverse<<<(int)((nc + 127) / 128), 128, 0, P->st>>>(C.dense, (int)nc, C.inv64, C.inv32);
+  k_dense_inverse<<<(int)((nc + 31) / 32), 32, 0, P->st>>>(C.dense, (int)nc, C.inv64, C.inv32);
   count_launch(3);
   int h = 0;
   HP_CUDA(cudaMemcpyAsync(&h, dstat, sizeof(int), cudaMemcpyDeviceToHost, P->st));
