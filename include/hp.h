@@ -95,6 +95,13 @@ typedef struct {
   int cg_max_iter;       /* inner CG cap                                                  */
   int full_newton;       /* 0: Gauss-Newton Hessian; 1: full Hessian (HP_FULL_NEWTON); the
                             CG stops on non-positive curvature (Steihaug) either way       */
+  int lowrank_k;         /* 0: CG preconditioned by R^-1 (Section 4.1).  > 0: by
+                            R^-1 - V diag(lambda / (1 + lambda)) V^T, the inverse (Woodbury)
+                            of R + R V Lambda V^T R with the lowrank_k leading eigenpairs of
+                            H_misfit v = lambda R v (double pass, Philox directions)        */
+  int lowrank_p;         /* oversampling of that eigensolve                                */
+  int lowrank_refresh;   /* recompute the eigenpairs every lowrank_refresh Newton
+                            iterations (0: only at the first)                              */
 } hp_newton_opts;
 
 typedef struct {
@@ -104,6 +111,7 @@ typedef struct {
   double J0, J;          /* initial and final cost                         */
   double gnorm0, gnorm;  /* initial and final |g|                          */
   int pde_solves;        /* total PDE block solves (state, adjoint, incremental, prior, mass) */
+  int eig_solves;        /* low-rank preconditioner eigensolves                         */
 } hp_newton_stats;
 
 /* ---- lifetime ------------------------------------------------------------ */
@@ -235,7 +243,8 @@ int hp_mass_solve_noalloc(hp_problem *P, const double *B, int ldb, double *X, in
 
 /* Inexact Newton-CG (Algorithm 1) from m_dev_inout (n values) to the MAP point.
  * opts may be NULL (defaults: rel_tol 1e-6, abs_tol 0, max_iter 50,
- * max_backtrack 10, c_armijo 1e-4, cg_max_iter 200).  The linearisation point
+ * max_backtrack 10, c_armijo 1e-4, cg_max_iter 200, Gauss-Newton, R^-1
+ * preconditioner).  The linearisation point
  * is left at the returned m. */
 int hp_newton_cg_map(hp_problem *P, double *m_dev_inout, const hp_newton_opts *opts,
                      hp_newton_stats *st);

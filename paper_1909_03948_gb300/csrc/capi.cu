@@ -393,6 +393,11 @@ static int Rinv_apply(hp_problem *P, const double *X, long ldx, double *Y, long 
   return 0;
 }
 
+// t_i *= lambda_i / (1 + lambda_i)
+__global__ void k_lowrank_scale(double *t, const double *__restrict__ lam, int k) {
+  for (int i = threadIdx.x; i < k; i += blockDim.x) t[i] *= lam[i] / (1.0 + lam[i]);
+}
+
 static int dot1(hp_problem *P, const double *a, const double *b, double *out) {
   HP_TRY(P->small.ensure(sizeof(double) * 64));
   double *d = P->small.as<double>();
@@ -770,8 +775,10 @@ int hp_mass_factor_apply(hp_problem *P, const double *eta, int ldeta, double *W,
 // ---------------------------------------------------------------------------
 int hp_newton_cg_map(hp_problem *P, double *m, const hp_newton_opts *opts_in, hp_newton_stats *out) {
   if (!P || !m) return set_error(HP_ERR_INVALID, "null");
-  hp_newton_opts o{1e-6, 0.0, 50, 10, 1e-4, 200, 0};
+  hp_newton_opts o{1e-6, 0.0, 50, 10, 1e-4, 200, 0, 0, 10, 0};
   if (opts_in) o = *opts_in;
+  const int lk = std::max(0, o.lowrank_k), lp = std::max(0, o.lowrank_p), ls = lk + lp;
+  if (lk > 0 && (ls > P->n || ls > 1024)) return set_error(HP_ERR_INVALID, "lowrank_k + lowrank_p too large");
   hp_newton_stats S{};
   const long n = P->n;
   std::vector<double *> v(8, nullptr);
@@ -781,11 +788,36 @@ int hp_newton_cg_map(hp_problem *P, double *m, const hp_newton_opts *opts_in, hp
         if (q) cudaFree(q);
       return set_error(HP_ERR_NOMEM, "newton workspace");
     }
+  // low-rank preconditioner: V (n x k), lambda (k), Omega (n x (k+p)), scratch (k)
+  double *Vl = nullptr, *laml = nullptr, *Oml = nullptr, *tk = nullptr;
+  auto free_lr = [&]() {
+    for (double *q : {Vl, laml, Oml, tk})
+      if (q) cudaFree(q);
+  };
+  if (lk > 0 && (cudaMalloc(&Vl, sizeof(double) * n * lk) != cudaSuccess ||
+                 cudaMalloc(&laml, sizeof(double) * lk) != cudaSuccess ||
+                 cudaMalloc(&Oml, sizeof(double) * n * ls) != cudaSuccess ||
+                 cudaMalloc(&tk, sizeof(double) * lk) != cudaSuccess)) {
+    free_lr();
+    for (auto q : v) cudaFree(q);
+    return set_error(HP_ERR_NOMEM, "newton low-rank workspace");
+  }
   double *g = v[0], *x = v[1], *r = v[2], *z = v[3], *d = v[4], *Hd = v[5], *mt = v[6];
   auto cleanup = [&](int rc) {
     for (auto q : v) cudaFree(q);
+    free_lr();
     if (out) *out = S;
     return rc;
+  };
+  bool have_lr = false;
+  // z -= V diag(lambda / (1 + lambda)) V^T r   (after z = R^-1 r)
+  auto lowrank_correct = [&](const double *rv, double *zv) -> int {
+    if (!have_lr) return 0;
+    HP_TRY(gram(P, Vl, n, lk, rv, n, 1, tk, lk, n));
+    k_lowrank_scale<<<1, 256, 0, P->st>>>(tk, laml, lk);
+    count_launch();
+    launch_gemm_nn(Vl, n, lk, tk, lk, 1, zv, n, n, -1.0, 1.0, P->st);
+    return 0;
   };
   int rc = 0;
   double J3[3];
@@ -813,11 +845,22 @@ int hp_newton_cg_map(hp_problem *P, double *m, const hp_newton_opts *opts_in, hp
       break;
     }
     const double eta = std::min(0.5, std::sqrt(gn / g0));
-    // CG-Steihaug on H x = -g, preconditioner R^{-1}: r0 = -g, z0 = -R^{-1} g
+    if (lk > 0 && (!have_lr || (o.lowrank_refresh > 0 && it % o.lowrank_refresh == 0))) {
+      // leading eigenpairs of the prior-preconditioned misfit Hessian at the current point
+      launch_philox_normals(0x6c72ULL + (unsigned long long)it, 0, ls, (int)n, Oml, n, 0, P->st);
+      hp_solve_stats es{};
+      if ((rc = hp_lowrank_eig(P, m, lk, lp, Oml, (int)n, laml, Vl, (int)n, 0, &es))) return cleanup(rc);
+      solves += es.solves;
+      S.eig_solves += 1;
+      have_lr = true;
+    }
+    // CG-Steihaug on H x = -g, preconditioner R^{-1} [- V D V^T]: r0 = -g, z0 = preconditioned r0
     launch_fill(x, n, n, 1, 0.0, P->st);
     launch_axpby(-1.0, g, n, 0.0, r, n, n, 1, P->st);
     launch_axpby(-1.0, z, n, 0.0, z, n, n, 1, P->st);
+    if ((rc = lowrank_correct(r, z))) return cleanup(rc);
     double rz = gRg;
+    if (have_lr && (rc = dot1(P, r, z, &rz))) return cleanup(rc);
     const double r0 = std::sqrt(rz);
     launch_axpby(1.0, z, n, 0.0, d, n, n, 1, P->st);
     int k = 0;
@@ -837,6 +880,7 @@ int hp_newton_cg_map(hp_problem *P, double *m, const hp_newton_opts *opts_in, hp
       launch_axpby(-alpha, Hd, n, 1.0, r, n, n, 1, P->st);
       if ((rc = Rinv_apply(P, r, n, z, n, 1))) return cleanup(rc);
       solves += 2;
+      if ((rc = lowrank_correct(r, z))) return cleanup(rc);
       double rzn = 0.0;
       if ((rc = dot1(P, r, z, &rzn))) return cleanup(rc);
       if (std::sqrt(std::max(rzn, 0.0)) <= eta * r0) break;

@@ -69,13 +69,14 @@ class Tuning(C.Structure):
 class NewtonOpts(C.Structure):
     _fields_ = [("rel_tol", C.c_double), ("abs_tol", C.c_double), ("max_iter", C.c_int),
                 ("max_backtrack", C.c_int), ("c_armijo", C.c_double), ("cg_max_iter", C.c_int),
-                ("full_newton", C.c_int)]
+                ("full_newton", C.c_int), ("lowrank_k", C.c_int), ("lowrank_p", C.c_int),
+                ("lowrank_refresh", C.c_int)]
 
 
 class NewtonStats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("cg_iterations", C.c_int), ("converged", C.c_int),
                 ("J0", C.c_double), ("J", C.c_double), ("gnorm0", C.c_double), ("gnorm", C.c_double),
-                ("pde_solves", C.c_int)]
+                ("pde_solves", C.c_int), ("eig_solves", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -476,9 +477,12 @@ class Problem:
 
     # ---- algorithms --------------------------------------------------------------
     def newton_cg_map(self, m0=None, rel_tol=1e-6, abs_tol=0.0, max_iter=50, max_backtrack=10,
-                      c_armijo=1e-4, cg_max_iter=200, full=False):
+                      c_armijo=1e-4, cg_max_iter=200, full=False, lowrank_k=0, lowrank_p=10, lowrank_refresh=0):
+        """Algorithm 1.  lowrank_k > 0 preconditions the CG with R^-1 - V D V^T from the
+        lowrank_k leading eigenpairs (recomputed every lowrank_refresh iterations, 0: once)."""
         m = self.zeros() if m0 is None else self._vec(m0, "m0").clone().reshape(-1)
-        o = NewtonOpts(rel_tol, abs_tol, max_iter, max_backtrack, c_armijo, cg_max_iter, 1 if full else 0)
+        o = NewtonOpts(rel_tol, abs_tol, max_iter, max_backtrack, c_armijo, cg_max_iter, 1 if full else 0,
+                       lowrank_k, lowrank_p, lowrank_refresh)
         st = NewtonStats()
         rc = lib().hp_newton_cg_map(self._h, _dptr(m), C.byref(o), C.byref(st))
         if rc not in (HP_OK, HP_ERR_NOT_CONVERGED):

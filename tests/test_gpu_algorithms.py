@@ -63,6 +63,20 @@ def test_full_newton_map_matches_oracle(small2d):
     assert st["iterations"] < small2d["res"].iterations
 
 
+def test_lowrank_preconditioned_newton_reaches_the_map(small2d):
+    """Newton-CG whose CG is preconditioned by R^-1 - V D V^T (k = 20 eigenpairs of the
+    prior-preconditioned misfit Hessian, refreshed every 2 Newton iterations) reaches the
+    same MAP point -- the oracle's full-Newton MAP, within ~1e-8 of the exact one -- to
+    relative 1e-6, in far fewer CG iterations than the R^-1-preconditioned run."""
+    orc, w, P = small2d["orc"], small2d["w"], small2d["P"]
+    m, st = P.newton_cg_map(rel_tol=1e-10, lowrank_k=20, lowrank_p=10, lowrank_refresh=2)
+    assert st["converged"] and st["eig_solves"] >= 2
+    ref_full = A.newton_cg(orc, rel_tol=1e-9, full=True)
+    assert np.linalg.norm(m.cpu().numpy() - ref_full.m) <= 1e-6 * np.linalg.norm(ref_full.m)
+    _, st0 = P.newton_cg_map(rel_tol=1e-10)
+    assert st["cg_iterations"] < 0.5 * st0["cg_iterations"], (st, st0)
+
+
 def test_newton_baseline_tolerance(small2d):
     """At the workload's relative gradient tolerance 1e-6 the GPU and the oracle take the
     same Newton path (same eta_i, same CG) to within one iteration."""
