@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-map", action="store_true", help="linearise at the true parameter instead of the MAP")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start leg (2D)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the library's default solver settings instead of the autotuned ones")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the plain one-vector FP64 GPU path (the speedup denominator)")
     ap.add_argument("--ws-draws", type=int, default=12, help="prior draws whose solves train the warm start")
@@ -321,7 +323,11 @@ def run_ours(args, rank, world):
         m_lin = m_true
     P.set_point(m_lin)
     from paper_1909_03948_gb300 import tuning
-    tune, tune_ms, tune_src = tuning.tuned(P, s, args.precision)
+    if args.no_autotune:
+        P.set_tuning()
+        tune, tune_ms, tune_src = P.get_tuning(), None, "library defaults"
+    else:
+        tune, tune_ms, tune_src = tuning.tuned(P, s, args.precision)
     Y = torch.empty_like(Omega)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
