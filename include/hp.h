@@ -301,11 +301,12 @@ int hp_pointwise_variance(hp_problem *P, int method, const double *Z_dev, int ld
  * Knobs of the PDE solver (no counterpart in the paper): nu damped-Jacobi sweeps
  * before and after each coarse correction and damping omega, the number of RHS
  * columns solved together (0 = all), and the grid-size cap of the node kernels.
- * Defaults: nu 3, omega 0.7, col_chunk 0, max_blocks 2048, smoother 1
+ * Defaults: nu 3, nu_coarse 0, omega 0.7, col_chunk 0, max_blocks 2048, smoother 1
  * (Chebyshev), cheb_alpha 10, fuse_transfer 0, fuse_from 0.  Every setting solves to the same
  * tolerance; only speed changes. */
 typedef struct {
   int nu;          /* 1..4 */
+  int nu_coarse;   /* 0 = nu, else the sweeps on the levels below the finest (1..4) */
   double omega;    /* (0, 1) */
   int col_chunk;   /* >= 0 */
   int max_blocks;  /* >= 64 */

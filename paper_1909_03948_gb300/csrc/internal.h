@@ -93,6 +93,7 @@ struct hp_problem {
   double inner_rtol = 1e-5;     // FP32 inner tolerance of the refinement
   int max_outer = 12;
   int nu = 3;                   // pre/post smoothing sweeps         (tuning)
+  int nu_coarse = 0;            // sweeps on the coarser levels, 0 = nu (tuning)
   double omega = 0.7;           // Jacobi damping                     (tuning)
   int col_chunk = 0;            // RHS columns per solve, 0 = all     (tuning)
   long max_blocks = 2048;       // grid cap of the node kernels       (tuning)

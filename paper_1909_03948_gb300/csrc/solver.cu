@@ -877,7 +877,8 @@ constexpr int VC_CL = 8;     // CTAs per cluster (portable maximum)
 constexpr int VC_NT = 512;   // threads per CTA
 
 template <typename T> struct VTail {
-  int l0, L, nu, full, zero_dirichlet, nc;
+  int l0, L, full, zero_dirichlet, nc;
+  int nu[HP_MAXL];  // smoothing sweeps per level
   T omega;
   T w[HP_MAXL][4];  // smoothing weights per level and sweep
   GridDesc g[HP_MAXL];
@@ -991,10 +992,11 @@ __global__ void __launch_bounds__(VC_NT) k_vcycle_tail(VTail<T> vt) {
   };
 
   for (int l = vt.l0; l + 1 < vt.L; ++l) {
-    T *c = vt.nu >= 2 ? vt.ea[l] : vt.eb[l], *o = vt.nu >= 2 ? vt.eb[l] : vt.ea[l];
-    sweep(l, vt.nu >= 2 ? 0 : 1, vt.rl[l], nullptr, c, vt.w[l][0], vt.w[l][1]);
+    const int nul = vt.nu[l];
+    T *c = nul >= 2 ? vt.ea[l] : vt.eb[l], *o = nul >= 2 ? vt.eb[l] : vt.ea[l];
+    sweep(l, nul >= 2 ? 0 : 1, vt.rl[l], nullptr, c, vt.w[l][0], vt.w[l][1]);
     cluster_barrier();
-    for (int k = 2; k < vt.nu; ++k) {
+    for (int k = 2; k < nul; ++k) {
       sweep(l, 2, c, vt.rl[l], o, vt.w[l][k], T(0));
       cluster_barrier();
       T *t = c; c = o; o = t;
@@ -1094,8 +1096,8 @@ __global__ void __launch_bounds__(VC_NT) k_vcycle_tail(VTail<T> vt) {
     }
     cluster_barrier();
     T *c = cur[l], *o = oth[l];
-    for (int k = 0; k < vt.nu; ++k) {
-      sweep(l, 2, c, vt.rl[l], o, vt.w[l][vt.nu - 1 - k], T(0));
+    for (int k = 0; k < vt.nu[l]; ++k) {
+      sweep(l, 2, c, vt.rl[l], o, vt.w[l][vt.nu[l] - 1 - k], T(0));
       cluster_barrier();
       T *t = c; c = o; o = t;
     }
@@ -1109,9 +1111,12 @@ __global__ void __launch_bounds__(VC_NT) k_vcycle_tail(VTail<T> vt) {
 // polynomial on [lmax / alpha, lmax], lmax the Gershgorin bound of diag^-1 S, so that the
 // smoother damps that interval optimally and every |1 - w lambda| product stays below 1 on
 // (0, lmax].
+// smoothing sweeps at level l (nu_coarse, when set, on the coarser levels)
+static int nu_at(const hp_problem *P, int l) { return (l > 0 && P->nu_coarse > 0) ? P->nu_coarse : P->nu; }
+
 template <typename T>
 static void smooth_weights(const hp_problem *P, OpKind op, int l, T w[4]) {
-  const int nu = P->nu;
+  const int nu = nu_at(P, l);
   if (P->smoother != 1) {
     for (int k = 0; k < 4; ++k) w[k] = (T)P->omega;
     return;
@@ -1135,11 +1140,11 @@ static void launch_vtail(hp_problem *P, OpKind op, int s, int l0, const T *const
   VTail<T> vt{};
   vt.l0 = l0;
   vt.L = L;
-  vt.nu = P->nu;
   vt.zero_dirichlet = op == OP_K;
   vt.nc = (int)P->lv[L - 1].g.n;
   vt.omega = (T)P->omega;
   for (int l = 0; l < L; ++l) {
+    vt.nu[l] = nu_at(P, l);
     smooth_weights<T>(P, op, l, vt.w[l]);
     const Stencil<T> &S = stencil_of<T>(P, op, l);
     vt.g[l] = P->lv[l].g;
@@ -1219,9 +1224,9 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
   }
   T *cur[HP_MAXL], *oth[HP_MAXL];
   const Fin nofin{};
-  const int nu = P->nu;
   const int l0 = tail_level(P);  // levels >= l0 run inside one cluster launch
   for (int l = 0; l + 1 < L; ++l) {
+    const int nu = nu_at(P, l);
     if (l >= l0) {  // buffer bookkeeping only: the fused kernel makes the same choices
       T *c = nu >= 2 ? ea[l] : eb[l], *o = nu >= 2 ? eb[l] : ea[l];
       for (int k = 2; k < nu; ++k) std::swap(c, o);
@@ -1287,7 +1292,7 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
     cur[L - 1] = ea[L - 1];
     for (int l = L - 2; l >= l0; --l) {
       T *c = cur[l], *o = oth[l];
-      for (int k = 0; k < nu; ++k) std::swap(c, o);
+      for (int k = 0; k < nu_at(P, l); ++k) std::swap(c, o);
       cur[l] = c;
     }
   } else {
@@ -1301,6 +1306,7 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
   for (int l = std::min(L, l0) - 2 + (l0 < L ? 1 : 0); l >= 0; --l) {
     const GridDesc &g = P->lv[l].g, &gc = P->lv[l + 1].g;
     const Stencil<T> &S = stencil_of<T>(P, op, l);
+    const int nu = nu_at(P, l);
     T *c = cur[l], *o = oth[l];
     T w[4];
     smooth_weights<T>(P, op, l, w);
@@ -1477,10 +1483,13 @@ static int kernels_per_iteration(const hp_problem *P, OpKind op) {
   // V-cycle: per non-coarsest level pre (1 + nu - 2), resid, restrict, prolong, nu post; coarse 1
   // (or one fused launch for the levels from tail_level on); plus p update, matvec, cg update,
   // condition and three dot finalisations
-  const int per_level = (P->nu >= 2 ? P->nu - 1 : 1) + P->nu +
-                        (P->fuse_transfer ? (P->nu >= 2 ? 1 : 2) : 3);
   const int separate = std::min(P->L, tail_level(P)) - 1 + (tail_level(P) < P->L ? 1 : 0);
-  return 7 + separate * per_level + 1 + 2 * (P->L == 1);
+  int vc = 0;
+  for (int l = 0; l < separate; ++l) {
+    const int nu = nu_at(P, l);
+    vc += (nu >= 2 ? nu - 1 : 1) + nu + (P->fuse_transfer ? (nu >= 2 ? 1 : 2) : 3);
+  }
+  return 7 + vc + 1 + 2 * (P->L == 1);
 }
 
 template <typename T, int VW>

@@ -20,14 +20,14 @@ extern "C" {
 
 int hp_set_tuning(hp_problem *P, const hp_tuning *t) {
   if (!P || !t) return set_error(HP_ERR_INVALID, "hp_set_tuning: null");
-  if (t->nu < 1 || t->nu > 4 || !(t->omega > 0.0 && t->omega < 1.0) || t->col_chunk < 0 || t->max_blocks < 64 ||
+  if (t->nu < 1 || t->nu > 4 || t->nu_coarse < 0 || t->nu_coarse > 4 || !(t->omega > 0.0 && t->omega < 1.0) || t->col_chunk < 0 || t->max_blocks < 64 ||
       t->max_blocks > (1 << 20) || t->fuse_from < 0 || t->fuse_from >= HP_MAXL || t->smoother < 0 ||
       t->smoother > 1 || (t->smoother == 1 && !(t->cheb_alpha > 1.0 && t->cheb_alpha < 1e6)) ||
       t->fuse_transfer < 0 || t->fuse_transfer > 1)
     return set_error(HP_ERR_INVALID, "hp_set_tuning: nu in [1,4], omega in (0,1), col_chunk >= 0, max_blocks >= 64, "
                                      "fuse_from in [0, 15], smoother 0/1, cheb_alpha > 1");
   HP_CUDA(cudaStreamSynchronize(P->st));
-  if (t->nu != P->nu || t->omega != P->omega || t->max_blocks != P->max_blocks || t->fuse_from != P->fuse_from ||
+  if (t->nu != P->nu || t->nu_coarse != P->nu_coarse || t->omega != P->omega || t->max_blocks != P->max_blocks || t->fuse_from != P->fuse_from ||
       t->smoother != P->smoother || (t->smoother == 1 && t->cheb_alpha != P->cheb_alpha) ||
       t->fuse_transfer != P->fuse_transfer)
     drop_graphs(P);
@@ -36,6 +36,7 @@ int hp_set_tuning(hp_problem *P, const hp_tuning *t) {
   P->smoother = t->smoother;
   if (t->smoother == 1) P->cheb_alpha = t->cheb_alpha;
   P->nu = t->nu;
+  P->nu_coarse = t->nu_coarse;
   P->omega = t->omega;
   P->col_chunk = t->col_chunk;
   P->max_blocks = t->max_blocks;
@@ -45,6 +46,7 @@ int hp_set_tuning(hp_problem *P, const hp_tuning *t) {
 int hp_get_tuning(const hp_problem *P, hp_tuning *t) {
   if (!P || !t) return set_error(HP_ERR_INVALID, "hp_get_tuning: null");
   t->nu = P->nu;
+  t->nu_coarse = P->nu_coarse;
   t->omega = P->omega;
   t->col_chunk = P->col_chunk;
   t->max_blocks = (int)P->max_blocks;

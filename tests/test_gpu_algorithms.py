@@ -360,7 +360,7 @@ def test_randomized_prior_variance_is_exact_with_full_rank(dim, N):
 def test_chebyshev_smoother_keeps_results(dim, N, precision):
     """Chebyshev smoothing weights change only the speed: Hessian actions and prior solves
     agree with the damped-Jacobi runs to the solve tolerance, also with the fused coarse
-    tail."""
+    tail and with fewer sweeps on the coarse levels (nu_coarse)."""
     from paper_1909_03948_gb300 import Problem
     w = W.make_workload(dim, N, 30, seed=78)
     dr = W.draws(w)
@@ -370,8 +370,8 @@ def test_chebyshev_smoother_keeps_results(dim, N, precision):
     P.set_point(m)
     Y0, _ = P.hessian_apply(X)
     Z0, _ = P.prior_solve(X)
-    for alpha, ff in ((3.0, 0), (8.0, 0), (5.0, 2)):
-        P.set_tuning(smoother=1, cheb_alpha=alpha, fuse_from=ff)
+    for alpha, ff, nc in ((3.0, 0, 0), (8.0, 0, 1), (5.0, 2, 2), (10.0, 1, 1)):
+        P.set_tuning(smoother=1, cheb_alpha=alpha, fuse_from=ff, nu_coarse=nc)
         P.set_point(m)
         Y1, st1 = P.hessian_apply(X)
         Z1, _ = P.prior_solve(X)
