@@ -291,9 +291,11 @@ static int full_terms_at_point(hp_problem *P) {
   const int nC = (1 << (P->dim + 1)) - 1;
   if (!P->Cbeta_p && cudaMalloc(&P->Cbeta_p, sizeof(double) * n * nC) != cudaSuccess)
     return set_error(HP_ERR_NOMEM, "full Hessian terms");
+  if (!P->CbetaE_p && cudaMalloc(&P->CbetaE_p, sizeof(double) * n * nC) != cudaSuccess)
+    return set_error(HP_ERR_NOMEM, "full Hessian terms");
   if (!P->wmm && cudaMalloc(&P->wmm, sizeof(double) * n) != cudaSuccess)
     return set_error(HP_ERR_NOMEM, "full Hessian terms");
-  launch_build_C_from(P, P->padj, P->Cbeta_p);
+  launch_build_C_from(P, P->padj, P->Cbeta_p, P->CbetaE_p);
   launch_Ct_apply(P, P->padj, n, P->wmm, n, 1, 1.0, 0.0);
   P->have_full = true;
   return 0;
@@ -346,7 +348,7 @@ static int hessian_block(hp_problem *P, const double *X, long ldx, double *Y, lo
   launch_obs_scatter(P, yq, t1, ld, s, -1.0 / (P->sigma * P->sigma));
   if (full) {
     launch_copy(t2, ld, uh, ld, n, s, P->st);
-    launch_C_apply_beta(P, P->Cbeta_p, X, ldx, t1, ld, s, -1.0, 1.0);
+    launch_C_apply_beta(P, P->CbetaE_p, X, ldx, t1, ld, s, -1.0, 1.0);
   }
   HP_TRY(solve_block(P, OP_K, t1, ld, t2, ld, s, P->rtol, st));
   // eq. incrementals3: Y = C^T Ph [+ C(p)^T Uh + X (.) C^T p]
@@ -491,7 +493,9 @@ int hp_problem_create(const hp_problem_desc *d, hp_problem **out) {
     if (cudaMalloc(pp, nb) != cudaSuccess) return fail(set_error(HP_ERR_NOMEM, "allocation"));
   }
   const int nC = (1 << (P->dim + 1)) - 1;
-  if (cudaMalloc(&P->Cbeta, sizeof(double) * P->n * nC) != cudaSuccess) return fail(set_error(HP_ERR_NOMEM, "allocation"));
+  if (cudaMalloc(&P->Cbeta, sizeof(double) * P->n * nC) != cudaSuccess ||
+      cudaMalloc(&P->CbetaE, sizeof(double) * P->n * nC) != cudaSuccess)
+    return fail(set_error(HP_ERR_NOMEM, "allocation"));
   if (cudaMalloc(&P->d_obs, sizeof(double) * std::max(1, P->nobs)) != cudaSuccess)
     return fail(set_error(HP_ERR_NOMEM, "allocation"));
   cudaMemset(P->d_obs, 0, sizeof(double) * std::max(1, P->nobs));
@@ -529,7 +533,7 @@ void hp_problem_destroy(hp_problem *P) {
       if (p) cudaFree(p);
   for (void *p : {(void *)P->M64.diag, (void *)P->M64.invdiag, (void *)P->M64.c, (void *)P->M32.diag,
                   (void *)P->M32.invdiag, (void *)P->M32.c, (void *)P->m, (void *)P->E, (void *)P->u,
-                  (void *)P->lift, (void *)P->Cbeta, (void *)P->padj, (void *)P->Cbeta_p, (void *)P->wmm, (void *)P->m_prior, (void *)P->f_load, (void *)P->d_obs, (void *)P->obs_node,
+                  (void *)P->lift, (void *)P->Cbeta, (void *)P->CbetaE, (void *)P->padj, (void *)P->Cbeta_p, (void *)P->CbetaE_p, (void *)P->wmm, (void *)P->m_prior, (void *)P->f_load, (void *)P->d_obs, (void *)P->obs_node,
                   (void *)P->obs_w, (void *)P->bt_row, (void *)P->bt_ptr, (void *)P->bt_ent})
     if (p) cudaFree(p);
   for (BlockWS<float> *W = &P->w32; W; W = nullptr) {

@@ -628,25 +628,43 @@ __device__ __forceinline__ bool shift_ok(const GridDesc &g, const int v[3], int 
   return ok;
 }
 
-// Y = scale * S_C (E (.) X) + yb * Y
+// betaE_q(i) = beta_q(i) E(i + o_q): the coefficients of C with e^m folded in (once per point),
+// so that C X costs one FMA per coupling
 template <int D>
-__global__ void k_C_apply(GridDesc g, const double *__restrict__ E, const double *__restrict__ beta,
-                          const double *__restrict__ X, long ldx, double *__restrict__ Y, long ldy, double scale,
-                          double yb) {
+__global__ void k_scale_C(GridDesc g, const double *__restrict__ E, const double *__restrict__ beta,
+                          double *__restrict__ betaE) {
+  constexpr int NC = (1 << (D + 1)) - 1;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
+    int v[3];
+    node_coords<D>(g, i, v);
+    betaE[i] = beta[i] * E[i];
+#pragma unroll
+    for (int q = 1; q < NC; ++q) {
+      int sg;
+      const int m = coff_mask<D>(q, &sg);
+      betaE[(long)q * g.n + i] =
+          shift_ok<D>(g, v, m, sg) ? beta[(long)q * g.n + i] * E[i + sg * mask_offset(g, m)] : 0.0;
+    }
+  }
+}
+
+// Y = scale * S_C (E (.) X) + yb * Y with the E-scaled coefficients betaE
+template <int D>
+__global__ void k_C_apply(GridDesc g, const double *__restrict__ betaE, const double *__restrict__ X, long ldx,
+                          double *__restrict__ Y, long ldy, double scale, double yb) {
   constexpr int NC = (1 << (D + 1)) - 1;
   const int j = blockIdx.y;
   const double *x = X + ldx * j;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
     int v[3];
     node_coords<D>(g, i, v);
-    double acc = beta[i] * E[i] * x[i];
+    double acc = betaE[i] * x[i];
 #pragma unroll
     for (int q = 1; q < NC; ++q) {
       int sg;
       const int m = coff_mask<D>(q, &sg);
       if (!shift_ok<D>(g, v, m, sg)) continue;
-      const long w = i + sg * mask_offset(g, m);
-      acc += beta[(long)q * g.n + i] * E[w] * x[w];
+      acc += betaE[(long)q * g.n + i] * x[i + sg * mask_offset(g, m)];
     }
     Y[ldy * j + i] = yb == 0.0 ? scale * acc : scale * acc + yb * Y[ldy * j + i];
   }
@@ -678,28 +696,31 @@ __global__ void k_Ct_apply(GridDesc g, const double *__restrict__ E, const doubl
   }
 }
 
-void launch_build_C_from(hp_problem *P, const double *w, double *beta) {
-  if (P->dim == 2)
+void launch_build_C_from(hp_problem *P, const double *w, double *beta, double *betaE) {
+  if (P->dim == 2) {
     k_build_C<2><<<grid_blocks(P->n), 256, 0, P->st>>>(P->lv[0].g, w, beta);
-  else
+    k_scale_C<2><<<grid_blocks(P->n), 256, 0, P->st>>>(P->lv[0].g, P->E, beta, betaE);
+  } else {
     k_build_C<3><<<grid_blocks(P->n), 256, 0, P->st>>>(P->lv[0].g, w, beta);
-  count_launch();
+    k_scale_C<3><<<grid_blocks(P->n), 256, 0, P->st>>>(P->lv[0].g, P->E, beta, betaE);
+  }
+  count_launch(2);
 }
 
-void launch_build_C(hp_problem *P) { launch_build_C_from(P, P->u, P->Cbeta); }
+void launch_build_C(hp_problem *P) { launch_build_C_from(P, P->u, P->Cbeta, P->CbetaE); }
 
-void launch_C_apply_beta(hp_problem *P, const double *beta, const double *X, long ldx, double *Y, long ldy, int s,
+void launch_C_apply_beta(hp_problem *P, const double *betaE, const double *X, long ldx, double *Y, long ldy, int s,
                          double scale, double yb) {
   dim3 grid(blocks_for(P->n, s), s);
   if (P->dim == 2)
-    k_C_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, beta, X, ldx, Y, ldy, scale, yb);
+    k_C_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, betaE, X, ldx, Y, ldy, scale, yb);
   else
-    k_C_apply<3><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, beta, X, ldx, Y, ldy, scale, yb);
+    k_C_apply<3><<<grid, NT, 0, P->st>>>(P->lv[0].g, betaE, X, ldx, Y, ldy, scale, yb);
   count_launch();
 }
 
 void launch_C_apply(hp_problem *P, const double *X, long ldx, double *Y, long ldy, int s, double scale) {
-  launch_C_apply_beta(P, P->Cbeta, X, ldx, Y, ldy, s, scale, 0.0);
+  launch_C_apply_beta(P, P->CbetaE, X, ldx, Y, ldy, s, scale, 0.0);
 }
 
 void launch_Ct_apply_beta(hp_problem *P, const double *beta_c, const double *W, long ldw, double *Y, long ldy, int s,

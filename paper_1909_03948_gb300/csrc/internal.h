@@ -115,9 +115,11 @@ struct hp_problem {
   bool have_point = false;
   double *m = nullptr, *E = nullptr, *u = nullptr, *lift = nullptr;
   double *Cbeta = nullptr;      // C as a stencil on e^m (.) X: (2^{D+1}-1) x n, built from u
+  double *CbetaE = nullptr;     // the same coefficients with e^m folded in (C X = CbetaE-stencil X)
   // adjoint terms of the full Newton Hessian (built on demand at the current point)
   double *padj = nullptr;       // adjoint p
   double *Cbeta_p = nullptr;    // C(p): the same stencil built from p
+  double *CbetaE_p = nullptr;   // ... with e^m folded in
   double *wmm = nullptr;        // C(u)^T p: weights of the diagonal second-derivative term
   bool have_p = false, have_full = false;
   // data
@@ -189,8 +191,9 @@ void prof_spin(hp_problem *P);  // profiling only: keep the GPU busy while the h
 int build_hierarchy_geometry(hp_problem *P);  // levels, allocs, prior/mass stencils, coarse A inverse
 int build_point(hp_problem *P, const double *m_dev);  // E, kappa hierarchy, K stencils, lift, coarse K inverse
 void launch_build_C(hp_problem *P);  // after the state solve
-void launch_build_C_from(hp_problem *P, const double *w, double *beta);  // C(w) stencil of any nodal w
-void launch_C_apply_beta(hp_problem *P, const double *beta, const double *X, long ldx, double *Y, long ldy, int s,
+// C(w) stencil of any nodal w: beta (for C^T) and betaE (beta with e^m folded in, for C)
+void launch_build_C_from(hp_problem *P, const double *w, double *beta, double *betaE);
+void launch_C_apply_beta(hp_problem *P, const double *betaE, const double *X, long ldx, double *Y, long ldy, int s,
                          double scale, double yb);
 void launch_Ct_apply_beta(hp_problem *P, const double *beta_c, const double *W, long ldw, double *Y, long ldy, int s,
                           double scale, double beta);
@@ -218,6 +221,10 @@ void launch_fill(double *X, long ldx, long n, int s, double v, cudaStream_t st);
 void launch_axpby(double a, const double *X, long ldx, double b, double *Y, long ldy, long n, int s,
                   cudaStream_t st);   // Y = a X + b Y
 void launch_ew_exp(const double *m, double *E, long n, cudaStream_t st);
+// B0 = B (the `face` nodes at each end of a column zeroed), X = 0, bb[j] = |B0_j|^2 and,
+// if rr_dev is non-null, rr[j] = bb[j]
+int ir_start(hp_problem *P, const double *B, long ldb, double *B0, long ld0, double *X, long ldx, long n, int s,
+             long face, double *bb_dev, double *rr_dev);
 // per-column deterministic dots: out[j] = sum_i X_ij Y_ij (FP64)
 int block_dot(hp_problem *P, const double *X, long ldx, const double *Y, long ldy, long n, int s,
               double *out_dev);
@@ -231,6 +238,8 @@ void unet_run(hp_unet *U, int N, cudaStream_t st);  // forward of the first N in
 // Stiffness solves: X (n x s) = initial guesses for the Dirichlet-zeroed right-hand
 // sides B when a network is attached and enabled; returns 1 if X was written, 0 if not.
 int warm_guess(hp_problem *P, const double *B, long ldb, double *X, long ldx, int s);
+// True when warm_guess would try a guess (a network attached and enabled, 2D).
+bool warm_attached(const hp_problem *P);
 // Columns j with flag[j] != 0 restart from zero: X_j = 0, R_j = B_j.
 void warm_fallback(hp_problem *P, const int *flag_host, int s, const double *B, long ldb, double *X, long ldx,
                    double *R, long ldr);

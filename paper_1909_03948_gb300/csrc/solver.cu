@@ -155,7 +155,7 @@ static void dot_finalize(const Fin &fin, unsigned nblk, int s, cudaStream_t st) 
 // and blocks, column groups over blockIdx.z.  Element (node i, group g) of a
 // block with group stride gs is at base + g*gs + i*VW.
 // ---------------------------------------------------------------------------
-enum { M_APPLY = 0, M_APPLY_DOT = 1, M_RESID = 2, M_JACOBI = 3, M_JACOBI_DOT = 4, M_JAC2 = 5 };
+enum { M_APPLY = 0, M_APPLY_DOT = 1, M_RESID = 2, M_JACOBI = 3, M_JACOBI_DOT = 4, M_JAC2 = 5, M_RESID_DOT = 6 };
 
 template <typename T, int VW, int D, bool FULL, int MODE>
 __global__ void __launch_bounds__(NB) k_st(GridDesc g, const T *__restrict__ diag, const T *__restrict__ invdiag,
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(NB) k_st(GridDesc g, const T *__restrict__ dia
   const int i0 = blockIdx.x * 32 + lane;
   const int nrows = D == 2 ? g.np : g.np * g.np;
   const int grp = blockIdx.z;
-  constexpr bool DOT = (MODE == M_APPLY_DOT || MODE == M_JACOBI_DOT);
+  constexpr bool DOT = (MODE == M_APPLY_DOT || MODE == M_JACOBI_DOT || MODE == M_RESID_DOT);
   PK acc = PK::zero();
   for (int row = blockIdx.y * (NB / 32) + (threadIdx.x >> 5); row < nrows; row += gridDim.y * (NB / 32)) {
     if (i0 >= g.np) break;
@@ -230,9 +230,12 @@ __global__ void __launch_bounds__(NB) k_st(GridDesc g, const T *__restrict__ dia
           for (int q = 0; q < VW; ++q) acc.v[q] += xc.v[q] * out.v[q];
       } else {
         const PK bb = PK::ld(B + grp * gb + id * VW);
-        if (MODE == M_RESID) {
+        if (MODE == M_RESID || MODE == M_RESID_DOT) {
 #pragma unroll
           for (int q = 0; q < VW; ++q) out.v[q] = bb.v[q] - sx.v[q];
+          if (DOT)
+#pragma unroll
+            for (int q = 0; q < VW; ++q) acc.v[q] += out.v[q] * out.v[q];
         } else {
           const T wi = omega * invdiag[id];
 #pragma unroll
@@ -747,7 +750,7 @@ static void st_launch(const GridDesc &g, const Stencil<T> &S, const T *X, long g
                                                      omega2, fin);
   }
   count_launch();
-  if (MODE == M_APPLY_DOT || MODE == M_JACOBI_DOT) dot_finalize(fin, grid.x * grid.y, s, st);
+  if (MODE == M_APPLY_DOT || MODE == M_JACOBI_DOT || MODE == M_RESID_DOT) dot_finalize(fin, grid.x * grid.y, s, st);
 }
 
 template <typename T>
@@ -1542,15 +1545,14 @@ int apply_op64(hp_problem *P, OpKind op, const double *X, long ldx, double *Y, l
   return cuda_check(cudaGetLastError(), "apply");
 }
 
-// FP64 residual R = B - S X (column-major) and per-column |R|^2 -> sc.rr
+// FP64 residual R = B - S X (column-major) with the per-column |R|^2 -> sc.rr in the same pass
 static int residual64(hp_problem *P, OpKind op, const double *B, long ldb, const double *X, long ldx, double *R,
                       long ldr, int s) {
   const int pr = prof_start(P, PROF_RESID64);
-  st_launch<double, 1, M_RESID>(P->lv[0].g, stencil_of<double>(P, op, 0), X, ldx, B, ldb, R, ldr, s, 0.0, Fin{},
-                                P->st);
+  st_launch<double, 1, M_RESID_DOT>(P->lv[0].g, stencil_of<double>(P, op, 0), X, ldx, B, ldb, R, ldr, s, 0.0,
+                                    make_fin(P, FIN_STORE, 0.0, P->sc.rr.as<double>()), P->st);
   prof_stop(P, pr);
-  HP_TRY(block_dot(P, R, ldr, R, ldr, P->n, s, P->sc.rr.as<double>()));
-  return 0;
+  return cuda_check(cudaGetLastError(), "residual");
 }
 
 template <typename T, int VW>
@@ -1565,17 +1567,19 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
   HP_TRY(P->r64.ensure(sizeof(double) * ld64 * s));
   HP_TRY(P->b64.ensure(sizeof(double) * ld64 * s));
   double *r64 = P->r64.as<double>(), *b64 = P->b64.as<double>();
-  launch_copy(B, ldb, b64, ld64, n, s, st);
-  if (op == OP_K) launch_zero_dirichlet(P, b64, ld64, s);
-  HP_TRY(block_dot(P, b64, ld64, b64, ld64, n, s, P->sc.bb.as<double>()));
+  // one pass over B: b64 = B (Dirichlet rows of a stiffness solve zeroed), X = 0, |b|^2;
+  // from x = 0 the first residual is b64 itself, so rr = bb
+  const GridDesc &g0 = P->lv[0].g;
+  const long face = op == OP_K ? (P->dim == 2 ? g0.np : (long)g0.np * g0.np) : 0;
+  const bool want_warm = op == OP_K && warm_attached(P);
+  HP_TRY(ir_start(P, B, ldb, b64, ld64, X, ldx, n, s, face, P->sc.bb.as<double>(),
+                  want_warm ? nullptr : P->sc.rr.as<double>()));
   // start from the learned guess (stiffness solves with a network attached) or from zero
-  const bool warm = op == OP_K && warm_guess(P, b64, ld64, X, ldx, s);
-  if (warm) {
-    HP_TRY(residual64(P, op, b64, ld64, X, ldx, r64, ld64, s));
-  } else {
+  const bool warm = want_warm && warm_guess(P, b64, ld64, X, ldx, s);
+  if (warm) HP_TRY(residual64(P, op, b64, ld64, X, ldx, r64, ld64, s));
+  else if (want_warm) {  // the guess was not made: X (possibly partly written) back to zero, rr = bb
     launch_fill(X, ldx, n, s, 0.0, st);
-    launch_copy(b64, ld64, r64, ld64, n, s, st);
-    HP_TRY(block_dot(P, r64, ld64, r64, ld64, n, s, P->sc.rr.as<double>()));
+    launch_copy(P->sc.bb.as<double>(), 0, P->sc.rr.as<double>(), 0, s, 1, st);
   }
   double *hrr = P->sc.h_rr, *hbb = P->sc.h_bb;
   HP_CUDA(cudaMemcpyAsync(hbb, P->sc.bb.p, sizeof(double) * s, cudaMemcpyDeviceToHost, st));
@@ -1586,10 +1590,12 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
     HP_CUDA(cudaMemcpyAsync(hrr, P->sc.rr.p, sizeof(double) * s, cudaMemcpyDeviceToHost, st));
     HP_CUDA(cudaStreamSynchronize(st));
     if (warm && outer == 0) {
-      // a guess whose residual is no smaller than |b| (or non-finite) is dropped for zero
+      // a guess whose residual is no smaller than |b| (or non-finite) is dropped for zero;
+      // |r|^2 and |b|^2 come from differently ordered reductions, so "no smaller" allows
+      // a relative rounding margin
       std::vector<int> flag(s);
       for (int j = 0; j < s; ++j) {
-        flag[j] = hbb[j] > 0.0 && !(hrr[j] < hbb[j]);
+        flag[j] = hbb[j] > 0.0 && !(hrr[j] < (1.0 - 1e-10) * hbb[j]);
         if (flag[j]) hrr[j] = hbb[j];
       }
       warm_fallback(P, flag.data(), s, b64, ld64, X, ldx, r64, ld64);
@@ -1618,7 +1624,9 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
     HP_CUDA(cudaMemcpyAsync(P->sc.scale.p, hscale.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
     HP_CUDA(cudaMemcpyAsync(P->sc.iscale.p, hiscale.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
     HP_CUDA(cudaMemcpyAsync(P->sc.tol2col.p, htol2.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
-    k_to_inner<T, VW><<<nodegrid(n, ng), NB, 0, st>>>(n, r64, ld64, P->sc.scale.as<double>(), s,
+    // the first residual of a solve from zero is b64 (r64 not yet written)
+    const double *rsrc = (outer == 0 && !warm) ? b64 : r64;
+    k_to_inner<T, VW><<<nodegrid(n, ng), NB, 0, st>>>(n, rsrc, ld64, P->sc.scale.as<double>(), s,
                                                       W.r.template as<T>(), gs);
     count_launch();
     int its = 0;

@@ -83,12 +83,45 @@ __global__ void k_dot_partial(const double *__restrict__ X, long ldx, const doub
   if (threadIdx.x == 0) part[(long)j * gridDim.x + blockIdx.x] = acc;
 }
 
-__global__ void k_dot_final(const double *__restrict__ part, int nb, double *__restrict__ out) {
+__global__ void k_dot_final(const double *__restrict__ part, int nb, double *__restrict__ out,
+                            double *__restrict__ out2) {
   const int j = blockIdx.x;
   double acc = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[(long)j * nb + b];
   acc = block_sum<NT>(acc);
-  if (threadIdx.x == 0) out[j] = acc;
+  if (threadIdx.x == 0) {
+    out[j] = acc;
+    if (out2) out2[j] = acc;
+  }
+}
+
+// Start of an iterative-refinement solve from x = 0, in one pass over B: B0 = B with the
+// `face` nodes at each end of a column zeroed (the Dirichlet rows; face = 0 keeps all),
+// X = 0, and the block partials of |B0_j|^2.  X may alias B (each thread reads its
+// entry of B before writing the same entry of X).
+__global__ void k_ir_start(const double *B, long ldb, double *__restrict__ B0, long ld0, double *X, long ldx,
+                           long n, long face, double *__restrict__ part) {
+  const int j = blockIdx.y;
+  double acc = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double v = (i < face || i >= n - face) ? 0.0 : B[ldb * j + i];
+    B0[ld0 * j + i] = v;
+    X[ldx * j + i] = 0.0;
+    acc += v * v;
+  }
+  acc = block_sum<NT>(acc);
+  if (threadIdx.x == 0) part[(long)j * gridDim.x + blockIdx.x] = acc;
+}
+
+int ir_start(hp_problem *P, const double *B, long ldb, double *B0, long ld0, double *X, long ldx, long n, int s,
+             long face, double *bb_dev, double *rr_dev) {
+  const int nb = blocks_for(n, s);
+  HP_TRY(P->sc.tmp.ensure(sizeof(double) * (size_t)nb * s));
+  double *part = P->sc.tmp.as<double>();
+  k_ir_start<<<dim3(nb, s), NT, 0, P->st>>>(B, ldb, B0, ld0, X, ldx, n, face, part);
+  k_dot_final<<<s, NT, 0, P->st>>>(part, nb, bb_dev, rr_dev);
+  count_launch(2);
+  return 0;
 }
 
 int block_dot(hp_problem *P, const double *X, long ldx, const double *Y, long ldy, long n, int s,
@@ -97,7 +130,7 @@ int block_dot(hp_problem *P, const double *X, long ldx, const double *Y, long ld
   HP_TRY(P->sc.tmp.ensure(sizeof(double) * (size_t)nb * s));
   double *part = P->sc.tmp.as<double>();
   k_dot_partial<<<dim3(nb, s), NT, 0, P->st>>>(X, ldx, Y, ldy, n, part);
-  k_dot_final<<<s, NT, 0, P->st>>>(part, nb, out_dev);
+  k_dot_final<<<s, NT, 0, P->st>>>(part, nb, out_dev, nullptr);
   count_launch(2);
   return 0;
 }

@@ -115,8 +115,10 @@ static int jacobi_scaled(hp_problem *P, const double *B, long ldb, double *Z, lo
   return block_dot(P, Z, ldz, Z, ldz, P->n, s, P->ws_bb.as<double>());
 }
 
+bool warm_attached(const hp_problem *P) { return P->ws_on && P->ws_net && P->dim == 2; }
+
 int warm_guess(hp_problem *P, const double *B, long ldb, double *X, long ldx, int s) {
-  if (!P->ws_on || !P->ws_net || P->dim != 2) return 0;
+  if (!warm_attached(P)) return 0;
   hp_unet *U = P->ws_net;
   int H, W;
   unet_dims(U, &H, &W);
