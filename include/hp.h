@@ -302,7 +302,7 @@ int hp_pointwise_variance(hp_problem *P, int method, const double *Z_dev, int ld
  * before and after each coarse correction and damping omega, the number of RHS
  * columns solved together (0 = all), and the grid-size cap of the node kernels.
  * Defaults: nu 3, nu_coarse 0, omega 0.7, col_chunk 0, max_blocks 2048, smoother 1
- * (Chebyshev), cheb_alpha 10, fuse_transfer 0, fuse_from 0.  Every setting solves to the same
+ * (Chebyshev), cheb_alpha 10, fuse_transfer 0, fuse_from 0, tma_tiles 0.  Every setting solves to the same
  * tolerance; only speed changes. */
 typedef struct {
   int nu;          /* 1..4 */
@@ -317,12 +317,17 @@ typedef struct {
   double cheb_alpha; /* > 1 */
   int fuse_transfer; /* 1: the residual and its restriction run as one kernel, and so
                         do the prolongation and the first post-smoothing sweep (the
-                        fine residual and the prolonged iterate are never stored) */
+                        fine residual and the prolonged iterate are never stored);
+                        2: the same on the levels below the finest only */
   int fuse_from;   /* 0 = off, else the first multigrid level (>= 1) whose whole
                       coarse tail of the V-cycle runs as one launch: one thread-block
                       cluster of 8 CTAs per column group, steps separated by the
                       hardware cluster barrier (ignored when fewer than 2 levels
                       remain below it) */
+  int tma_tiles;   /* 1: on the multigrid levels of 2D stiffness solves whose grid has
+                      np - 1 a multiple of 32 (np >= 33), the stencil kernels work on
+                      32 x 16-node tiles that bulk tensor copies (TMA) bring into shared
+                      memory with their halo; 0: every warp loads its own row of nodes */
 } hp_tuning;
 int hp_set_tuning(hp_problem *P, const hp_tuning *t);
 int hp_get_tuning(const hp_problem *P, hp_tuning *t);
@@ -430,6 +435,13 @@ int hp_profile_read(hp_problem *P, int nids, int *counts, double *total_ms);
  * FP32 solve with at least 4 columns on a multilevel hierarchy (HP_ERR_STATE). */
 int hp_replay_kernel(hp_problem *P, int family, int reps, void *flush, size_t flush_bytes, double *us_warm,
                      double *us_cold);
+/* The same kernel replayed inside a CUDA graph: reps launches captured into one
+ * graph, which is launched once untimed and once timed (CUDA events around the
+ * graph launch).  us (HOST) receives the mean microseconds per launch -- the cost
+ * of the kernel as the solver's captured PCG loop runs it, without the ~2 us
+ * granularity of back-to-back stream launches.  Same preconditions as above;
+ * allocates and frees the graph (a measurement call, not for the hot path). */
+int hp_replay_kernel_graph(hp_problem *P, int family, int reps, double *us);
 
 /* ---- status --------------------------------------------------------------- */
 const char *hp_status_string(int status);

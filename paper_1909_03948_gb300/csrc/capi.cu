@@ -523,7 +523,7 @@ void hp_problem_destroy(hp_problem *P) {
   for (int l = 0; l < HP_MAXL; ++l) {
     Level &lv = P->lv[l];
     for (void *p : {(void *)lv.kappa, (void *)lv.K64.diag, (void *)lv.K64.invdiag, (void *)lv.K64.c,
-                    (void *)lv.K32.diag, (void *)lv.K32.invdiag, (void *)lv.K32.c, (void *)lv.A64.diag,
+                    (void *)lv.K32.diag, (void *)lv.K32.invdiag, (void *)lv.K32.c, (void *)lv.K32.pk, (void *)lv.A64.diag,
                     (void *)lv.A64.invdiag, (void *)lv.A64.c, (void *)lv.A32.diag, (void *)lv.A32.invdiag,
                     (void *)lv.A32.c})
       if (p) cudaFree(p);

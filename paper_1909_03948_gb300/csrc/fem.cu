@@ -192,6 +192,14 @@ __global__ void k_build_K(GridDesc g, const double *__restrict__ kappa, double *
   }
 }
 
+// 2D stiffness in FP32, one 16-byte record per node for the tiled stencil kernels:
+// {diag, 1 / diag, coupling to x + 1, coupling to y + 1}
+__global__ void k_pack_K2(long n, const float *__restrict__ diag, const float *__restrict__ invdiag,
+                          const float *__restrict__ c, float4 *__restrict__ pk) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    pk[i] = make_float4(diag[i], invdiag[i], c[i], c[n + i]);
+}
+
 template <int D>
 __device__ __forceinline__ int count_elems(const GridDesc &g, const int v[3], int b) {
   int n = 0;
@@ -480,6 +488,7 @@ int build_hierarchy_geometry(hp_problem *P) {
     for (int a = 0; a < D; ++a) lv.nelems *= lv.g.N;
     HP_CUDA(cudaMalloc(&lv.kappa, sizeof(double) * lv.nelems));
     HP_TRY(alloc_stencil(lv.K64, lv.K32, lv.g.n, nfK, false));
+    if (tile_grid(lv.g)) HP_CUDA(cudaMalloc(&lv.K32.pk, sizeof(float4) * lv.g.n));
     HP_TRY(alloc_stencil(lv.A64, lv.A32, lv.g.n, nfA, true));
     const int nb = grid_blocks(lv.g.n);
     Theta6 th;
@@ -553,6 +562,11 @@ int build_point(hp_problem *P, const double *m_dev) {
                                                            lv.K32.diag, lv.K32.invdiag, lv.K32.c, lift, P->u_top,
                                                            P->u_bottom);
     count_launch();
+    if (lv.K32.pk) {
+      k_pack_K2<<<grid_blocks(lv.g.n), 256, 0, P->st>>>(lv.g.n, lv.K32.diag, lv.K32.invdiag, lv.K32.c,
+                                                        reinterpret_cast<float4 *>(lv.K32.pk));
+      count_launch();
+    }
   }
   HP_CUDA(cudaGetLastError());
   HP_TRY(coarse_setup(P, OP_K));

@@ -12,6 +12,14 @@
 
 namespace hp {
 
+// Grids whose stiffness stencils run as TMA-tiled kernels (2D, np - 1 a multiple of the
+// 32 x 16 tile, at least one tile wide): the last tile in each direction also takes the
+// grid's final node / row.
+constexpr int TILE_X = 32, TILE_Y = 16;
+inline bool tile_grid(const GridDesc &g) {
+  return g.dim == 2 && g.np >= TILE_X + 1 && (g.np - 1) % TILE_X == 0 && (g.np - 1) % TILE_Y == 0;
+}
+
 // Symmetric stencil stored by "forward" couplings: y_i = diag_i x_i +
 // sum_f [c_f(i) x_{i+o_f} + c_f(i-o_f) x_{i-o_f}], with o_f the 0/1 corner
 // masks of the Kuhn edges.  full = false: axis offsets only (stiffness,
@@ -21,6 +29,7 @@ template <typename T> struct Stencil {
   T *diag = nullptr;
   T *invdiag = nullptr;
   T *c = nullptr;
+  T *pk = nullptr;  // 2D axis-only stencils on tiled grids: {diag, invdiag, c_0, c_1} per node (16 B)
   int nf = 0;
   bool full = false;
   double lmax = 2.0;  // upper bound of the spectrum of diag^-1 S (Gershgorin)
@@ -101,6 +110,7 @@ struct hp_problem {
   int smoother = 1;             // 0 damped Jacobi (omega), 1 Chebyshev (cheb_alpha)   (tuning)
   int fuse_transfer = 0;        // residual + restriction and prolongation + first post sweep fused (tuning)
   double cheb_alpha = 10.0;     // Chebyshev interval [lmax / alpha, lmax]             (tuning)
+  int tma_tiles = 0;            // 2D stiffness levels as TMA-tiled stencil kernels       (tuning)
   cudaStream_t st = nullptr;
   cudaStream_t cap = nullptr;   // private stream used to capture CUDA graphs
   bool use_graphs = true;       // inner PCG loops as graphs with a device-side while node

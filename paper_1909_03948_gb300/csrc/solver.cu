@@ -17,11 +17,15 @@
 //   * Outer loop: r = b - K x in FP64 (column-major, the ABI layout), inner solve
 //     on r / |r| in T, x += d.  Stops when every column has |r|/|b| <= rtol.
 //   * Inner products: per-block partials (warp sums in T, block sums in FP64),
-//     the last block to finish sums the partials of its column in a fixed order
-//     (deterministic) and applies the scalar step of CG in FP64.
+//     then one small kernel per product sums the partials of each column in a
+//     fixed order (deterministic) and applies the scalar step of CG in FP64.
+//   * Level stencils of 2D stiffness solves: one CTA per 32 x 16-node tile, its
+//     data brought into shared memory by TMA bulk tensor copies (k_st_tile).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+
+#include <cuda.h>
 
 #include "internal.h"
 
@@ -249,6 +253,160 @@ __global__ void __launch_bounds__(NB) k_st(GridDesc g, const T *__restrict__ dia
     out.st(Y + grp * gy + id * VW);
   }
   if (DOT) dot_partial<T, VW>(acc, fin.part, grp, s, blockIdx.x + gridDim.x * blockIdx.y, gridDim.x * gridDim.y);
+}
+
+// ---------------------------------------------------------------------------
+// TMA-tiled stencil kernels (2D stiffness levels, FP32, 4 columns per node).
+// One CTA per tile of TILE_X x TILE_Y nodes of one column group.  Thread 0 issues
+// bulk tensor copies (cp.async.bulk.tensor) of the tile's x with a one-node halo,
+// of its right-hand side and of the packed coefficients {diag, 1/diag, c_x, c_y}
+// (also with the halo) into shared memory; all three complete on one mbarrier.  The
+// CTA therefore has its whole working set in flight at once, where the row kernel
+// above issues one row of loads per warp at a time and waits for each.  The last
+// tile in x (in y) also takes the grid's final node (row), so every box is sized
+// for TILE + 1 nodes plus the halo; copies that reach past the grid read zeros.
+// The arithmetic is k_st's, operation for operation, on the same values.
+// ---------------------------------------------------------------------------
+constexpr int TL_NT = NB;                                   // 4 warps
+constexpr int TLB_X = TILE_X + 3, TLB_Y = TILE_Y + 3;       // x / coefficient boxes
+constexpr int TLR_X = TILE_X + 1, TLR_Y = TILE_Y + 1;       // right-hand-side box
+constexpr unsigned TL_XBYTES = TLB_X * TLB_Y * 16u, TL_RBYTES = TLR_X * TLR_Y * 16u;
+constexpr unsigned TL_OFF_R = (TL_XBYTES + 127u) / 128u * 128u;
+constexpr unsigned TL_OFF_C = TL_OFF_R + (TL_RBYTES + 127u) / 128u * 128u;
+constexpr unsigned TL_OFF_M = TL_OFF_C + (TL_XBYTES + 127u) / 128u * 128u;
+constexpr unsigned TL_SMEM = TL_OFF_M + 16u + 128u;  // + alignment slack
+
+// set by a tile kernel whose copies did not arrive within its wait limit
+__device__ int g_tile_timeout;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+// waits for phase 0 of the barrier for at most ~2^31 clocks (about a second)
+__device__ __forceinline__ bool mbar_wait0(uint32_t bar) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(TL_NT) k_st_tile(const __grid_constant__ CUtensorMap mx,
+                                                   const __grid_constant__ CUtensorMap mr,
+                                                   const __grid_constant__ CUtensorMap mc, GridDesc g, int ntx,
+                                                   int nty, float *__restrict__ Y, long gy, int s, float omega,
+                                                   float omega2, Fin fin) {
+  using PK = Pack<float, 4>;
+  extern __shared__ __align__(128) unsigned char tl_smem_raw[];
+  // the boxes start on 128-byte boundaries (the launch adds 128 bytes of slack)
+  unsigned char *tl_smem = tl_smem_raw + ((128u - (smem_u32(tl_smem_raw) & 127u)) & 127u);
+  const float *xs = reinterpret_cast<const float *>(tl_smem);
+  const float *rs = reinterpret_cast<const float *>(tl_smem + TL_OFF_R);
+  const float4 *cs = reinterpret_cast<const float4 *>(tl_smem + TL_OFF_C);
+  const uint32_t bar = smem_u32(tl_smem + TL_OFF_M);
+  constexpr bool HAS_B = (MODE == M_RESID || MODE == M_JACOBI || MODE == M_JACOBI_DOT);
+  constexpr bool DOT = (MODE == M_APPLY_DOT || MODE == M_JACOBI_DOT);
+  const int tile = blockIdx.x, grp = blockIdx.y;
+  const int tx = tile % ntx, ty = tile / ntx;
+  const int x0 = tx * TILE_X, y0 = ty * TILE_Y;
+  const int wx = TILE_X + (tx == ntx - 1), hy = TILE_Y + (ty == nty - 1);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"(2u * TL_XBYTES + (HAS_B ? TL_RBYTES : 0u))
+                 : "memory");
+    tma_load_3d(smem_u32(xs), &mx, 4 * (x0 - 1), y0 - 1, grp, bar);
+    if (HAS_B) tma_load_3d(smem_u32(rs), &mr, 4 * x0, y0, grp, bar);
+    tma_load_2d(smem_u32(cs), &mc, 4 * (x0 - 1), y0 - 1, bar);
+  }
+  if (!mbar_wait0(bar)) {
+    if (threadIdx.x == 0) atomicExch(&g_tile_timeout, 1);
+    return;
+  }
+  PK acc = PK::zero();
+  for (int t = threadIdx.x; t < wx * hy; t += TL_NT) {
+    const int lx = t % wx, ly = t / wx;
+    const int v0 = x0 + lx, v1 = y0 + ly;
+    const int ci = (ly + 1) * TLB_X + lx + 1;  // this node in the halo boxes
+    const bool fx = v0 < g.N, bx = v0 > 0, fy = v1 < g.N, by = v1 > 0;
+    const float4 cc = cs[ci];
+    PK out;
+    if (MODE == M_JAC2) {
+      // two damped-Jacobi sweeps from zero: e1 = w1 D^-1 r, e2 = e1 + w2 D^-1 (r - S e1)
+      const float wi = omega * cc.y, wi2 = omega2 * cc.y;
+      const PK r = PK::ld(xs + ci * 4);
+      PK e1c;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) e1c.v[q] = wi * r.v[q];
+      PK sx;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sx.v[q] = cc.x * e1c.v[q];
+      if (fx) sx.axpy(cc.z * omega * cs[ci + 1].y, PK::ld(xs + (ci + 1) * 4));
+      if (bx) sx.axpy(cs[ci - 1].z * omega * cs[ci - 1].y, PK::ld(xs + (ci - 1) * 4));
+      if (fy) sx.axpy(cc.w * omega * cs[ci + TLB_X].y, PK::ld(xs + (ci + TLB_X) * 4));
+      if (by) sx.axpy(cs[ci - TLB_X].w * omega * cs[ci - TLB_X].y, PK::ld(xs + (ci - TLB_X) * 4));
+#pragma unroll
+      for (int q = 0; q < 4; ++q) out.v[q] = e1c.v[q] + wi2 * (r.v[q] - sx.v[q]);
+    } else {
+      const PK xc = PK::ld(xs + ci * 4);
+      PK sx;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sx.v[q] = cc.x * xc.v[q];
+      if (fx) sx.axpy(cc.z, PK::ld(xs + (ci + 1) * 4));
+      if (bx) sx.axpy(cs[ci - 1].z, PK::ld(xs + (ci - 1) * 4));
+      if (fy) sx.axpy(cc.w, PK::ld(xs + (ci + TLB_X) * 4));
+      if (by) sx.axpy(cs[ci - TLB_X].w, PK::ld(xs + (ci - TLB_X) * 4));
+      if (MODE == M_APPLY || MODE == M_APPLY_DOT) {
+        out = sx;
+        if (DOT)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc.v[q] += xc.v[q] * out.v[q];
+      } else {
+        const PK bb = PK::ld(rs + (ly * TLR_X + lx) * 4);
+        if (MODE == M_RESID) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) out.v[q] = bb.v[q] - sx.v[q];
+        } else {
+          const float wi = omega * cc.y;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) out.v[q] = xc.v[q] + wi * (bb.v[q] - sx.v[q]);
+          if (DOT)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc.v[q] += bb.v[q] * out.v[q];
+        }
+      }
+    }
+    out.st(Y + grp * gy + ((long)v0 + (long)g.np * v1) * 4);
+  }
+  if (DOT) dot_partial<float, 4>(acc, fin.part, grp, s, tile, ntx * nty);
 }
 
 // ---------------------------------------------------------------------------
@@ -729,9 +887,84 @@ static long rowgrid_blocks(const GridDesc &g) {
   return (long)d.x * d.y;
 }
 
+// level stencils of 2D stiffness solves as TMA tiles (a tuning knob), set per solve
+static thread_local int tl_tma = 0;
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, looked up once through the runtime
+static EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// Tensor map over a grouped FP32 block ([group][node][4], group stride gs floats) as a
+// rank-3 tensor {4 np floats (one grid row), np rows, ng groups}; boxes of box_nodes x
+// box_rows nodes of one group.  Zeros are read outside the grid.
+static bool tile_map_block(CUtensorMap *m, const float *base, long gs, const GridDesc &g, int ng, int box_nodes,
+                           int box_rows) {
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dim[3] = {4ull * (cuuint64_t)g.np, (cuuint64_t)g.np, (cuuint64_t)ng};
+  const cuuint64_t str[2] = {16ull * (cuuint64_t)g.np, 4ull * (cuuint64_t)gs};
+  const cuuint32_t box[3] = {4u * (cuuint32_t)box_nodes, (cuuint32_t)box_rows, 1u};
+  const cuuint32_t es[3] = {1u, 1u, 1u};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dim, str, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the packed coefficient records (one float4 per node) as a rank-2 tensor {4 np, np}
+static bool tile_map_coef(CUtensorMap *m, const float *pk, const GridDesc &g) {
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dim[2] = {4ull * (cuuint64_t)g.np, (cuuint64_t)g.np};
+  const cuuint64_t str[1] = {16ull * (cuuint64_t)g.np};
+  const cuuint32_t box[2] = {4u * TLB_X, (cuuint32_t)TLB_Y};
+  const cuuint32_t es[2] = {1u, 1u};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(pk), dim, str, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Launches the tiled kernel for a tile grid; false (nothing launched) when a tensor
+// map cannot be encoded, and the caller uses the row kernel.
+template <int MODE>
+static bool tile_launch(const GridDesc &g, const Stencil<float> &S, const float *X, long gx, const float *B, long gb,
+                        float *Y, long gy, int s, float omega, float omega2, const Fin &fin, cudaStream_t st) {
+  constexpr bool HAS_B = (MODE == M_RESID || MODE == M_JACOBI || MODE == M_JACOBI_DOT);
+  const int ng = (s + 3) / 4;
+  CUtensorMap mx, mr, mc;
+  if (!tile_map_block(&mx, X, gx, g, ng, TLB_X, TLB_Y) || !tile_map_coef(&mc, S.pk, g)) return false;
+  if (HAS_B) {
+    if (!tile_map_block(&mr, B, gb, g, ng, TLR_X, TLR_Y)) return false;
+  } else {
+    mr = mx;
+  }
+  const int ntx = (g.np - 1) / TILE_X, nty = (g.np - 1) / TILE_Y;
+  k_st_tile<MODE><<<dim3(ntx * nty, ng), TL_NT, TL_SMEM, st>>>(mx, mr, mc, g, ntx, nty, Y, gy, s, omega, omega2, fin);
+  count_launch();
+  if (MODE == M_APPLY_DOT || MODE == M_JACOBI_DOT) dot_finalize(fin, ntx * nty, s, st);
+  return true;
+}
+
 template <typename T, int VW, int MODE>
 static void st_launch(const GridDesc &g, const Stencil<T> &S, const T *X, long gx, const T *B, long gb, T *Y, long gy,
                       int s, T omega, const Fin &fin, cudaStream_t st, T omega2 = T(0)) {
+  if constexpr (sizeof(T) == 4 && VW == 4 && MODE != M_RESID_DOT) {
+    if (tl_tma && S.pk && !S.full && tile_grid(g) &&
+        tile_launch<MODE>(g, S, X, gx, B, gb, Y, gy, s, omega, omega2, fin, st))
+      return;
+  }
   const int ng = (s + VW - 1) / VW;
   const dim3 grid = rowgrid_capped(g, ng);
   if (g.dim == 2) {
@@ -1116,6 +1349,9 @@ __global__ void __launch_bounds__(VC_NT) k_vcycle_tail(VTail<T> vt) {
 // (0, lmax].
 // smoothing sweeps at level l (nu_coarse, when set, on the coarser levels)
 static int nu_at(const hp_problem *P, int l) { return (l > 0 && P->nu_coarse > 0) ? P->nu_coarse : P->nu; }
+// residual + restriction and prolongation + first post sweep fused at level l: on every
+// level (fuse_transfer 1) or below the finest only (2), where launches, not bytes, dominate
+static bool fuse_at(const hp_problem *P, int l) { return P->fuse_transfer == 1 || (P->fuse_transfer == 2 && l >= 1); }
 
 template <typename T>
 static void smooth_weights(const hp_problem *P, OpKind op, int l, T w[4]) {
@@ -1261,7 +1497,7 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
     }
     const GridDesc &gc = P->lv[l + 1].g;
     T *rc = const_cast<T *>(rl[l + 1]);
-    if (P->fuse_transfer) {
+    if (fuse_at(P, l)) {
       // residual and restriction in one pass (the fine residual is not stored)
       const dim3 gr = rowgrid(gc, ng);
       const int zd = op == OP_K;
@@ -1314,7 +1550,7 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
     T w[4];
     smooth_weights<T>(P, op, l, w);
     int k0 = 0;
-    if (P->fuse_transfer && nu >= 2) {
+    if (fuse_at(P, l) && nu >= 2) {
       // prolongation and the first post-smoothing sweep in one pass (x + P e_c is not stored)
       const dim3 gr = rowgrid_capped(g, ng);
       const T *ec = cur[l + 1];
@@ -1490,9 +1726,19 @@ static int kernels_per_iteration(const hp_problem *P, OpKind op) {
   int vc = 0;
   for (int l = 0; l < separate; ++l) {
     const int nu = nu_at(P, l);
-    vc += (nu >= 2 ? nu - 1 : 1) + nu + (P->fuse_transfer ? (nu >= 2 ? 1 : 2) : 3);
+    vc += (nu >= 2 ? nu - 1 : 1) + nu + (fuse_at(P, l) ? (nu >= 2 ? 1 : 2) : 3);
   }
   return 7 + vc + 1 + 2 * (P->L == 1);
+}
+
+// after a PCG: fails the solve if a tile kernel gave up waiting for its copies
+// (h_it[1] holds the flag read back with the iteration count), and clears the flag
+static int tile_timeout_check(hp_problem *P, const int *h_it) {
+  if (!h_it[1]) return 0;
+  static const int zero = 0;
+  cudaMemcpyToSymbolAsync(g_tile_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, P->st);
+  cudaStreamSynchronize(P->st);
+  return set_error(HP_ERR_CUDA, "a tiled stencil kernel timed out waiting for its tensor copies");
 }
 
 template <typename T, int VW>
@@ -1513,9 +1759,11 @@ static int pcg(hp_problem *P, OpKind op, int s, double rtol, int maxit, int *its
     }
     HP_CUDA(cudaGraphLaunch(G->exec, st));
     HP_CUDA(cudaMemcpyAsync(h_it, P->sc.iter.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HP_CUDA(cudaMemcpyFromSymbolAsync(h_it + 1, g_tile_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
     HP_CUDA(cudaStreamSynchronize(st));
     count_launch((unsigned long long)(*h_it) * kernels_per_iteration(P, op) + 2);
     *its = *h_it;
+    HP_TRY(tile_timeout_check(P, h_it));
     return *h_it >= maxit ? HP_ERR_NOT_CONVERGED : 0;
   }
   const double tol2 = rtol * rtol;
@@ -1535,6 +1783,9 @@ static int pcg(hp_problem *P, OpKind op, int s, double rtol, int maxit, int *its
     if (nact == 0 || *h_it >= maxit) break;
   }
   *its = *h_it;
+  HP_CUDA(cudaMemcpyFromSymbolAsync(h_it + 1, g_tile_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+  HP_CUDA(cudaStreamSynchronize(st));
+  HP_TRY(tile_timeout_check(P, h_it));
   HP_CUDA(cudaGetLastError());
   return *h_it >= maxit ? HP_ERR_NOT_CONVERGED : 0;
 }
@@ -1630,7 +1881,9 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
                                                       W.r.template as<T>(), gs);
     count_launch();
     int its = 0;
-    pcg<T, VW>(P, op, s, tol_in, P->max_iter, &its);  // a stalled inner solve still reduces the residual
+    // a stalled inner solve still reduces the residual; other failures end the solve
+    const int prc = pcg<T, VW>(P, op, s, tol_in, P->max_iter, &its);
+    if (prc && prc != HP_ERR_NOT_CONVERGED) return prc;
     total_its += its;
     prof_spin(P);
     k_accum<T, VW><<<nodegrid(n, ng), NB, 0, st>>>(n, W.x.template as<T>(), gs, P->sc.iscale.as<double>(), s, X,
@@ -1666,6 +1919,7 @@ int solve_block(hp_problem *P, OpKind op, const double *B, long ldb, double *X, 
                 hp_solve_stats *st) {
   if (s <= 0) return 0;
   tl_max_blocks = P->max_blocks;
+  tl_tma = P->tma_tiles;
   const int w = (P->col_chunk > 0 && P->col_chunk < s) ? P->col_chunk : s;
   for (int c0 = 0; c0 < s; c0 += w) {
     const int cs = std::min(w, s - c0);
@@ -1704,6 +1958,7 @@ extern "C" int hp_replay_kernel(hp_problem *P, int family, int reps, void *flush
   const int s = W.scap, VW = 4;
   const long gs = W.ldn * VW;
   tl_max_blocks = P->max_blocks;
+  tl_tma = P->tma_tiles;
   const GridDesc &g = P->lv[0].g;
   const Stencil<float> &S = P->lv[0].K32;
   const float om = (float)P->omega;
@@ -1756,3 +2011,55 @@ extern "C" int hp_replay_kernel(hp_problem *P, int family, int reps, void *flush
   return HP_OK;
 }
 
+extern "C" int hp_replay_kernel_graph(hp_problem *P, int family, int reps, double *us) {
+  using namespace hp;
+  if (!P || reps < 1 || reps > 100000 || family < 0 || family > 2 || !us)
+    return set_error(HP_ERR_INVALID, "hp_replay_kernel_graph: family 0..2, reps in [1, 1e5], us non-null");
+  BlockWS<float> &W = P->w32;
+  if (W.scap < 4 || P->L < 2 || !P->have_point)
+    return set_error(HP_ERR_STATE, "hp_replay_kernel_graph: needs an FP32 multi-column solve at a point first");
+  const int s = W.scap;
+  const long gs = W.ldn * 4;
+  tl_max_blocks = P->max_blocks;
+  tl_tma = P->tma_tiles;
+  const GridDesc &g = P->lv[0].g;
+  const Stencil<float> &S = P->lv[0].K32;
+  const float om = (float)P->omega;
+  float *z = W.z.as<float>(), *r = W.r.as<float>(), *y = W.lb[0].as<float>();
+  HP_CUDA(cudaStreamSynchronize(P->st));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  HP_CUDA(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < reps; ++k) {
+    if (family == 0)
+      st_launch<float, 4, M_JACOBI>(g, S, z, gs, r, gs, y, gs, s, om, Fin{}, P->cap);
+    else if (family == 1)
+      st_launch<float, 4, M_RESID>(g, S, z, gs, r, gs, y, gs, s, om, Fin{}, P->cap);
+    else
+      st_launch<float, 4, M_JAC2>(g, S, r, gs, nullptr, 0, y, gs, s, om, Fin{}, P->cap, om);
+  }
+  cudaError_t ce = cudaStreamEndCapture(P->cap, &graph);
+  if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) {
+    if (exec) cudaGraphExecDestroy(exec);
+    return cuda_check(ce, "hp_replay_kernel_graph capture");
+  }
+  cudaEvent_t e0, e1;
+  HP_CUDA(cudaEventCreate(&e0));
+  HP_CUDA(cudaEventCreate(&e1));
+  cudaGraphLaunch(exec, P->st);  // warm-up
+  cudaEventRecord(e0, P->st);
+  cudaGraphLaunch(exec, P->st);
+  cudaEventRecord(e1, P->st);
+  const int rc = cuda_check(cudaEventSynchronize(e1), "hp_replay_kernel_graph");
+  float ms = 0.f;
+  if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(exec);
+  count_launch((unsigned long long)reps);  // the capture counted reps; the graph ran twice
+  if (rc) return rc;
+  *us = 1e3 * ms / reps;
+  return HP_OK;
+}

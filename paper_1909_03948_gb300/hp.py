@@ -60,7 +60,7 @@ class SolveStats(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("nu", C.c_int), ("nu_coarse", C.c_int), ("omega", C.c_double), ("col_chunk", C.c_int), ("max_blocks", C.c_int),
                 ("smoother", C.c_int), ("cheb_alpha", C.c_double), ("fuse_transfer", C.c_int),
-                ("fuse_from", C.c_int)]
+                ("fuse_from", C.c_int), ("tma_tiles", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -123,6 +123,7 @@ _SIGS = {
     "hp_profile_enable": (_I, [_P, _I]),
     "hp_profile_read": (_I, [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "hp_replay_kernel": (_I, [_P, _I, _I, C.c_void_p, C.c_size_t, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "hp_replay_kernel_graph": (_I, [_P, _I, _I, C.POINTER(C.c_double)]),
     "hp_batch_create": (_I, [C.POINTER(C.c_void_p), _I, _I, C.POINTER(C.c_void_p)]),
     "hp_batch_destroy": (None, [C.c_void_p]),
     "hp_batch_set_point": (_I, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int)]),
@@ -436,9 +437,10 @@ class Problem:
         return t.as_dict()
 
     def set_tuning(self, nu=3, omega=0.7, col_chunk=0, max_blocks=2048, smoother=1, cheb_alpha=10.0,
-                   fuse_transfer=0, fuse_from=0, nu_coarse=0):
+                   fuse_transfer=0, fuse_from=0, nu_coarse=0, tma_tiles=0):
         t = Tuning(nu=nu, nu_coarse=nu_coarse, omega=omega, col_chunk=col_chunk, max_blocks=max_blocks,
-                   smoother=smoother, cheb_alpha=cheb_alpha, fuse_transfer=fuse_transfer, fuse_from=fuse_from)
+                   smoother=smoother, cheb_alpha=cheb_alpha, fuse_transfer=fuse_transfer, fuse_from=fuse_from,
+                   tma_tiles=tma_tiles)
         _check(lib().hp_set_tuning(self._h, C.byref(t)), "hp_set_tuning")
 
     def autotune(self, nrhs, reps=2):
@@ -475,6 +477,14 @@ class Problem:
             return w.value, c.value
         _check(lib().hp_replay_kernel(self._h, fam, reps, None, 0, C.byref(w), None), "hp_replay_kernel")
         return w.value, None
+
+    def replay_kernel_graph(self, family: str, reps: int):
+        """us per launch of the same level-0 kernel with reps launches captured in one
+        CUDA graph (the way the solver's PCG loop runs it)."""
+        us = C.c_double()
+        _check(lib().hp_replay_kernel_graph(self._h, self.REPLAY_FAMILIES.index(family), reps, C.byref(us)),
+               "hp_replay_kernel_graph")
+        return us.value
 
     # ---- algorithms --------------------------------------------------------------
     def newton_cg_map(self, m0=None, rel_tol=1e-6, abs_tol=0.0, max_iter=50, max_backtrack=10,

@@ -67,20 +67,23 @@ def test_full_newton_map_matches_oracle(small2d):
 
 def test_lowrank_preconditioned_newton_reaches_the_map(small2d):
     """Newton-CG whose CG is preconditioned by R^-1 - V D V^T (k = 20 eigenpairs of the
-    prior-preconditioned misfit Hessian, refreshed every 2 Newton iterations) reaches the
-    same MAP point -- the oracle's full-Newton MAP, within ~1e-8 of the exact one -- to
-    relative 1e-6, in far fewer CG iterations than the R^-1-preconditioned run."""
+    prior-preconditioned misfit Hessian, refreshed every 2 Newton iterations) stops at
+    relative gradient 1e-9 near the MAP point, in far fewer CG iterations than the
+    R^-1-preconditioned run.  The reference is the oracle's full-Newton MAP, within ~1e-8
+    of the exact one; a Gauss-Newton iterate at relative gradient 1e-9 lies about 1.6e-6
+    (relative) from it on this problem (the oracle's own Gauss-Newton run), and a
+    different CG preconditioner takes a different path into that ball, hence 5e-6.
+    (Below ~1e-10 the Armijo test compares cost decreases smaller than the cost's own
+    accuracy, so a tighter gradient tolerance is not a reliable stopping target.)"""
     orc, w = small2d["orc"], small2d["w"]
-    # PDE solves to 1e-12 so that the line search resolves the cost decreases of a 1e-10
-    # gradient tolerance (see test_newton_map_matches_oracle)
     P = _gpu_problem(orc, w, rtol=1e-12)
     try:
-        m, st = P.newton_cg_map(rel_tol=1e-10, lowrank_k=20, lowrank_p=10, lowrank_refresh=2)
-        assert st["converged"] and st["eig_solves"] >= 2
+        m, st = P.newton_cg_map(rel_tol=1e-9, lowrank_k=20, lowrank_p=10, lowrank_refresh=2)
+        assert st["converged"] and st["eig_solves"] >= 2, st
         ref_full = A.newton_cg(orc, rel_tol=1e-9, full=True)
-        assert np.linalg.norm(m.cpu().numpy() - ref_full.m) <= 1e-6 * np.linalg.norm(ref_full.m)
-        _, st0 = P.newton_cg_map(rel_tol=1e-10)
-        assert st0["converged"]
+        assert np.linalg.norm(m.cpu().numpy() - ref_full.m) <= 5e-6 * np.linalg.norm(ref_full.m)
+        _, st0 = P.newton_cg_map(rel_tol=1e-9)
+        assert st0["converged"], st0
         assert st["cg_iterations"] < 0.5 * st0["cg_iterations"], (st, st0)
     finally:
         P.close()
@@ -399,7 +402,7 @@ def test_fused_transfers_keep_results(dim, N, precision, nu):
     """Residual + restriction and prolongation + first post sweep fused (the fine residual
     and the prolonged iterate never stored): the same Hessian actions and prior solves to
     the solve tolerance, for the stiffness (axis stencil) and the prior (full stencil),
-    alone and with the fused coarse tail."""
+    on every level or below the finest only, alone and with the fused coarse tail."""
     from paper_1909_03948_gb300 import Problem
     w = W.make_workload(dim, N, 30, seed=79)
     dr = W.draws(w)
@@ -410,13 +413,39 @@ def test_fused_transfers_keep_results(dim, N, precision, nu):
     P.set_point(m)
     Y0, st0 = P.hessian_apply(X)
     Z0, _ = P.prior_solve(X)
-    for ff in (0, 2):
-        P.set_tuning(nu=nu, fuse_transfer=1, fuse_from=ff)
+    for ft, ff in ((1, 0), (1, 2), (2, 0)):
+        P.set_tuning(nu=nu, fuse_transfer=ft, fuse_from=ff)
         P.set_point(m)
         Y1, st1 = P.hessian_apply(X)
         Z1, _ = P.prior_solve(X)
-        assert float(torch.linalg.norm(Y1 - Y0) / torch.linalg.norm(Y0)) <= 1e-8, ff
-        assert float(torch.linalg.norm(Z1 - Z0) / torch.linalg.norm(Z0)) <= 1e-8, ff
+        assert float(torch.linalg.norm(Y1 - Y0) / torch.linalg.norm(Y0)) <= 1e-8, (ft, ff)
+        assert float(torch.linalg.norm(Z1 - Z0) / torch.linalg.norm(Z0)) <= 1e-8, (ft, ff)
         assert abs(st1["iterations"] - st0["iterations"]) <= 2, (st0, st1)
+    P.set_tuning()
+    P.close()
+
+
+@pytest.mark.parametrize("N,ncols", [(32, 5), (96, 8), (256, 60)])
+def test_tma_tiles_keep_results(N, ncols):
+    """The TMA-tiled stencil kernels (2D stiffness levels whose np - 1 is a multiple of
+    32: all of N = 32 and 256, only the finest level of N = 96) against the row kernels:
+    the same Hessian actions and stiffness solves to the solve tolerance, within one PCG
+    iteration (the two differ only in the order of the inner-product partial sums), with
+    a column count that leaves part of the last group of 4 empty (N = 32)."""
+    from paper_1909_03948_gb300 import Problem
+    w = W.make_workload(2, N, 30, seed=83)
+    dr = W.draws(w)
+    P = Problem(2, N, w.gamma, w.delta, 0.01, dr.obs_xyz, rtol=1e-10)
+    m = 0.3 * torch.tensor(np.random.default_rng(7).standard_normal(P.n), device=DEV)
+    X = torch.tensor(np.random.default_rng(8).standard_normal((ncols, P.n)), device=DEV)
+    out = {}
+    for tt in (0, 1):
+        P.set_tuning(tma_tiles=tt)
+        P.set_point(m)
+        out[tt] = P.hessian_apply(X) + (P.state_solve(X)[0],)
+    (Y0, st0, U0), (Y1, st1, U1) = out[0], out[1]
+    assert float(torch.linalg.norm(Y1 - Y0) / torch.linalg.norm(Y0)) <= 1e-8
+    assert float(torch.linalg.norm(U1 - U0) / torch.linalg.norm(U0)) <= 1e-8
+    assert abs(st1["iterations"] - st0["iterations"]) <= 1, (st0, st1)
     P.set_tuning()
     P.close()
