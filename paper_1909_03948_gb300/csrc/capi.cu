@@ -557,11 +557,12 @@ void hp_problem_destroy(hp_problem *P) {
   if (P->cap) cudaStreamDestroy(P->cap);
   free_scalars_host(P);
   ScalarWS &S = P->sc;
-  for (DBuf *b : {&S.iter, &S.rz, &S.pq, &S.rr, &S.bb, &S.alpha, &S.beta, &S.scale, &S.iscale, &S.tol2col, &S.tmp, &S.active, &S.partial, &S.counter})
+  for (DBuf *b : {&S.iter, &S.rz, &S.pq, &S.rr, &S.bb, &S.alpha, &S.beta, &S.scale, &S.iscale, &S.tol2col, &S.bbr, &S.tmp, &S.active, &S.partial, &S.counter})
     b->release();
-  for (DBuf *b : {&P->r64, &P->b64, &P->t64a, &P->t64b, &P->t64c, &P->obsbuf, &P->small, &P->etabuf, &P->ws_flag,
-                  &P->ws_bb, &P->ws_z})
+  for (DBuf *b : {&P->r64, &P->b64, &P->x64, &P->rctl, &P->t64a, &P->t64b, &P->t64c, &P->obsbuf, &P->small,
+                  &P->etabuf, &P->ws_flag, &P->ws_bb, &P->ws_z})
     b->release();
+  if (P->h_rctl) cudaFreeHost(P->h_rctl);
   for (int i = 0; i < 6; ++i) P->vtmp[i].release();
   for (cudaEvent_t e : P->prof_ev) cudaEventDestroy(e);
   delete P;

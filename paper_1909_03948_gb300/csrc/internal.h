@@ -75,9 +75,28 @@ struct PcgGraph {
   cudaGraphExec_t exec;
 };
 
+// Device-side state of a graph-driven iterative refinement (one solve at a time).
+struct RefineCtl {
+  int outer;       // refinement steps run
+  int total_its;   // inner PCG iterations, summed over the steps
+  int flags;       // 1: not converged within max_outer, 2: non-finite residual
+  int pad;
+  double worst;    // max_j |r_j| / |b_j| at the last check
+};
+
+// a captured refinement loop: a while node over the refinement steps, each with the
+// scaling into the inner precision, the PCG (nested while node), the accumulation,
+// the FP64 residual and the convergence control; cached per configuration
+struct SolveGraph {
+  int op, tbytes, vw, s, maxit, max_outer;
+  double rtol, tol_in;
+  cudaGraphExec_t exec;
+};
+
 struct ScalarWS {
   int scap = 0;
   DBuf rz, pq, rr, bb, alpha, beta, scale, iscale, tol2col, tmp;   // double per column
+  DBuf bbr;                                        // |b|^2 of a graph-driven refinement (the PCG reuses bb)
   DBuf active;                                     // int per column
   DBuf partial;                                    // double [slot][col][block]
   DBuf counter;                                    // unsigned [slot][col]
@@ -115,6 +134,7 @@ struct hp_problem {
   cudaStream_t cap = nullptr;   // private stream used to capture CUDA graphs
   bool use_graphs = true;       // inner PCG loops as graphs with a device-side while node
   std::vector<hp::PcgGraph> graphs;
+  std::vector<hp::SolveGraph> sgraphs;
 
   hp::Level lv[HP_MAXL];
   hp::CoarseInv cK, cA;
@@ -147,6 +167,9 @@ struct hp_problem {
   hp::BlockWS<double> w64;
   hp::ScalarWS sc;
   hp::DBuf r64, b64, t64a, t64b, t64c, obsbuf, small, etabuf, vtmp[6];
+  hp::DBuf x64;                     // iterate of a graph-driven refinement (copied out at the end)
+  hp::DBuf rctl;                    // RefineCtl of the graph-driven refinement
+  hp::RefineCtl *h_rctl = nullptr;  // pinned host mirror
 
   // optional CUDA-event timing of selected kernels (hp_profile_*)
   bool prof_on = false;

@@ -757,6 +757,83 @@ __global__ void __launch_bounds__(NB) k_to_inner(long n, const double *__restric
   }
 }
 
+// The same scaling inside a graph-driven refinement: the first step (ctl->outer == 1,
+// counted before the step runs) starts from x = 0, so its residual is b0 itself.
+template <typename T, int VW>
+__global__ void __launch_bounds__(NB) k_to_inner_ctl(long n, const double *__restrict__ B0,
+                                                     const double *__restrict__ R, long ldr,
+                                                     const RefineCtl *__restrict__ ctl,
+                                                     const double *__restrict__ scale, int s, T *__restrict__ rt,
+                                                     long gs) {
+  using PK = Pack<T, VW>;
+  const double *src = ctl->outer == 1 ? B0 : R;
+  const int grp = blockIdx.y;
+  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
+    PK o;
+#pragma unroll
+    for (int q = 0; q < VW; ++q) {
+      const int col = grp * VW + q;
+      o.v[q] = col < s ? (T)(scale[col] * src[ldr * col + i]) : T(0);
+    }
+    o.st(rt + grp * gs + i * VW);
+  }
+}
+
+// Convergence control of a graph-driven refinement (one block): for every column the
+// test |r|^2 <= rtol^2 |b|^2, the scale 1/|r| into the inner solve and back, and the
+// inner tolerance (the finer of tol_in and what is left to reach rtol, with a factor 1/4
+// of margin); then the loop condition: another step while a column is open, a
+// non-finite residual or max_outer steps end the loop with a flag.  after_body adds the
+// inner iterations of the step that just ran.
+__global__ void k_refine_ctl(int s, const double *__restrict__ rr, const double *__restrict__ bb, double rtol,
+                             double tol_in, double *__restrict__ scale, double *__restrict__ iscale,
+                             double *__restrict__ tol2col, const int *__restrict__ pcg_iter, int after_body,
+                             int max_outer, RefineCtl *ctl, cudaGraphConditionalHandle h) {
+  __shared__ int nact_s, bad_s;
+  __shared__ double worst_s[256];
+  if (threadIdx.x == 0) nact_s = bad_s = 0;
+  __syncthreads();
+  int nact = 0, bad = 0;
+  double worst = 0.0;
+  for (int j = threadIdx.x; j < s; j += blockDim.x) {
+    const double r2 = rr[j], b2 = bb[j];
+    if (!isfinite(r2)) bad = 1;
+    const double rel = b2 > 0 ? sqrt(r2 / b2) : 0.0;
+    worst = fmax(worst, rel);
+    const bool done = b2 == 0.0 || r2 <= rtol * rtol * b2;
+    scale[j] = done ? 0.0 : 1.0 / sqrt(r2);
+    iscale[j] = done ? 0.0 : sqrt(r2);
+    const double need = r2 > 0 ? 0.25 * rtol * sqrt(b2 / r2) : 1.0;
+    const double t = fmin(0.5, fmax(tol_in, need));
+    tol2col[j] = t * t;
+    nact += !done;
+  }
+  if (nact) atomicAdd(&nact_s, nact);
+  if (bad) atomicOr(&bad_s, 1);
+  worst_s[threadIdx.x] = worst;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) worst_s[threadIdx.x] = fmax(worst_s[threadIdx.x], worst_s[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (after_body) ctl->total_its += *pcg_iter;
+    ctl->worst = worst_s[0];
+    unsigned cond = 0;
+    if (bad_s) {
+      ctl->flags |= 2;
+    } else if (nact_s > 0) {
+      if (ctl->outer >= max_outer) {
+        ctl->flags |= 1;
+      } else {
+        cond = 1;
+        ctl->outer += 1;
+      }
+    }
+    cudaGraphSetConditional(h, cond);
+  }
+}
+
 // X (column-major FP64) += d / scale for the columns with scale != 0
 template <typename T, int VW>
 __global__ void __launch_bounds__(NB) k_accum(long n, const T *__restrict__ d, long gs, const double *__restrict__ iscale,
@@ -1053,11 +1130,12 @@ int ensure_scalars(hp_problem *P, int s) {
   HP_TRY(S.scale.ensure(b));
   HP_TRY(S.iscale.ensure(b));
   HP_TRY(S.tol2col.ensure(b));
+  HP_TRY(S.bbr.ensure(b));
   HP_TRY(S.active.ensure(sizeof(int) * sc));
   HP_TRY(S.partial.ensure(sizeof(double) * (size_t)nbmax * sc));
   HP_TRY(S.counter.ensure(sizeof(unsigned) * sc));
   HP_TRY(S.iter.ensure(sizeof(int) * 4));
-  for (DBuf *d : {&S.rz, &S.pq, &S.rr, &S.bb, &S.alpha, &S.beta, &S.scale, &S.iscale, &S.tol2col})
+  for (DBuf *d : {&S.rz, &S.pq, &S.rr, &S.bb, &S.alpha, &S.beta, &S.scale, &S.iscale, &S.tol2col, &S.bbr})
     HP_CUDA(cudaMemsetAsync(d->p, 0, b, P->st));
   HP_CUDA(cudaMemsetAsync(S.active.p, 0, sizeof(int) * sc, P->st));
   HP_CUDA(cudaMemsetAsync(S.counter.p, 0, sizeof(unsigned) * sc, P->st));
@@ -1652,69 +1730,87 @@ static void pcg_body(hp_problem *P, OpKind op, int s, double tol2, cudaGraphCond
 void drop_graphs(hp_problem *P) {
   for (auto &g : P->graphs) cudaGraphExecDestroy(g.exec);
   P->graphs.clear();
+  for (auto &g : P->sgraphs) cudaGraphExecDestroy(g.exec);
+  P->sgraphs.clear();
 }
 
-// Captures init + a conditional WHILE node whose body is one PCG iteration.
+// the node a capture on `st` would depend on next (the last one captured)
+static cudaError_t capture_leaf(cudaStream_t st, cudaGraphNode_t *leaf) {
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive || nd != 1) return cudaErrorStreamCaptureInvalidated;
+  *leaf = deps[0];
+  return cudaSuccess;
+}
+
+// Appends the PCG to graph g after node dep (none if null): the captured init, then a
+// conditional WHILE node whose body is one PCG iteration; *last receives the while node.
+// Capture runs on P->cap with P->st pointed at it by the caller.
 template <typename T, int VW>
-static int build_graph(hp_problem *P, OpKind op, int s, double tol, int maxit, PcgGraph *out) {
+static cudaError_t append_pcg(hp_problem *P, OpKind op, int s, double tol, int maxit, cudaGraph_t g,
+                              cudaGraphNode_t dep, cudaGraphNode_t *last) {
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCaptureToGraph(P->cap, g, dep ? &dep : nullptr, nullptr, dep ? 1 : 0,
+                                    cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return e;
+  pcg_init<T, VW>(P, op, s, h, 1, maxit);
+  cudaGraphNode_t leaf = nullptr;
+  const cudaError_t el = capture_leaf(P->cap, &leaf);
+  cudaGraph_t gg = g;
+  e = cudaStreamEndCapture(P->cap, &gg);
+  if (el != cudaSuccess) return el;
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  e = cudaGraphAddNode(last, g, &leaf, nullptr, 1, &cp);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(P->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return e;
+  pcg_body<T, VW>(P, op, s, tol * tol, h, 1, maxit);
+  return cudaStreamEndCapture(P->cap, &body);
+}
+
+// Runs fn with launches redirected to the capture stream, profiling off and the launch
+// counter paused (captured launches are counted when the graph runs).
+template <typename F>
+static int with_capture_stream(hp_problem *P, F fn) {
   if (!P->cap) HP_CUDA(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
   cudaStream_t saved = P->st;
   const bool saved_prof = P->prof_on;
   P->prof_on = false;
   P->st = P->cap;
   tl_no_count = 1;
-  cudaGraph_t g = nullptr;
-  auto fail = [&](cudaError_t e, const char *w) {
-    const int rc = cuda_check(e, w);
-    P->st = saved;
-    P->prof_on = saved_prof;
-    tl_no_count = 0;
-    if (g) cudaGraphDestroy(g);
-    return rc;
-  };
-  cudaError_t e = cudaGraphCreate(&g, 0);
-  if (e != cudaSuccess) return fail(e, "cudaGraphCreate");
-  cudaGraphConditionalHandle h;
-  e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
-  if (e != cudaSuccess) return fail(e, "cudaGraphConditionalHandleCreate");
-  e = cudaStreamBeginCaptureToGraph(P->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-  if (e != cudaSuccess) return fail(e, "capture init");
-  pcg_init<T, VW>(P, op, s, h, 1, maxit);
-  e = cudaStreamEndCapture(P->cap, &g);
-  if (e != cudaSuccess) return fail(e, "end capture init");
-  size_t nn = 0;
-  cudaGraphGetNodes(g, nullptr, &nn);
-  std::vector<cudaGraphNode_t> nodes(nn);
-  cudaGraphGetNodes(g, nodes.data(), &nn);
-  cudaGraphNode_t leaf = nullptr;
-  for (auto nd : nodes) {
-    size_t nd_out = 0;
-    cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &nd_out);
-    if (nd_out == 0) leaf = nd;
-  }
-  cudaGraphNodeParams cp = {};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = h;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  cudaGraphNode_t cn;
-  e = cudaGraphAddNode(&cn, g, leaf ? &leaf : nullptr, nullptr, leaf ? 1 : 0, &cp);
-  if (e != cudaSuccess) return fail(e, "add conditional node");
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
-  e = cudaStreamBeginCaptureToGraph(P->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-  if (e != cudaSuccess) return fail(e, "capture body");
-  pcg_body<T, VW>(P, op, s, tol * tol, h, 1, maxit);
-  e = cudaStreamEndCapture(P->cap, &body);
-  if (e != cudaSuccess) return fail(e, "end capture body");
-  cudaGraphExec_t ex;
-  e = cudaGraphInstantiate(&ex, g, 0);
-  if (e != cudaSuccess) return fail(e, "instantiate");
-  cudaGraphDestroy(g);
+  const int rc = fn();
   P->st = saved;
   P->prof_on = saved_prof;
-  tl_no_count = 0;  // captured launches are counted when the graph runs
-  *out = PcgGraph{(int)op, (int)sizeof(T), VW, s, maxit, tol, ex};
-  return 0;
+  tl_no_count = 0;
+  return rc;
+}
+
+// Captures init + a conditional WHILE node whose body is one PCG iteration.
+template <typename T, int VW>
+static int build_graph(hp_problem *P, OpKind op, int s, double tol, int maxit, PcgGraph *out) {
+  return with_capture_stream(P, [&]() -> int {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    cudaGraphNode_t last = nullptr;
+    if (e == cudaSuccess) e = append_pcg<T, VW>(P, op, s, tol, maxit, g, nullptr, &last);
+    cudaGraphExec_t ex = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_check(e, "PCG graph");
+    *out = PcgGraph{(int)op, (int)sizeof(T), VW, s, maxit, tol, ex};
+    return 0;
+  });
 }
 
 static int kernels_per_iteration(const hp_problem *P, OpKind op) {
@@ -1806,6 +1902,132 @@ static int residual64(hp_problem *P, OpKind op, const double *B, long ldb, const
   return cuda_check(cudaGetLastError(), "residual");
 }
 
+// DBuf::ensure that drops the captured graphs when the buffer moves (they hold its address)
+static int ensure_kept(hp_problem *P, DBuf &b, size_t bytes) {
+  void *old = b.p;
+  HP_TRY(b.ensure(bytes));
+  if (b.p != old) drop_graphs(P);
+  return 0;
+}
+
+// Captures the whole refinement loop of one configuration: reset of the control block and
+// the first convergence check, then a WHILE node whose body is one refinement step --
+// scaling into the inner precision, the PCG (a nested WHILE node), x += d, the FP64
+// residual with its norm, and the control kernel that sets the loop condition.
+template <typename T, int VW>
+static int build_solve_graph(hp_problem *P, OpKind op, int s, double rtol, double tol_in, SolveGraph *out) {
+  BlockWS<T> &W = ws_of<T>(P);
+  const long n = P->n, ld64 = padded(n);
+  const int ng = (s + VW - 1) / VW;
+  const long gs = W.ldn * VW;
+  double *r64 = P->r64.as<double>(), *b64 = P->b64.as<double>(), *x64 = P->x64.as<double>();
+  RefineCtl *ctl = P->rctl.as<RefineCtl>();
+  const int maxit = P->max_iter, max_outer = P->max_outer;
+  double *scale = P->sc.scale.as<double>(), *iscale = P->sc.iscale.as<double>();
+  double *tol2col = P->sc.tol2col.as<double>(), *rr = P->sc.rr.as<double>(), *bb = P->sc.bbr.as<double>();
+  const int *iter = P->sc.iter.as<int>();
+  return with_capture_stream(P, [&]() -> int {
+    cudaStream_t cs = P->cap;
+    cudaGraph_t g = nullptr, body = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    cudaGraphConditionalHandle ho;
+    cudaGraphNode_t leaf = nullptr, wn = nullptr, pw = nullptr;
+    auto end_capture = [&](cudaGraph_t gr, bool want_leaf) {
+      cudaError_t el = want_leaf ? capture_leaf(cs, &leaf) : cudaSuccess;
+      cudaGraph_t gg = gr;
+      const cudaError_t ee = cudaStreamEndCapture(cs, &gg);
+      return el != cudaSuccess ? el : ee;
+    };
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&ho, g, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      cudaMemsetAsync(ctl, 0, sizeof(RefineCtl), cs);
+      k_refine_ctl<<<1, 256, 0, cs>>>(s, rr, bb, rtol, tol_in, scale, iscale, tol2col, iter, 0, max_outer, ctl, ho);
+      e = end_capture(g, true);
+    }
+    if (e == cudaSuccess) {
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = ho;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&wn, g, &leaf, nullptr, 1, &cp);
+      if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      k_to_inner_ctl<T, VW><<<nodegrid(n, ng), NB, 0, cs>>>(n, b64, r64, ld64, ctl, scale, s, W.r.template as<T>(),
+                                                            gs);
+      e = end_capture(body, true);
+    }
+    if (e == cudaSuccess) e = append_pcg<T, VW>(P, op, s, tol_in, maxit, body, leaf, &pw);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, &pw, nullptr, 1, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      k_accum<T, VW><<<nodegrid(n, ng), NB, 0, cs>>>(n, W.x.template as<T>(), gs, iscale, s, x64, ld64);
+      const int rc = residual64(P, op, b64, ld64, x64, ld64, r64, ld64, s);
+      k_refine_ctl<<<1, 256, 0, cs>>>(s, rr, bb, rtol, tol_in, scale, iscale, tol2col, iter, 1, max_outer, ctl, ho);
+      e = end_capture(body, false);
+      if (e == cudaSuccess && rc) e = cudaErrorUnknown;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_check(e, "refinement graph");
+    *out = SolveGraph{(int)op, (int)sizeof(T), VW, s, maxit, max_outer, rtol, tol_in, ex};
+    return 0;
+  });
+}
+
+// The refinement of ir_solve from x = 0 as one graph launch: the one-pass start, the
+// captured loop, the copy of the iterate to X and one read-back of the control block.
+template <typename T, int VW>
+static int ir_solve_graph(hp_problem *P, OpKind op, const double *B, long ldb, double *X, long ldx, int s,
+                          double rtol, double tol_in, hp_solve_stats *stats) {
+  cudaStream_t st = P->st;
+  const long n = P->n, ld64 = padded(n);
+  HP_TRY(ensure_kept(P, P->x64, sizeof(double) * ld64 * s));
+  HP_TRY(ensure_kept(P, P->rctl, sizeof(RefineCtl)));
+  if (!P->h_rctl) HP_CUDA(cudaMallocHost(&P->h_rctl, sizeof(RefineCtl)));
+  double *b64 = P->b64.as<double>(), *x64 = P->x64.as<double>();
+  const GridDesc &g0 = P->lv[0].g;
+  const long face = op == OP_K ? (P->dim == 2 ? g0.np : (long)g0.np * g0.np) : 0;
+  HP_TRY(ir_start(P, B, ldb, b64, ld64, x64, ld64, n, s, face, P->sc.bbr.as<double>(), P->sc.rr.as<double>()));
+  SolveGraph *G = nullptr;
+  for (auto &sg : P->sgraphs)
+    if (sg.op == (int)op && sg.tbytes == (int)sizeof(T) && sg.vw == VW && sg.s == s && sg.maxit == P->max_iter &&
+        sg.max_outer == P->max_outer && sg.rtol == rtol && sg.tol_in == tol_in)
+      G = &sg;
+  if (!G) {
+    SolveGraph ng;
+    HP_TRY((build_solve_graph<T, VW>(P, op, s, rtol, tol_in, &ng)));
+    P->sgraphs.push_back(ng);
+    G = &P->sgraphs.back();
+  }
+  HP_CUDA(cudaGraphLaunch(G->exec, st));
+  HP_CUDA(cudaMemcpy2DAsync(X, sizeof(double) * ldx, x64, sizeof(double) * ld64, sizeof(double) * n, s,
+                            cudaMemcpyDeviceToDevice, st));
+  int *h_it = P->sc.h_iter;
+  HP_CUDA(cudaMemcpyAsync(P->h_rctl, P->rctl.p, sizeof(RefineCtl), cudaMemcpyDeviceToHost, st));
+  HP_CUDA(cudaMemcpyFromSymbolAsync(h_it + 1, g_tile_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+  HP_CUDA(cudaStreamSynchronize(st));
+  const RefineCtl c = *P->h_rctl;
+  HP_TRY(tile_timeout_check(P, h_it));
+  // kernels run: the first check, and per step the scaling, the PCG init (3) and
+  // iterations, the accumulation, the residual with its finalisation and the check
+  count_launch(1ull + 8ull * (unsigned long long)c.outer +
+               (unsigned long long)c.total_its * (unsigned long long)kernels_per_iteration(P, op));
+  if (c.flags & 2) return set_error(HP_ERR_NONFINITE, "non-finite residual in a PDE solve");
+  if (stats) {
+    stats->iterations += c.total_its;
+    stats->outer += c.outer;
+    stats->solves += 1;
+    stats->rel_res = std::max(stats->rel_res, c.worst);
+  }
+  if (c.flags & 1) return set_error(HP_ERR_NOT_CONVERGED, "PDE solve did not reach the requested tolerance");
+  if (op == OP_K) warm_record(P, b64, ld64, X, ldx, s);
+  return cuda_check(cudaGetLastError(), "ir_solve");
+}
+
 template <typename T, int VW>
 static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double *X, long ldx, int s, double rtol,
                     double tol_in, hp_solve_stats *stats) {
@@ -1815,8 +2037,11 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
   const long ld64 = padded(n);
   const int ng = (s + VW - 1) / VW;
   const long gs = W.ldn * VW;
-  HP_TRY(P->r64.ensure(sizeof(double) * ld64 * s));
-  HP_TRY(P->b64.ensure(sizeof(double) * ld64 * s));
+  HP_TRY(ensure_kept(P, P->r64, sizeof(double) * ld64 * s));
+  HP_TRY(ensure_kept(P, P->b64, sizeof(double) * ld64 * s));
+  // from x = 0 with graphs on, the whole refinement runs as one captured loop
+  if (P->use_graphs && !P->prof_on && !(op == OP_K && warm_attached(P)))
+    return ir_solve_graph<T, VW>(P, op, B, ldb, X, ldx, s, rtol, tol_in, stats);
   double *r64 = P->r64.as<double>(), *b64 = P->b64.as<double>();
   // one pass over B: b64 = B (Dirichlet rows of a stiffness solve zeroed), X = 0, |b|^2;
   // from x = 0 the first residual is b64 itself, so rr = bb
