@@ -302,7 +302,7 @@ int hp_pointwise_variance(hp_problem *P, int method, const double *Z_dev, int ld
  * before and after each coarse correction and damping omega, the number of RHS
  * columns solved together (0 = all), and the grid-size cap of the node kernels.
  * Defaults: nu 3, nu_coarse 0, omega 0.7, col_chunk 0, max_blocks 2048, smoother 1
- * (Chebyshev), cheb_alpha 10, fuse_transfer 0, fuse_from 0, tma_tiles 0.  Every setting solves to the same
+ * (Chebyshev), cheb_alpha 10, fuse_transfer 0, fuse_from 0, tma_tiles 0, smem_tail 0.  Every setting solves to the same
  * tolerance; only speed changes. */
 typedef struct {
   int nu;          /* 1..4 */
@@ -328,6 +328,12 @@ typedef struct {
                       np - 1 a multiple of 32 (np >= 33), the stencil kernels work on
                       32 x 16-node tiles that bulk tensor copies (TMA) bring into shared
                       memory with their halo; 0: every warp loads its own row of nodes */
+  int smem_tail;   /* k >= 1: the coarse end of the V-cycle -- from the finest level l >= k
+                      whose vectors, and those of every level below it, fit in one CTA's
+                      shared memory -- runs as one launch of one CTA per column group, its
+                      steps separated by block barriers only (takes precedence over
+                      fuse_from); the result equals the per-level kernels' bit for bit.
+                      0: off */
 } hp_tuning;
 int hp_set_tuning(hp_problem *P, const hp_tuning *t);
 int hp_get_tuning(const hp_problem *P, hp_tuning *t);

@@ -106,6 +106,16 @@ __device__ __forceinline__ void for_elems_with(const GridDesc &g, const int v[3]
 }
 
 // ---- reductions -------------------------------------------------------------
+// Multiply-add with one rounding, and a product / sum each rounded on its own: the
+// compiler never fuses or splits these, so kernels that mirror one another's arithmetic
+// (the per-level, fused-tail and tiled stencil kernels) produce the same bits.
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mulr(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mulr(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float addr(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double addr(double a, double b) { return __dadd_rn(a, b); }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);

@@ -130,6 +130,7 @@ struct hp_problem {
   int fuse_transfer = 0;        // residual + restriction and prolongation + first post sweep fused (tuning)
   double cheb_alpha = 10.0;     // Chebyshev interval [lmax / alpha, lmax]             (tuning)
   int tma_tiles = 0;            // 2D stiffness levels as TMA-tiled stencil kernels       (tuning)
+  int smem_tail = 0;            // coarse V-cycle levels in one shared-memory CTA per group (tuning)
   cudaStream_t st = nullptr;
   cudaStream_t cap = nullptr;   // private stream used to capture CUDA graphs
   bool use_graphs = true;       // inner PCG loops as graphs with a device-side while node

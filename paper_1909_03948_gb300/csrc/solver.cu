@@ -104,7 +104,7 @@ template <typename T, int VW> struct Pack {
   }
   __device__ __forceinline__ void axpy(T a, const Pack &x) {  // this += a x
 #pragma unroll
-    for (int q = 0; q < VW; ++q) v[q] += a * x.v[q];
+    for (int q = 0; q < VW; ++q) v[q] = fmadd(a, x.v[q], v[q]);
   }
 };
 
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(NB) k_st(GridDesc g, const T *__restrict__ dia
         if (bw) sx.axpy(c[(long)f * g.n + id - off] * omega * invdiag[id - off], PK::ld(x + (id - off) * VW));
       }
 #pragma unroll
-      for (int q = 0; q < VW; ++q) out.v[q] = e1c.v[q] + wi2 * (r.v[q] - sx.v[q]);
+      for (int q = 0; q < VW; ++q) out.v[q] = fmadd(wi2, r.v[q] - sx.v[q], e1c.v[q]);
     } else {
       const PK xc = PK::ld(x + id * VW);
       PK sx;
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(NB) k_st(GridDesc g, const T *__restrict__ dia
         out = sx;
         if (DOT)
 #pragma unroll
-          for (int q = 0; q < VW; ++q) acc.v[q] += xc.v[q] * out.v[q];
+          for (int q = 0; q < VW; ++q) acc.v[q] = fmadd(xc.v[q], out.v[q], acc.v[q]);
       } else {
         const PK bb = PK::ld(B + grp * gb + id * VW);
         if (MODE == M_RESID || MODE == M_RESID_DOT) {
@@ -239,14 +239,14 @@ __global__ void __launch_bounds__(NB) k_st(GridDesc g, const T *__restrict__ dia
           for (int q = 0; q < VW; ++q) out.v[q] = bb.v[q] - sx.v[q];
           if (DOT)
 #pragma unroll
-            for (int q = 0; q < VW; ++q) acc.v[q] += out.v[q] * out.v[q];
+            for (int q = 0; q < VW; ++q) acc.v[q] = fmadd(out.v[q], out.v[q], acc.v[q]);
         } else {
           const T wi = omega * invdiag[id];
 #pragma unroll
-          for (int q = 0; q < VW; ++q) out.v[q] = xc.v[q] + wi * (bb.v[q] - sx.v[q]);
+          for (int q = 0; q < VW; ++q) out.v[q] = fmadd(wi, bb.v[q] - sx.v[q], xc.v[q]);
           if (DOT)
 #pragma unroll
-            for (int q = 0; q < VW; ++q) acc.v[q] += bb.v[q] * out.v[q];
+            for (int q = 0; q < VW; ++q) acc.v[q] = fmadd(bb.v[q], out.v[q], acc.v[q]);
         }
       }
     }
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(TL_NT) k_st_tile(const __grid_constant__ CUten
       if (fy) sx.axpy(cc.w * omega * cs[ci + TLB_X].y, PK::ld(xs + (ci + TLB_X) * 4));
       if (by) sx.axpy(cs[ci - TLB_X].w * omega * cs[ci - TLB_X].y, PK::ld(xs + (ci - TLB_X) * 4));
 #pragma unroll
-      for (int q = 0; q < 4; ++q) out.v[q] = e1c.v[q] + wi2 * (r.v[q] - sx.v[q]);
+      for (int q = 0; q < 4; ++q) out.v[q] = fmadd(wi2, r.v[q] - sx.v[q], e1c.v[q]);
     } else {
       const PK xc = PK::ld(xs + ci * 4);
       PK sx;
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(TL_NT) k_st_tile(const __grid_constant__ CUten
         out = sx;
         if (DOT)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc.v[q] += xc.v[q] * out.v[q];
+          for (int q = 0; q < 4; ++q) acc.v[q] = fmadd(xc.v[q], out.v[q], acc.v[q]);
       } else {
         const PK bb = PK::ld(rs + (ly * TLR_X + lx) * 4);
         if (MODE == M_RESID) {
@@ -397,10 +397,10 @@ __global__ void __launch_bounds__(TL_NT) k_st_tile(const __grid_constant__ CUten
         } else {
           const float wi = omega * cc.y;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) out.v[q] = xc.v[q] + wi * (bb.v[q] - sx.v[q]);
+          for (int q = 0; q < 4; ++q) out.v[q] = fmadd(wi, bb.v[q] - sx.v[q], xc.v[q]);
           if (DOT)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc.v[q] += bb.v[q] * out.v[q];
+            for (int q = 0; q < 4; ++q) acc.v[q] = fmadd(bb.v[q], out.v[q], acc.v[q]);
         }
       }
     }
@@ -466,12 +466,12 @@ __global__ void __launch_bounds__(NB) k_prolong_add(GridDesc gf, GridDesc gc, co
   if (b) {
     const PK v2 = PK::ld(e + (ic + mask_offset(gc, b)) * VW);
 #pragma unroll
-    for (int q = 0; q < VW; ++q) val.v[q] = T(0.5) * (val.v[q] + v2.v[q]);
+    for (int q = 0; q < VW; ++q) val.v[q] = mulr(T(0.5), val.v[q] + v2.v[q]);
   }
   T *o = ef + blockIdx.z * gsf + i * VW;
   PK cur = PK::ld(o);
 #pragma unroll
-  for (int q = 0; q < VW; ++q) cur.v[q] += val.v[q];
+  for (int q = 0; q < VW; ++q) cur.v[q] = addr(cur.v[q], val.v[q]);
   cur.st(o);
 }
 
@@ -580,10 +580,10 @@ __global__ void __launch_bounds__(NB) k_prolong_sweep(GridDesc gf, GridDesc gc, 
     if (bm) {
       const PK e1 = PK::ld(eg + (ic + mask_offset(gc, bm)) * VW);
 #pragma unroll
-      for (int q = 0; q < VW; ++q) val.v[q] += T(0.5) * (e0.v[q] + e1.v[q]);
+      for (int q = 0; q < VW; ++q) val.v[q] = addr(val.v[q], mulr(T(0.5), e0.v[q] + e1.v[q]));
     } else {
 #pragma unroll
-      for (int q = 0; q < VW; ++q) val.v[q] += e0.v[q];
+      for (int q = 0; q < VW; ++q) val.v[q] = addr(val.v[q], e0.v[q]);
     }
     return val;
   };
@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(NB) k_prolong_sweep(GridDesc gf, GridDesc gc, 
     const T wi = omega * invdiag[id];
     PK out;
 #pragma unroll
-    for (int q = 0; q < VW; ++q) out.v[q] = xc.v[q] + wi * (bb.v[q] - sx.v[q]);
+    for (int q = 0; q < VW; ++q) out.v[q] = fmadd(wi, bb.v[q] - sx.v[q], xc.v[q]);
     out.st(y + blockIdx.z * gsf + id * VW);
   }
 }
@@ -644,7 +644,7 @@ __global__ void __launch_bounds__(256) k_coarse_apply(const T *__restrict__ inv,
     for (int k = w; k < nc; k += 8) {
       const T a = inv[(long)k * nc + i];
 #pragma unroll
-      for (int q = 0; q < VW; ++q) acc.v[q] += a * r[k * VW + q];
+      for (int q = 0; q < VW; ++q) acc.v[q] = fmadd(a, r[k * VW + q], acc.v[q]);
     }
   }
 #pragma unroll
@@ -674,7 +674,7 @@ __global__ void __launch_bounds__(NB) k_jacobi0(long n, const T *__restrict__ in
 #pragma unroll
     for (int q = 0; q < VW; ++q) {
       z.v[q] = w * b.v[q];
-      acc.v[q] += b.v[q] * z.v[q];
+      acc.v[q] = fmadd(b.v[q], z.v[q], acc.v[q]);
     }
     z.st(Y + grp * gs + i * VW);
   }
@@ -1282,7 +1282,7 @@ __global__ void __launch_bounds__(VC_NT) k_vcycle_tail(VTail<T> vt) {
         for (int q = 0; q < VW; ++q) e1c.v[q] = wi * r.v[q];
         const PK sx = vt_apply<T, VW, D, FULL, true>(g, vt.diag[l], vt.invdiag[l], vt.c[l], xg, id, v, w1, e1c);
 #pragma unroll
-        for (int q = 0; q < VW; ++q) out.v[q] = e1c.v[q] + wi2 * (r.v[q] - sx.v[q]);
+        for (int q = 0; q < VW; ++q) out.v[q] = fmadd(wi2, r.v[q] - sx.v[q], e1c.v[q]);
       } else if (mode == 1) {
         const T wi = w1 * vt.invdiag[l][id];
         const PK r = PK::ld(xg + id * VW);
@@ -1298,7 +1298,7 @@ __global__ void __launch_bounds__(VC_NT) k_vcycle_tail(VTail<T> vt) {
         } else {
           const T wi = w1 * vt.invdiag[l][id];
 #pragma unroll
-          for (int q = 0; q < VW; ++q) out.v[q] = xc.v[q] + wi * (bb.v[q] - sx.v[q]);
+          for (int q = 0; q < VW; ++q) out.v[q] = fmadd(wi, bb.v[q] - sx.v[q], xc.v[q]);
         }
       }
       out.st(yg + id * VW);
@@ -1367,7 +1367,7 @@ __global__ void __launch_bounds__(VC_NT) k_vcycle_tail(VTail<T> vt) {
         for (int k = w; k < nc; k += VC_NT / 32) {
           const T a = vt.cinv[(long)k * nc + i];
 #pragma unroll
-          for (int q = 0; q < VW; ++q) acc.v[q] += a * r[k * VW + q];
+          for (int q = 0; q < VW; ++q) acc.v[q] = fmadd(a, r[k * VW + q], acc.v[q]);
         }
 #pragma unroll
       for (int q = 0; q < VW; ++q) red[w][lane][q] = acc.v[q];
@@ -1400,11 +1400,11 @@ __global__ void __launch_bounds__(VC_NT) k_vcycle_tail(VTail<T> vt) {
         if (b) {
           const PK v2 = PK::ld(e + (ic + mask_offset(gc, b)) * VW);
 #pragma unroll
-          for (int q = 0; q < VW; ++q) val.v[q] = T(0.5) * (val.v[q] + v2.v[q]);
+          for (int q = 0; q < VW; ++q) val.v[q] = mulr(T(0.5), val.v[q] + v2.v[q]);
         }
         PK cv = PK::ld(ef + i * VW);
 #pragma unroll
-        for (int q = 0; q < VW; ++q) cv.v[q] += val.v[q];
+        for (int q = 0; q < VW; ++q) cv.v[q] = addr(cv.v[q], val.v[q]);
         cv.st(ef + i * VW);
       }
     }
@@ -1414,6 +1414,188 @@ __global__ void __launch_bounds__(VC_NT) k_vcycle_tail(VTail<T> vt) {
       sweep(l, 2, c, vt.rl[l], o, vt.w[l][vt.nu[l] - 1 - k], T(0));
       cluster_barrier();
       T *t = c; c = o; o = t;
+    }
+    cur[l] = c;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory coarse tail: the levels l0 .. L-2 of one column group run in one CTA of
+// VS_NT threads with their vectors in shared memory -- the two iterates of level l0 (its
+// right-hand side stays in global memory, where the restriction of level l0 - 1 wrote
+// it), and the right-hand side and both iterates of each level below -- so the smoothing
+// and transfer steps are separated by __syncthreads only, not by launches.  Two launches
+// bracket the dense coarse solve (k_coarse_apply, spread over many CTAs): PART 0 runs the
+// down leg and leaves each level's iterate (and the right-hand sides below l0) in its
+// global level buffers; PART 1 reloads them with the coarse solution and runs the up leg.
+// The arithmetic mirrors k_st / k_jacobi0 / k_restrict / k_prolong_add step for step
+// (same operations in the same order, explicitly rounded), so the result equals the
+// per-level path bit for bit.  The level-l0 correction is written to `dst`.
+// ---------------------------------------------------------------------------
+constexpr int VS_NT = 1024;
+
+template <typename T> struct VTailS {
+  int l0, L, zero_dirichlet, nc;
+  int nu[HP_MAXL];
+  T w[HP_MAXL][4];
+  GridDesc g[HP_MAXL];
+  const T *diag[HP_MAXL], *invdiag[HP_MAXL], *c[HP_MAXL];
+  const T *r0;  // level-l0 right-hand side (global, group stride gs0)
+  T *dst;       // level-l0 correction (global, group stride gs0)
+  long gs0;
+  T *rg[HP_MAXL], *ag[HP_MAXL];  // global right-hand side / iterate buffers of each level
+  long gs[HP_MAXL];               // their group strides
+  unsigned off_r[HP_MAXL], off_a[HP_MAXL], off_b[HP_MAXL];  // shared-memory byte offsets
+};
+
+template <typename T, int VW, int D, bool FULL, int PART>
+__global__ void __launch_bounds__(VS_NT) k_vtail_smem(VTailS<T> vt) {
+  using PK = Pack<T, VW>;
+  extern __shared__ __align__(16) unsigned char vs_smem[];
+  const int grp = blockIdx.y;
+  auto S = [&](unsigned off) { return reinterpret_cast<T *>(vs_smem + off); };
+  // one node step over level l: mode 0 two sweeps from zero (x = rhs, weights w1, w2),
+  // 1 one sweep from zero (w1), 2 sweep (x, rhs b, w1), 3 residual b - S x
+  auto sweep = [&](int l, int mode, const T *x, const T *b, T *y, T w1, T w2) {
+    const GridDesc &g = vt.g[l];
+    const T *dg = vt.diag[l], *iv = vt.invdiag[l], *cc = vt.c[l];
+    for (long id = threadIdx.x; id < g.n; id += VS_NT) {
+      int v[3];
+      vt_coords<D>(g, id, v);
+      PK out;
+      if (mode == 0) {
+        const T wi = w1 * iv[id], wi2 = w2 * iv[id];
+        const PK r = PK::ld(x + id * VW);
+        PK e1c;
+#pragma unroll
+        for (int q = 0; q < VW; ++q) e1c.v[q] = wi * r.v[q];
+        const PK sx = vt_apply<T, VW, D, FULL, true>(g, dg, iv, cc, x, id, v, w1, e1c);
+#pragma unroll
+        for (int q = 0; q < VW; ++q) out.v[q] = fmadd(wi2, r.v[q] - sx.v[q], e1c.v[q]);
+      } else if (mode == 1) {
+        const T wi = w1 * iv[id];
+        const PK r = PK::ld(x + id * VW);
+#pragma unroll
+        for (int q = 0; q < VW; ++q) out.v[q] = wi * r.v[q];
+      } else {
+        const PK xc = PK::ld(x + id * VW);
+        const PK sx = vt_apply<T, VW, D, FULL, false>(g, dg, iv, cc, x, id, v, T(0), xc);
+        const PK bb = PK::ld(b + id * VW);
+        if (mode == 3) {
+#pragma unroll
+          for (int q = 0; q < VW; ++q) out.v[q] = bb.v[q] - sx.v[q];
+        } else {
+          const T wi = w1 * iv[id];
+#pragma unroll
+          for (int q = 0; q < VW; ++q) out.v[q] = fmadd(wi, bb.v[q] - sx.v[q], xc.v[q]);
+        }
+      }
+      out.st(y + id * VW);
+    }
+    __syncthreads();
+  };
+  auto copy = [&](long n, const T *src, T *dst_) {
+    for (long id = threadIdx.x; id < n; id += VS_NT) PK::ld(src + id * VW).st(dst_ + id * VW);
+  };
+  const T *r0 = vt.r0 + grp * vt.gs0;
+  T *cur[HP_MAXL], *oth[HP_MAXL];
+  if (PART == 1) {
+    // reload: each level's iterate and the right-hand sides below l0, the coarse solution
+    for (int l = vt.l0; l < vt.L; ++l) {
+      copy(vt.g[l].n, vt.ag[l] + grp * vt.gs[l], S(vt.off_a[l]));
+      if (l > vt.l0 && l + 1 < vt.L) copy(vt.g[l].n, vt.rg[l] + grp * vt.gs[l], S(vt.off_r[l]));
+      cur[l] = S(vt.off_a[l]);
+      oth[l] = S(vt.off_b[l]);
+    }
+    __syncthreads();
+  }
+  for (int l = vt.l0; PART == 0 && l + 1 < vt.L; ++l) {
+    const T *rl = l == vt.l0 ? r0 : S(vt.off_r[l]);
+    const int nul = vt.nu[l];
+    T *c = nul >= 2 ? S(vt.off_a[l]) : S(vt.off_b[l]);
+    T *o = nul >= 2 ? S(vt.off_b[l]) : S(vt.off_a[l]);
+    sweep(l, nul >= 2 ? 0 : 1, rl, nullptr, c, vt.w[l][0], vt.w[l][1]);
+    for (int k = 2; k < nul; ++k) {
+      sweep(l, 2, c, rl, o, vt.w[l][k], T(0));
+      T *t = c;
+      c = o;
+      o = t;
+    }
+    sweep(l, 3, c, rl, o, T(0), T(0));
+    // restriction to level l + 1 (transpose of the P1 prolongation)
+    {
+      const GridDesc &gf = vt.g[l], &gc = vt.g[l + 1];
+      T *rc = S(vt.off_r[l + 1]);
+      for (long I = threadIdx.x; I < gc.n; I += VS_NT) {
+        int J[3];
+        vt_coords<D>(gc, I, J);
+        PK out = PK::zero();
+        if (!(vt.zero_dirichlet && (J[D - 1] == 0 || J[D - 1] == gc.N))) {
+          const long f0 = 2 * (long)J[0] + (long)gf.np * (2 * (long)J[1] + (D == 3 ? (long)gf.np * 2 * J[2] : 0));
+          out = PK::ld(o + f0 * VW);
+#pragma unroll
+          for (int b = 1; b < (1 << D); ++b) {
+            bool fw = true, bw = true;
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+              if ((b >> a) & 1) {
+                fw = fw && (J[a] < gc.N);
+                bw = bw && (J[a] > 0);
+              }
+            const long off = mask_offset(gf, b);
+            if (fw) out.axpy(T(0.5), PK::ld(o + (f0 + off) * VW));
+            if (bw) out.axpy(T(0.5), PK::ld(o + (f0 - off) * VW));
+          }
+        }
+        out.st(rc + I * VW);
+      }
+    }
+    __syncthreads();
+    cur[l] = c;
+    oth[l] = o;
+  }
+  if (PART == 0) {
+    // hand over through the global level buffers: iterates, and the right-hand sides
+    // below l0 (the coarsest one is the coarse solve's input)
+    for (int l = vt.l0; l < vt.L; ++l) {
+      if (l + 1 < vt.L) copy(vt.g[l].n, cur[l], vt.ag[l] + grp * vt.gs[l]);
+      if (l > vt.l0) copy(vt.g[l].n, S(vt.off_r[l]), vt.rg[l] + grp * vt.gs[l]);
+    }
+    return;
+  }
+  for (int l = vt.L - 2; l >= vt.l0; --l) {
+    // e_l += P e_{l+1}
+    {
+      const GridDesc &gf = vt.g[l], &gc = vt.g[l + 1];
+      const T *e = cur[l + 1];
+      T *ef = cur[l];
+      for (long i = threadIdx.x; i < gf.n; i += VS_NT) {
+        int v[3];
+        vt_coords<D>(gf, i, v);
+        const int b = (v[0] & 1) | ((v[1] & 1) << 1) | ((v[2] & 1) << 2);
+        const long ic = (v[0] >> 1) + (long)gc.np * ((v[1] >> 1) + (long)gc.np * (v[2] >> 1));
+        PK val = PK::ld(e + ic * VW);
+        if (b) {
+          const PK v2 = PK::ld(e + (ic + mask_offset(gc, b)) * VW);
+#pragma unroll
+          for (int q = 0; q < VW; ++q) val.v[q] = mulr(T(0.5), val.v[q] + v2.v[q]);
+        }
+        PK cv = PK::ld(ef + i * VW);
+#pragma unroll
+        for (int q = 0; q < VW; ++q) cv.v[q] = addr(cv.v[q], val.v[q]);
+        cv.st(ef + i * VW);
+      }
+    }
+    __syncthreads();
+    const T *rl = l == vt.l0 ? r0 : S(vt.off_r[l]);
+    T *c = cur[l], *o = oth[l];
+    const int nul = vt.nu[l];
+    for (int k = 0; k < nul; ++k) {
+      T *y = (l == vt.l0 && k == nul - 1) ? vt.dst + grp * vt.gs0 : o;
+      sweep(l, 2, c, rl, y, vt.w[l][nul - 1 - k], T(0));
+      T *t = c;
+      c = o;
+      o = t;
     }
     cur[l] = c;
   }
@@ -1444,10 +1626,100 @@ static void smooth_weights(const hp_problem *P, OpKind op, int l, T w[4]) {
     w[k] = k < nu ? (T)(1.0 / (c - d * std::cos(M_PI * (2.0 * k + 1.0) / (2.0 * nu)))) : T(0);
 }
 
-// first level of the fused coarse tail for this solve, or L (no fusion)
-static int tail_level(const hp_problem *P) {
+// opt-in maximum of shared memory per CTA on the current device
+static int smem_optin() {
+  static thread_local int dev = -1, val = 0;
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) return 0;
+  if (d != dev) {
+    if (cudaDeviceGetAttribute(&val, cudaDevAttrMaxSharedMemoryPerBlockOptin, d) != cudaSuccess) val = 0;
+    dev = d;
+  }
+  return val;
+}
+
+// Shared-memory layout of the coarse tail from level l0 for node_bytes per node (bytes of
+// one group's values at one node); fills the offsets when vt is given, returns the total.
+template <typename T>
+static size_t smem_tail_layout(const hp_problem *P, int l0, int node_bytes, VTailS<T> *vt) {
+  const int L = P->L;
+  size_t off = 0;
+  auto take = [&](long n) {
+    const size_t o = off;
+    off += ((size_t)n * node_bytes + 15) / 16 * 16;
+    return (unsigned)o;
+  };
+  for (int l = l0; l < L; ++l) {
+    const long n = P->lv[l].g.n;
+    const unsigned r = (l > l0) ? take(n) : 0u;  // level l0 reads its right-hand side from global memory
+    const unsigned a = take(n);
+    const unsigned b = (l < L - 1) ? take(n) : 0u;
+    if (vt) {
+      vt->off_r[l] = r;
+      vt->off_a[l] = a;
+      vt->off_b[l] = b;
+    }
+  }
+  return off;
+}
+
+// first level of the fused coarse tail for this solve, or L (no fusion): with the
+// shared-memory tail the lowest level, from smem_tail on, whose tail fits in a CTA's shared
+// memory (at least one level above the coarsest), else the cluster tail's fuse_from
+static int tail_level(const hp_problem *P, int node_bytes) {
+  if (P->smem_tail) {
+    const size_t cap = (size_t)smem_optin();
+    for (int l0 = std::max(1, P->smem_tail); l0 + 2 <= P->L; ++l0)
+      if (smem_tail_layout<float>(P, l0, node_bytes, nullptr) <= cap) return l0;
+    return P->L;
+  }
   const int f = P->fuse_from;
   return (f >= 1 && f + 2 <= P->L) ? f : P->L;
+}
+
+// The shared-memory tail as its two launches around the dense coarse solve.
+template <typename T, int VW>
+static void launch_vtail_smem(hp_problem *P, OpKind op, int s, int l0, const T *const *rl, T *const *ea,
+                              const long *gsl, T *dst) {
+  const int L = P->L, ng = (s + VW - 1) / VW;
+  VTailS<T> vt{};
+  vt.l0 = l0;
+  vt.L = L;
+  vt.zero_dirichlet = op == OP_K;
+  vt.nc = (int)P->lv[L - 1].g.n;
+  for (int l = 0; l < L; ++l) {
+    vt.nu[l] = nu_at(P, l);
+    smooth_weights<T>(P, op, l, vt.w[l]);
+    const Stencil<T> &S = stencil_of<T>(P, op, l);
+    vt.g[l] = P->lv[l].g;
+    vt.diag[l] = S.diag;
+    vt.invdiag[l] = S.invdiag;
+    vt.c[l] = S.c;
+    vt.rg[l] = const_cast<T *>(rl[l]);
+    vt.ag[l] = ea[l];
+    vt.gs[l] = gsl[l];
+  }
+  vt.r0 = rl[l0];
+  vt.dst = dst;
+  vt.gs0 = gsl[l0];
+  const size_t bytes = smem_tail_layout<T>(P, l0, (int)(sizeof(T) * VW), &vt);
+  const bool full = stencil_of<T>(P, op, l0).full;
+  void (*down)(VTailS<T>) = nullptr, (*up)(VTailS<T>) = nullptr;
+  if (P->lv[0].g.dim == 2) {
+    down = full ? k_vtail_smem<T, VW, 2, true, 0> : k_vtail_smem<T, VW, 2, false, 0>;
+    up = full ? k_vtail_smem<T, VW, 2, true, 1> : k_vtail_smem<T, VW, 2, false, 1>;
+  } else {
+    down = full ? k_vtail_smem<T, VW, 3, true, 0> : k_vtail_smem<T, VW, 3, false, 0>;
+    up = full ? k_vtail_smem<T, VW, 3, true, 1> : k_vtail_smem<T, VW, 3, false, 1>;
+  }
+  cudaFuncSetAttribute(down, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(up, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  down<<<dim3(1, ng), VS_NT, bytes, P->st>>>(vt);
+  const int lc = L - 1, nc = (int)P->lv[lc].g.n;
+  k_coarse_apply<T, VW><<<dim3((nc + 31) / 32, ng), 256, sizeof(T) * nc * VW, P->st>>>(
+      coarse_inv<T>(P, op), nc, rl[lc], gsl[lc], ea[lc], gsl[lc]);
+  up<<<dim3(1, ng), VS_NT, bytes, P->st>>>(vt);
+  count_launch(3);
 }
 
 template <typename T, int VW>
@@ -1541,7 +1813,7 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
   }
   T *cur[HP_MAXL], *oth[HP_MAXL];
   const Fin nofin{};
-  const int l0 = tail_level(P);  // levels >= l0 run inside one cluster launch
+  const int l0 = tail_level(P, (int)(sizeof(T) * VW));  // levels >= l0 run inside one launch
   for (int l = 0; l + 1 < L; ++l) {
     const int nu = nu_at(P, l);
     if (l >= l0) {  // buffer bookkeeping only: the fused kernel makes the same choices
@@ -1605,13 +1877,16 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
     oth[l] = o;
   }
   if (l0 < L) {
-    launch_vtail<T, VW>(P, op, s, l0, rl, ea, eb, gsl);
     cur[L - 1] = ea[L - 1];
     for (int l = L - 2; l >= l0; --l) {
       T *c = cur[l], *o = oth[l];
       for (int k = 0; k < nu_at(P, l); ++k) std::swap(c, o);
       cur[l] = c;
     }
+    if (P->smem_tail)  // the level-l0 correction lands where the cluster tail would leave it
+      launch_vtail_smem<T, VW>(P, op, s, l0, rl, ea, gsl, cur[l0]);
+    else
+      launch_vtail<T, VW>(P, op, s, l0, rl, ea, eb, gsl);
   } else {
     const int lc = L - 1;
     const int nc = (int)P->lv[lc].g.n;
@@ -1813,18 +2088,20 @@ static int build_graph(hp_problem *P, OpKind op, int s, double tol, int maxit, P
   });
 }
 
-static int kernels_per_iteration(const hp_problem *P, OpKind op) {
+static int kernels_per_iteration(const hp_problem *P, OpKind op, int node_bytes) {
   if (op == OP_M) return 8;
   // V-cycle: per non-coarsest level pre (1 + nu - 2), resid, restrict, prolong, nu post; coarse 1
   // (or one fused launch for the levels from tail_level on); plus p update, matvec, cg update,
   // condition and three dot finalisations
-  const int separate = std::min(P->L, tail_level(P)) - 1 + (tail_level(P) < P->L ? 1 : 0);
+  // (the shared-memory tail: down leg, coarse solve, up leg = 3 launches)
+  const int tl = tail_level(P, node_bytes);
+  const int separate = std::min(P->L, tl) - 1 + (tl < P->L ? 1 : 0);
   int vc = 0;
   for (int l = 0; l < separate; ++l) {
     const int nu = nu_at(P, l);
     vc += (nu >= 2 ? nu - 1 : 1) + nu + (fuse_at(P, l) ? (nu >= 2 ? 1 : 2) : 3);
   }
-  return 7 + vc + 1 + 2 * (P->L == 1);
+  return 7 + vc + 1 + 2 * (P->L == 1) + ((P->smem_tail && tl < P->L) ? 2 : 0);
 }
 
 // after a PCG: fails the solve if a tile kernel gave up waiting for its copies
@@ -1857,7 +2134,7 @@ static int pcg(hp_problem *P, OpKind op, int s, double rtol, int maxit, int *its
     HP_CUDA(cudaMemcpyAsync(h_it, P->sc.iter.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     HP_CUDA(cudaMemcpyFromSymbolAsync(h_it + 1, g_tile_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
     HP_CUDA(cudaStreamSynchronize(st));
-    count_launch((unsigned long long)(*h_it) * kernels_per_iteration(P, op) + 2);
+    count_launch((unsigned long long)(*h_it) * kernels_per_iteration(P, op, (int)(sizeof(T) * VW)) + 2);
     *its = *h_it;
     HP_TRY(tile_timeout_check(P, h_it));
     return *h_it >= maxit ? HP_ERR_NOT_CONVERGED : 0;
@@ -2015,7 +2292,7 @@ static int ir_solve_graph(hp_problem *P, OpKind op, const double *B, long ldb, d
   // kernels run: the first check, and per step the scaling, the PCG init (3) and
   // iterations, the accumulation, the residual with its finalisation and the check
   count_launch(1ull + 8ull * (unsigned long long)c.outer +
-               (unsigned long long)c.total_its * (unsigned long long)kernels_per_iteration(P, op));
+               (unsigned long long)c.total_its * (unsigned long long)kernels_per_iteration(P, op, (int)(sizeof(T) * VW)));
   if (c.flags & 2) return set_error(HP_ERR_NONFINITE, "non-finite residual in a PDE solve");
   if (stats) {
     stats->iterations += c.total_its;
@@ -2252,6 +2529,7 @@ extern "C" int hp_replay_kernel_graph(hp_problem *P, int family, int reps, doubl
   const float om = (float)P->omega;
   float *z = W.z.as<float>(), *r = W.r.as<float>(), *y = W.lb[0].as<float>();
   HP_CUDA(cudaStreamSynchronize(P->st));
+  if (!P->cap) HP_CUDA(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   HP_CUDA(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal));

@@ -23,15 +23,17 @@ int hp_set_tuning(hp_problem *P, const hp_tuning *t) {
   if (t->nu < 1 || t->nu > 4 || t->nu_coarse < 0 || t->nu_coarse > 4 || !(t->omega > 0.0 && t->omega < 1.0) || t->col_chunk < 0 || t->max_blocks < 64 ||
       t->max_blocks > (1 << 20) || t->fuse_from < 0 || t->fuse_from >= HP_MAXL || t->smoother < 0 ||
       t->smoother > 1 || (t->smoother == 1 && !(t->cheb_alpha > 1.0 && t->cheb_alpha < 1e6)) ||
-      t->fuse_transfer < 0 || t->fuse_transfer > 2 || t->tma_tiles < 0 || t->tma_tiles > 1)
+      t->fuse_transfer < 0 || t->fuse_transfer > 2 || t->tma_tiles < 0 || t->tma_tiles > 1 ||
+      t->smem_tail < 0 || t->smem_tail >= HP_MAXL)
     return set_error(HP_ERR_INVALID, "hp_set_tuning: nu in [1,4], omega in (0,1), col_chunk >= 0, max_blocks >= 64, "
-                                     "fuse_from in [0, 15], smoother 0/1, cheb_alpha > 1, fuse_transfer 0..2, tma_tiles 0/1");
+                                     "fuse_from in [0, 15], smoother 0/1, cheb_alpha > 1, fuse_transfer 0..2, tma_tiles 0/1, smem_tail in [0, 15]");
   HP_CUDA(cudaStreamSynchronize(P->st));
   if (t->nu != P->nu || t->nu_coarse != P->nu_coarse || t->omega != P->omega || t->max_blocks != P->max_blocks || t->fuse_from != P->fuse_from ||
       t->smoother != P->smoother || (t->smoother == 1 && t->cheb_alpha != P->cheb_alpha) ||
-      t->fuse_transfer != P->fuse_transfer || t->tma_tiles != P->tma_tiles)
+      t->fuse_transfer != P->fuse_transfer || t->tma_tiles != P->tma_tiles || t->smem_tail != P->smem_tail)
     drop_graphs(P);
   P->tma_tiles = t->tma_tiles;
+  P->smem_tail = t->smem_tail;
   P->fuse_transfer = t->fuse_transfer;
   P->fuse_from = t->fuse_from;
   P->smoother = t->smoother;
@@ -56,6 +58,7 @@ int hp_get_tuning(const hp_problem *P, hp_tuning *t) {
   t->cheb_alpha = P->cheb_alpha;
   t->fuse_transfer = P->fuse_transfer;
   t->tma_tiles = P->tma_tiles;
+  t->smem_tail = P->smem_tail;
   return HP_OK;
 }
 
@@ -144,8 +147,18 @@ int hp_autotune(hp_problem *P, int nrhs, int reps, hp_tuning *best, double *best
       cur_ms = ms;
     }
   }
+  for (int st : {1}) {
+    hp_tuning t = cur;
+    t.smem_tail = st;
+    double ms;
+    if ((rc = time_it(t, &ms))) return cleanup(rc);
+    if (ms < cur_ms) {
+      cur = t;
+      cur_ms = ms;
+    }
+  }
   for (int ff : {1, 2}) {
-    if (ff + 2 > P->L) continue;
+    if (ff + 2 > P->L || cur.smem_tail) continue;
     hp_tuning t = cur;
     t.fuse_from = ff;
     double ms;

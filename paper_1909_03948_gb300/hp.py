@@ -60,7 +60,7 @@ class SolveStats(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("nu", C.c_int), ("nu_coarse", C.c_int), ("omega", C.c_double), ("col_chunk", C.c_int), ("max_blocks", C.c_int),
                 ("smoother", C.c_int), ("cheb_alpha", C.c_double), ("fuse_transfer", C.c_int),
-                ("fuse_from", C.c_int), ("tma_tiles", C.c_int)]
+                ("fuse_from", C.c_int), ("tma_tiles", C.c_int), ("smem_tail", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -437,10 +437,10 @@ class Problem:
         return t.as_dict()
 
     def set_tuning(self, nu=3, omega=0.7, col_chunk=0, max_blocks=2048, smoother=1, cheb_alpha=10.0,
-                   fuse_transfer=0, fuse_from=0, nu_coarse=0, tma_tiles=0):
+                   fuse_transfer=0, fuse_from=0, nu_coarse=0, tma_tiles=0, smem_tail=0):
         t = Tuning(nu=nu, nu_coarse=nu_coarse, omega=omega, col_chunk=col_chunk, max_blocks=max_blocks,
                    smoother=smoother, cheb_alpha=cheb_alpha, fuse_transfer=fuse_transfer, fuse_from=fuse_from,
-                   tma_tiles=tma_tiles)
+                   tma_tiles=tma_tiles, smem_tail=smem_tail)
         _check(lib().hp_set_tuning(self._h, C.byref(t)), "hp_set_tuning")
 
     def autotune(self, nrhs, reps=2):

@@ -449,3 +449,30 @@ def test_tma_tiles_keep_results(N, ncols):
     assert abs(st1["iterations"] - st0["iterations"]) <= 1, (st0, st1)
     P.set_tuning()
     P.close()
+
+
+@pytest.mark.parametrize("dim,N,precision", [(2, 256, "fp32_ir"), (2, 64, "fp32_ir"), (2, 128, "fp64"),
+                                             (3, 32, "fp32_ir"), (3, 16, "fp64")])
+@pytest.mark.parametrize("nu,nu_coarse", [(1, 0), (2, 0), (3, 0), (3, 2)])
+def test_smem_tail_equals_per_level_kernels(dim, N, precision, nu, nu_coarse):
+    """The shared-memory coarse tail (one CTA per column group runs the levels whose vectors
+    fit in its shared memory, and the dense coarse solve) mirrors the per-level kernels step
+    for step, so Hessian actions (stiffness, axis stencil) and prior solves (full stencil)
+    equal theirs bit for bit, with the same PCG iteration counts."""
+    from paper_1909_03948_gb300 import Problem
+    w = W.make_workload(dim, N, 30, seed=91)
+    dr = W.draws(w)
+    P = Problem(dim, N, w.gamma, w.delta, 0.01, dr.obs_xyz, rtol=1e-9, precision=precision)
+    m = 0.3 * torch.tensor(np.random.default_rng(9).standard_normal(P.n), device=DEV)
+    X = torch.tensor(np.random.default_rng(10).standard_normal((6, P.n)), device=DEV)
+    out = {}
+    for st_ in (0, 1):
+        P.set_tuning(nu=nu, nu_coarse=nu_coarse, smem_tail=st_)
+        P.set_point(m)
+        Y, sy = P.hessian_apply(X)
+        Z, sz = P.prior_solve(X)
+        out[st_] = (Y, Z, sy["iterations"], sz["iterations"])
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    assert out[0][2:] == out[1][2:]
+    P.set_tuning()
+    P.close()
