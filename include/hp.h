@@ -324,10 +324,11 @@ typedef struct {
                       cluster of 8 CTAs per column group, steps separated by the
                       hardware cluster barrier (ignored when fewer than 2 levels
                       remain below it) */
-  int tma_tiles;   /* 1: on the multigrid levels of 2D stiffness solves whose grid has
-                      np - 1 a multiple of 32 (np >= 33), the stencil kernels work on
-                      32 x 16-node tiles that bulk tensor copies (TMA) bring into shared
-                      memory with their halo; 0: every warp loads its own row of nodes */
+  int tma_tiles;   /* 1: on the multigrid levels of stiffness solves whose grid has np - 1 a
+                      multiple of 32 (2D: and of 16; 3D: and of 16 planes), the stencil
+                      kernels work on tiles that bulk tensor copies (TMA) bring into shared
+                      memory with their halo -- 32 x 16 nodes in 2D, 32 x 8 nodes marching
+                      through z in 3D; 0: every warp loads its own row of nodes */
   int smem_tail;   /* k >= 1: the coarse end of the V-cycle -- from the finest level l >= k
                       whose vectors, and those of every level below it, fit in one CTA's
                       shared memory -- runs as one launch of one CTA per column group, its

@@ -200,6 +200,19 @@ __global__ void k_pack_K2(long n, const float *__restrict__ diag, const float *_
     pk[i] = make_float4(diag[i], invdiag[i], c[i], c[n + i]);
 }
 
+// 3D stiffness in FP32 for the tiled kernels: one 16-byte record per node {diag, 1 / diag,
+// coupling to x + 1, coupling to y + 1}, and the coupling to z + 1 in rows padded to a
+// multiple of 4 nodes (a tensor map's row stride must be a multiple of 16 bytes)
+__global__ void k_pack_K3(GridDesc g, const float *__restrict__ diag, const float *__restrict__ invdiag,
+                          const float *__restrict__ c, float4 *__restrict__ pk, float *__restrict__ cz) {
+  const long n = g.n, ldr = (g.np + 3) / 4 * 4;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    pk[i] = make_float4(diag[i], invdiag[i], c[i], c[n + i]);
+    const long x = i % g.np, row = i / g.np;
+    cz[row * ldr + x] = c[2 * n + i];
+  }
+}
+
 template <int D>
 __device__ __forceinline__ int count_elems(const GridDesc &g, const int v[3], int b) {
   int n = 0;
@@ -489,6 +502,12 @@ int build_hierarchy_geometry(hp_problem *P) {
     HP_CUDA(cudaMalloc(&lv.kappa, sizeof(double) * lv.nelems));
     HP_TRY(alloc_stencil(lv.K64, lv.K32, lv.g.n, nfK, false));
     if (tile_grid(lv.g)) HP_CUDA(cudaMalloc(&lv.K32.pk, sizeof(float4) * lv.g.n));
+    if (tile3_grid(lv.g)) {
+      const long ldr = (lv.g.np + 3) / 4 * 4;
+      const size_t bytes = sizeof(float4) * lv.g.n + sizeof(float) * ldr * lv.g.np * lv.g.np;
+      HP_CUDA(cudaMalloc(&lv.K32.pk, bytes));
+      HP_CUDA(cudaMemset(lv.K32.pk, 0, bytes));  // the row padding of the z couplings stays zero
+    }
     HP_TRY(alloc_stencil(lv.A64, lv.A32, lv.g.n, nfA, true));
     const int nb = grid_blocks(lv.g.n);
     Theta6 th;
@@ -563,8 +582,13 @@ int build_point(hp_problem *P, const double *m_dev) {
                                                            P->u_bottom);
     count_launch();
     if (lv.K32.pk) {
-      k_pack_K2<<<grid_blocks(lv.g.n), 256, 0, P->st>>>(lv.g.n, lv.K32.diag, lv.K32.invdiag, lv.K32.c,
-                                                        reinterpret_cast<float4 *>(lv.K32.pk));
+      if (D == 2)
+        k_pack_K2<<<grid_blocks(lv.g.n), 256, 0, P->st>>>(lv.g.n, lv.K32.diag, lv.K32.invdiag, lv.K32.c,
+                                                          reinterpret_cast<float4 *>(lv.K32.pk));
+      else
+        k_pack_K3<<<grid_blocks(lv.g.n), 256, 0, P->st>>>(lv.g, lv.K32.diag, lv.K32.invdiag, lv.K32.c,
+                                                          reinterpret_cast<float4 *>(lv.K32.pk),
+                                                          lv.K32.pk + 4 * lv.g.n);
       count_launch();
     }
   }

@@ -19,6 +19,13 @@ constexpr int TILE_X = 32, TILE_Y = 16;
 inline bool tile_grid(const GridDesc &g) {
   return g.dim == 2 && g.np >= TILE_X + 1 && (g.np - 1) % TILE_X == 0 && (g.np - 1) % TILE_Y == 0;
 }
+// 3D: 32 x 8-node xy tiles marching through z segments of 16 planes (the last tile or
+// segment in each direction also takes the grid's final node / row / plane)
+constexpr int TILE3_X = 32, TILE3_Y = 8, TILE3_Z = 16;
+inline bool tile3_grid(const GridDesc &g) {
+  return g.dim == 3 && g.np >= TILE3_X + 1 && (g.np - 1) % TILE3_X == 0 && (g.np - 1) % TILE3_Y == 0 &&
+         (g.np - 1) % TILE3_Z == 0;
+}
 
 // Symmetric stencil stored by "forward" couplings: y_i = diag_i x_i +
 // sum_f [c_f(i) x_{i+o_f} + c_f(i-o_f) x_{i-o_f}], with o_f the 0/1 corner
@@ -29,7 +36,8 @@ template <typename T> struct Stencil {
   T *diag = nullptr;
   T *invdiag = nullptr;
   T *c = nullptr;
-  T *pk = nullptr;  // 2D axis-only stencils on tiled grids: {diag, invdiag, c_0, c_1} per node (16 B)
+  T *pk = nullptr;  // axis stencils on tiled grids: one record {diag, invdiag, c_0, c_1} per node
+                    // (16 B); in 3D followed by c_2 in rows of (np + 3) / 4 * 4 (16-byte strides)
   int nf = 0;
   bool full = false;
   double lmax = 2.0;  // upper bound of the spectrum of diag^-1 S (Gershgorin)

@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(TL_NT) k_st_tile(const __grid_constant__ CUten
     if (HAS_B) tma_load_3d(smem_u32(rs), &mr, 4 * x0, y0, grp, bar);
     tma_load_2d(smem_u32(cs), &mc, 4 * (x0 - 1), y0 - 1, bar);
   }
-  if (!mbar_wait0(bar)) {
+  if (!__syncthreads_and(mbar_wait0(bar))) {  // every thread leaves together if any wait ran out
     if (threadIdx.x == 0) atomicExch(&g_tile_timeout, 1);
     return;
   }
@@ -407,6 +407,185 @@ __global__ void __launch_bounds__(TL_NT) k_st_tile(const __grid_constant__ CUten
     out.st(Y + grp * gy + ((long)v0 + (long)g.np * v1) * 4);
   }
   if (DOT) dot_partial<float, 4>(acc, fin.part, grp, s, tile, ntx * nty);
+}
+
+// ---------------------------------------------------------------------------
+// TMA z-marching stencil kernels (3D stiffness levels, FP32, 4 columns per node).
+// One CTA per xy tile of TILE3_X x TILE3_Y nodes, one z segment of TILE3_Z planes and one
+// column group.  A ring of TL3_NS shared-memory slots holds consecutive planes: the plane
+// of x with a one-node xy halo, the plane of 32-byte coefficient records with the same
+// halo, and the plane of b; each slot completes on its own mbarrier (the use count's
+// parity is the phase).  Plane p is computed from the slots of p - 1, p and p + 1 while
+// thread 0 keeps the copies of planes p + 2 .. p + TL3_NS - 2 in flight, so every plane's
+// data is requested TL3_NS - 3 steps before it is needed.  Copies past the grid read zeros; the boundary tests
+// keep them out of the arithmetic, which is k_st's, operation for operation.
+// ---------------------------------------------------------------------------
+constexpr int TL3_NT = NB;
+constexpr int TL3_NS = 4;                                          // ring slots
+constexpr int TL3B_X = TILE3_X + 3, TL3B_Y = TILE3_Y + 3;          // x / record boxes (one plane)
+constexpr int TL3R_X = TILE3_X + 1, TL3R_Y = TILE3_Y + 1;          // b box (one plane)
+constexpr int TL3Z_X = TILE3_X + 4;                                // c_z box width (16-byte multiple)
+constexpr unsigned TL3_XB = TL3B_X * TL3B_Y * 16u, TL3_CB = TL3B_X * TL3B_Y * 16u, TL3_RB = TL3R_X * TL3R_Y * 16u;
+constexpr unsigned TL3_ZB = TL3Z_X * TL3R_Y * 4u;
+constexpr unsigned TL3_OFF_C = (TL3_XB + 127u) / 128u * 128u;
+constexpr unsigned TL3_OFF_Z = TL3_OFF_C + (TL3_CB + 127u) / 128u * 128u;
+constexpr unsigned TL3_OFF_R = TL3_OFF_Z + (TL3_ZB + 127u) / 128u * 128u;
+constexpr unsigned TL3_SLOT = TL3_OFF_R + (TL3_RB + 127u) / 128u * 128u;
+constexpr unsigned TL3_OFF_BAR = TL3_NS * TL3_SLOT;
+constexpr unsigned TL3_SMEM = TL3_OFF_BAR + 8u * TL3_NS + 128u;  // + alignment slack
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+// waits for the given phase parity of a barrier for at most ~2^31 clocks
+__device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUtensorMap mx,
+                                                     const __grid_constant__ CUtensorMap mr,
+                                                     const __grid_constant__ CUtensorMap mc,
+                                                     const __grid_constant__ CUtensorMap mz, GridDesc g, int ntx,
+                                                     int nty, int nzs, float *__restrict__ Y, long gy, int s,
+                                                     float omega, float omega2, Fin fin) {
+  using PK = Pack<float, 4>;
+  extern __shared__ __align__(128) unsigned char tl3_raw[];
+  unsigned char *sm = tl3_raw + ((128u - (smem_u32(tl3_raw) & 127u)) & 127u);
+  constexpr bool HAS_B = (MODE == M_RESID || MODE == M_JACOBI || MODE == M_JACOBI_DOT);
+  constexpr bool DOT = (MODE == M_APPLY_DOT || MODE == M_JACOBI_DOT);
+  const int tile = blockIdx.x, grp = blockIdx.y;
+  const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+  const int x0 = tx * TILE3_X, y0 = ty * TILE3_Y, zb = tz * TILE3_Z;
+  const int wx = TILE3_X + (tx == ntx - 1), hy = TILE3_Y + (ty == nty - 1);
+  const int ze = zb + TILE3_Z + (tz == nzs - 1);  // planes zb .. ze - 1
+  const uint32_t bar0 = smem_u32(sm + TL3_OFF_BAR);
+  const unsigned bytes = TL3_XB + TL3_CB + TL3_ZB + (HAS_B ? TL3_RB : 0u);
+  // plane q sits in slot (q - zb + 1) % NS; its barrier's phase is the slot's use count
+  auto issue = [&](int q) {
+    const int r = q - zb + 1, k = r % TL3_NS;
+    unsigned char *sl = sm + k * TL3_SLOT;
+    const uint32_t bar = bar0 + 8u * k;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    tma_load_4d(smem_u32(sl), &mx, 4 * (x0 - 1), y0 - 1, q, grp, bar);
+    tma_load_3d(smem_u32(sl + TL3_OFF_C), &mc, 4 * (x0 - 1), y0 - 1, q, bar);
+    tma_load_3d(smem_u32(sl + TL3_OFF_Z), &mz, x0, y0, q, bar);
+    if (HAS_B) tma_load_4d(smem_u32(sl + TL3_OFF_R), &mr, 4 * x0, y0, q, grp, bar);
+  };
+  auto ready = [&](int q) {
+    const int r = q - zb + 1;
+    return mbar_wait_parity(bar0 + 8u * (r % TL3_NS), (unsigned)((r / TL3_NS) & 1));
+  };
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < TL3_NS; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8u * k) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)  // the planes below, at and above the first one, and the prefetch
+    for (int q = zb - 1; q <= zb + TL3_NS - 3 && q <= ze; ++q) issue(q);
+  PK acc = PK::zero();
+  bool ok = true;
+  for (int p = zb; p < ze; ++p) {
+    __syncthreads();  // every thread is done with plane p - 2's slot
+    if (threadIdx.x == 0 && p + TL3_NS - 2 <= ze) issue(p + TL3_NS - 2);
+    ok = ready(p - 1) && ready(p) && ready(p + 1);
+    if (!__syncthreads_and(ok)) {  // every thread leaves together if any wait ran out
+      ok = false;
+      break;
+    }
+    const unsigned char *sm_m = sm + ((p - zb) % TL3_NS) * TL3_SLOT;       // plane p - 1
+    const unsigned char *sm_0 = sm + ((p - zb + 1) % TL3_NS) * TL3_SLOT;   // plane p
+    const unsigned char *sm_p = sm + ((p - zb + 2) % TL3_NS) * TL3_SLOT;   // plane p + 1
+    const float *xm = reinterpret_cast<const float *>(sm_m), *x0s = reinterpret_cast<const float *>(sm_0),
+                *xp = reinterpret_cast<const float *>(sm_p);
+    const float4 *c0s = reinterpret_cast<const float4 *>(sm_0 + TL3_OFF_C),
+                 *cp = reinterpret_cast<const float4 *>(sm_p + TL3_OFF_C),
+                 *cm = reinterpret_cast<const float4 *>(sm_m + TL3_OFF_C);
+    const float *zm = reinterpret_cast<const float *>(sm_m + TL3_OFF_Z),
+                *z0 = reinterpret_cast<const float *>(sm_0 + TL3_OFF_Z);
+    const float *rs = reinterpret_cast<const float *>(sm_0 + TL3_OFF_R);
+    const bool fz = p < g.N, bz = p > 0;
+    for (int t = threadIdx.x; t < wx * hy; t += TL3_NT) {
+      const int lx = t % wx, ly = t / wx;
+      const int v0 = x0 + lx, v1 = y0 + ly;
+      const int ci = (ly + 1) * TL3B_X + lx + 1;  // this node in the halo boxes
+      const int zi = ly * TL3Z_X + lx;            // ... in the c_z box
+      const bool fx = v0 < g.N, bx = v0 > 0, fy = v1 < g.N, by = v1 > 0;
+      const float4 cc = c0s[ci];  // diag, invdiag, c_x, c_y
+      const float cz = z0[zi];    // c_z
+      PK out;
+      if (MODE == M_JAC2) {
+        const float wi = omega * cc.y, wi2 = omega2 * cc.y;
+        const PK r = PK::ld(x0s + ci * 4);
+        PK e1c;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) e1c.v[q] = wi * r.v[q];
+        PK sx;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sx.v[q] = cc.x * e1c.v[q];
+        if (fx) sx.axpy(cc.z * omega * c0s[ci + 1].y, PK::ld(x0s + (ci + 1) * 4));
+        if (bx) sx.axpy(c0s[ci - 1].z * omega * c0s[ci - 1].y, PK::ld(x0s + (ci - 1) * 4));
+        if (fy) sx.axpy(cc.w * omega * c0s[ci + TL3B_X].y, PK::ld(x0s + (ci + TL3B_X) * 4));
+        if (by) sx.axpy(c0s[ci - TL3B_X].w * omega * c0s[ci - TL3B_X].y, PK::ld(x0s + (ci - TL3B_X) * 4));
+        if (fz) sx.axpy(cz * omega * cp[ci].y, PK::ld(xp + ci * 4));
+        if (bz) sx.axpy(zm[zi] * omega * cm[ci].y, PK::ld(xm + ci * 4));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) out.v[q] = fmadd(wi2, r.v[q] - sx.v[q], e1c.v[q]);
+      } else {
+        const PK xc = PK::ld(x0s + ci * 4);
+        PK sx;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sx.v[q] = cc.x * xc.v[q];
+        if (fx) sx.axpy(cc.z, PK::ld(x0s + (ci + 1) * 4));
+        if (bx) sx.axpy(c0s[ci - 1].z, PK::ld(x0s + (ci - 1) * 4));
+        if (fy) sx.axpy(cc.w, PK::ld(x0s + (ci + TL3B_X) * 4));
+        if (by) sx.axpy(c0s[ci - TL3B_X].w, PK::ld(x0s + (ci - TL3B_X) * 4));
+        if (fz) sx.axpy(cz, PK::ld(xp + ci * 4));
+        if (bz) sx.axpy(zm[zi], PK::ld(xm + ci * 4));
+        if (MODE == M_APPLY || MODE == M_APPLY_DOT) {
+          out = sx;
+          if (DOT)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc.v[q] = fmadd(xc.v[q], out.v[q], acc.v[q]);
+        } else {
+          const PK bb = PK::ld(rs + (ly * TL3R_X + lx) * 4);
+          if (MODE == M_RESID) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) out.v[q] = bb.v[q] - sx.v[q];
+          } else {
+            const float wi = omega * cc.y;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) out.v[q] = fmadd(wi, bb.v[q] - sx.v[q], xc.v[q]);
+            if (DOT)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) acc.v[q] = fmadd(bb.v[q], out.v[q], acc.v[q]);
+          }
+        }
+      }
+      out.st(Y + grp * gy + ((long)v0 + (long)g.np * ((long)v1 + (long)g.np * p)) * 4);
+    }
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(&g_tile_timeout, 1);
+    return;
+  }
+  if (DOT) dot_partial<float, 4>(acc, fin.part, grp, s, tile, ntx * nty * nzs);
 }
 
 // ---------------------------------------------------------------------------
@@ -1034,12 +1213,83 @@ static bool tile_launch(const GridDesc &g, const Stencil<float> &S, const float 
   return true;
 }
 
+// 3D: a grouped block as a rank-4 tensor {4 np floats (one grid row), np rows, np planes,
+// ng groups}; boxes of box_x x box_y nodes of one plane of one group
+static bool tile3_map_block(CUtensorMap *m, const float *base, long gs, const GridDesc &g, int ng, int box_x,
+                            int box_y) {
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t np = (cuuint64_t)g.np;
+  const cuuint64_t dim[4] = {4ull * np, np, np, (cuuint64_t)ng};
+  const cuuint64_t str[3] = {16ull * np, 16ull * np * np, 4ull * (cuuint64_t)gs};
+  const cuuint32_t box[4] = {4u * (cuuint32_t)box_x, (cuuint32_t)box_y, 1u, 1u};
+  const cuuint32_t es[4] = {1u, 1u, 1u, 1u};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(base), dim, str, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 3D coefficient records as a rank-3 tensor {4 np floats, np, np} (halo boxes), and the
+// z couplings in padded rows as a rank-3 tensor {ldr, np, np} (boxes without halo)
+static bool tile3_map_coef(CUtensorMap *m, CUtensorMap *mz, const float *pk, const GridDesc &g) {
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t np = (cuuint64_t)g.np, ldr = (np + 3) / 4 * 4;
+  const cuuint64_t dim[3] = {4ull * np, np, np};
+  const cuuint64_t str[2] = {16ull * np, 16ull * np * np};
+  const cuuint32_t box[3] = {4u * TL3B_X, (cuuint32_t)TL3B_Y, 1u};
+  const cuuint32_t es[3] = {1u, 1u, 1u};
+  if (fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(pk), dim, str, box, es,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  const cuuint64_t dimz[3] = {ldr, np, np};
+  const cuuint64_t strz[2] = {4ull * ldr, 4ull * ldr * np};
+  const cuuint32_t boxz[3] = {(cuuint32_t)TL3Z_X, (cuuint32_t)TL3R_Y, 1u};
+  return fn(mz, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(pk + 4 * g.n), dimz, strz, boxz, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int MODE>
+static bool tile3_launch(const GridDesc &g, const Stencil<float> &S, const float *X, long gx, const float *B,
+                         long gb, float *Y, long gy, int s, float omega, float omega2, const Fin &fin,
+                         cudaStream_t st) {
+  constexpr bool HAS_B = (MODE == M_RESID || MODE == M_JACOBI || MODE == M_JACOBI_DOT);
+  const int ng = (s + 3) / 4;
+  CUtensorMap mx, mr, mc, mz;
+  if (!tile3_map_block(&mx, X, gx, g, ng, TL3B_X, TL3B_Y) || !tile3_map_coef(&mc, &mz, S.pk, g)) return false;
+  if (HAS_B) {
+    if (!tile3_map_block(&mr, B, gb, g, ng, TL3R_X, TL3R_Y)) return false;
+  } else {
+    mr = mx;
+  }
+  const int ntx = (g.np - 1) / TILE3_X, nty = (g.np - 1) / TILE3_Y, nzs = (g.np - 1) / TILE3_Z;
+  static unsigned long long attr_set = 0;  // the opt-in shared-memory size, once per mode and device
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return false;
+  if (!(attr_set & (1ull << dev))) {
+    if (cudaFuncSetAttribute(k_st_tile3<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL3_SMEM) !=
+        cudaSuccess)
+      return false;
+    attr_set |= 1ull << dev;
+  }
+  k_st_tile3<MODE><<<dim3(ntx * nty * nzs, ng), TL3_NT, TL3_SMEM, st>>>(mx, mr, mc, mz, g, ntx, nty, nzs, Y, gy,
+                                                                       s, omega, omega2, fin);
+  count_launch();
+  if (MODE == M_APPLY_DOT || MODE == M_JACOBI_DOT) dot_finalize(fin, ntx * nty * nzs, s, st);
+  return true;
+}
+
 template <typename T, int VW, int MODE>
 static void st_launch(const GridDesc &g, const Stencil<T> &S, const T *X, long gx, const T *B, long gb, T *Y, long gy,
                       int s, T omega, const Fin &fin, cudaStream_t st, T omega2 = T(0)) {
   if constexpr (sizeof(T) == 4 && VW == 4 && MODE != M_RESID_DOT) {
     if (tl_tma && S.pk && !S.full && tile_grid(g) &&
         tile_launch<MODE>(g, S, X, gx, B, gb, Y, gy, s, omega, omega2, fin, st))
+      return;
+    if (tl_tma && S.pk && !S.full && tile3_grid(g) &&
+        tile3_launch<MODE>(g, S, X, gx, B, gb, Y, gy, s, omega, omega2, fin, st))
       return;
   }
   const int ng = (s + VW - 1) / VW;

@@ -425,17 +425,19 @@ def test_fused_transfers_keep_results(dim, N, precision, nu):
     P.close()
 
 
-@pytest.mark.parametrize("N,ncols", [(32, 5), (96, 8), (256, 60)])
-def test_tma_tiles_keep_results(N, ncols):
-    """The TMA-tiled stencil kernels (2D stiffness levels whose np - 1 is a multiple of
-    32: all of N = 32 and 256, only the finest level of N = 96) against the row kernels:
-    the same Hessian actions and stiffness solves to the solve tolerance, within one PCG
-    iteration (the two differ only in the order of the inner-product partial sums), with
-    a column count that leaves part of the last group of 4 empty (N = 32)."""
+@pytest.mark.parametrize("dim,N,ncols", [(2, 32, 5), (2, 96, 8), (2, 256, 60), (3, 32, 6), (3, 64, 8)])
+def test_tma_tiles_keep_results(dim, N, ncols):
+    """The TMA-tiled stencil kernels against the row kernels: in 2D the levels whose np - 1
+    is a multiple of 32 (all of N = 32 and 256, only the finest level of N = 96), in 3D the
+    z-marching kernel on levels with np - 1 a multiple of 32 (the finest of N = 32, the two
+    finest of N = 64).  The same Hessian actions and stiffness solves to the solve
+    tolerance, within one PCG iteration (the two differ only in the order of the
+    inner-product partial sums), with column counts that leave part of the last group of 4
+    empty."""
     from paper_1909_03948_gb300 import Problem
-    w = W.make_workload(2, N, 30, seed=83)
+    w = W.make_workload(dim, N, 30, seed=83)
     dr = W.draws(w)
-    P = Problem(2, N, w.gamma, w.delta, 0.01, dr.obs_xyz, rtol=1e-10)
+    P = Problem(dim, N, w.gamma, w.delta, 0.01, dr.obs_xyz, rtol=1e-10)
     m = 0.3 * torch.tensor(np.random.default_rng(7).standard_normal(P.n), device=DEV)
     X = torch.tensor(np.random.default_rng(8).standard_normal((ncols, P.n)), device=DEV)
     out = {}
