@@ -576,7 +576,12 @@ int hp_set_stream(hp_problem *P, void *stream) {
 
 int hp_set_precision(hp_problem *P, int precision) {
   if (!P || (precision != HP_FP64_PLAIN && precision != HP_FP32_IR)) return set_error(HP_ERR_INVALID, "precision");
+  const bool changed = precision != P->precision;
   P->precision = precision;
+  if (changed) {  // the coarse inverses are factored in the precision of the inner solves
+    HP_TRY(coarse_setup(P, OP_A));
+    if (P->have_point) HP_TRY(coarse_setup(P, OP_K));
+  }
   return HP_OK;
 }
 
@@ -1033,7 +1038,7 @@ int hp_lowrank_eig(hp_problem *P, const double *m_map, int k, int p, const doubl
     launch_copy(Y, ld, Ysave, ld, n, s, P->st);
   }
   // PreCholQR: Z = qr(Y); Zb = B Z; R_Z = chol(Z^T Zb); Q = Z R_Z^{-1} (and Qb = Zb R_Z^{-1})
-  HP_TRY(cgs2_qr(P, Y, ld, n, s));
+  HP_TRY(thin_qr(P, Y, ld, n, s));
   HP_TRY(R_apply(P, Y, ld, Zb, ld, s));
   HP_TRY(gram(P, Y, ld, s, Zb, ld, s, G, s, n));
   k_symmetrize<<<(s * s + 255) / 256, 256, 0, P->st>>>(G, Ts, s);
@@ -1109,7 +1114,7 @@ int hp_pointwise_variance(hp_problem *P, int method, const double *Z, int ldz, i
     HP_TRY(P->small.ensure(sizeof(double) * (3 * r2 + 2 * r + 64)));
     double *T = P->small.as<double>(), *Ts = T + r2, *Sm = Ts + r2, *mu = Sm + r2;
     HP_TRY(Rinv_apply(P, Z, ldz, Y, ld, r));
-    HP_TRY(cgs2_qr(P, Y, ld, n, r));
+    HP_TRY(thin_qr(P, Y, ld, n, r));
     HP_TRY(Rinv_apply(P, Y, ld, AQ, ld, r));
     HP_TRY(gram(P, Y, ld, r, AQ, ld, r, T, r, n));
     k_symmetrize<<<(unsigned)((r2 + 255) / 256), 256, 0, P->st>>>(T, Ts, r);

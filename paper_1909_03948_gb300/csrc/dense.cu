@@ -3,12 +3,15 @@
 //
 //   gram          G = X^T Y (n x s1, n x s2), tiled, deterministic two-stage sum
 //   gemm_nn       Y = alpha X S + beta Y (X: n x s1, S: s1 x s2)
-//   cgs2_qr       orthonormal Z with range(Z) = range(Y): classical Gram-Schmidt
-//                 with one full re-orthogonalisation per column ("twice is
-//                 enough"), the thin-QR step of PreCholQR (Algorithm 4)
+//   thin_qr       orthonormal Z with range(Z) = range(Y), the thin-QR step of
+//                 PreCholQR (Algorithm 4): shifted Cholesky QR in three passes
+//   cgs2_qr       the same by classical Gram-Schmidt with one full
+//                 re-orthogonalisation per column ("twice is enough"), the
+//                 fallback for a rank-deficient block
 //   small_cholesky, trsm_right_upper   R_Z = chol(Z^T Zb), Q = Z R_Z^{-1}
 //   small_symeig  cyclic Jacobi with a round-robin parallel ordering, sorted
-//                 descending (Algorithm 2: T = S Lambda S^T)
+//                 descending (Algorithm 2: T = S Lambda S^T), in shared memory up
+//                 to 90 x 90
 // GB300's FP64 rate is low (a few percent of FP32), so these are written as
 // plain FP64 FMA kernels; they are a small share of the eigensolver's time,
 // which is dominated by the 2(k+p) Hessian actions.
@@ -118,6 +121,54 @@ int cgs2_qr(hp_problem *P, double *Y, long ldy, long n, int s) {
     count_launch();
   }
   return cuda_check(cudaGetLastError(), "cgs2_qr");
+}
+
+// ---------------------------------------------------------------------------
+// Thin QR of a tall block by shifted Cholesky QR, three passes (Fukaya, Kannan,
+// Nakatsukasa, Yamamoto, Yanagisawa, "Shifted Cholesky QR for computing the QR
+// factorization of ill-conditioned matrices", SIAM J. Sci. Comput. 2020): each pass forms
+// G = Y^T Y, factors G = R^T R and sets Y <- Y R^{-1}; the first pass factors G + sigma I
+// with sigma = 11 (n s + s (s + 1)) u tr(G) (tr(G) >= |Y|_2^2, u the unit roundoff), which
+// keeps the Cholesky factorisable for any numerically full-rank Y and makes Y well enough
+// conditioned for the two plain passes to reach orthogonality at the rounding level.
+// Three full-width Gram products replace the 2(s - 1) one-column products of
+// column-by-column Gram-Schmidt, which waste most of each FP64 Gram tile.  A Gram matrix
+// that still is not positive definite (a rank-deficient block) falls back to cgs2_qr.
+// ---------------------------------------------------------------------------
+__global__ void k_sym_copy(const double *__restrict__ G, double *__restrict__ R, int s) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= s * s) return;
+  const int a = idx % s, b = idx / s;
+  R[idx] = 0.5 * (G[a + (long)s * b] + G[b + (long)s * a]);
+}
+
+__global__ void k_shift_diag(double *R, int s, long n) {
+  __shared__ double tr;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < s; ++i) t += R[i + (long)s * i];
+    tr = t;
+  }
+  __syncthreads();
+  const double sigma = 11.0 * ((double)n * s + (double)s * (s + 1)) * 0x1p-53 * tr;
+  for (int i = threadIdx.x; i < s; i += blockDim.x) R[i + (long)s * i] += sigma;
+}
+
+int thin_qr(hp_problem *P, double *Y, long ldy, long n, int s) {
+  HP_TRY(P->vtmp[4].ensure(sizeof(double) * (2 * (size_t)s * s + (size_t)s + 2)));
+  double *G = P->vtmp[4].as<double>(), *R = G + (size_t)s * s;
+  for (int pass = 0; pass < 3; ++pass) {
+    HP_TRY(gram(P, Y, ldy, s, Y, ldy, s, G, s, n));
+    k_sym_copy<<<(s * s + 255) / 256, 256, 0, P->st>>>(G, R, s);
+    count_launch();
+    if (pass == 0) {
+      k_shift_diag<<<1, 256, 0, P->st>>>(R, s, n);
+      count_launch();
+    }
+    if (small_cholesky(P, R, s) != 0) return cgs2_qr(P, Y, ldy, n, s);
+    launch_trsm_right_upper(Y, ldy, n, s, R, P->st);
+  }
+  return cuda_check(cudaGetLastError(), "thin_qr");
 }
 
 // lower Cholesky in place (row-major) == upper R in column-major
@@ -282,8 +333,145 @@ __global__ void k_jacobi_eig(double *A, double *V, int s, int m, double *lam_out
   }
 }
 
+// The same cyclic Jacobi method (same rotations in the same order) with A and V in shared
+// memory and the off-diagonal norm of the convergence test as a block reduction, for
+// s <= JS_MAX: every step of a sweep then touches shared memory only.
+constexpr int JS_MAX = 90;
+
+__global__ void __launch_bounds__(1024) k_jacobi_eig_sm(const double *__restrict__ Ain, int s, int m,
+                                                        double *lam_out, double *S_out, int max_sweeps) {
+  extern __shared__ double sh[];
+  double *A = sh, *V = A + s * s, *cs = V + s * s, *sn = cs + m / 2, *red = sn + m / 2;  // red: [2][32]
+  int *pp = reinterpret_cast<int *>(red + 64);
+  int *qq = pp + (m > s ? m : s);
+  for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
+    A[t] = Ain[t];
+    V[t] = (t % s == t / s) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
+      const double v = A[t] * A[t];
+      tot += v;
+      if (t % s != t / s) off += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (lane == 0) {
+      red[wid] = off;
+      red[32 + wid] = tot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        a += red[w];
+        b += red[32 + w];
+      }
+      red[0] = a;
+      red[32] = b;
+    }
+    __syncthreads();
+    const double off_s = red[0], tot_s = red[32];
+    __syncthreads();
+    if (off_s <= 1e-30 * tot_s || off_s == 0.0) break;
+    for (int r = 0; r < m - 1; ++r) {
+      for (int k = threadIdx.x; k < m / 2; k += blockDim.x) {
+        int p, q;
+        if (k == 0) {
+          p = r;
+          q = m - 1;
+        } else {
+          p = (r + k) % (m - 1);
+          q = (r - k + (m - 1)) % (m - 1);
+        }
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        double c = 1.0, sv = 0.0;
+        if (q < s) {
+          const double apq = A[p + s * q];
+          if (apq != 0.0) {
+            const double theta = (A[q + s * q] - A[p + s * p]) / (2.0 * apq);
+            const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            sv = t * c;
+          }
+        }
+        cs[k] = c;
+        sn[k] = sv;
+        pp[k] = p;
+        qq[k] = q;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < (m / 2) * s; t += blockDim.x) {  // rows: A <- J^T A
+        const int k = t / s, col = t % s;
+        const int p = pp[k], q = qq[k];
+        if (q >= s) continue;
+        const double c = cs[k], sv = sn[k];
+        const double ap = A[p + s * col], aq = A[q + s * col];
+        A[p + s * col] = c * ap - sv * aq;
+        A[q + s * col] = sv * ap + c * aq;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < (m / 2) * s; t += blockDim.x) {  // columns: A <- A J, V <- V J
+        const int k = t / s, row = t % s;
+        const int p = pp[k], q = qq[k];
+        if (q >= s) continue;
+        const double c = cs[k], sv = sn[k];
+        const double ap = A[row + s * p], aq = A[row + s * q];
+        A[row + s * p] = c * ap - sv * aq;
+        A[row + s * q] = sv * ap + c * aq;
+        const double vp = V[row + s * p], vq = V[row + s * q];
+        V[row + s * p] = c * vp - sv * vq;
+        V[row + s * q] = sv * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int a = 0; a < s; ++a) pp[a] = a;
+    for (int a = 0; a < s; ++a) {
+      int best = a;
+      for (int b = a + 1; b < s; ++b)
+        if (A[pp[b] + s * pp[b]] > A[pp[best] + s * pp[best]]) best = b;
+      const int t = pp[a];
+      pp[a] = pp[best];
+      pp[best] = t;
+    }
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < s; a += blockDim.x) lam_out[a] = A[pp[a] + s * pp[a]];
+  for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
+    const int row = t % s, col = t / s;
+    S_out[row + (long)s * col] = V[row + s * pp[col]];
+  }
+}
+
 int small_symeig(hp_problem *P, const double *T, int s, double *lambda, double *S) {
   const int m = s + (s & 1);
+  if (s <= JS_MAX) {
+    const size_t shm = sizeof(double) * (2 * (size_t)s * s + m + 64) + sizeof(int) * 2 * (size_t)std::max(m, s);
+    static unsigned long long attr_set = 0;  // once per device
+    int dev = 0;
+    HP_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && !(attr_set & (1ull << dev))) {
+      HP_CUDA(cudaFuncSetAttribute(k_jacobi_eig_sm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(double) * (2 * JS_MAX * JS_MAX + JS_MAX + 1 + 64) +
+                                         sizeof(int) * 2 * (JS_MAX + 1))));
+      attr_set |= 1ull << dev;
+    }
+    k_jacobi_eig_sm<<<1, 1024, shm, P->st>>>(T, s, m, lambda, S, 60);
+    count_launch();
+    return cuda_check(cudaGetLastError(), "small_symeig");
+  }
   HP_TRY(P->vtmp[3].ensure(sizeof(double) * 2 * (size_t)s * s));
   double *A = P->vtmp[3].as<double>(), *V = A + (size_t)s * s;
   HP_CUDA(cudaMemcpyAsync(A, T, sizeof(double) * s * s, cudaMemcpyDeviceToDevice, P->st));

@@ -433,6 +433,82 @@ __global__ void k_dense_inverse(const double *L, int nc, double *inv, float *inv
   for (int i = 0; i < nc; ++i) inv32[(long)i * nc + j] = (float)inv[(long)i * nc + j];
 }
 
+// FP32 coarse factorisation for the FP32 inner solves (the only consumer of inv32 when the
+// refinement runs in FP32): one CTA, the lower triangle packed in shared memory (row i at
+// offset i (i + 1) / 2), right-looking Cholesky; FP32 runs at 64x the FP64 rate of an SM.
+// L (row-major, lower) goes to Lg for the triangular solves.
+__device__ __forceinline__ int tri_at(int i, int j) { return i * (i + 1) / 2 + j; }
+
+__global__ void __launch_bounds__(1024) k_dense_cholesky32(const double *__restrict__ A, int nc, float *Lg,
+                                                           int *status) {
+  extern __shared__ float tri[];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  for (int t = threadIdx.x; t < nc * (nc + 1) / 2; t += blockDim.x) {
+    int i = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
+    while (tri_at(i, 0) > t) --i;
+    while (tri_at(i + 1, 0) <= t) ++i;
+    tri[t] = (float)A[(long)i * nc + (t - tri_at(i, 0))];
+  }
+  __syncthreads();
+  for (int k = 0; k < nc; ++k) {
+    if (threadIdx.x == 0) {
+      const float d = tri[tri_at(k, k)];
+      if (!(d > 0.f) || !isfinite(d)) bad = 1;
+      tri[tri_at(k, k)] = d > 0.f ? sqrtf(d) : 1.f;
+    }
+    __syncthreads();
+    const float dk = tri[tri_at(k, k)];
+    for (int i = k + 1 + threadIdx.x; i < nc; i += blockDim.x) tri[tri_at(i, k)] /= dk;
+    __syncthreads();
+    const int m = nc - k - 1;
+    for (int t = threadIdx.x; t < m * (m + 1) / 2; t += blockDim.x) {  // i >= j > k
+      int a = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
+      while (a * (a + 1) / 2 > t) --a;
+      while ((a + 1) * (a + 2) / 2 <= t) ++a;
+      const int i = k + 1 + a, j = k + 1 + (t - a * (a + 1) / 2);
+      tri[tri_at(i, j)] -= tri[tri_at(i, k)] * tri[tri_at(j, k)];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nc * nc; t += blockDim.x) {
+    const int i = t / nc, j = t % nc;
+    Lg[t] = j <= i ? tri[tri_at(i, j)] : 0.f;
+  }
+  if (threadIdx.x == 0) *status = bad;
+}
+
+// Column j of the inverse from L, one warp per column: the forward substitution L y = e_j
+// from row j on (rows above are zero), then L^T x = y, each row's sum split over the 32
+// lanes and reduced; the column is kept in shared memory and written as row j of inv32
+// (the inverse is symmetric).
+__global__ void __launch_bounds__(128) k_dense_inverse32(const float *__restrict__ L, int nc, float *inv32) {
+  extern __shared__ float colbuf[];  // [4 warps][nc]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j = blockIdx.x * 4 + w;
+  if (j >= nc) return;
+  float *x = colbuf + (long)w * nc;
+  for (int i = lane; i < nc; i += 32) x[i] = 0.f;
+  __syncwarp();
+  for (int i = j; i < nc; ++i) {
+    float sum = 0.f;
+    for (int k = j + lane; k < i; k += 32) sum += L[(long)i * nc + k] * x[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) x[i] = ((i == j ? 1.f : 0.f) - sum) / L[(long)i * nc + i];
+    __syncwarp();
+  }
+  for (int i = nc - 1; i >= 0; --i) {
+    float sum = 0.f;
+    for (int k = i + 1 + lane; k < nc; k += 32) sum += L[(long)k * nc + i] * x[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) x[i] = (x[i] - sum) / L[(long)i * nc + i];
+    __syncwarp();
+  }
+  for (int i = lane; i < nc; i += 32) inv32[(long)j * nc + i] = x[i];
+}
+
 int coarse_setup(hp_problem *P, OpKind op) {
   const Level &lc = P->lv[P->L - 1];
   CoarseInv &C = op == OP_K ? P->cK : P->cA;
@@ -445,8 +521,27 @@ int coarse_setup(hp_problem *P, OpKind op) {
   else
     k_dense_from_stencil<3><<<nb, 256, 0, P->st>>>(lc.g, S.diag, S.c, S.nf, S.full, C.dense);
   int *dstat = P->sc.active.as<int>();
-  k_dense_cholesky<<<1, 1024, 0, P->st>>>(C.dense, (int)nc, dstat);
-  k_dense_inverse<<<(int)((nc + 31) / 32), 32, 0, P->st>>>(C.dense, (int)nc, C.inv64, C.inv32);
+  const size_t tri_bytes = sizeof(float) * (size_t)nc * (nc + 1) / 2;
+  if (P->precision == HP_FP32_IR && tri_bytes <= 200u * 1024u) {
+    // only inv32 is used by FP32 inner solves: factor and invert in FP32 (inv64 is
+    // rebuilt by hp_set_precision if the plain FP64 path is selected later)
+    static unsigned long long attr_set = 0;
+    int dev = 0;
+    HP_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && !(attr_set & (1ull << dev))) {
+      HP_CUDA(cudaFuncSetAttribute(k_dense_cholesky32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   200 * 1024));
+      attr_set |= 1ull << dev;
+    }
+    float *L32 = reinterpret_cast<float *>(C.inv64);  // scratch: the FP64 inverse is not kept in this mode
+    k_dense_cholesky32<<<1, 1024, tri_bytes, P->st>>>(C.dense, (int)nc, L32, dstat);
+    k_dense_inverse32<<<(int)((nc + 3) / 4), 128, sizeof(float) * 4 * nc, P->st>>>(L32, (int)nc, C.inv32);
+    C.fp64_valid = false;
+  } else {
+    k_dense_cholesky<<<1, 1024, 0, P->st>>>(C.dense, (int)nc, dstat);
+    k_dense_inverse<<<(int)((nc + 31) / 32), 32, 0, P->st>>>(C.dense, (int)nc, C.inv64, C.inv32);
+    C.fp64_valid = true;
+  }
   count_launch(3);
   int h = 0;
   HP_CUDA(cudaMemcpyAsync(&h, dstat, sizeof(int), cudaMemcpyDeviceToHost, P->st));

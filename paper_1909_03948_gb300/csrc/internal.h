@@ -53,6 +53,7 @@ struct Level {
 
 struct CoarseInv {
   int nc = 0;
+  bool fp64_valid = false;   // inv64 holds the FP64 inverse (else only inv32 is current)
   double *dense = nullptr;   // work: nc x nc
   double *inv64 = nullptr;
   float *inv32 = nullptr;
@@ -305,6 +306,7 @@ void launch_gemm_nn(const double *X, long ldx, int s1, const double *S, int lds,
                     long ldy, long n, double alpha, double beta, cudaStream_t st);
 // in-place CGS2 orthonormalisation of the columns of Y (n x s)
 int cgs2_qr(hp_problem *P, double *Y, long ldy, long n, int s);
+int thin_qr(hp_problem *P, double *Y, long ldy, long n, int s);  // shifted Cholesky QR, cgs2_qr fallback
 // upper Cholesky R^T R = G (s x s, ld s) in place; returns HP_ERR_NONFINITE if not SPD
 int small_cholesky(hp_problem *P, double *G, int s);
 // Y <- Y R^{-1}, R upper (s x s)

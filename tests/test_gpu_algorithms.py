@@ -50,17 +50,24 @@ def test_newton_map_matches_oracle(small2d, precision):
 
 
 def test_full_newton_map_matches_oracle(small2d):
-    """Newton-CG with the full Hessian (Steihaug exit on negative curvature) reaches the
-    oracle's full-Newton MAP point to relative 1e-6 in the same number of Newton iterations
-    (give or take one), fewer than Gauss-Newton needs.  The reference is the oracle's
-    full-Newton run: it converges quadratically, so at relative gradient 1e-9 it is within
-    ~1e-8 of the exact MAP, while the Gauss-Newton run stops ~1.6e-6 away from it."""
-    orc, w, P = small2d["orc"], small2d["w"], small2d["P"]
-    m, st = P.newton_cg_map(rel_tol=1e-9, full=True)
-    assert st["converged"]
+    """Newton-CG with the full Hessian (Steihaug exit on negative curvature) stops at relative
+    gradient 1e-9 near the oracle's full-Newton MAP point, in the same number of Newton
+    iterations (give or take one), fewer than Gauss-Newton needs.  The reference is the
+    oracle's full-Newton run, within ~1e-8 of the exact MAP.  An iterate that stops at
+    relative gradient 1e-9 lies up to ~1.6e-6 (relative) from the exact MAP on this problem
+    (the Gauss-Newton runs show it); the full-Newton run usually lands far closer because its
+    last, quadratic step overshoots the tolerance, but that is not guaranteed, hence 5e-6."""
+    orc, w = small2d["orc"], small2d["w"]
+    # PDE solves to 1e-12 for a 1e-9 gradient tolerance (see test_newton_map_matches_oracle)
+    P = _gpu_problem(orc, w, rtol=1e-12)
+    try:
+        m, st = P.newton_cg_map(rel_tol=1e-9, full=True)
+    finally:
+        P.close()
+    assert st["converged"], st
     ref_full = A.newton_cg(orc, rel_tol=1e-9, full=True)
     assert ref_full.converged
-    assert np.linalg.norm(m.cpu().numpy() - ref_full.m) <= 1e-6 * np.linalg.norm(ref_full.m)
+    assert np.linalg.norm(m.cpu().numpy() - ref_full.m) <= 5e-6 * np.linalg.norm(ref_full.m)
     assert abs(st["iterations"] - ref_full.iterations) <= 1
     assert st["iterations"] < small2d["res"].iterations
 
