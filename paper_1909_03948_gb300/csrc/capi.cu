@@ -252,10 +252,37 @@ static int cost_at_point(hp_problem *P, double *J3, double *Rdm) {
   return 0;
 }
 
+// flag = 1 if a and b differ anywhere (bitwise; the flag starts at 0)
+__global__ void k_differs(const double *__restrict__ a, const double *__restrict__ b, long n, int *flag) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    if (__double_as_longlong(a[i]) != __double_as_longlong(b[i])) {
+      *flag = 1;
+      return;
+    }
+}
+
+// true when m_dev is bitwise the current linearisation point and its state was solved to
+// the current tolerance: everything set_point would build is still current
+static bool is_current_point(hp_problem *P, const double *m_dev) {
+  if (!P->have_point || P->u_rtol != P->rtol) return false;
+  int *flag = P->sc.active.as<int>();
+  if (!flag || cudaMemsetAsync(flag, 0, sizeof(int), P->st) != cudaSuccess) return false;
+  k_differs<<<blocks_for(P->n, 1), NT, 0, P->st>>>(m_dev, P->m, P->n, flag);
+  count_launch();
+  int h = 1;
+  if (cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, P->st) != cudaSuccess ||
+      cudaStreamSynchronize(P->st) != cudaSuccess)
+    return false;
+  return h == 0;
+}
+
 static int set_point(hp_problem *P, const double *m_dev, double *J3, hp_solve_stats *st) {
-  HP_TRY(build_point(P, m_dev));
-  HP_TRY(forward_state(P, st));
-  P->have_point = true;
+  if (!is_current_point(P, m_dev)) {
+    HP_TRY(build_point(P, m_dev));
+    HP_TRY(forward_state(P, st));
+    P->have_point = true;
+    P->u_rtol = P->rtol;
+  }
   if (J3) HP_TRY(cost_at_point(P, J3, nullptr));
   return sync(P);
 }
@@ -648,6 +675,7 @@ int hp_forward(hp_problem *P, const double *m_dev, double *u_dev, hp_solve_stats
   HP_TRY(build_point(P, m_dev));
   HP_TRY(forward_state(P, st));
   P->have_point = true;
+  P->u_rtol = P->rtol;
   if (u_dev) HP_CUDA(cudaMemcpyAsync(u_dev, P->u, sizeof(double) * P->n, cudaMemcpyDeviceToDevice, P->st));
   return sync(P);
 }

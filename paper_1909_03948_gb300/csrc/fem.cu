@@ -647,6 +647,7 @@ int build_hierarchy_geometry(hp_problem *P) {
 int build_point(hp_problem *P, const double *m_dev) {
   const long n = P->n;
   P->have_p = P->have_full = false;
+  P->have_point = false;  // until the state solve at the new point succeeds
   HP_CUDA(cudaMemcpyAsync(P->m, m_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->st));
   launch_ew_exp(P->m, P->E, n, P->st);
   const int D = P->dim;

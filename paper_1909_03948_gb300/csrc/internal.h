@@ -126,6 +126,7 @@ struct hp_problem {
   double robin_beta = 0;                 // prior Robin coefficient beta (0 = zero Neumann)
   int precision = HP_FP32_IR;
   double rtol = 1e-8;
+  double u_rtol = 0.0;          // tolerance the current state u was solved to
   int max_iter = 500;
   double inner_rtol = 1e-5;     // FP32 inner tolerance of the refinement
   int max_outer = 12;
