@@ -501,6 +501,12 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
     for (int q = zb - 1; q <= zb + TL3_NS - 3 && q <= ze; ++q) issue(q);
   PK acc = PK::zero();
   bool ok = true;
+  // Each thread keeps its nodes (t = threadIdx.x + j * TL3_NT) for the whole march, so x at
+  // planes p - 1 and p, and c_z and 1/diag at p - 1, rotate through registers: per node and
+  // plane only x at p + 1 and the xy neighbours come from shared memory.
+  constexpr int NPT = (TL3R_X * TL3R_Y + TL3_NT - 1) / TL3_NT;
+  PK rxm[NPT], rx0[NPT];
+  float rzm[NPT], rvm[NPT];
   for (int p = zb; p < ze; ++p) {
     __syncthreads();  // every thread is done with plane p - 2's slot
     if (threadIdx.x == 0 && p + TL3_NS - 2 <= ze) issue(p + TL3_NS - 2);
@@ -521,7 +527,10 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
                 *z0 = reinterpret_cast<const float *>(sm_0 + TL3_OFF_Z);
     const float *rs = reinterpret_cast<const float *>(sm_0 + TL3_OFF_R);
     const bool fz = p < g.N, bz = p > 0;
-    for (int t = threadIdx.x; t < wx * hy; t += TL3_NT) {
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+      const int t = threadIdx.x + j * TL3_NT;
+      if (t >= wx * hy) continue;
       const int lx = t % wx, ly = t / wx;
       const int v0 = x0 + lx, v1 = y0 + ly;
       const int ci = (ly + 1) * TL3B_X + lx + 1;  // this node in the halo boxes
@@ -529,10 +538,17 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
       const bool fx = v0 < g.N, bx = v0 > 0, fy = v1 < g.N, by = v1 > 0;
       const float4 cc = c0s[ci];  // diag, invdiag, c_x, c_y
       const float cz = z0[zi];    // c_z
+      if (p == zb) {  // first plane: fill the registers from the p - 1 and p slots
+        rxm[j] = PK::ld(xm + ci * 4);
+        rx0[j] = PK::ld(x0s + ci * 4);
+        rzm[j] = zm[zi];
+        rvm[j] = cm[ci].y;
+      }
+      const PK xpv = PK::ld(xp + ci * 4);  // x at p + 1
       PK out;
       if (MODE == M_JAC2) {
         const float wi = omega * cc.y, wi2 = omega2 * cc.y;
-        const PK r = PK::ld(x0s + ci * 4);
+        const PK r = rx0[j];
         PK e1c;
 #pragma unroll
         for (int q = 0; q < 4; ++q) e1c.v[q] = wi * r.v[q];
@@ -543,12 +559,12 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
         if (bx) sx.axpy(c0s[ci - 1].z * omega * c0s[ci - 1].y, PK::ld(x0s + (ci - 1) * 4));
         if (fy) sx.axpy(cc.w * omega * c0s[ci + TL3B_X].y, PK::ld(x0s + (ci + TL3B_X) * 4));
         if (by) sx.axpy(c0s[ci - TL3B_X].w * omega * c0s[ci - TL3B_X].y, PK::ld(x0s + (ci - TL3B_X) * 4));
-        if (fz) sx.axpy(cz * omega * cp[ci].y, PK::ld(xp + ci * 4));
-        if (bz) sx.axpy(zm[zi] * omega * cm[ci].y, PK::ld(xm + ci * 4));
+        if (fz) sx.axpy(cz * omega * cp[ci].y, xpv);
+        if (bz) sx.axpy(rzm[j] * omega * rvm[j], rxm[j]);
 #pragma unroll
         for (int q = 0; q < 4; ++q) out.v[q] = fmadd(wi2, r.v[q] - sx.v[q], e1c.v[q]);
       } else {
-        const PK xc = PK::ld(x0s + ci * 4);
+        const PK xc = rx0[j];
         PK sx;
 #pragma unroll
         for (int q = 0; q < 4; ++q) sx.v[q] = cc.x * xc.v[q];
@@ -556,8 +572,8 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
         if (bx) sx.axpy(c0s[ci - 1].z, PK::ld(x0s + (ci - 1) * 4));
         if (fy) sx.axpy(cc.w, PK::ld(x0s + (ci + TL3B_X) * 4));
         if (by) sx.axpy(c0s[ci - TL3B_X].w, PK::ld(x0s + (ci - TL3B_X) * 4));
-        if (fz) sx.axpy(cz, PK::ld(xp + ci * 4));
-        if (bz) sx.axpy(zm[zi], PK::ld(xm + ci * 4));
+        if (fz) sx.axpy(cz, xpv);
+        if (bz) sx.axpy(rzm[j], rxm[j]);
         if (MODE == M_APPLY || MODE == M_APPLY_DOT) {
           out = sx;
           if (DOT)
@@ -579,6 +595,10 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
         }
       }
       out.st(Y + grp * gy + ((long)v0 + (long)g.np * ((long)v1 + (long)g.np * p)) * 4);
+      rxm[j] = rx0[j];
+      rx0[j] = xpv;
+      rzm[j] = cz;
+      rvm[j] = cc.y;
     }
   }
   if (!ok) {
