@@ -301,7 +301,7 @@ int hp_pointwise_variance(hp_problem *P, int method, const double *Z_dev, int ld
  * Knobs of the PDE solver (no counterpart in the paper): nu damped-Jacobi sweeps
  * before and after each coarse correction and damping omega, the number of RHS
  * columns solved together (0 = all), and the grid-size cap of the node kernels.
- * Defaults: nu 3, nu_coarse 0, omega 0.7, col_chunk 0, max_blocks 2048, smoother 1
+ * Defaults: nu 3, nu_coarse 0, omega 0.7, col_chunk 0, max_blocks 4096, smoother 1
  * (Chebyshev), cheb_alpha 10, fuse_transfer 0, fuse_from 0, tma_tiles 0, smem_tail 0.  Every setting solves to the same
  * tolerance; only speed changes. */
 typedef struct {

@@ -134,7 +134,7 @@ struct hp_problem {
   int nu_coarse = 0;            // sweeps on the coarser levels, 0 = nu (tuning)
   double omega = 0.7;           // Jacobi damping                     (tuning)
   int col_chunk = 0;            // RHS columns per solve, 0 = all     (tuning)
-  long max_blocks = 2048;       // grid cap of the node kernels       (tuning)
+  long max_blocks = 4096;       // grid cap of the node kernels       (tuning)
   int fuse_from = 0;            // first multigrid level of the fused coarse tail, 0 = none (tuning)
   int smoother = 1;             // 0 damped Jacobi (omega), 1 Chebyshev (cheb_alpha)   (tuning)
   int fuse_transfer = 0;        // residual + restriction and prolongation + first post sweep fused (tuning)

@@ -1141,9 +1141,10 @@ template <> const double *coarse_inv<double>(const hp_problem *P, OpKind op) {
   return op == OP_K ? P->cK.inv64 : P->cA.inv64;
 }
 
-// grid-size cap of the node kernels (a tuning knob; default ~13 resident 128-thread blocks
-// per SM on 152 SMs), set per solve from the problem's tuning
-static thread_local long tl_max_blocks = 2048;
+// grid-size cap of the node kernels (a tuning knob; the default 4096 is about 27 128-thread
+// blocks per SM on 152 SMs, two rounds of the ~13-16 that are resident at once, which keeps
+// a launch's tail short), set per solve from the problem's tuning
+static thread_local long tl_max_blocks = 4096;
 
 // uncapped row grid (grid transfer kernels: one node per thread)
 static dim3 rowgrid(const GridDesc &g, int ngroups) {

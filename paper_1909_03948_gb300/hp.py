@@ -436,7 +436,7 @@ class Problem:
         _check(lib().hp_get_tuning(self._h, C.byref(t)), "hp_get_tuning")
         return t.as_dict()
 
-    def set_tuning(self, nu=3, omega=0.7, col_chunk=0, max_blocks=2048, smoother=1, cheb_alpha=10.0,
+    def set_tuning(self, nu=3, omega=0.7, col_chunk=0, max_blocks=4096, smoother=1, cheb_alpha=10.0,
                    fuse_transfer=0, fuse_from=0, nu_coarse=0, tma_tiles=0, smem_tail=0):
         t = Tuning(nu=nu, nu_coarse=nu_coarse, omega=omega, col_chunk=col_chunk, max_blocks=max_blocks,
                    smoother=smoother, cheb_alpha=cheb_alpha, fuse_transfer=fuse_transfer, fuse_from=fuse_from,
