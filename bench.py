@@ -66,7 +66,8 @@ def parse():
 
 
 def workload_desc(w, precision):
-    prec = "FP32 MG-PCG in FP64 refinement" if precision == "fp32_ir" else "FP64 MG-PCG"
+    prec = {"fp32_ir": "FP32 MG-PCG in FP64 refinement", "fp64": "FP64 MG-PCG",
+            "oracle": "FP64 CPU oracle with sparse direct solves (exact to rounding)"}[precision]
     return (f"{w.name}: {w.dim}D {'x'.join([str(w.N)] * w.dim)} P1 "
             f"({'right triangles' if w.dim == 2 else 'Kuhn tetrahedra'}), n={w.nnodes}, q={w.nobs}, "
             f"block of k+p={w.k + w.p} Gauss-Newton Hessian actions at the MAP, {prec}, rel-res 1e-8")
@@ -132,7 +133,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": val, "unit": "actions/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(w, "fp64") + f"; reference arm: {s_ref} columns per step",
+        "config": {"workload": workload_desc(w, "oracle") + f"; reference arm: {s_ref} columns per step",
                    "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": val, "unit": "actions/s", "cores": 1, "kind": "oracle",
                          "sample": f"{s_ref} Hessian-action columns per step, K(m) factorised once in warm-up"},
