@@ -102,6 +102,10 @@ typedef struct {
   int lowrank_p;         /* oversampling of that eigensolve                                */
   int lowrank_refresh;   /* recompute the eigenpairs every lowrank_refresh Newton
                             iterations (0: only at the first)                              */
+  double prec_rtol;      /* relative tolerance of the two prior solves of R^-1 when it
+                            preconditions the CG (0: the problem's tolerance).  The
+                            gradient and its R^-1 norm, which decide convergence, always
+                            use the problem's tolerance.  No counterpart in the paper.     */
 } hp_newton_opts;
 
 typedef struct {

@@ -409,16 +409,17 @@ static int R_apply(hp_problem *P, const double *X, long ldx, double *Y, long ldy
   return 0;
 }
 
-static int Rinv_apply(hp_problem *P, const double *X, long ldx, double *Y, long ldy, int s) {
+static int Rinv_apply(hp_problem *P, const double *X, long ldx, double *Y, long ldy, int s, double tol = 0.0) {
   int rc = 0;
   const long ld = padded(P->n);
+  const double rt = tol > 0.0 ? tol : P->rtol;
   double *t1 = col64(P->t64a, P, s, &rc);
   HP_TRY(rc);
   double *t2 = col64(P->t64b, P, s, &rc);
   HP_TRY(rc);
-  HP_TRY(solve_block(P, OP_A, X, ldx, t1, ld, s, P->rtol, nullptr));
+  HP_TRY(solve_block(P, OP_A, X, ldx, t1, ld, s, rt, nullptr));
   HP_TRY(apply_op64(P, OP_M, t1, ld, t2, ld, s));
-  HP_TRY(solve_block(P, OP_A, t2, ld, Y, ldy, s, P->rtol, nullptr));
+  HP_TRY(solve_block(P, OP_A, t2, ld, Y, ldy, s, rt, nullptr));
   return 0;
 }
 
@@ -813,8 +814,9 @@ int hp_mass_factor_apply(hp_problem *P, const double *eta, int ldeta, double *W,
 // ---------------------------------------------------------------------------
 int hp_newton_cg_map(hp_problem *P, double *m, const hp_newton_opts *opts_in, hp_newton_stats *out) {
   if (!P || !m) return set_error(HP_ERR_INVALID, "null");
-  hp_newton_opts o{1e-6, 0.0, 50, 10, 1e-4, 200, 0, 0, 10, 0};
+  hp_newton_opts o{1e-6, 0.0, 50, 10, 1e-4, 200, 0, 0, 10, 0, 0.0};
   if (opts_in) o = *opts_in;
+  if (!(o.prec_rtol >= 0.0 && o.prec_rtol < 1.0)) return set_error(HP_ERR_INVALID, "prec_rtol in [0, 1)");
   const int lk = std::max(0, o.lowrank_k), lp = std::max(0, o.lowrank_p), ls = lk + lp;
   if (lk > 0 && (ls > P->n || ls > 1024)) return set_error(HP_ERR_INVALID, "lowrank_k + lowrank_p too large");
   hp_newton_stats S{};
@@ -916,7 +918,7 @@ int hp_newton_cg_map(hp_problem *P, double *m, const hp_newton_opts *opts_in, hp
       const double alpha = rz / dHd;
       launch_axpby(alpha, d, n, 1.0, x, n, n, 1, P->st);
       launch_axpby(-alpha, Hd, n, 1.0, r, n, n, 1, P->st);
-      if ((rc = Rinv_apply(P, r, n, z, n, 1))) return cleanup(rc);
+      if ((rc = Rinv_apply(P, r, n, z, n, 1, o.prec_rtol))) return cleanup(rc);
       solves += 2;
       if ((rc = lowrank_correct(r, z))) return cleanup(rc);
       double rzn = 0.0;

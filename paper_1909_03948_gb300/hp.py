@@ -70,7 +70,7 @@ class NewtonOpts(C.Structure):
     _fields_ = [("rel_tol", C.c_double), ("abs_tol", C.c_double), ("max_iter", C.c_int),
                 ("max_backtrack", C.c_int), ("c_armijo", C.c_double), ("cg_max_iter", C.c_int),
                 ("full_newton", C.c_int), ("lowrank_k", C.c_int), ("lowrank_p", C.c_int),
-                ("lowrank_refresh", C.c_int)]
+                ("lowrank_refresh", C.c_int), ("prec_rtol", C.c_double)]
 
 
 class NewtonStats(C.Structure):
@@ -488,12 +488,14 @@ class Problem:
 
     # ---- algorithms --------------------------------------------------------------
     def newton_cg_map(self, m0=None, rel_tol=1e-6, abs_tol=0.0, max_iter=50, max_backtrack=10,
-                      c_armijo=1e-4, cg_max_iter=200, full=False, lowrank_k=0, lowrank_p=10, lowrank_refresh=0):
+                      c_armijo=1e-4, cg_max_iter=200, full=False, lowrank_k=0, lowrank_p=10, lowrank_refresh=0,
+                      prec_rtol=0.0):
         """Algorithm 1.  lowrank_k > 0 preconditions the CG with R^-1 - V D V^T from the
-        lowrank_k leading eigenpairs (recomputed every lowrank_refresh iterations, 0: once)."""
+        lowrank_k leading eigenpairs (recomputed every lowrank_refresh iterations, 0: once);
+        prec_rtol > 0 solves the prior solves of that preconditioner to this tolerance."""
         m = self.zeros() if m0 is None else self._vec(m0, "m0").clone().reshape(-1)
         o = NewtonOpts(rel_tol, abs_tol, max_iter, max_backtrack, c_armijo, cg_max_iter, 1 if full else 0,
-                       lowrank_k, lowrank_p, lowrank_refresh)
+                       lowrank_k, lowrank_p, lowrank_refresh, prec_rtol)
         st = NewtonStats()
         rc = lib().hp_newton_cg_map(self._h, _dptr(m), C.byref(o), C.byref(st))
         if rc not in (HP_OK, HP_ERR_NOT_CONVERGED):

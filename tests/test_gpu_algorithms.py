@@ -96,6 +96,27 @@ def test_lowrank_preconditioned_newton_reaches_the_map(small2d):
         P.close()
 
 
+def test_inexact_prior_preconditioner_keeps_the_map(small2d):
+    """Newton-CG with the prior solves of the CG preconditioner R^-1 run to 1e-5 (the gradient
+    and its R^-1 norm, which decide convergence, stay at the problem's tolerance) stops in
+    the same number of Newton iterations, within a few CG iterations of the exact
+    preconditioner, at the same MAP point up to the gradient tolerance's ball."""
+    orc, w = small2d["orc"], small2d["w"]
+    P = _gpu_problem(orc, w, rtol=1e-12)
+    try:
+        m0, st0 = P.newton_cg_map(rel_tol=1e-9, lowrank_k=20, lowrank_p=10, lowrank_refresh=2)
+        m1, st1 = P.newton_cg_map(rel_tol=1e-9, lowrank_k=20, lowrank_p=10, lowrank_refresh=2, prec_rtol=1e-5)
+        with pytest.raises(Exception):
+            P.newton_cg_map(rel_tol=1e-9, prec_rtol=1.5)
+    finally:
+        P.close()
+    assert st0["converged"] and st1["converged"], (st0, st1)
+    assert abs(st1["iterations"] - st0["iterations"]) <= 1
+    assert st1["cg_iterations"] <= st0["cg_iterations"] + 5, (st0, st1)
+    ref = A.newton_cg(orc, rel_tol=1e-9, full=True).m
+    assert np.linalg.norm(m1.cpu().numpy() - ref) <= 5e-6 * np.linalg.norm(ref)
+
+
 def test_newton_baseline_tolerance(small2d):
     """At the workload's relative gradient tolerance 1e-6 the GPU and the oracle take the
     same Newton path (same eta_i, same CG) to within one iteration."""
