@@ -66,8 +66,58 @@ __global__ void k_gram_final(const double *__restrict__ part, int nchunk, int nt
   G[a + (long)ldg * b] = s;
 }
 
+// G = X^T y for a single column y: each block sums its chunk of rows for 8 columns of X at a
+// time (coalesced along the rows), the partials [chunk][column] are added in chunk order
+__global__ void k_gemv_t_partial(const double *__restrict__ X, long ldx, int s1, const double *__restrict__ y,
+                                 long n, long rows_per_chunk, double *__restrict__ part) {
+  __shared__ double red[8][8];  // [warp][column of the group]
+  const int ch = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long r0 = ch * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+  for (int a0 = 0; a0 < s1; a0 += 8) {
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const double yi = y[i];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (a0 + q < s1) acc[q] = fmadd(X[ldx * (a0 + q) + i], yi, acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+      if (lane == 0) red[w][q] = acc[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < 8 && a0 + (int)threadIdx.x < s1) {
+      double t = 0.0;
+      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += red[ww][threadIdx.x];
+      part[(long)ch * s1 + a0 + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_gemv_t_final(const double *__restrict__ part, int nchunk, int s1, double *__restrict__ G) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= s1) return;
+  double t = 0.0;
+  for (int c = 0; c < nchunk; ++c) t += part[(long)c * s1 + a];
+  G[a] = t;
+}
+
 int gram(hp_problem *P, const double *X, long ldx, int s1, const double *Y, long ldy, int s2, double *G, int ldg,
          long n) {
+  if (s2 == 1) {  // a matrix-vector product: the tiled kernel would compute a whole tile of X^T Y
+    int nchunk = 2 * NSM;
+    const long rpc = std::max<long>(256, (n + nchunk - 1) / nchunk);
+    nchunk = (int)((n + rpc - 1) / rpc);
+    HP_TRY(P->vtmp[5].ensure(sizeof(double) * (size_t)nchunk * s1));
+    double *part = P->vtmp[5].as<double>();
+    k_gemv_t_partial<<<nchunk, 256, 0, P->st>>>(X, ldx, s1, Y, n, rpc, part);
+    k_gemv_t_final<<<(s1 + 255) / 256, 256, 0, P->st>>>(part, nchunk, s1, G);
+    count_launch(2);
+    return cuda_check(cudaGetLastError(), "gram");
+  }
   const int nta = (s1 + GT - 1) / GT, ntb = (s2 + GT - 1) / GT;
   int nchunk = std::max(1, (2 * NSM) / (nta * ntb));
   long rpc = (n + nchunk - 1) / nchunk;
