@@ -10,8 +10,8 @@
 //                 fallback for a rank-deficient block
 //   small_cholesky, trsm_right_upper   R_Z = chol(Z^T Zb), Q = Z R_Z^{-1}
 //   small_symeig  cyclic Jacobi with a round-robin parallel ordering, sorted
-//                 descending (Algorithm 2: T = S Lambda S^T), in shared memory up
-//                 to 90 x 90
+//                 descending (Algorithm 2: T = S Lambda S^T), A in shared memory up
+//                 to 160 x 160 (and V with it up to 90 x 90)
 // GB300's FP64 rate is low (a few percent of FP32), so these are written as
 // plain FP64 FMA kernels; they are a small share of the eigensolver's time,
 // which is dominated by the 2(k+p) Hessian actions.
@@ -383,15 +383,17 @@ __global__ void k_jacobi_eig(double *A, double *V, int s, int m, double *lam_out
   }
 }
 
-// The same cyclic Jacobi method (same rotations in the same order) with A and V in shared
-// memory and the off-diagonal norm of the convergence test as a block reduction, for
-// s <= JS_MAX: every step of a sweep then touches shared memory only.
-constexpr int JS_MAX = 90;
+// The same cyclic Jacobi method (same rotations in the same order) with A in shared memory
+// and the off-diagonal norm of the convergence test as a block reduction: V shares the
+// shared memory for s <= JS_MAX, and lives in the global scratch Vg up to JS_MAX_A.
+constexpr int JS_MAX = 90, JS_MAX_A = 160;
 
 __global__ void __launch_bounds__(1024) k_jacobi_eig_sm(const double *__restrict__ Ain, int s, int m,
-                                                        double *lam_out, double *S_out, int max_sweeps) {
+                                                        double *lam_out, double *S_out, int max_sweeps,
+                                                        double *Vg) {
   extern __shared__ double sh[];
-  double *A = sh, *V = A + s * s, *cs = V + s * s, *sn = cs + m / 2, *red = sn + m / 2;  // red: [2][32]
+  double *A = sh, *V = Vg ? Vg : A + s * s;
+  double *cs = A + s * s + (Vg ? 0 : s * s), *sn = cs + m / 2, *red = sn + m / 2;  // red: [2][32]
   int *pp = reinterpret_cast<int *>(red + 64);
   int *qq = pp + (m > s ? m : s);
   for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
@@ -507,18 +509,27 @@ __global__ void __launch_bounds__(1024) k_jacobi_eig_sm(const double *__restrict
 
 int small_symeig(hp_problem *P, const double *T, int s, double *lambda, double *S) {
   const int m = s + (s & 1);
-  if (s <= JS_MAX) {
-    const size_t shm = sizeof(double) * (2 * (size_t)s * s + m + 64) + sizeof(int) * 2 * (size_t)std::max(m, s);
-    static unsigned long long attr_set = 0;  // once per device
+  if (s <= JS_MAX_A) {
+    const bool v_shared = s <= JS_MAX;
+    double *Vg = nullptr;
+    if (!v_shared) {
+      HP_TRY(P->vtmp[3].ensure(sizeof(double) * (size_t)s * s));
+      Vg = P->vtmp[3].as<double>();
+    }
+    const size_t shm = sizeof(double) * ((v_shared ? 2 : 1) * (size_t)s * s + m + 64) +
+                       sizeof(int) * 2 * (size_t)std::max(m, s);
+    static unsigned long long attr_set = 0;  // once per device: the largest size either layout needs
     int dev = 0;
     HP_CUDA(cudaGetDevice(&dev));
     if (dev < 64 && !(attr_set & (1ull << dev))) {
-      HP_CUDA(cudaFuncSetAttribute(k_jacobi_eig_sm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(sizeof(double) * (2 * JS_MAX * JS_MAX + JS_MAX + 1 + 64) +
-                                         sizeof(int) * 2 * (JS_MAX + 1))));
+      const size_t cap = std::max(sizeof(double) * (2 * JS_MAX * JS_MAX + JS_MAX + 1 + 64) +
+                                      sizeof(int) * 2 * (JS_MAX + 1),
+                                  sizeof(double) * (JS_MAX_A * JS_MAX_A + JS_MAX_A + 64) +
+                                      sizeof(int) * 2 * JS_MAX_A);
+      HP_CUDA(cudaFuncSetAttribute(k_jacobi_eig_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
       attr_set |= 1ull << dev;
     }
-    k_jacobi_eig_sm<<<1, 1024, shm, P->st>>>(T, s, m, lambda, S, 60);
+    k_jacobi_eig_sm<<<1, 1024, shm, P->st>>>(T, s, m, lambda, S, 60, Vg);
     count_launch();
     return cuda_check(cudaGetLastError(), "small_symeig");
   }

@@ -155,6 +155,24 @@ def test_lowrank_eig_matches_oracle(small2d):
     assert np.all(np.abs(c - 1) < 1e-5), c
 
 
+def test_lowrank_eig_with_a_wide_block_matches_oracle(small2d):
+    """k + p = 120 (wider than the 90 x 90 that fit A and V of the Rayleigh-Ritz eigensolve
+    in shared memory together: V moves to global memory): the eigenvalues above 0.1 match
+    the oracle's with the same Omega, and V is R-orthonormal."""
+    orc, w, P = small2d["orc"], small2d["w"], small2d["P"]
+    m_map = small2d["m_map"]
+    k, p = 100, 20
+    Om = np.random.default_rng(77).standard_normal((orc.n, k + p))
+    lam_ref, _ = A.lowrank_eig(orc, m_map, Om, k)
+    lam, V, _ = P.lowrank_eig(torch.tensor(m_map, device=DEV), k, p,
+                              torch.tensor(np.ascontiguousarray(Om.T), device=DEV))
+    lam, V = lam.cpu().numpy(), V.cpu().numpy().T
+    big = lam_ref > 0.1
+    assert big.sum() >= 10
+    assert np.all(np.abs(lam[big] - lam_ref[big]) <= 1e-6 * lam_ref[big])
+    assert np.allclose(V.T @ orc.R_apply(V), np.eye(k), atol=1e-7)
+
+
 def test_samples_with_identical_normals(small2d):
     orc, w, P = small2d["orc"], small2d["w"], small2d["P"]
     m_map = small2d["m_map"]
