@@ -105,7 +105,11 @@ typedef struct {
   double prec_rtol;      /* relative tolerance of the two prior solves of R^-1 when it
                             preconditions the CG (0: the problem's tolerance).  The
                             gradient and its R^-1 norm, which decide convergence, always
-                            use the problem's tolerance.  No counterpart in the paper.     */
+                            use the problem's tolerance.  A looser value makes the
+                            preconditioner vary between CG iterations: it saved a few
+                            percent where the CG needs few iterations, and stalled Newton
+                            where it needs many (64^3 with k = 100).  No counterpart in
+                            the paper.                                                     */
 } hp_newton_opts;
 
 typedef struct {
