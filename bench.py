@@ -58,11 +58,29 @@ def parse():
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start leg (2D)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the library's default solver settings instead of the autotuned ones")
+    ap.add_argument("--tuning", default="",
+                    help="fixed solver settings instead of the autotuned ones, as key=value pairs separated by "
+                         "commas (hp_tuning member names, e.g. tma_tiles=1,col_chunk=32); unnamed members keep "
+                         "the library defaults")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the plain one-vector FP64 GPU path (the speedup denominator)")
     ap.add_argument("--ws-draws", type=int, default=12, help="prior draws whose solves train the warm start")
     ap.add_argument("--ws-epochs", type=int, default=8, help="training epochs of the warm start")
     return ap.parse_args()
+
+
+def parse_tuning(text):
+    """{'name': number} from "name=value,name=value" (integers where the value is one)."""
+    out = {}
+    for item in filter(None, (t.strip() for t in text.split(","))):
+        key, _, val = item.partition("=")
+        if not key or not val:
+            raise SystemExit(f"--tuning: expected name=value, got {item!r}")
+        try:
+            out[key.strip()] = int(val)
+        except ValueError:
+            out[key.strip()] = float(val)
+    return out
 
 
 def workload_desc(w, precision):
@@ -222,29 +240,49 @@ def family_bytes(fam, n, s, dim, fp32):
     return None
 
 
-def stencil_kernel_sha256():
-    """sha256 of the row stencil kernel's source: the Pack / reduction / k_st block of
-    csrc/solver.cu (up to the tiled kernels) and csrc/common.cuh (the code an ncu traffic
-    record belongs to)."""
+def stencil_kernel_sha256(kind="row"):
+    """sha256 of a level-0 stencil kernel's source (the code an ncu traffic record belongs
+    to), with csrc/common.cuh.  kind "row": the Pack / reduction / k_st block of
+    csrc/solver.cu up to the tiled kernels; kind "tiled": the TMA-tiled kernels k_st_tile and
+    k_st_tile3 with the tile shapes of csrc/internal.h."""
     csrc = os.path.join(ROOT, "paper_1909_03948_gb300", "csrc")
     src = open(os.path.join(csrc, "solver.cu")).read()
-    a = src.index("template <typename T, int VW> struct Pack {")
-    b = src.index("// TMA-tiled stencil kernels")
-    h = hashlib.sha256(src[a:b].encode())
+    if kind == "row":
+        a = src.index("template <typename T, int VW> struct Pack {")
+        b = src.index("// TMA-tiled stencil kernels")
+        h = hashlib.sha256(src[a:b].encode())
+    else:
+        a = src.index("// TMA-tiled stencil kernels")
+        b = src.index("// grid transfer, coarse solve")
+        h = hashlib.sha256(src[a:b].encode())
+        hdr = open(os.path.join(csrc, "internal.h")).read()
+        h.update(hdr[hdr.index("// Grids whose stiffness stencils run as TMA-tiled kernels"):
+                     hdr.index("// Symmetric stencil stored")].encode())
     h.update(open(os.path.join(csrc, "common.cuh"), "rb").read())
     return h.hexdigest()
 
 
-def traffic_record(fam, workload):
-    """ncu DRAM bytes per launch recorded in profiles/traffic.json, valid only while
-    the stencil kernel's source is unchanged (stencil_kernel_sha256)."""
+def level0_kernel_kind(dim, N, tune, fp32):
+    """"tiled" when the level-0 stiffness sweeps run as TMA-tiled kernels, else "row": the
+    tiled kernels are FP32, enabled by the tma_tiles setting, and take grids whose N is a
+    multiple of the tile (32 x 16 in 2D; 32 x 8 xy tiles and 16-plane z segments in 3D)."""
+    if not (fp32 and tune and tune.get("tma_tiles")) or N < 32:
+        return "row"
+    ok = N % 32 == 0 and N % 16 == 0 if dim == 2 else N % 32 == 0 and N % 8 == 0 and N % 16 == 0
+    return "tiled" if ok else "row"
+
+
+def traffic_record(fam, workload, kind="row"):
+    """ncu DRAM bytes per launch recorded in profiles/traffic.json for a level-0 kernel
+    family, valid only for the kernel form that ran (row or tiled) while that kernel's
+    source is unchanged (stencil_kernel_sha256)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     try:
         d = json.load(open(p))
         rec = d.get(workload, {}).get(fam)
-        if rec and rec.get("src_sha256") == stencil_kernel_sha256():
+        if rec and rec.get("kind", "row") == kind and rec.get("src_sha256") == stencil_kernel_sha256(kind):
             return rec.get("dram_bytes_per_launch")
     except Exception:
         return None
@@ -325,7 +363,11 @@ def run_ours(args, rank, world):
         m_lin = m_true
     P.set_point(m_lin)
     from paper_1909_03948_gb300 import tuning
-    if args.no_autotune:
+    if args.tuning:
+        fixed = parse_tuning(args.tuning)
+        P.set_tuning(**fixed)
+        tune, tune_ms, tune_src = P.get_tuning(), None, f"library defaults with {args.tuning}"
+    elif args.no_autotune:
         P.set_tuning()
         tune, tune_ms, tune_src = P.get_tuning(), None, "library defaults"
     else:
@@ -396,6 +438,7 @@ def run_ours(args, rank, world):
         cnt, ms = fams[dom]
         fp32 = args.precision == "fp32_ir" and dom != "resid64"
         bpl = family_bytes(dom, P.n, s, w.dim, fp32)
+        kind = level0_kernel_kind(w.dim, w.N, tune, fp32) if dom != "cg_update" else "vector"
         in_step_s = ms / cnt / 1e3
         peak, src = measured_peak()
         warm_us = cold_us = graph_us = None
@@ -412,7 +455,7 @@ def run_ours(args, rank, world):
         dur_s = graph_us * 1e-6 if graph_us else in_step_s
         ach = bpl / dur_s / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": traffic_record(dom, w.name), "kernel": dom, "launches": cnt,
+                "traffic": traffic_record(dom, w.name, kind), "kernel": dom, "kernel_form": kind, "launches": cnt,
                 "avg_launch_us": dur_s * 1e6, "algorithmic_bytes_per_launch": bpl, "peak_source": src,
                 "measured_in": ("the step's own level-0 launch, 200 launches captured in one CUDA graph on the live "
                                 "workspace after the timed region, CUDA events around the graph launch "

@@ -1,0 +1,48 @@
+"""Host-side pieces of bench.py that need no GPU: the fixed-tuning option and the
+algorithmic byte counts the roofline divides by."""
+import pytest
+
+import bench
+
+
+def test_parse_tuning_reads_names_and_numbers():
+    assert bench.parse_tuning("tma_tiles=1, col_chunk=32,omega=0.65") == {"tma_tiles": 1, "col_chunk": 32,
+                                                                        "omega": 0.65}
+    assert bench.parse_tuning("") == {}
+    with pytest.raises(SystemExit):
+        bench.parse_tuning("tma_tiles")
+
+
+def test_parse_tuning_names_are_set_tuning_keywords():
+    import inspect
+    from paper_1909_03948_gb300.hp import Problem, Tuning
+    keywords = set(inspect.signature(Problem.set_tuning).parameters) - {"self"}
+    assert keywords == {f for f, _ in Tuning._fields_}
+
+
+def test_family_bytes_medium2d_smoothing_sweep():
+    # 257^2 nodes, 60 FP32 columns: x and b read, y written (3 x 60 x 4 bytes per node)
+    # plus diag, inverse diag and the two forward couplings (4 x 4 bytes per node)
+    n = 257 * 257
+    assert bench.family_bytes("smooth", n, 60, 2, True) == n * (720 + 16) == 48_612_064
+    # 65^3 nodes, three forward couplings in 3D
+    assert bench.family_bytes("smooth", 65 ** 3, 120, 3, True) == 65 ** 3 * (1440 + 20)
+
+
+def test_level0_kernel_kind_follows_the_tile_shapes():
+    on = {"tma_tiles": 1}
+    assert bench.level0_kernel_kind(2, 256, on, True) == "tiled"
+    assert bench.level0_kernel_kind(2, 256, {"tma_tiles": 0}, True) == "row"
+    assert bench.level0_kernel_kind(2, 256, on, False) == "row"      # the tiled kernels are FP32
+    assert bench.level0_kernel_kind(2, 16, on, True) == "row"        # narrower than one tile
+    assert bench.level0_kernel_kind(3, 64, on, True) == "tiled"
+    assert bench.level0_kernel_kind(3, 40, on, True) == "row"        # 40 is no multiple of the 32-wide tile
+
+
+def test_traffic_records_belong_to_the_kernel_form_that_ran():
+    # the committed ncu records match the current kernel sources; a record taken on one
+    # kernel form is never reported for the other
+    assert bench.traffic_record("smooth", "medium2d", "row") == 32_776_960
+    assert bench.traffic_record("smooth", "medium2d", "tiled") is None
+    assert bench.traffic_record("smooth", "cube3d", "tiled") == 392_526_336
+    assert bench.traffic_record("smooth", "cube3d", "row") is None
