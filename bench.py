@@ -272,11 +272,11 @@ def level0_kernel_kind(dim, N, tune, fp32):
     return "tiled" if ok else "row"
 
 
-def traffic_record(fam, workload, kind="row"):
-    """ncu DRAM bytes per launch recorded in profiles/traffic.json for a level-0 kernel
-    family, valid only for the kernel form that ran (row or tiled) while that kernel's
-    source is unchanged (stencil_kernel_sha256)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+def traffic_record(fam, workload, kind="row", path=None):
+    """ncu DRAM bytes per launch recorded in profiles/traffic.json (or ``path``) for a
+    level-0 kernel family, valid only for the kernel form that ran (row or tiled) while
+    that kernel's source is unchanged (stencil_kernel_sha256)."""
+    p = path or os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     try:

@@ -412,16 +412,18 @@ __global__ void __launch_bounds__(TL_NT) k_st_tile(const __grid_constant__ CUten
 // ---------------------------------------------------------------------------
 // TMA z-marching stencil kernels (3D stiffness levels, FP32, 4 columns per node).
 // One CTA per xy tile of TILE3_X x TILE3_Y nodes, one z segment of TILE3_Z planes and one
-// column group.  A ring of TL3_NS shared-memory slots holds consecutive planes: the plane
-// of x with a one-node xy halo, the plane of 32-byte coefficient records with the same
-// halo, and the plane of b; each slot completes on its own mbarrier (the use count's
-// parity is the phase).  Plane p is computed from the slots of p - 1, p and p + 1 while
-// thread 0 keeps the copies of planes p + 2 .. p + TL3_NS - 2 in flight, so every plane's
-// data is requested TL3_NS - 3 steps before it is needed.  Copies past the grid read zeros; the boundary tests
-// keep them out of the arithmetic, which is k_st's, operation for operation.
+// column group.  A ring of TL3_NS = 3 shared-memory slots holds consecutive planes: the
+// plane of x with a one-node xy halo, the plane of 16-byte coefficient records with the
+// same halo, the z couplings and the plane of b; each slot completes on its own mbarrier
+// (the use count's parity is the phase).  Plane p is computed from the slots of p and
+// p + 1 while the copy of plane p + 2 is in flight, in the slot plane p - 1 has left.  What
+// the march needs of plane p - 1 (x, c_z, 1/diag) stays in registers from the step before;
+// at a segment's first plane it comes from global memory with plain loads that overlap the
+// first copies.  Copies past the grid read zeros; the boundary tests keep them out of the
+// arithmetic, which is k_st's, operation for operation.
 // ---------------------------------------------------------------------------
 constexpr int TL3_NT = NB;
-constexpr int TL3_NS = 4;                                          // ring slots
+constexpr int TL3_NS = 3;                                          // ring slots
 constexpr int TL3B_X = TILE3_X + 3, TL3B_Y = TILE3_Y + 3;          // x / record boxes (one plane)
 constexpr int TL3R_X = TILE3_X + 1, TL3R_Y = TILE3_Y + 1;          // b box (one plane)
 constexpr int TL3Z_X = TILE3_X + 4;                                // c_z box width (16-byte multiple)
@@ -462,8 +464,10 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
                                                      const __grid_constant__ CUtensorMap mr,
                                                      const __grid_constant__ CUtensorMap mc,
                                                      const __grid_constant__ CUtensorMap mz, GridDesc g, int ntx,
-                                                     int nty, int nzs, float *__restrict__ Y, long gy, int s,
-                                                     float omega, float omega2, Fin fin) {
+                                                     int nty, int nzs, const float *__restrict__ Xg, long gx,
+                                                     const float *__restrict__ pkg, const float *__restrict__ czg,
+                                                     float *__restrict__ Y, long gy, int s, float omega, float omega2,
+                                                     Fin fin) {
   using PK = Pack<float, 4>;
   extern __shared__ __align__(128) unsigned char tl3_raw[];
   unsigned char *sm = tl3_raw + ((128u - (smem_u32(tl3_raw) & 127u)) & 127u);
@@ -476,9 +480,9 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
   const int ze = zb + TILE3_Z + (tz == nzs - 1);  // planes zb .. ze - 1
   const uint32_t bar0 = smem_u32(sm + TL3_OFF_BAR);
   const unsigned bytes = TL3_XB + TL3_CB + TL3_ZB + (HAS_B ? TL3_RB : 0u);
-  // plane q sits in slot (q - zb + 1) % NS; its barrier's phase is the slot's use count
+  // plane q sits in slot (q - zb) % NS; its barrier's phase is the slot's use count
   auto issue = [&](int q) {
-    const int r = q - zb + 1, k = r % TL3_NS;
+    const int r = q - zb, k = r % TL3_NS;
     unsigned char *sl = sm + k * TL3_SLOT;
     const uint32_t bar = bar0 + 8u * k;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -488,7 +492,7 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
     if (HAS_B) tma_load_4d(smem_u32(sl + TL3_OFF_R), &mr, 4 * x0, y0, q, grp, bar);
   };
   auto ready = [&](int q) {
-    const int r = q - zb + 1;
+    const int r = q - zb;
     return mbar_wait_parity(bar0 + 8u * (r % TL3_NS), (unsigned)((r / TL3_NS) & 1));
   };
   if (threadIdx.x == 0) {
@@ -497,8 +501,8 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
-  if (threadIdx.x == 0)  // the planes below, at and above the first one, and the prefetch
-    for (int q = zb - 1; q <= zb + TL3_NS - 3 && q <= ze; ++q) issue(q);
+  if (threadIdx.x == 0)  // the first plane and the one above it
+    for (int q = zb; q <= zb + 1 && q <= ze; ++q) issue(q);
   PK acc = PK::zero();
   bool ok = true;
   // Each thread keeps its nodes (t = threadIdx.x + j * TL3_NT) for the whole march, so x at
@@ -507,24 +511,35 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
   constexpr int NPT = (TL3R_X * TL3R_Y + TL3_NT - 1) / TL3_NT;
   PK rxm[NPT], rx0[NPT];
   float rzm[NPT], rvm[NPT];
+  {
+    const long np = g.np, ldr = (np + 3) / 4 * 4;
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {  // plane zb - 1 (absent below the grid: never read there)
+      const int t = threadIdx.x + j * TL3_NT;
+      rxm[j] = PK::zero();
+      rzm[j] = 0.f;
+      rvm[j] = 0.f;
+      if (t >= wx * hy || zb == 0) continue;
+      const long v0 = x0 + t % wx, v1 = y0 + t / wx, row = (long)(zb - 1) * np + v1;
+      rxm[j] = PK::ld(Xg + grp * gx + (row * np + v0) * 4);
+      rzm[j] = czg[row * ldr + v0];
+      rvm[j] = pkg[(row * np + v0) * 4 + 1];
+    }
+  }
   for (int p = zb; p < ze; ++p) {
-    __syncthreads();  // every thread is done with plane p - 2's slot
-    if (threadIdx.x == 0 && p + TL3_NS - 2 <= ze) issue(p + TL3_NS - 2);
-    ok = ready(p - 1) && ready(p) && ready(p + 1);
+    __syncthreads();  // every thread is done with plane p - 1's slot
+    if (threadIdx.x == 0 && p + 2 <= ze) issue(p + 2);
+    ok = ready(p) && ready(p + 1);
     if (!__syncthreads_and(ok)) {  // every thread leaves together if any wait ran out
       ok = false;
       break;
     }
-    const unsigned char *sm_m = sm + ((p - zb) % TL3_NS) * TL3_SLOT;       // plane p - 1
-    const unsigned char *sm_0 = sm + ((p - zb + 1) % TL3_NS) * TL3_SLOT;   // plane p
-    const unsigned char *sm_p = sm + ((p - zb + 2) % TL3_NS) * TL3_SLOT;   // plane p + 1
-    const float *xm = reinterpret_cast<const float *>(sm_m), *x0s = reinterpret_cast<const float *>(sm_0),
-                *xp = reinterpret_cast<const float *>(sm_p);
+    const unsigned char *sm_0 = sm + ((p - zb) % TL3_NS) * TL3_SLOT;       // plane p
+    const unsigned char *sm_p = sm + ((p - zb + 1) % TL3_NS) * TL3_SLOT;   // plane p + 1
+    const float *x0s = reinterpret_cast<const float *>(sm_0), *xp = reinterpret_cast<const float *>(sm_p);
     const float4 *c0s = reinterpret_cast<const float4 *>(sm_0 + TL3_OFF_C),
-                 *cp = reinterpret_cast<const float4 *>(sm_p + TL3_OFF_C),
-                 *cm = reinterpret_cast<const float4 *>(sm_m + TL3_OFF_C);
-    const float *zm = reinterpret_cast<const float *>(sm_m + TL3_OFF_Z),
-                *z0 = reinterpret_cast<const float *>(sm_0 + TL3_OFF_Z);
+                 *cp = reinterpret_cast<const float4 *>(sm_p + TL3_OFF_C);
+    const float *z0 = reinterpret_cast<const float *>(sm_0 + TL3_OFF_Z);
     const float *rs = reinterpret_cast<const float *>(sm_0 + TL3_OFF_R);
     const bool fz = p < g.N, bz = p > 0;
 #pragma unroll
@@ -538,12 +553,7 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
       const bool fx = v0 < g.N, bx = v0 > 0, fy = v1 < g.N, by = v1 > 0;
       const float4 cc = c0s[ci];  // diag, invdiag, c_x, c_y
       const float cz = z0[zi];    // c_z
-      if (p == zb) {  // first plane: fill the registers from the p - 1 and p slots
-        rxm[j] = PK::ld(xm + ci * 4);
-        rx0[j] = PK::ld(x0s + ci * 4);
-        rzm[j] = zm[zi];
-        rvm[j] = cm[ci].y;
-      }
+      if (p == zb) rx0[j] = PK::ld(x0s + ci * 4);  // first plane: x at p from its slot
       const PK xpv = PK::ld(xp + ci * 4);  // x at p + 1
       PK out;
       if (MODE == M_JAC2) {
@@ -1295,8 +1305,8 @@ static bool tile3_launch(const GridDesc &g, const Stencil<float> &S, const float
       return false;
     attr_set |= 1ull << dev;
   }
-  k_st_tile3<MODE><<<dim3(ntx * nty * nzs, ng), TL3_NT, TL3_SMEM, st>>>(mx, mr, mc, mz, g, ntx, nty, nzs, Y, gy,
-                                                                       s, omega, omega2, fin);
+  k_st_tile3<MODE><<<dim3(ntx * nty * nzs, ng), TL3_NT, TL3_SMEM, st>>>(
+      mx, mr, mc, mz, g, ntx, nty, nzs, X, gx, S.pk, S.pk + 4 * g.n, Y, gy, s, omega, omega2, fin);
   count_launch();
   if (MODE == M_APPLY_DOT || MODE == M_JACOBI_DOT) dot_finalize(fin, ntx * nty * nzs, s, st);
   return true;

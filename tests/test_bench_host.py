@@ -39,10 +39,24 @@ def test_level0_kernel_kind_follows_the_tile_shapes():
     assert bench.level0_kernel_kind(3, 40, on, True) == "row"        # 40 is no multiple of the 32-wide tile
 
 
-def test_traffic_records_belong_to_the_kernel_form_that_ran():
-    # the committed ncu records match the current kernel sources; a record taken on one
-    # kernel form is never reported for the other
-    assert bench.traffic_record("smooth", "medium2d", "row") == 32_776_960
-    assert bench.traffic_record("smooth", "medium2d", "tiled") is None
-    assert bench.traffic_record("smooth", "cube3d", "tiled") == 392_526_336
-    assert bench.traffic_record("smooth", "cube3d", "row") is None
+def test_traffic_records_belong_to_the_kernel_form_that_ran(tmp_path):
+    # a record taken on one kernel form is never reported for the other, nor once that
+    # form's source has changed since the capture
+    import json
+    rec = {"medium2d": {"smooth": {"dram_bytes_per_launch": 111, "kind": "row",
+                                   "src_sha256": bench.stencil_kernel_sha256("row")}},
+           "cube3d": {"smooth": {"dram_bytes_per_launch": 222, "kind": "tiled",
+                                 "src_sha256": bench.stencil_kernel_sha256("tiled")},
+                      "resid_mg": {"dram_bytes_per_launch": 333, "kind": "tiled", "src_sha256": "0" * 64}}}
+    p = tmp_path / "traffic.json"
+    p.write_text(json.dumps(rec))
+    assert bench.traffic_record("smooth", "medium2d", "row", str(p)) == 111
+    assert bench.traffic_record("smooth", "medium2d", "tiled", str(p)) is None
+    assert bench.traffic_record("smooth", "cube3d", "tiled", str(p)) == 222
+    assert bench.traffic_record("smooth", "cube3d", "row", str(p)) is None
+    assert bench.traffic_record("resid_mg", "cube3d", "tiled", str(p)) is None
+    assert bench.traffic_record("matvec", "cube3d", "tiled", str(p)) is None
+
+
+def test_the_two_kernel_forms_hash_different_sources():
+    assert bench.stencil_kernel_sha256("row") != bench.stencil_kernel_sha256("tiled")
