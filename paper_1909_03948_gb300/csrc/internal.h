@@ -19,8 +19,9 @@ constexpr int TILE_X = 32, TILE_Y = 16;
 inline bool tile_grid(const GridDesc &g) {
   return g.dim == 2 && g.np >= TILE_X + 1 && (g.np - 1) % TILE_X == 0 && (g.np - 1) % TILE_Y == 0;
 }
-// 3D: 32 x 8-node xy tiles marching through z segments of 16 planes (the last tile or
-// segment in each direction also takes the grid's final node / row / plane)
+// 3D: 32 x 8-node xy tiles marching through z segments of 16 planes, or of 8 where that
+// fills the GPU's last wave of CTAs better (the last tile or segment in each direction also
+// takes the grid's final node / row / plane)
 constexpr int TILE3_X = 32, TILE3_Y = 8, TILE3_Z = 16;
 inline bool tile3_grid(const GridDesc &g) {
   return g.dim == 3 && g.np >= TILE3_X + 1 && (g.np - 1) % TILE3_X == 0 && (g.np - 1) % TILE3_Y == 0 &&

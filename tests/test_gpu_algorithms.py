@@ -471,12 +471,14 @@ def test_fused_transfers_keep_results(dim, N, precision, nu):
     P.close()
 
 
-@pytest.mark.parametrize("dim,N,ncols", [(2, 32, 5), (2, 96, 8), (2, 256, 60), (3, 32, 6), (3, 64, 8)])
+@pytest.mark.parametrize("dim,N,ncols", [(2, 32, 5), (2, 96, 8), (2, 256, 60), (3, 32, 6), (3, 64, 8),
+                                         (3, 64, 60)])
 def test_tma_tiles_keep_results(dim, N, ncols):
     """The TMA-tiled stencil kernels against the row kernels: in 2D the levels whose np - 1
     is a multiple of 32 (all of N = 32 and 256, only the finest level of N = 96), in 3D the
     z-marching kernel on levels with np - 1 a multiple of 32 (the finest of N = 32, the two
-    finest of N = 64).  The same Hessian actions and stiffness solves to the solve
+    finest of N = 64; 16-plane z segments on the finest level of N = 64 with 60 columns,
+    8-plane ones elsewhere).  The same Hessian actions and stiffness solves to the solve
     tolerance, within one PCG iteration (the two differ only in the order of the
     inner-product partial sums), with column counts that leave part of the last group of 4
     empty."""
