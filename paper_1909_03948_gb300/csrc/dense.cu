@@ -16,6 +16,7 @@
 // plain FP64 FMA kernels; they are a small share of the eigensolver's time,
 // which is dominated by the 2(k+p) Hessian actions.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <vector>
 
@@ -518,16 +519,16 @@ int small_symeig(hp_problem *P, const double *T, int s, double *lambda, double *
     }
     const size_t shm = sizeof(double) * ((v_shared ? 2 : 1) * (size_t)s * s + m + 64) +
                        sizeof(int) * 2 * (size_t)std::max(m, s);
-    static unsigned long long attr_set = 0;  // once per device: the largest size either layout needs
+    static std::atomic<unsigned long long> attr_set{0};  // once per device: the largest size either layout needs
     int dev = 0;
     HP_CUDA(cudaGetDevice(&dev));
-    if (dev < 64 && !(attr_set & (1ull << dev))) {
+    if (dev < 64 && !(attr_set.load(std::memory_order_acquire) & (1ull << dev))) {
       const size_t cap = std::max(sizeof(double) * (2 * JS_MAX * JS_MAX + JS_MAX + 1 + 64) +
                                       sizeof(int) * 2 * (JS_MAX + 1),
                                   sizeof(double) * (JS_MAX_A * JS_MAX_A + JS_MAX_A + 64) +
                                       sizeof(int) * 2 * JS_MAX_A);
       HP_CUDA(cudaFuncSetAttribute(k_jacobi_eig_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
-      attr_set |= 1ull << dev;
+      attr_set.fetch_or(1ull << dev, std::memory_order_release);
     }
     k_jacobi_eig_sm<<<1, 1024, shm, P->st>>>(T, s, m, lambda, S, 60, Vg);
     count_launch();

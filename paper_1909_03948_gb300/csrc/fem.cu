@@ -24,6 +24,7 @@
 // C_M   = rectangular factor of M from a degree-2 element rule (Appendix C,
 //               eq. (rect_decomp)).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -525,13 +526,13 @@ int coarse_setup(hp_problem *P, OpKind op) {
   if (P->precision == HP_FP32_IR && tri_bytes <= 200u * 1024u) {
     // only inv32 is used by FP32 inner solves: factor and invert in FP32 (inv64 is
     // rebuilt by hp_set_precision if the plain FP64 path is selected later)
-    static unsigned long long attr_set = 0;
+    static std::atomic<unsigned long long> attr_set{0};
     int dev = 0;
     HP_CUDA(cudaGetDevice(&dev));
-    if (dev < 64 && !(attr_set & (1ull << dev))) {
+    if (dev < 64 && !(attr_set.load(std::memory_order_acquire) & (1ull << dev))) {
       HP_CUDA(cudaFuncSetAttribute(k_dense_cholesky32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    200 * 1024));
-      attr_set |= 1ull << dev;
+      attr_set.fetch_or(1ull << dev, std::memory_order_release);
     }
     float *L32 = reinterpret_cast<float *>(C.inv64);  // scratch: the FP64 inverse is not kept in this mode
     k_dense_cholesky32<<<1, 1024, tri_bytes, P->st>>>(C.dense, (int)nc, L32, dstat);

@@ -22,6 +22,7 @@
 //   * Level stencils of 2D stiffness solves: one CTA per 32 x 16-node tile, its
 //     data brought into shared memory by TMA bulk tensor copies (k_st_tile).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -1296,20 +1297,21 @@ static bool tile3_launch(const GridDesc &g, const Stencil<float> &S, const float
   } else {
     mr = mx;
   }
-  static unsigned long long attr_set = 0;  // the opt-in shared-memory size, once per mode and device
-  static int slots[64];                     // resident CTAs on the whole device
+  // the opt-in shared-memory size and the device's resident CTAs, once per mode and device
+  // (solves of a batch launch from several host threads; setting the attribute twice is harmless)
+  static std::atomic<int> slots[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return false;
-  if (!(attr_set & (1ull << dev))) {
+  if (slots[dev].load(std::memory_order_acquire) == 0) {
     int per_sm = 0, sms = 0;
     if (cudaFuncSetAttribute(k_st_tile3<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL3_SMEM) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_st_tile3<MODE>, TL3_NT, TL3_SMEM) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
       return false;
-    slots[dev] = per_sm * sms;
-    attr_set |= 1ull << dev;
+    slots[dev].store(per_sm * sms, std::memory_order_release);
   }
+  const int nslots = slots[dev].load(std::memory_order_acquire);
   // z segments of 16 or 8 planes, whichever the model ceil(w) / w * (zs + 1) / zs puts
   // lower, w being the launch's CTAs over the resident slots: the last, partly filled wave
   // against the per-segment start (the first plane's copies and the plane below).
@@ -1321,7 +1323,7 @@ static bool tile3_launch(const GridDesc &g, const Stencil<float> &S, const float
     double best = 0.0;
     for (int zs = TILE3_Z; zs >= TILE3_Z / 2; zs /= 2) {
       if ((g.np - 1) % zs) continue;
-      const double w = (double)ntx * nty * ((g.np - 1) / zs) * ng / slots[dev];
+      const double w = (double)ntx * nty * ((g.np - 1) / zs) * ng / nslots;
       const double cost = std::ceil(w) / w * (zs + 1.0) / zs;
       if (best == 0.0 || cost < best * (1.0 - 1e-9)) {
         best = cost;
@@ -2017,8 +2019,11 @@ static void launch_vtail_smem(hp_problem *P, OpKind op, int s, int l0, const T *
     down = full ? k_vtail_smem<T, VW, 3, true, 0> : k_vtail_smem<T, VW, 3, false, 0>;
     up = full ? k_vtail_smem<T, VW, 3, true, 1> : k_vtail_smem<T, VW, 3, false, 1>;
   }
-  cudaFuncSetAttribute(down, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  cudaFuncSetAttribute(up, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  // every caller sets the same (largest) limit, so solves launching from several host
+  // threads never lower it under one another's launch
+  const int cap = smem_optin();
+  cudaFuncSetAttribute(down, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(up, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   down<<<dim3(1, ng), VS_NT, bytes, P->st>>>(vt);
   const int lc = L - 1, nc = (int)P->lv[lc].g.n;
   k_coarse_apply<T, VW><<<dim3((nc + 31) / 32, ng), 256, sizeof(T) * nc * VW, P->st>>>(
