@@ -44,3 +44,53 @@ def test_normals_have_standard_normal_law():
     # samples are uncorrelated
     Z = philox.normals(2024, 0, 2, 50000)
     assert abs(np.corrcoef(Z[:, 0], Z[:, 1])[0, 1]) < 4 / np.sqrt(50000)
+
+
+_TRITON_PHILOX = r"""
+import os, sys
+os.environ["TRITON_INTERPRET"] = "1"   # Triton's CPU interpreter: no GPU needed
+import numpy as np, torch, triton, triton.language as tl
+
+@triton.jit
+def k(c0p, c1p, c2p, c3p, o0, o1, o2, o3, seed, N: tl.constexpr):
+    i = tl.arange(0, N)
+    r0, r1, r2, r3 = tl.philox(seed, tl.load(c0p + i), tl.load(c1p + i), tl.load(c2p + i), tl.load(c3p + i))
+    tl.store(o0 + i, r0)
+    tl.store(o1 + i, r1)
+    tl.store(o2 + i, r2)
+    tl.store(o3 + i, r3)
+
+ctr = np.load(sys.argv[1])
+seed = int(sys.argv[2])
+cs = [torch.from_numpy(np.ascontiguousarray(ctr[:, j]).view(np.int32)) for j in range(4)]
+outs = [torch.empty(ctr.shape[0], dtype=torch.int32) for _ in range(4)]
+k[(1,)](*cs, *outs, seed, N=ctr.shape[0])
+np.save(sys.argv[3], np.stack([o.numpy().view(np.uint32) for o in outs], -1))
+"""
+
+
+def test_equals_an_independent_library_philox(tmp_path):
+    # Triton ships its own Philox4x32-10 (tl.philox: key = the seed's low and high words,
+    # ten rounds); run through its CPU interpreter it must give the oracle's words exactly,
+    # which pins the round constants, the key schedule and the round count
+    import os
+    import subprocess
+    import sys
+
+    import pytest
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(5)
+    ctr = rng.integers(0, 2 ** 32, (64, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:4] = [[0, 0, 0, 0], [1, 0, 0, 0], [0xFFFFFFFF] * 4, [0, 0, 0, 1]]
+    for seed in (0, 20240607, (0xBEEF << 32) | 0x12345678):
+        src, out = tmp_path / "ctr.npy", tmp_path / "out.npy"
+        np.save(src, ctr)
+        script = tmp_path / "tri.py"
+        script.write_text(_TRITON_PHILOX)
+        env = {**os.environ, "TRITON_INTERPRET": "1"}
+        subprocess.run([sys.executable, str(script), str(src), str(seed), str(out)], check=True, env=env,
+                       timeout=300)
+        key = np.stack([np.full(len(ctr), seed & 0xFFFFFFFF, np.uint64), np.full(len(ctr), seed >> 32, np.uint64)],
+                       -1)
+        ref = philox.philox4x32_10(ctr.astype(np.uint64), key).astype(np.uint32)
+        assert np.array_equal(ref, np.load(out)), seed
