@@ -46,6 +46,20 @@ def test_normals_have_standard_normal_law():
     assert abs(np.corrcoef(Z[:, 0], Z[:, 1])[0, 1]) < 4 / np.sqrt(50000)
 
 
+def test_box_muller_pairs_are_independent_normals():
+    # the two normals of one Box-Muller pair (entries 2i, 2i + 1 of a sample) are
+    # uncorrelated, their squared radius is chi-square with 2 degrees of freedom
+    # (exponential, mean 2) and their angle is uniform: a pair built from one trigonometric
+    # function twice, or a radius without the factor 2, fails here
+    z = philox.normals(77, 3, 1, 100000)[:, 0]
+    a, b = z[0::2], z[1::2]
+    assert abs(np.corrcoef(a, b)[0, 1]) < 4 / np.sqrt(len(a))
+    assert abs(np.corrcoef(a ** 2, b ** 2)[0, 1]) < 4 / np.sqrt(len(a))
+    r2 = a ** 2 + b ** 2
+    assert stats.kstest(r2, "expon", args=(0, 2)).pvalue > 1e-3
+    assert stats.kstest(np.arctan2(b, a), "uniform", args=(-np.pi, 2 * np.pi)).pvalue > 1e-3
+
+
 _TRITON_PHILOX = r"""
 import os, sys
 os.environ["TRITON_INTERPRET"] = "1"   # Triton's CPU interpreter: no GPU needed
