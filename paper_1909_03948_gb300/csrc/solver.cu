@@ -2019,11 +2019,20 @@ static void launch_vtail_smem(hp_problem *P, OpKind op, int s, int l0, const T *
     down = full ? k_vtail_smem<T, VW, 3, true, 0> : k_vtail_smem<T, VW, 3, false, 0>;
     up = full ? k_vtail_smem<T, VW, 3, true, 1> : k_vtail_smem<T, VW, 3, false, 1>;
   }
-  // every caller sets the same (largest) limit, so solves launching from several host
-  // threads never lower it under one another's launch
-  const int cap = smem_optin();
-  cudaFuncSetAttribute(down, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(up, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  // every caller sets the same limit (the device's opt-in maximum less the kernel's static
+  // shared memory), so solves launching from several host threads never lower it under
+  // one another's launch; the launch's own size is the fallback
+  auto allow = [&](void (*k)(VTailS<T>)) {
+    cudaFuncAttributes fa{};
+    int cap = smem_optin();
+    if (cudaFuncGetAttributes(&fa, k) == cudaSuccess) cap -= (int)fa.sharedSizeBytes;
+    if (cap < (int)bytes || cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess) {
+      (void)cudaGetLastError();  // a refused limit is not an error of the solve
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    }
+  };
+  allow(down);
+  allow(up);
   down<<<dim3(1, ng), VS_NT, bytes, P->st>>>(vt);
   const int lc = L - 1, nc = (int)P->lv[lc].g.n;
   k_coarse_apply<T, VW><<<dim3((nc + 31) / 32, ng), 256, sizeof(T) * nc * VW, P->st>>>(
