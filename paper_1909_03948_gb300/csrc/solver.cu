@@ -1307,8 +1307,10 @@ static bool tile3_launch(const GridDesc &g, const Stencil<float> &S, const float
     if (cudaFuncSetAttribute(k_st_tile3<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL3_SMEM) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_st_tile3<MODE>, TL3_NT, TL3_SMEM) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1) {
+      (void)cudaGetLastError();  // the row kernels run instead; the refusal is not the solve's error
       return false;
+    }
     slots[dev].store(per_sm * sms, std::memory_order_release);
   }
   const int nslots = slots[dev].load(std::memory_order_acquire);
