@@ -336,7 +336,9 @@ typedef struct {
                       multiple of 32 (2D: and of 16; 3D: and of 16 planes), the stencil
                       kernels work on tiles that bulk tensor copies (TMA) bring into shared
                       memory with their halo -- 32 x 16 nodes in 2D, 32 x 8 nodes marching
-                      through z in 3D; 0: every warp loads its own row of nodes */
+                      through z segments of 16 or 8 planes in 3D (the launch picks the
+                      length that fills the GPU's last wave of CTAs better); 0: every warp
+                      loads its own row of nodes */
   int smem_tail;   /* k >= 1: the coarse end of the V-cycle -- from the finest level l >= k
                       whose vectors, and those of every level below it, fit in one CTA's
                       shared memory -- runs as one launch of one CTA per column group, its
