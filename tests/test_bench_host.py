@@ -60,3 +60,20 @@ def test_traffic_records_belong_to_the_kernel_form_that_ran(tmp_path):
 
 def test_the_two_kernel_forms_hash_different_sources():
     assert bench.stencil_kernel_sha256("row") != bench.stencil_kernel_sha256("tiled")
+
+
+def test_oracle_legs_stay_bounded_on_the_3d_workload():
+    # the oracle's set-up does not finish in minutes at 64^3: both CPU legs say so at once
+    import json
+    import os
+    import subprocess
+    import sys
+
+    import workloads as W
+    cpu = bench.cpu_baseline_block(W.WORKLOADS["cube3d"])
+    assert cpu["value"] is None and cpu["sample"].startswith("not measured")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
+                          "cube3d"], check=True, capture_output=True, text=True, timeout=120).stdout
+    line = json.loads(out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and "unavailable" in line
