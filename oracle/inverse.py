@@ -29,6 +29,13 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from .fem import Mesh
+from .pcg import jacobi_pcg
+
+# Meshes with more nodes than this in 3D are solved by Jacobi-preconditioned CG to
+# relative residual CG_RTOL instead of a sparse direct factorisation, which does not
+# finish in minutes on 3D meshes of that size.
+CG_NODES_3D = 20_000
+CG_RTOL = 1e-13
 
 
 class Problem:
@@ -36,7 +43,14 @@ class Problem:
                  d_obs: np.ndarray | None, sigma: float, m_prior: np.ndarray | None = None,
                  f: np.ndarray | None = None, u_top: float = 1.0, u_bottom: float = 0.0,
                  dirichlet_mask: np.ndarray | None = None, dirichlet_values: np.ndarray | None = None,
-                 theta=None, robin_beta: float = 0.0):
+                 theta=None, robin_beta: float = 0.0, solver: str = "auto"):
+        """solver: "direct" (scipy SuperLU, exact to rounding), "cg" (Jacobi-preconditioned
+        CG to relative residual CG_RTOL in the true residual), or "auto" (cg for 3D meshes
+        above CG_NODES_3D nodes, else direct)."""
+        if solver == "auto":
+            solver = "cg" if (mesh.dim == 3 and mesh.n > CG_NODES_3D) else "direct"
+        assert solver in ("direct", "cg")
+        self.solver = solver
         self.mesh = mesh
         self.n = mesh.n
         self.gamma, self.delta, self.sigma = float(gamma), float(delta), float(sigma)
@@ -59,9 +73,12 @@ class Problem:
         A = self.gamma * self.K1 + self.delta * self.M
         if self.robin_beta != 0.0:
             A = A + self.gamma * self.robin_beta * mesh.boundary_mass
-        self.A = A.tocsc()
-        self._A_lu = spla.splu(self.A)
-        self._M_lu = spla.splu(self.M.tocsc())
+        if solver == "direct":
+            self.A = A.tocsc()
+            self._A_lu = spla.splu(self.A)
+            self._M_lu = spla.splu(self.M.tocsc())
+        else:
+            self.A = A.tocsr()
         self._cache_key = None
 
     # ---- state operator ----------------------------------------------------
@@ -76,8 +93,13 @@ class Problem:
         if key != self._cache_key:
             K = self.stiffness(m)
             self._K = K
-            Kff = K[self.free][:, self.free].tocsc()
-            self._Kff_lu = spla.splu(Kff)
+            if self.solver == "direct":
+                Kff = K[self.free][:, self.free].tocsc()
+                self._Kff_lu = spla.splu(Kff)
+            else:
+                Kff = K[self.free][:, self.free].tocsr()
+                Kff.eliminate_zeros()       # the exactly-zero off-axis couplings (same operator)
+                self._Kff_lu = _CGSolve(Kff)
             self._cache_key = key
         return self._K, self._Kff_lu
 
@@ -101,9 +123,13 @@ class Problem:
 
     # ---- prior -------------------------------------------------------------
     def A_solve(self, b: np.ndarray) -> np.ndarray:
+        if self.solver == "cg":
+            return jacobi_pcg(self.A, b, CG_RTOL)
         return self._A_lu.solve(np.ascontiguousarray(b))
 
     def M_solve(self, b: np.ndarray) -> np.ndarray:
+        if self.solver == "cg":
+            return jacobi_pcg(self.M, b, CG_RTOL)
         return self._M_lu.solve(np.ascontiguousarray(b))
 
     def R_apply(self, x: np.ndarray) -> np.ndarray:
@@ -205,11 +231,21 @@ class Problem:
         return self.observe(self.forward(m))
 
 
-def make_problem(w, draws, dtype=float):
+class _CGSolve:
+    """The .solve interface of a factorisation, by Jacobi-preconditioned CG on K_ff."""
+
+    def __init__(self, K):
+        self.K = K
+
+    def solve(self, b):
+        return jacobi_pcg(self.K, np.asarray(b), CG_RTOL)
+
+
+def make_problem(w, draws, dtype=float, solver: str = "auto"):
     """Build the oracle problem for a workload: m_true = prior draw from the
     workload's normals, d = B u(m_true) + sigma * xi with sigma = level * max|u|."""
     mesh = Mesh(w.dim, w.N)
-    prob = Problem(mesh, w.gamma, w.delta, draws.obs_xyz, None, 1.0)
+    prob = Problem(mesh, w.gamma, w.delta, draws.obs_xyz, None, 1.0, solver=solver)
     m_true = prob.prior_sample(draws.eta_true.reshape(-1))
     u_true = prob.forward(m_true)
     sigma = w.noise_level * float(np.max(np.abs(u_true)))
