@@ -16,7 +16,10 @@ the roofline of the dominant kernel measured live with CUDA events, clocks
 sampled during the timed region, and the FP64 CPU oracle on a bounded sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload medium2d|small2d|cube3d] [--precision fp32_ir|fp64]
+                    [--workload cube3d|medium2d|small2d|batch64] [--precision fp32_ir|fp64]
+
+The default workload is cube3d (64^3 Kuhn tetrahedra, 274,625 nodes, 120 columns): the
+largest single-GPU configuration, whose blocks do not fit in L2.
 """
 from __future__ import annotations
 
@@ -51,7 +54,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="medium2d", choices=sorted(W.WORKLOADS) + ["batch64"])
+    ap.add_argument("--workload", default="cube3d", choices=sorted(W.WORKLOADS) + ["batch64"])
     ap.add_argument("--precision", default="fp32_ir", choices=["fp32_ir", "fp64"])
     ap.add_argument("--no-map", action="store_true", help="linearise at the true parameter instead of the MAP")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
@@ -85,7 +88,8 @@ def parse_tuning(text):
 
 def workload_desc(w, precision):
     prec = {"fp32_ir": "FP32 MG-PCG in FP64 refinement", "fp64": "FP64 MG-PCG",
-            "oracle": "FP64 CPU oracle with sparse direct solves (exact to rounding)"}[precision]
+            "oracle_direct": "FP64 CPU oracle with sparse direct solves (exact to rounding)",
+            "oracle_cg": "FP64 CPU oracle with Jacobi-preconditioned CG solves to relative residual 1e-13"}[precision]
     return (f"{w.name}: {w.dim}D {'x'.join([str(w.N)] * w.dim)} P1 "
             f"({'right triangles' if w.dim == 2 else 'Kuhn tetrahedra'}), n={w.nnodes}, q={w.nobs}, "
             f"block of k+p={w.k + w.p} Gauss-Newton Hessian actions at the MAP, {prec}, rel-res 1e-8")
@@ -95,9 +99,10 @@ def workload_desc(w, precision):
 # CPU oracle leg (the only place besides --impl reference that runs oracle/)
 # ---------------------------------------------------------------------------
 def oracle_rate(w, ncols_sample, seconds_hint=20.0):
-    """Oracle Hessian actions/s for a (k+p)-column block, from a bounded sample:
-    one factorisation at the linearisation point + ncols_sample columns,
-    extrapolated to the full block."""
+    """Oracle Hessian actions/s for a (k+p)-column block, from a bounded sample: the
+    linearisation point's set-up (2D: one sparse direct factorisation of K(m); 3D: none,
+    every solve is a Jacobi-preconditioned CG) + ncols_sample columns, extrapolated to the
+    full block."""
     from oracle.inverse import make_problem
     dr = W.draws(w)
     prob, m_true, _ = make_problem(w, dr)
@@ -105,8 +110,8 @@ def oracle_rate(w, ncols_sample, seconds_hint=20.0):
     s_full = w.k + w.p
     X = W.omega(w)
     t0 = time.perf_counter()
-    u = prob.forward(m)                       # factorises K(m)
-    t_fac = time.perf_counter() - t0
+    u = prob.forward(m)                       # 2D: factorises K(m); 3D: one CG solve
+    t_fac = time.perf_counter() - t0 if prob.solver == "direct" else 0.0
     cols = 0
     t1 = time.perf_counter()
     while cols < ncols_sample:
@@ -120,24 +125,26 @@ def oracle_rate(w, ncols_sample, seconds_hint=20.0):
     return s_full / block_time, cols, t_fac, per_col
 
 
-# workloads the oracle cannot sample in minutes: its set-up alone (a prior draw and the state,
-# each a sparse direct factorisation in 3D) did not finish in 15 minutes on 274,625 nodes
-ORACLE_OUT_OF_REACH = {
-    "cube3d": "the FP64 oracle's sparse direct factorisations at 274,625 nodes (3D) did not finish in 15 "
-              "minutes, so no bounded sample of this workload exists",
+ORACLE_SOLVES = {
+    "direct": "sparse direct solves (SuperLU), exact to rounding",
+    "cg": "Jacobi-preconditioned CG solves to relative residual 1e-13 (a sparse direct factorisation does not "
+          "finish in minutes on 3D meshes of this size)",
 }
 
 
+def host_cores():
+    return os.cpu_count() or 1
+
+
 def cpu_baseline_block(w):
-    if w.name in ORACLE_OUT_OF_REACH:
-        return {"value": None, "unit": "actions/s", "cores": 1, "kind": "oracle",
-                "sample": "not measured: " + ORACLE_OUT_OF_REACH[w.name]}
-    ncols = {"small2d": 30, "medium2d": 8}[w.name]
+    ncols = {"small2d": 30, "medium2d": 8, "cube3d": 1}[w.name]
     rate, cols, t_fac, per_col = oracle_rate(w, ncols)
-    return {"value": rate, "unit": "actions/s", "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 scipy oracle (sparse direct solves), one K(m) factorisation ({t_fac:.2f} s) + "
-                       f"{cols} of {w.k + w.p} columns ({per_col * 1e3:.1f} ms each), extrapolated to the "
-                       f"{w.k + w.p}-column block, 1 thread")}
+    kind = "cg" if w.dim == 3 else "direct"
+    setup = (f"one K(m) factorisation ({t_fac:.2f} s) + " if kind == "direct" else "")
+    return {"value": rate, "unit": "actions/s", "cores": 1, "host_cores": host_cores(), "kind": "oracle",
+            "sample": (f"FP64 numpy/scipy oracle ({ORACLE_SOLVES[kind]}), {setup}{cols} of {w.k + w.p} columns "
+                       f"({per_col:.2f} s each), extrapolated to the {w.k + w.p}-column block; 1 thread of "
+                       f"{host_cores()} host cores")}
 
 
 def oracle_batch_rate(ws, every=8, ncols=1):
@@ -180,24 +187,22 @@ def run_reference(args, rank, world):
             "config": {"workload": f"batch64: {len(ws)} independent 2D problems, one block of k+p=40 GN Hessian "
                                    f"actions per problem, FP64 CPU oracle with sparse direct solves",
                        "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": val, "unit": "actions/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": val, "unit": "actions/s", "cores": 1, "host_cores": host_cores(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "actions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}), flush=True)
         return
     w = W.WORKLOADS[args.workload]
-    if w.name in ORACLE_OUT_OF_REACH:
-        print(json.dumps({"impl": "reference", "metric": METRIC, "unit": "actions/s", "higher_is_better": True,
-                          "config": {"workload": workload_desc(w, "oracle")},
-                          "unavailable": ORACLE_OUT_OF_REACH[w.name]}), flush=True)
-        return
     from oracle.inverse import make_problem
     dr = W.draws(w)
     prob, m_true, _ = make_problem(w, dr)
     m = m_true
     X = W.omega(w)
-    s_ref = {"small2d": 10, "medium2d": 2}[w.name]
+    s_ref = {"small2d": 10, "medium2d": 2, "cube3d": 1}[w.name]
     u = prob.forward(m)
-    for i in range(args.warmup):
+    # the oracle keeps nothing between steps, so one warm-up step stands for any number
+    warm = min(args.warmup, 1) if prob.solver == "cg" else args.warmup
+    for i in range(warm):
         prob.hessian_misfit(m, u, X[:, :s_ref])
     t0 = time.perf_counter()
     for i in range(args.steps):
@@ -206,12 +211,16 @@ def run_reference(args, rank, world):
     val = args.steps * s_ref / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "actions/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "steps": args.steps, "warmup": warm, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(w, "oracle") + f"; reference arm: {s_ref} columns per step",
+        "config": {"workload": workload_desc(w, "oracle_" + prob.solver) + f"; reference arm: {s_ref} column(s) "
+                                                                            f"per step",
                    "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": val, "unit": "actions/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{s_ref} Hessian-action columns per step, K(m) factorised once in warm-up"},
+        "cpu_baseline": {"value": val, "unit": "actions/s", "cores": 1, "host_cores": host_cores(), "kind": "oracle",
+                         "sample": (f"{s_ref} Hessian-action column(s) per step, " +
+                                    ("K(m) factorised once before the warm-up" if prob.solver == "direct" else
+                                     "every solve a Jacobi-preconditioned CG to 1e-13") +
+                                    f"; 1 thread of {host_cores()} host cores")},
         "e2e": {"value": val, "unit": "actions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
@@ -361,7 +370,7 @@ def weak_scaling_value(t_local, units_per_rank, world, device="cpu"):
 
 def run_ours(args, rank, world):
     import torch
-    from paper_1909_03948_gb300 import Problem, kernel_launches
+    from paper_1909_03948_gb300 import Problem, algorithmic_bytes, kernel_launches
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -459,8 +468,10 @@ def run_ours(args, rank, world):
     clk = clocks.stop()
     t_total = sum(times)
     # ---- same K steps again with CUDA events around the level-0 kernels (roofline) ----
+    # (direct launches: the library also counts every launch's algorithmic bytes here)
     P.profile_enable(True)
     t_prof = 0.0
+    b0, lp0 = algorithmic_bytes(), kernel_launches()
     for _ in range(args.steps):
         flush.fill_(1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -471,6 +482,9 @@ def run_ours(args, rank, world):
         t_prof += e0.elapsed_time(e1) / 1e3
     prof = P.profile_read()
     P.profile_enable(False)
+    b1, lp1 = algorithmic_bytes(), kernel_launches()
+    step_bytes = {k: (b1[k] - b0[k]) / args.steps for k in b0}
+    launches_direct = lp1 - lp0
     value, t_total = weak_scaling_value(t_total, args.steps * s, world, dev)
     # ---- e2e through the C ABI with host buffers ----
     Xh = torch.empty((s, P.n), dtype=torch.float64).pin_memory()
@@ -530,6 +544,29 @@ def run_ours(args, rank, world):
                                       "to back come in steps of about 2 us, graph nodes do not)")},
                 "share_of_step": ms / 1e3 / t_prof,
                 "families": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
+        # fractions of the other two durations, beside the in-graph one
+        roof["frac_in_step_direct_launch"] = bpl / in_step_s / 1e9 / peak
+        if cold_us:
+            roof["frac_hbm_cold_replay"] = bpl / (cold_us * 1e-6) / 1e9 / peak
+        # working set of the inner solves: 5 FP32 blocks plus about 1.4 blocks for the coarser
+        # levels; while it fits in the 129 MB L2, kernels between flushes run from L2
+        ws = 6.4 * P.n * s * 4
+        roof["working_set_mb"] = ws / 1e6
+        roof["residency"] = ("L2-resident (the in-graph figure is an L2 replay, not an HBM one)"
+                             if ws < 120e6 else "spills L2 (HBM-bound)")
+        # step level: every launch's algorithmic bytes in one step over the timed step's duration
+        tot = sum(step_bytes.values())
+        ms_step = 1e3 * t_total / args.steps
+        roof["step"] = {
+            "achieved": tot / (ms_step * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": tot / (ms_step * 1e-3) / 1e9 / peak, "bytes_per_step": tot, "ms_per_step": ms_step,
+            "families": {k: {"bytes_per_step": v, "share_of_bytes": v / tot if tot else None}
+                         for k, v in step_bytes.items()},
+            "how": ("algorithmic bytes of every launch in a step (each array a kernel must read or write, once per "
+                    "launch; counted by the library on the direct-launch pass, which runs the same kernels and "
+                    "iterations as the graph-driven timed steps) over the timed steps' mean duration"),
+            "launches_per_step_direct": launches_direct / args.steps,
+            "launches_per_step_timed": launches / args.steps}
     if rank != 0:
         return
     if not args.no_plain:

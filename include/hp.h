@@ -465,6 +465,26 @@ const char *hp_status_string(int status);
 const char *hp_last_error(void);
 /* Number of this library's kernel launches since load (for launch accounting). */
 unsigned long long hp_kernel_launches(void);
+/* Of those, the launches of the TMA-tiled stencil kernels (2D tiles and the 3D
+ * z-marching kernel), so that a caller can tell which kernel form a solve ran. */
+unsigned long long hp_tiled_kernel_launches(void);
+/* Algorithmic DRAM bytes (every array a kernel must read or write, counted once per
+ * launch) of the kernels on the Hessian-action path since load, summed over direct
+ * launches only: launches recorded into CUDA graphs are not counted, so measure a
+ * step with profiling on (hp_profile_enable, which launches directly) and divide the
+ * difference by the step's duration for its bandwidth.  out (HOST) receives nfam
+ * cumulative totals, indexed by the families below (entries past the last family
+ * are 0).  Kernels counted: the stencil kernels on every level (row and tiled forms),
+ * the dense coarse solve, restriction and prolongation, the PCG vector updates and
+ * inner products, the FP64 refinement passes, C, C^T and the observation operator. */
+#define HP_BYTES_STENCIL0 0 /* stencil kernels on the finest level (PCG matvec, sweeps, residual) */
+#define HP_BYTES_STENCILC 1 /* stencil kernels on coarser levels and the dense coarse solve   */
+#define HP_BYTES_TRANSFER 2 /* restriction and prolongation                                  */
+#define HP_BYTES_VECTOR 3   /* PCG vector updates and inner products                         */
+#define HP_BYTES_REFINE 4   /* FP64 refinement: start, residual with norm, scaling, update   */
+#define HP_BYTES_CCT 5      /* C, C^T and the observation gather / scatter                   */
+#define HP_BYTES_FAMILIES 6
+int hp_algorithmic_bytes(double *out, int nfam);
 
 #ifdef __cplusplus
 }

@@ -7,8 +7,8 @@ package does not load the library; the first call does, and raises if it is
 missing.  ``warmstart`` generates training data for, and trains, the learned
 initial guess of the 2D stiffness solves (``UNet``).
 """
-from .hp import (Batch, Problem, UNet, HPError, lib, kernel_launches, philox_normals,  # noqa: F401
-                 EXPORTED, LIB_PATH)
+from .hp import (Batch, Problem, UNet, HPError, lib, kernel_launches, tiled_kernel_launches,  # noqa: F401
+                 algorithmic_bytes, philox_normals, EXPORTED, LIB_PATH)
 
-__all__ = ["Batch", "Problem", "UNet", "HPError", "lib", "kernel_launches", "philox_normals", "EXPORTED",
-           "LIB_PATH"]
+__all__ = ["Batch", "Problem", "UNet", "HPError", "lib", "kernel_launches", "tiled_kernel_launches",
+           "algorithmic_bytes", "philox_normals", "EXPORTED", "LIB_PATH"]

@@ -11,6 +11,7 @@ from __future__ import annotations
 import argparse
 import concurrent.futures as cf
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -57,8 +58,18 @@ def _compile(src, force, verbose, extra):
     return obj
 
 
+def _stamp() -> str:
+    """The machine and compiler the objects in _build/ were made by."""
+    r = subprocess.run([nvcc(), "--version"], capture_output=True, text=True)
+    return f"{platform.machine()}\n{r.stdout.strip().splitlines()[-1] if r.stdout.strip() else ''}\n"
+
+
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    # objects built on another machine or by another compiler are rebuilt
+    stamp_path, stamp = os.path.join(BUILD, "STAMP"), _stamp()
+    if not os.path.exists(stamp_path) or open(stamp_path).read() != stamp:
+        force = True
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, force, verbose, list(extra)), srcs))
@@ -69,6 +80,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, LIB)
+    with open(stamp_path, "w") as f:
+        f.write(stamp)
     return LIB
 
 

@@ -460,6 +460,12 @@ const char *hp_status_string(int s) {
 
 const char *hp_last_error(void) { return g_err.c_str(); }
 unsigned long long hp_kernel_launches(void) { return g_launches.load(); }
+unsigned long long hp_tiled_kernel_launches(void) { return g_tiled_launches.load(); }
+int hp_algorithmic_bytes(double *out, int nfam) {
+  if (!out || nfam < 0) return set_error(HP_ERR_INVALID, "hp_algorithmic_bytes: bad arguments");
+  for (int f = 0; f < nfam; ++f) out[f] = f < BYTES_FAMILIES ? (double)g_alg_bytes[f].load() : 0.0;
+  return HP_OK;
+}
 
 int hp_problem_create(const hp_problem_desc *d, hp_problem **out) {
   if (!d || !out) return set_error(HP_ERR_INVALID, "null argument");

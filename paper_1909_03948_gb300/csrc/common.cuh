@@ -143,10 +143,24 @@ __device__ __forceinline__ double block_sum(double v) {
 #include <atomic>
 namespace hp {
 extern std::atomic<unsigned long long> g_launches;
+extern std::atomic<unsigned long long> g_tiled_launches;  // TMA-tiled stencil kernels alone
 extern thread_local int tl_no_count;  // set while capturing graphs: launches count when the graph runs
 inline void count_launch(unsigned long long k = 1) {
   if (!tl_no_count) g_launches.fetch_add(k, std::memory_order_relaxed);
 }
+// Algorithmic DRAM bytes of the launches on the Hessian-action path (each array read or
+// written once per launch), by family (HP_BYTES_* in hp.h).  Only direct launches count:
+// launches recorded into a CUDA graph do not, so a caller measures per-step bytes on a
+// pass with graphs off (profiling on) and carries them over to the graph-driven steps,
+// which launch the same kernels.
+constexpr int BYTES_FAMILIES = 6;
+enum : int { BY_STENCIL0 = 0, BY_STENCILC = 1, BY_TRANSFER = 2, BY_VECTOR = 3, BY_REFINE = 4, BY_CCT = 5 };
+extern std::atomic<unsigned long long> g_alg_bytes[BYTES_FAMILIES];
+extern thread_local long tl_n0;  // finest-level node count of the solve being launched (0: none)
+inline void count_bytes(int fam, double bytes) {
+  if (!tl_no_count && bytes > 0.0) g_alg_bytes[fam].fetch_add((unsigned long long)(bytes + 0.5), std::memory_order_relaxed);
+}
+inline int level_family(long n) { return n == tl_n0 ? BY_STENCIL0 : BY_STENCILC; }
 constexpr int NT = 256;   // threads per block of the streaming kernels
 constexpr int NSM = 152;  // SMs of a GB300
 inline int blocks_for(long n, int s) {

@@ -852,6 +852,10 @@ void launch_C_apply_beta(hp_problem *P, const double *betaE, const double *X, lo
   else
     k_C_apply<3><<<grid, NT, 0, P->st>>>(P->lv[0].g, betaE, X, ldx, Y, ldy, scale, yb);
   count_launch();
+  {  // read X (and Y when yb != 0), write Y, the (2^{D+1} - 1) coefficients per node
+    const double nc = P->dim == 2 ? 7.0 : 15.0;
+    count_bytes(BY_CCT, 8.0 * (double)P->n * ((yb == 0.0 ? 2.0 : 3.0) * s + nc));
+  }
 }
 
 void launch_C_apply(hp_problem *P, const double *X, long ldx, double *Y, long ldy, int s, double scale) {
@@ -866,6 +870,10 @@ void launch_Ct_apply_beta(hp_problem *P, const double *beta_c, const double *W, 
   else
     k_Ct_apply<3><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, beta_c, W, ldw, Y, ldy, scale, beta);
   count_launch();
+  {  // read W (and Y when beta != 0), write Y, e^m and the coefficients per node
+    const double nc = P->dim == 2 ? 7.0 : 15.0;
+    count_bytes(BY_CCT, 8.0 * (double)P->n * ((beta == 0.0 ? 2.0 : 3.0) * s + nc + 1.0));
+  }
 }
 
 void launch_Ct_apply(hp_problem *P, const double *W, long ldw, double *Y, long ldy, int s, double scale,
@@ -908,6 +916,7 @@ void launch_obs_gather(hp_problem *P, const double *X, long ldx, double *Yq, int
   dim3 grid((P->nobs + 127) / 128, s);
   k_obs_gather<<<grid, 128, 0, P->st>>>(P->obs_node, P->obs_w, P->nobs, P->dim + 1, X, ldx, Yq);
   count_launch();
+  count_bytes(BY_CCT, 8.0 * (double)P->nobs * s * (P->dim + 2));
 }
 
 void launch_obs_scatter(hp_problem *P, const double *Yq, double *X, long ldx, int s, double scale) {
@@ -915,6 +924,7 @@ void launch_obs_scatter(hp_problem *P, const double *Yq, double *X, long ldx, in
   k_obs_scatter<<<grid, NT, 0, P->st>>>(P->n, P->bt_row, P->bt_ptr, P->bt_ent, P->obs_w, P->nobs, P->dim + 1,
                                         Yq, X, ldx, scale);
   count_launch();
+  count_bytes(BY_CCT, 8.0 * ((double)P->n + (double)P->nobs) * s);
 }
 
 // ---------------------------------------------------------------------------

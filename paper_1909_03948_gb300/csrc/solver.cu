@@ -1242,6 +1242,7 @@ static bool tile_launch(const GridDesc &g, const Stencil<float> &S, const float 
   const int ntx = (g.np - 1) / TILE_X, nty = (g.np - 1) / TILE_Y;
   k_st_tile<MODE><<<dim3(ntx * nty, ng), TL_NT, TL_SMEM, st>>>(mx, mr, mc, g, ntx, nty, Y, gy, s, omega, omega2, fin);
   count_launch();
+  if (!tl_no_count) g_tiled_launches.fetch_add(1, std::memory_order_relaxed);
   if (MODE == M_APPLY_DOT || MODE == M_JACOBI_DOT) dot_finalize(fin, ntx * nty, s, st);
   return true;
 }
@@ -1336,13 +1337,24 @@ static bool tile3_launch(const GridDesc &g, const Stencil<float> &S, const float
   k_st_tile3<MODE><<<dim3(ntx * nty * nzs, ng), TL3_NT, TL3_SMEM, st>>>(
       mx, mr, mc, mz, g, ntx, nty, nzs, X, gx, S.pk, S.pk + 4 * g.n, Y, gy, s, omega, omega2, fin);
   count_launch();
+  if (!tl_no_count) g_tiled_launches.fetch_add(1, std::memory_order_relaxed);
   if (MODE == M_APPLY_DOT || MODE == M_JACOBI_DOT) dot_finalize(fin, ntx * nty * nzs, s, st);
   return true;
+}
+
+// Algorithmic bytes of one stencil launch: the vectors it reads and writes once (x and y;
+// b as well for the residual and sweep modes) and the per-node coefficients (the diagonal
+// and the forward couplings; the inverse diagonal as well for the sweeps).
+template <typename T, int MODE> static double st_bytes(const GridDesc &g, const Stencil<T> &S, int s) {
+  const bool sweep = MODE == M_JACOBI || MODE == M_JACOBI_DOT || MODE == M_JAC2;
+  const bool two = MODE == M_APPLY || MODE == M_APPLY_DOT || MODE == M_JAC2;
+  return (double)sizeof(T) * (double)g.n * ((two ? 2.0 : 3.0) * s + (sweep ? 2.0 : 1.0) + S.nf);
 }
 
 template <typename T, int VW, int MODE>
 static void st_launch(const GridDesc &g, const Stencil<T> &S, const T *X, long gx, const T *B, long gb, T *Y, long gy,
                       int s, T omega, const Fin &fin, cudaStream_t st, T omega2 = T(0)) {
+  count_bytes(sizeof(T) == 8 && MODE == M_RESID_DOT ? BY_REFINE : level_family(g.n), st_bytes<T, MODE>(g, S, s));
   if constexpr (sizeof(T) == 4 && VW == 4 && MODE != M_RESID_DOT) {
     if (tl_tma && S.pk && !S.full && tile_grid(g) &&
         tile_launch<MODE>(g, S, X, gx, B, gb, Y, gy, s, omega, omega2, fin, st))
@@ -2108,6 +2120,7 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
     const dim3 gr = nodegrid(P->n, ng);
     k_jacobi0<T, VW><<<gr, NB, 0, st>>>(P->n, S.invdiag, r0, gs0, z0, T(1), s, fin, 1);
     count_launch();
+    count_bytes(BY_STENCIL0, (double)sizeof(T) * (double)P->n * (2.0 * s + 1.0));
     dot_finalize(fin, gr.x, s, st);
     return;
   }
@@ -2117,6 +2130,7 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
     k_coarse_apply<T, VW><<<dim3((nc + 31) / 32, ng), 256, sizeof(T) * nc * VW, st>>>(coarse_inv<T>(P, op), nc, r0,
                                                                                        gs0, z0, gs0);
     count_launch();
+    count_bytes(BY_STENCILC, (double)sizeof(T) * ((double)nc * nc + 2.0 * nc * s));
     return;
   }
   const T *rl[HP_MAXL];
@@ -2158,6 +2172,7 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
     } else {
       k_jacobi0<T, VW><<<nodegrid(g.n, ng), NB, 0, st>>>(g.n, S.invdiag, rl[l], gsl[l], c, w[0], s, nofin, 0);
       count_launch();
+      count_bytes(level_family(g.n), (double)sizeof(T) * (double)g.n * (2.0 * s + 1.0));
     }
     prof_stop(P, pr);
     for (int k = 2; k < nu; ++k) {
@@ -2184,6 +2199,7 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
           k_resid_restrict<T, VW, 3, false><<<gr, NB, 0, st>>>(g, gc, S.diag, S.c, c, rl[l], gsl[l], rc, gsl[l + 1], zd);
       }
       count_launch();
+      count_bytes(BY_TRANSFER, (double)sizeof(T) * ((2.0 * s + 1.0 + S.nf) * (double)g.n + (double)s * gc.n));
     } else {
       pr = prof_start(P, l == 0 ? PROF_RESID_MG : -1);
       st_launch<T, VW, M_RESID>(g, S, c, gsl[l], rl[l], gsl[l], o, gsl[l], s, om, nofin, st);
@@ -2193,6 +2209,7 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
       else
         k_restrict<T, VW, 3><<<rowgrid(gc, ng), NB, 0, st>>>(g, gc, o, gsl[l], rc, gsl[l + 1], op == OP_K);
       count_launch();
+      count_bytes(BY_TRANSFER, (double)sizeof(T) * s * ((double)g.n + (double)gc.n));
     }
     cur[l] = c;
     oth[l] = o;
@@ -2214,6 +2231,7 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
     k_coarse_apply<T, VW><<<dim3((nc + 31) / 32, ng), 256, sizeof(T) * nc * VW, st>>>(coarse_inv<T>(P, op), nc,
                                                                                        rl[lc], gsl[lc], ea[lc], gsl[lc]);
     count_launch();
+    count_bytes(BY_STENCILC, (double)sizeof(T) * ((double)nc * nc + 2.0 * nc * s));
     cur[lc] = ea[lc];
   }
   for (int l = std::min(L, l0) - 2 + (l0 < L ? 1 : 0); l >= 0; --l) {
@@ -2244,6 +2262,7 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
                                                               o, gsl[l], w[nu - 1]);
       }
       count_launch();
+      count_bytes(BY_TRANSFER, (double)sizeof(T) * ((3.0 * s + 2.0 + S.nf) * (double)g.n + (double)s * gc.n));
       std::swap(c, o);
       k0 = 1;
     } else {
@@ -2252,6 +2271,7 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
       else
         k_prolong_add<T, VW, 3><<<rowgrid(g, ng), NB, 0, st>>>(g, gc, cur[l + 1], gsl[l + 1], cur[l], gsl[l]);
       count_launch();
+      count_bytes(BY_TRANSFER, (double)sizeof(T) * s * (2.0 * (double)g.n + (double)gc.n));
     }
     for (int k = k0; k < nu; ++k) {
       const int pr = prof_start(P, l == 0 ? PROF_SMOOTH : -1);
@@ -2284,6 +2304,7 @@ static void pcg_init(hp_problem *P, OpKind op, int s, cudaGraphConditionalHandle
   const dim3 gr = nodegrid(P->n, ng);
   k_dot<T, VW><<<gr, NB, 0, st>>>(P->n, gs, r, r, s, make_fin(P, FIN_INIT));
   dot_finalize(make_fin(P, FIN_INIT), gr.x, s, st);
+  count_bytes(BY_VECTOR, (double)sizeof(T) * (double)P->n * s);
   k_pcg_cond<<<1, 256, 0, st>>>(P->sc.active.as<int>(), s, P->sc.iter.as<int>(), maxit, 0, h, use_handle);
   count_launch(2);
 }
@@ -2307,10 +2328,12 @@ static void pcg_body(hp_problem *P, OpKind op, int s, double tol2, cudaGraphCond
     const dim3 gr = nodegrid(n, ng);
     k_dot<T, VW><<<gr, NB, 0, st>>>(n, gs, r, z, s, make_fin(P, FIN_BETA));
     count_launch();
+    count_bytes(BY_VECTOR, (double)sizeof(T) * (double)n * 2.0 * s);
     dot_finalize(make_fin(P, FIN_BETA), gr.x, s, st);
   }
   k_p_update<T, VW><<<nodegrid(n, ng), NB, 0, st>>>(n, gs, z, p, P->sc.beta.as<double>());
   count_launch();
+  count_bytes(BY_VECTOR, (double)sizeof(T) * (double)n * 3.0 * s);
   pr = prof_start(P, PROF_MATVEC);
   st_launch<T, VW, M_APPLY_DOT>(g0, S0, p, gs, nullptr, 0, q, gs, s, T(0), make_fin(P, FIN_ALPHA), st);
   prof_stop(P, pr);
@@ -2318,6 +2341,7 @@ static void pcg_body(hp_problem *P, OpKind op, int s, double tol2, cudaGraphCond
   const dim3 gu = nodegrid(n, ng);
   k_cg_update<T, VW><<<gu, NB, 0, st>>>(n, gs, p, q, x, r, P->sc.alpha.as<double>(), s, make_fin(P, FIN_RR, tol2));
   dot_finalize(make_fin(P, FIN_RR, tol2), gu.x, s, st);
+  count_bytes(BY_VECTOR, (double)sizeof(T) * (double)n * 6.0 * s);
   prof_stop(P, pr);
   k_pcg_cond<<<1, 256, 0, st>>>(P->sc.active.as<int>(), s, P->sc.iter.as<int>(), maxit, 1, h, use_handle);
   count_launch(2);
@@ -2703,6 +2727,7 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
     k_to_inner<T, VW><<<nodegrid(n, ng), NB, 0, st>>>(n, rsrc, ld64, P->sc.scale.as<double>(), s,
                                                       W.r.template as<T>(), gs);
     count_launch();
+    count_bytes(BY_REFINE, (8.0 + sizeof(T)) * (double)n * s);  // read the FP64 residual, write the inner one
     int its = 0;
     // a stalled inner solve still reduces the residual; other failures end the solve
     const int prc = pcg<T, VW>(P, op, s, tol_in, P->max_iter, &its);
@@ -2712,6 +2737,7 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
     k_accum<T, VW><<<nodegrid(n, ng), NB, 0, st>>>(n, W.x.template as<T>(), gs, P->sc.iscale.as<double>(), s, X,
                                                    ldx);
     count_launch();
+    count_bytes(BY_REFINE, (16.0 + sizeof(T)) * (double)n * s);  // read the correction, read and write x
     HP_TRY(residual64(P, op, b64, ld64, X, ldx, r64, ld64, s));
   }
   if (stats) {
@@ -2743,6 +2769,7 @@ int solve_block(hp_problem *P, OpKind op, const double *B, long ldb, double *X, 
   if (s <= 0) return 0;
   tl_max_blocks = P->max_blocks;
   tl_tma = P->tma_tiles;
+  tl_n0 = P->n;
   const int w = (P->col_chunk > 0 && P->col_chunk < s) ? P->col_chunk : s;
   for (int c0 = 0; c0 < s; c0 += w) {
     const int cs = std::min(w, s - c0);
@@ -2782,6 +2809,7 @@ extern "C" int hp_replay_kernel(hp_problem *P, int family, int reps, void *flush
   const long gs = W.ldn * VW;
   tl_max_blocks = P->max_blocks;
   tl_tma = P->tma_tiles;
+  tl_n0 = P->n;
   const GridDesc &g = P->lv[0].g;
   const Stencil<float> &S = P->lv[0].K32;
   const float om = (float)P->omega;
@@ -2845,6 +2873,7 @@ extern "C" int hp_replay_kernel_graph(hp_problem *P, int family, int reps, doubl
   const long gs = W.ldn * 4;
   tl_max_blocks = P->max_blocks;
   tl_tma = P->tma_tiles;
+  tl_n0 = P->n;
   const GridDesc &g = P->lv[0].g;
   const Stencil<float> &S = P->lv[0].K32;
   const float om = (float)P->omega;

@@ -7,6 +7,9 @@
 namespace hp {
 
 std::atomic<unsigned long long> g_launches{0};
+std::atomic<unsigned long long> g_tiled_launches{0};
+std::atomic<unsigned long long> g_alg_bytes[BYTES_FAMILIES] = {};
+thread_local long tl_n0 = 0;
 thread_local int tl_no_count = 0;
 
 int DBuf::ensure(size_t b) {
@@ -121,6 +124,7 @@ int ir_start(hp_problem *P, const double *B, long ldb, double *B0, long ld0, dou
   k_ir_start<<<dim3(nb, s), NT, 0, P->st>>>(B, ldb, B0, ld0, X, ldx, n, face, part);
   k_dot_final<<<s, NT, 0, P->st>>>(part, nb, bb_dev, rr_dev);
   count_launch(2);
+  count_bytes(BY_REFINE, 3.0 * 8.0 * (double)n * s);  // read B, write B0 and X
   return 0;
 }
 

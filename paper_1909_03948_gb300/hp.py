@@ -153,6 +153,8 @@ _SIGS = {
     "hp_status_string": (C.c_char_p, [_I]),
     "hp_last_error": (C.c_char_p, []),
     "hp_kernel_launches": (C.c_ulonglong, []),
+    "hp_tiled_kernel_launches": (C.c_ulonglong, []),
+    "hp_algorithmic_bytes": (_I, [C.POINTER(C.c_double), _I]),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -175,6 +177,22 @@ def lib():
 
 def kernel_launches() -> int:
     return int(lib().hp_kernel_launches())
+
+
+def tiled_kernel_launches() -> int:
+    """Launches of the TMA-tiled stencil kernels since the library was loaded."""
+    return int(lib().hp_tiled_kernel_launches())
+
+
+BYTES_FAMILIES = ("stencil_level0", "stencil_coarse", "transfer", "vector", "refine64", "C_Ct_obs")
+
+
+def algorithmic_bytes() -> dict:
+    """Cumulative algorithmic DRAM bytes of direct launches since load, by kernel family
+    (launches inside CUDA graphs are not counted: measure with profiling on)."""
+    out = (C.c_double * len(BYTES_FAMILIES))()
+    _check(lib().hp_algorithmic_bytes(out, len(BYTES_FAMILIES)), "hp_algorithmic_bytes")
+    return dict(zip(BYTES_FAMILIES, [float(v) for v in out]))
 
 
 def _check(code, where):

@@ -49,6 +49,25 @@ def test_newton_map_matches_oracle(small2d, precision):
     assert abs(st["J"] - orc.cost(ref)[0]) <= 1e-8 * abs(st["J"])
 
 
+@pytest.mark.parametrize("precision", ["fp32_ir", "fp64"])
+def test_3d_newton_map_matches_oracle(precision):
+    """Newton-CG (Algorithm 1) on a 16^3 Kuhn-tetrahedron problem (4,913 nodes, 60
+    observations, gamma 0.05, delta 0.5 as the 3D workload) to relative gradient 1e-9, PDE
+    solves to 1e-12: the MAP point within 1e-6 of the oracle's, and the same final cost."""
+    w = W.make_workload(3, 16, 60, gamma=0.05, seed=W.SEED_BASE + 89)
+    orc, m_true, _ = make_problem(w, W.draws(w))
+    ref = A.newton_cg(orc, rel_tol=1e-9)
+    assert ref.converged
+    P = _gpu_problem(orc, w, rtol=1e-12, precision=precision)
+    try:
+        m, st = P.newton_cg_map(rel_tol=1e-9)
+    finally:
+        P.close()
+    assert st["converged"], st
+    assert np.linalg.norm(m.cpu().numpy() - ref.m) <= 1e-6 * np.linalg.norm(ref.m)
+    assert abs(st["J"] - orc.cost(ref.m)[0]) <= 1e-8 * abs(st["J"])
+
+
 def test_full_newton_map_matches_oracle(small2d):
     """Newton-CG with the full Hessian (Steihaug exit on negative curvature) stops at relative
     gradient 1e-9 near the oracle's full-Newton MAP point, in the same number of Newton
