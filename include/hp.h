@@ -225,23 +225,24 @@ int hp_batch_hessian_apply(hp_batch *B, const double *const *X, const int *ldx, 
 /* ---- solve without device allocation ---------------------------------------
  * The paper has no counterpart to this entry point: it serves callers that
  * cannot allocate device memory when they solve.  hp_mass_solve grows the
- * problem's workspace with cudaMalloc on first use; a caller that is capturing
- * a stream into a CUDA graph cannot allocate (allocation is not capturable), and
- * an application that reserves all device memory at start-up may forbid later
- * allocation.  hp_mass_solve_noalloc computes the same X = M^{-1} B (FP64
- * diagonally preconditioned CG, per-column relative residual
+ * problem's workspace with cudaMalloc on first use; an application that reserves
+ * all device memory at start-up, or must keep its device footprint fixed while it
+ * runs, cannot allow that.  hp_mass_solve_noalloc computes the same X = M^{-1} B
+ * (FP64 diagonally preconditioned CG, per-column relative residual
  * min(rtol, 1e-10)) using one fixed file-scope device array as scratch, and
  * calls no cudaMalloc / cudaFree or allocating library routine.
  *  - Limits: nrhs <= HP_NOALLOC_MAX_COLS and n * nrhs <= HP_NOALLOC_MAX_ENTRIES,
- *    else HP_ERR_INVALID.  The scratch array (about 11 MB) lives on every GPU that
- *    loads the library until the process exits.
+ *    else HP_ERR_INVALID.  The scratch array (4 * HP_NOALLOC_MAX_ENTRIES doubles
+ *    plus per-column partials, about 8.5 MB) lives on every GPU that loads the
+ *    library until the process exits.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    (cudaGetSymbolAddress).
  *  - All calls share the one array: calls that overlap on the GPU (other streams,
  *    other threads, other problems) race and must be serialised by the caller.
  *    Each call re-initialises what it reads, so no state carries over.
  *  - The call synchronises the problem's stream once per CG iteration (it reads
- *    the per-column convergence flags into a host array). */
+ *    the per-column convergence flags into a host array), so it cannot be
+ *    recorded into a CUDA graph. */
 #define HP_NOALLOC_MAX_COLS 64
 #define HP_NOALLOC_MAX_ENTRIES 262144
 int hp_mass_solve_noalloc(hp_problem *P, const double *B, int ldb, double *X, int ldx, int nrhs,
@@ -345,6 +346,14 @@ typedef struct {
                       steps separated by block barriers only (takes precedence over
                       fuse_from); the result equals the per-level kernels' bit for bit.
                       0: off */
+  int refine_df;   /* arithmetic of the FP64 iterative refinement around FP32 inner solves
+                      (the residual b - K x with its norm, the scaling into the inner
+                      precision and the update x += d): 0 (default) FP64 instructions; 1
+                      double-float arithmetic (pairs of floats, about 48 significand
+                      bits: compensated products and sums on the FP32 pipe, FP64 data
+                      converted by bit manipulation) for solve tolerances >= 1e-9, FP64
+                      below; 2 double-float at every tolerance.  The data stay FP64 in
+                      memory either way. */
 } hp_tuning;
 int hp_set_tuning(hp_problem *P, const hp_tuning *t);
 int hp_get_tuning(const hp_problem *P, hp_tuning *t);
@@ -465,8 +474,10 @@ const char *hp_status_string(int status);
 const char *hp_last_error(void);
 /* Number of this library's kernel launches since load (for launch accounting). */
 unsigned long long hp_kernel_launches(void);
-/* Of those, the launches of the TMA-tiled stencil kernels (2D tiles and the 3D
- * z-marching kernel), so that a caller can tell which kernel form a solve ran. */
+/* Launches of the TMA-tiled stencil kernels (2D tiles and the 3D z-marching kernel)
+ * made directly, so that a caller can tell which kernel form a solve ran.  Kernels
+ * recorded into or replayed from CUDA graphs are not counted: with profiling on
+ * (hp_profile_enable) every kernel is launched directly. */
 unsigned long long hp_tiled_kernel_launches(void);
 /* Algorithmic DRAM bytes (every array a kernel must read or write, counted once per
  * launch) of the kernels on the Hessian-action path since load, summed over direct

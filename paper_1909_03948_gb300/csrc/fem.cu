@@ -30,6 +30,7 @@
 #include <mutex>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace hp {
@@ -831,6 +832,101 @@ __global__ void k_Ct_apply(GridDesc g, const double *__restrict__ E, const doubl
   }
 }
 
+// The same two stencils in double-float arithmetic on the FP32 pipe (FP64 data converted
+// by bit manipulation, the products summed by the compensated Dot2 scheme): four columns
+// per thread share the converted coefficients.  The result's error is about 2^-47 of the
+// sum of the terms' magnitudes, far below the solve tolerances these are used with; the
+// final scaling (and the accumulation into Y when yb != 0) stays in FP64, one or two
+// operations per element.
+template <int D>
+__global__ void __launch_bounds__(NT, 3) k_C_apply_df(GridDesc g, const double *__restrict__ betaE, const double *__restrict__ X, long ldx,
+                             double *__restrict__ Y, long ldy, int s, double scale, double yb) {
+  constexpr int NC = (1 << (D + 1)) - 1;
+  const int grp = blockIdx.y;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
+    int v[3];
+    node_coords<D>(g, i, v);
+    dfl cq[NC];
+    int oq[NC];  // offsets of the neighbours (|offset| < n fits in an int)
+    bool okq[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      int sg;
+      const int m = coff_mask<D>(q, &sg);
+      okq[q] = q == 0 || shift_ok<D>(g, v, m, sg);
+      oq[q] = q == 0 ? 0 : sg * (int)mask_offset(g, m);
+      cq[q] = okq[q] ? d2df(betaE[(long)q * g.n + i]) : dfl{0.f, 0.f};
+    }
+    // four columns term by term: four independent compensated sums (columns past s
+    // repeat the last column and are not stored)
+    const double *xj[4];
+    Dot2 a[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) xj[j] = X + ldx * min(grp * 4 + j, s - 1);
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+      if (okq[q])
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[j].fma(cq[q], d2df(xj[j][i + oq[q]]));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int col = grp * 4 + j;
+      if (col < s) {
+        const double val = scale * df2d(a[j].result());
+        Y[ldy * col + i] = yb == 0.0 ? val : val + yb * Y[ldy * col + i];
+      }
+    }
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(NT, 3) k_Ct_apply_df(GridDesc g, const double *__restrict__ E, const double *__restrict__ beta,
+                              const double *__restrict__ W, long ldw, double *__restrict__ Y, long ldy, int s,
+                              double scale, double yb) {
+  constexpr int NC = (1 << (D + 1)) - 1;
+  const int grp = blockIdx.y;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
+    int v[3];
+    node_coords<D>(g, i, v);
+    dfl cq[NC];
+    int oq[NC];  // the row r whose offset q points at node i is r = i + oq
+    bool okq[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      int sg;
+      const int m = coff_mask<D>(q, &sg);
+      okq[q] = q == 0 || shift_ok<D>(g, v, m, -sg);
+      oq[q] = q == 0 ? 0 : -sg * (int)mask_offset(g, m);
+      cq[q] = okq[q] ? d2df(beta[(long)q * g.n + i + oq[q]]) : dfl{0.f, 0.f};
+    }
+    const dfl e = d2df(E[i]);
+    const double *wj[4];
+    Dot2 a[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) wj[j] = W + ldw * min(grp * 4 + j, s - 1);
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+      if (okq[q])
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[j].fma(cq[q], d2df(wj[j][i + oq[q]]));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int col = grp * 4 + j;
+      if (col < s) {
+        Dot2 b;  // e^{m_i} times the sum, as a double-float product
+        b.fma(e, a[j].result());
+        const double val = scale * df2d(b.result());
+        Y[ldy * col + i] = yb == 0.0 ? val : val + yb * Y[ldy * col + i];
+      }
+    }
+  }
+}
+
+// double-float C and C^T at the solve tolerances where the refinement runs in double-float
+static bool cct_df(const hp_problem *P) {
+  return P->precision == HP_FP32_IR && (P->refine_df == 2 || (P->refine_df == 1 && P->rtol >= 1e-9));
+}
+
 void launch_build_C_from(hp_problem *P, const double *w, double *beta, double *betaE) {
   if (P->dim == 2) {
     k_build_C<2><<<grid_blocks(P->n), 256, 0, P->st>>>(P->lv[0].g, w, beta);
@@ -846,6 +942,18 @@ void launch_build_C(hp_problem *P) { launch_build_C_from(P, P->u, P->Cbeta, P->C
 
 void launch_C_apply_beta(hp_problem *P, const double *betaE, const double *X, long ldx, double *Y, long ldy, int s,
                          double scale, double yb) {
+  if (cct_df(P)) {
+    const int ng = (s + 3) / 4;
+    dim3 gd(blocks_for(P->n, ng), ng);
+    if (P->dim == 2)
+      k_C_apply_df<2><<<gd, NT, 0, P->st>>>(P->lv[0].g, betaE, X, ldx, Y, ldy, s, scale, yb);
+    else
+      k_C_apply_df<3><<<gd, NT, 0, P->st>>>(P->lv[0].g, betaE, X, ldx, Y, ldy, s, scale, yb);
+    count_launch();
+    const double nc = P->dim == 2 ? 7.0 : 15.0;
+    count_bytes(BY_CCT, 8.0 * (double)P->n * ((yb == 0.0 ? 2.0 : 3.0) * s + nc));
+    return;
+  }
   dim3 grid(blocks_for(P->n, s), s);
   if (P->dim == 2)
     k_C_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, betaE, X, ldx, Y, ldy, scale, yb);
@@ -864,6 +972,18 @@ void launch_C_apply(hp_problem *P, const double *X, long ldx, double *Y, long ld
 
 void launch_Ct_apply_beta(hp_problem *P, const double *beta_c, const double *W, long ldw, double *Y, long ldy, int s,
                           double scale, double beta) {
+  if (cct_df(P)) {
+    const int ng = (s + 3) / 4;
+    dim3 gd(blocks_for(P->n, ng), ng);
+    if (P->dim == 2)
+      k_Ct_apply_df<2><<<gd, NT, 0, P->st>>>(P->lv[0].g, P->E, beta_c, W, ldw, Y, ldy, s, scale, beta);
+    else
+      k_Ct_apply_df<3><<<gd, NT, 0, P->st>>>(P->lv[0].g, P->E, beta_c, W, ldw, Y, ldy, s, scale, beta);
+    count_launch();
+    const double nc = P->dim == 2 ? 7.0 : 15.0;
+    count_bytes(BY_CCT, 8.0 * (double)P->n * ((beta == 0.0 ? 2.0 : 3.0) * s + nc + 1.0));
+    return;
+  }
   dim3 grid(blocks_for(P->n, s), s);
   if (P->dim == 2)
     k_Ct_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, beta_c, W, ldw, Y, ldy, scale, beta);

@@ -142,6 +142,8 @@ struct hp_problem {
   double cheb_alpha = 10.0;     // Chebyshev interval [lmax / alpha, lmax]             (tuning)
   int tma_tiles = 0;            // 2D stiffness levels as TMA-tiled stencil kernels       (tuning)
   int smem_tail = 0;            // coarse V-cycle levels in one shared-memory CTA per group (tuning)
+  int refine_df = 0;            // FP64 refinement arithmetic in double-float on the FP32 pipe:
+                                // 0 never, 1 for tolerances >= DF_MIN_RTOL, 2 always (tuning)
   cudaStream_t st = nullptr;
   cudaStream_t cap = nullptr;   // private stream used to capture CUDA graphs
   bool use_graphs = true;       // inner PCG loops as graphs with a device-side while node

@@ -2,11 +2,11 @@
 // without any device allocation.
 //
 // hp_mass_solve grows the problem's workspace on first use (cudaMalloc).  Some
-// callers cannot allocate at solve time: code running while a stream is being
-// captured into a CUDA graph (allocation is not a capturable operation), or a
-// host application that pre-reserves all device memory and forbids allocation
-// after start-up.  This variant keeps its temporaries in one file-scope device
-// array of fixed size instead.
+// callers cannot allocate at solve time: a host application that reserves all
+// device memory at start-up and forbids allocation afterwards, or one that must
+// not change the device's memory footprint while it runs.  This variant keeps its
+// temporaries in one file-scope device array of fixed size instead (about 8.5 MB:
+// four vectors of HP_NOALLOC_MAX_ENTRIES doubles plus per-column partials).
 //
 // Method: FP64 conjugate gradients on M preconditioned by diag(M), per-column
 // stopping at |r| <= tol |b| with tol = min(problem rtol, 1e-10) and at most
@@ -33,9 +33,8 @@ static __device__ __align__(256) double g_na_scratch[kNaSize];
 static std::mutex g_na_mutex;
 static double *g_na_ptr[256] = {};  // device address of g_na_scratch, per device
 
-// Device address of the scratch array on the current device.  The first call on
-// a device resolves it with cudaGetSymbolAddress (which must not run while the
-// stream is being captured).
+// Device address of the scratch array on the current device, resolved with
+// cudaGetSymbolAddress by the first call on that device.
 static int na_scratch(double **out) {
   int dev = 0;
   HP_CUDA(cudaGetDevice(&dev));

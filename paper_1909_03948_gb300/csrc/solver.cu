@@ -28,6 +28,7 @@
 
 #include <cuda.h>
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace hp {
@@ -349,7 +350,12 @@ __global__ void __launch_bounds__(TL_NT) k_st_tile(const __grid_constant__ CUten
     tma_load_2d(smem_u32(cs), &mc, 4 * (x0 - 1), y0 - 1, bar);
   }
   if (!__syncthreads_and(mbar_wait0(bar))) {  // every thread leaves together if any wait ran out
-    if (threadIdx.x == 0) atomicExch(&g_tile_timeout, 1);
+    // thread 0 raises the flag and waits once more (again bounded) for the copies it issued,
+    // so that the CTA's shared memory is not released with bulk copies still landing in it
+    if (threadIdx.x == 0) {
+      atomicExch(&g_tile_timeout, 1);
+      (void)mbar_wait0(bar);
+    }
     return;
   }
   PK acc = PK::zero();
@@ -507,6 +513,7 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
     for (int q = zb; q <= zb + 1 && q <= ze; ++q) issue(q);
   PK acc = PK::zero();
   bool ok = true;
+  int p_fail = ze;  // the plane whose wait ran out (planes up to p_fail + 2 may have copies in flight)
   // Each thread keeps its nodes (t = threadIdx.x + j * TL3_NT) for the whole march, so x at
   // planes p - 1 and p, and c_z and 1/diag at p - 1, rotate through registers: per node and
   // plane only x at p + 1 and the xy neighbours come from shared memory.
@@ -534,6 +541,7 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
     ok = ready(p) && ready(p + 1);
     if (!__syncthreads_and(ok)) {  // every thread leaves together if any wait ran out
       ok = false;
+      p_fail = p;
       break;
     }
     const unsigned char *sm_0 = sm + ((p - zb) % TL3_NS) * TL3_SLOT;       // plane p
@@ -614,7 +622,13 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
     }
   }
   if (!ok) {
-    if (threadIdx.x == 0) atomicExch(&g_tile_timeout, 1);
+    // thread 0 raises the flag and waits once more (each wait bounded) for the planes it may
+    // still have copies in flight for, so that the CTA does not leave with bulk copies
+    // landing in shared memory that the next CTA on the SM receives
+    if (threadIdx.x == 0) {
+      atomicExch(&g_tile_timeout, 1);
+      for (int q = p_fail; q <= p_fail + 2 && q <= ze; ++q) (void)ready(q);
+    }
     return;
   }
   if (DOT) dot_partial<float, 4>(acc, fin.part, grp, s, tile, ntx * nty * nzs);
@@ -952,17 +966,33 @@ __global__ void __launch_bounds__(NB) k_dot(long n, long gs, const T *__restrict
 }
 
 // r_T (grouped) = scale * r64 (column-major); columns >= s and converged ones are 0
-template <typename T, int VW>
+// One element of the inner right-hand side: scale * r.  In double-float mode (DF, FP32
+// inner solves only) r's leading 24 bits times the float scale, on the FP32 pipe: the
+// inner solve sees its right-hand side to FP32 precision either way.
+template <typename T, bool DF>
+__device__ __forceinline__ T inner_value(double r, double scale, float scale_f) {
+  if constexpr (DF) return d2df(r).hi * scale_f;
+  else return (T)(scale * r);
+}
+
+template <typename T, int VW, bool DF>
 __global__ void __launch_bounds__(NB) k_to_inner(long n, const double *__restrict__ R, long ldr,
                                                  const double *__restrict__ scale, int s, T *__restrict__ rt, long gs) {
   using PK = Pack<T, VW>;
   const int grp = blockIdx.y;
+  double sc[VW];
+  float scf[VW];
+#pragma unroll
+  for (int q = 0; q < VW; ++q) {
+    sc[q] = grp * VW + q < s ? scale[grp * VW + q] : 0.0;
+    scf[q] = (float)sc[q];
+  }
   for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
     PK o;
 #pragma unroll
     for (int q = 0; q < VW; ++q) {
       const int col = grp * VW + q;
-      o.v[q] = col < s ? (T)(scale[col] * R[ldr * col + i]) : T(0);
+      o.v[q] = col < s ? inner_value<T, DF>(R[ldr * col + i], sc[q], scf[q]) : T(0);
     }
     o.st(rt + grp * gs + i * VW);
   }
@@ -970,7 +1000,7 @@ __global__ void __launch_bounds__(NB) k_to_inner(long n, const double *__restric
 
 // The same scaling inside a graph-driven refinement: the first step (ctl->outer == 1,
 // counted before the step runs) starts from x = 0, so its residual is b0 itself.
-template <typename T, int VW>
+template <typename T, int VW, bool DF>
 __global__ void __launch_bounds__(NB) k_to_inner_ctl(long n, const double *__restrict__ B0,
                                                      const double *__restrict__ R, long ldr,
                                                      const RefineCtl *__restrict__ ctl,
@@ -979,12 +1009,19 @@ __global__ void __launch_bounds__(NB) k_to_inner_ctl(long n, const double *__res
   using PK = Pack<T, VW>;
   const double *src = ctl->outer == 1 ? B0 : R;
   const int grp = blockIdx.y;
+  double sc[VW];
+  float scf[VW];
+#pragma unroll
+  for (int q = 0; q < VW; ++q) {
+    sc[q] = grp * VW + q < s ? scale[grp * VW + q] : 0.0;
+    scf[q] = (float)sc[q];
+  }
   for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
     PK o;
 #pragma unroll
     for (int q = 0; q < VW; ++q) {
       const int col = grp * VW + q;
-      o.v[q] = col < s ? (T)(scale[col] * src[ldr * col + i]) : T(0);
+      o.v[q] = col < s ? inner_value<T, DF>(src[ldr * col + i], sc[q], scf[q]) : T(0);
     }
     o.st(rt + grp * gs + i * VW);
   }
@@ -1045,23 +1082,296 @@ __global__ void k_refine_ctl(int s, const double *__restrict__ rr, const double 
   }
 }
 
-// X (column-major FP64) += d / scale for the columns with scale != 0
-template <typename T, int VW>
+// X (column-major FP64) += d / scale for the columns with scale != 0.  In double-float
+// mode (DF, FP32 inner solves only) the sum is formed on the FP32 pipe: x as a
+// double-float pair plus the exact product of d and the float |r| (two_prod), then
+// joined back into a double; the correction carries the inner solve's accuracy only, so
+// rounding |r| to float changes nothing that matters.
+template <typename T, int VW, bool DF>
 __global__ void __launch_bounds__(NB) k_accum(long n, const T *__restrict__ d, long gs, const double *__restrict__ iscale,
                                               int s, double *__restrict__ X, long ldx) {
   using PK = Pack<T, VW>;
   const int grp = blockIdx.y;
+  double is[VW];
+  float isf[VW];
+#pragma unroll
+  for (int q = 0; q < VW; ++q) {
+    is[q] = grp * VW + q < s ? iscale[grp * VW + q] : 0.0;  // |r| of the column, 0 once converged
+    isf[q] = (float)is[q];
+  }
   for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
     const PK v = PK::ld(d + grp * gs + i * VW);
 #pragma unroll
     for (int q = 0; q < VW; ++q) {
       const int col = grp * VW + q;
-      if (col < s) {
-        const double is = iscale[col];  // |r| of the column, 0 when it has converged
-        if (is != 0.0) X[ldx * col + i] += (double)v.v[q] * is;
+      if (col < s && is[q] != 0.0) {
+        double *xp = X + ldx * col + i;
+        if constexpr (DF) {
+          Dot2 a;
+          a.add(d2df(*xp));
+          a.add(two_prod((float)v.v[q], isf[q]));
+          *xp = df2d(a.result());
+        } else {
+          *xp += (double)v.v[q] * is[q];
+        }
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 refinement with its data held as double-float pairs (float2 {hi, lo}, 8 bytes per
+// value like a double): the right-hand side b and the iterate x of a solve live in the
+// refinement's own workspace in this form, so the residual and the update read and write
+// pairs directly and execute no conversion and no FP64 instruction per value.  The
+// caller's FP64 B is converted once when the solve starts (k_ir_start_df) and the result
+// joined back into its FP64 X once when it ends (k_df_out).  The residual is kept as its
+// leading float (the inner solve's right-hand side needs no more), so the scaling into the
+// inner precision reads 4 bytes per value.
+// ---------------------------------------------------------------------------
+
+// b = B (Dirichlet rows of a stiffness solve zeroed) as pairs, x = 0, the first residual
+// r = hi(b), and the per-block partials of |B|^2 (FP64)
+__global__ void __launch_bounds__(NB) k_ir_start_df(const double *__restrict__ B, long ldb, float2 *__restrict__ Bd,
+                                                    float2 *__restrict__ Xd, float *__restrict__ Rf, long ld, long n,
+                                                    long face, double *__restrict__ part) {
+  const int j = blockIdx.y;
+  double acc = 0.0;
+  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
+    const double v = (i < face || i >= n - face) ? 0.0 : B[ldb * j + i];
+    const dfl d = d2df(v);
+    Bd[ld * j + i] = make_float2(d.hi, d.lo);
+    Xd[ld * j + i] = make_float2(0.f, 0.f);
+    Rf[ld * j + i] = d.hi;
+    acc = fma(v, v, acc);
+  }
+  acc = block_sum<NB>(acc);
+  if (threadIdx.x == 0) part[(long)j * gridDim.x + blockIdx.x] = acc;
+}
+
+// r = b - S x from pairs, its leading float stored, and the per-column |r|^2 partials:
+// the squares are summed in FP32 on r scaled by 1/|b| (so that they stay far from the
+// float range's ends) and each block's sum is scaled back by |b|^2 in FP64.
+template <int D, bool FULL>
+__global__ void __launch_bounds__(NB) k_resid_df2(GridDesc g, const double *__restrict__ diag,
+                                                  const double *__restrict__ c, const float2 *__restrict__ Xd,
+                                                  const float2 *__restrict__ Bd, long ld, float *__restrict__ Rf,
+                                                  int s, const double *__restrict__ bb, Fin fin) {
+  constexpr int NF = FULL ? (1 << D) - 1 : D;
+  const int lane = threadIdx.x & 31;
+  const int i0 = blockIdx.x * 32 + lane;
+  const int nrows = D == 2 ? g.np : g.np * g.np;
+  const int grp = blockIdx.z;
+  float sb[4], accf[4] = {0.f, 0.f, 0.f, 0.f};
+  const float2 *xq[4];
+  const float2 *bq[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int col = min(grp * 4 + q, s - 1);  // columns past s repeat the last one, unstored
+    const double b2 = bb[col];
+    sb[q] = b2 > 0.0 ? (float)(1.0 / sqrt(b2)) : 1.f;
+    xq[q] = Xd + ld * col;
+    bq[q] = Bd + ld * col;
+  }
+  for (int row = blockIdx.y * (NB / 32) + (threadIdx.x >> 5); row < nrows; row += gridDim.y * (NB / 32)) {
+    if (i0 >= g.np) break;
+    const int v[3] = {i0, D == 2 ? row : row % g.np, D == 2 ? 0 : row / g.np};
+    const long id = i0 + (long)g.np * row;
+    Dot2 a[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 t = bq[q][id];
+      a[q].add(dfl{t.x, t.y});
+    }
+    {
+      const dfl dg = d2df(diag[id]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 t = xq[q][id];
+        a[q].fms(dg, dfl{t.x, t.y});
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const int b = FULL ? f + 1 : (1 << f);
+      bool fw = true, bw = true;
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+        if ((b >> k) & 1) {
+          fw = fw && (v[k] < g.N);
+          bw = bw && (v[k] > 0);
+        }
+      const long off = mask_offset(g, b);
+      if (fw) {
+        const dfl cf = d2df(c[(long)f * g.n + id]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 t = xq[q][id + off];
+          a[q].fms(cf, dfl{t.x, t.y});
+        }
+      }
+      if (bw) {
+        const dfl cb = d2df(c[(long)f * g.n + id - off]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 t = xq[q][id - off];
+          a[q].fms(cb, dfl{t.x, t.y});
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int col = grp * 4 + q;
+      if (col < s) {
+        const float r = a[q].result().hi;
+        Rf[ld * col + id] = r;
+        const float t = r * sb[q];
+        accf[q] = fmaf(t, t, accf[q]);
+      }
+    }
+  }
+  Pack<double, 4> acc;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc.v[q] = (double)accf[q];
+  __shared__ double bbs[4];
+  if (threadIdx.x < 4) bbs[threadIdx.x] = grp * 4 + threadIdx.x < s ? bb[grp * 4 + threadIdx.x] : 0.0;
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc.v[q] *= bbs[q] > 0.0 ? bbs[q] : 1.0;
+  dot_partial<double, 4>(acc, fin.part, grp, s, blockIdx.x + gridDim.x * blockIdx.y, gridDim.x * gridDim.y);
+}
+
+// inner right-hand side rt = r * scale from the residual's leading floats
+template <int VW>
+__global__ void __launch_bounds__(NB) k_to_inner_df2(long n, const float *__restrict__ Rf, long ld,
+                                                     const double *__restrict__ scale, int s, float *__restrict__ rt,
+                                                     long gs) {
+  using PK = Pack<float, VW>;
+  const int grp = blockIdx.y;
+  float sc[VW];
+#pragma unroll
+  for (int q = 0; q < VW; ++q) sc[q] = grp * VW + q < s ? (float)scale[grp * VW + q] : 0.f;
+  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
+    PK o;
+#pragma unroll
+    for (int q = 0; q < VW; ++q) {
+      const int col = grp * VW + q;
+      o.v[q] = col < s ? Rf[ld * col + i] * sc[q] : 0.f;
+    }
+    o.st(rt + grp * gs + i * VW);
+  }
+}
+
+// x += d * |r| on the pairs, for the columns with |r| != 0
+template <int VW>
+__global__ void __launch_bounds__(NB) k_accum_df2(long n, const float *__restrict__ d, long gs,
+                                                  const double *__restrict__ iscale, int s, float2 *__restrict__ Xd,
+                                                  long ld) {
+  using PK = Pack<float, VW>;
+  const int grp = blockIdx.y;
+  float isf[VW];
+#pragma unroll
+  for (int q = 0; q < VW; ++q) isf[q] = grp * VW + q < s ? (float)iscale[grp * VW + q] : 0.f;
+  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
+    const PK v = PK::ld(d + grp * gs + i * VW);
+#pragma unroll
+    for (int q = 0; q < VW; ++q) {
+      const int col = grp * VW + q;
+      if (col < s && isf[q] != 0.f) {
+        float2 *xp = Xd + ld * col + i;
+        const float2 x = *xp;
+        Dot2 a;
+        a.add(dfl{x.x, x.y});
+        a.add(two_prod(v.v[q], isf[q]));
+        const dfl r = a.result();
+        *xp = make_float2(r.hi, r.lo);
+      }
+    }
+  }
+}
+
+// X (FP64) = the pairs joined, column by column
+__global__ void __launch_bounds__(NB) k_df_out(const float2 *__restrict__ Xd, long ld, double *__restrict__ X,
+                                               long ldx, long n) {
+  const int j = blockIdx.y;
+  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
+    const float2 t = Xd[ld * j + i];
+    X[ldx * j + i] = df2d(dfl{t.x, t.y});
+  }
+}
+
+// FP64 refinement residual R = B - S X with its per-column norm, evaluated in
+// double-float arithmetic on the FP32 pipe (Dot2 accumulation of the stencil's products,
+// FP64 data converted by bit manipulation).  Stencil as k_st (the same coefficient
+// arrays); four columns per thread share the converted coefficients; the squared norm is
+// summed in FP64 (one FP64 operation per element, under the memory time).
+template <int D, bool FULL>
+__global__ void __launch_bounds__(NB) k_resid_df(GridDesc g, const double *__restrict__ diag,
+                                                 const double *__restrict__ c, const double *__restrict__ X, long ldx,
+                                                 const double *__restrict__ B, long ldb, double *__restrict__ R,
+                                                 long ldr, int s, Fin fin) {
+  constexpr int NF = FULL ? (1 << D) - 1 : D;
+  const int lane = threadIdx.x & 31;
+  const int i0 = blockIdx.x * 32 + lane;
+  const int nrows = D == 2 ? g.np : g.np * g.np;
+  const int grp = blockIdx.z;
+  Pack<double, 4> acc = Pack<double, 4>::zero();
+  for (int row = blockIdx.y * (NB / 32) + (threadIdx.x >> 5); row < nrows; row += gridDim.y * (NB / 32)) {
+    if (i0 >= g.np) break;
+    const int v[3] = {i0, D == 2 ? row : row % g.np, D == 2 ? 0 : row / g.np};
+    const long id = i0 + (long)g.np * row;
+    const dfl dg = d2df(diag[id]);
+    dfl cf[NF], cb[NF];
+    long off[NF];
+    bool fw[NF], bw[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const int b = FULL ? f + 1 : (1 << f);
+      fw[f] = true;
+      bw[f] = true;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        if ((b >> a) & 1) {
+          fw[f] = fw[f] && (v[a] < g.N);
+          bw[f] = bw[f] && (v[a] > 0);
+        }
+      off[f] = mask_offset(g, b);
+      cf[f] = fw[f] ? d2df(c[(long)f * g.n + id]) : dfl{0.f, 0.f};
+      cb[f] = bw[f] ? d2df(c[(long)f * g.n + id - off[f]]) : dfl{0.f, 0.f};
+    }
+    // the group's four columns advance together, term by term, so that their four
+    // compensated sums are independent dependency chains (columns past s repeat the
+    // last column and are not stored)
+    const double *xq[4];
+    Dot2 a[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int col = min(grp * 4 + q, s - 1);
+      xq[q] = X + ldx * col;
+      a[q].add(d2df(B[ldb * col + id]));
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a[q].fms(dg, d2df(xq[q][id]));
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      if (fw[f])
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q].fms(cf[f], d2df(xq[q][id + off[f]]));
+      if (bw[f])
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q].fms(cb[f], d2df(xq[q][id - off[f]]));
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int col = grp * 4 + q;
+      if (col < s) {
+        const double r = df2d(a[q].result());
+        R[ldr * col + id] = r;
+        acc.v[q] = fma(r, r, acc.v[q]);
+      }
+    }
+  }
+  dot_partial<double, 4>(acc, fin.part, grp, s, blockIdx.x + gridDim.x * blockIdx.y, gridDim.x * gridDim.y);
 }
 
 // End of a PCG iteration: count it and decide whether another one runs.  In
@@ -1304,12 +1614,15 @@ static bool tile3_launch(const GridDesc &g, const Stencil<float> &S, const float
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return false;
   if (slots[dev].load(std::memory_order_acquire) == 0) {
+    // an error left pending by earlier work stays for the caller to see: give up the tiled
+    // form for this launch without touching it
+    if (cudaPeekAtLastError() != cudaSuccess) return false;
     int per_sm = 0, sms = 0;
     if (cudaFuncSetAttribute(k_st_tile3<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL3_SMEM) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_st_tile3<MODE>, TL3_NT, TL3_SMEM) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1) {
-      (void)cudaGetLastError();  // the row kernels run instead; the refusal is not the solve's error
+      (void)cudaGetLastError();  // clears only the refused set-up call's error: the row kernels run instead
       return false;
     }
     slots[dev].store(per_sm * sms, std::memory_order_release);
@@ -2515,11 +2828,45 @@ int apply_op64(hp_problem *P, OpKind op, const double *X, long ldx, double *Y, l
 }
 
 // FP64 residual R = B - S X (column-major) with the per-column |R|^2 -> sc.rr in the same pass
+// Whether the FP64 refinement of the solve being launched evaluates its residuals, scaling
+// and updates in double-float arithmetic (FP32 inner solves only).  Double-float carries
+// about 48 significand bits against FP64's 53, and its residual's error grows with
+// |S| |x| / |b|: at tolerances from DF_MIN_RTOL up it leaves a wide margin (the attained
+// FP64 residual is checked against the oracle at 1e-8), below it the solve keeps the FP64
+// arithmetic.
+constexpr double DF_MIN_RTOL = 1e-9;
+static thread_local bool tl_df = false;
+static bool use_df(const hp_problem *P, int tbytes, double rtol) {
+  return tbytes == 4 && (P->refine_df == 2 || (P->refine_df == 1 && rtol >= DF_MIN_RTOL));
+}
+
+template <bool FULL>
+static void launch_resid_df(const GridDesc &g, const Stencil<double> &S, const double *X, long ldx, const double *B,
+                            long ldb, double *R, long ldr, int s, const Fin &fin, cudaStream_t st) {
+  const int ng = (s + 3) / 4;
+  const dim3 grid = rowgrid_capped(g, ng);
+  if (g.dim == 2)
+    k_resid_df<2, FULL><<<grid, NB, 0, st>>>(g, S.diag, S.c, X, ldx, B, ldb, R, ldr, s, fin);
+  else
+    k_resid_df<3, FULL><<<grid, NB, 0, st>>>(g, S.diag, S.c, X, ldx, B, ldb, R, ldr, s, fin);
+  count_launch();
+  count_bytes(BY_REFINE, 8.0 * (double)g.n * (3.0 * s + 1.0 + S.nf));
+  dot_finalize(fin, grid.x * grid.y, s, st);
+}
+
 static int residual64(hp_problem *P, OpKind op, const double *B, long ldb, const double *X, long ldx, double *R,
                       long ldr, int s) {
   const int pr = prof_start(P, PROF_RESID64);
-  st_launch<double, 1, M_RESID_DOT>(P->lv[0].g, stencil_of<double>(P, op, 0), X, ldx, B, ldb, R, ldr, s, 0.0,
-                                    make_fin(P, FIN_STORE, 0.0, P->sc.rr.as<double>()), P->st);
+  const Stencil<double> &S = stencil_of<double>(P, op, 0);
+  const Fin fin = make_fin(P, FIN_STORE, 0.0, P->sc.rr.as<double>());
+  if (tl_df) {
+    if (S.full)
+      launch_resid_df<true>(P->lv[0].g, S, X, ldx, B, ldb, R, ldr, s, fin, P->st);
+    else
+      launch_resid_df<false>(P->lv[0].g, S, X, ldx, B, ldb, R, ldr, s, fin, P->st);
+  } else {
+    st_launch<double, 1, M_RESID_DOT>(P->lv[0].g, S, X, ldx, B, ldb, R, ldr, s, 0.0, fin, P->st);
+  }
   prof_stop(P, pr);
   return cuda_check(cudaGetLastError(), "residual");
 }
@@ -2579,14 +2926,21 @@ static int build_solve_graph(hp_problem *P, OpKind op, int s, double rtol, doubl
     }
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-      k_to_inner_ctl<T, VW><<<nodegrid(n, ng), NB, 0, cs>>>(n, b64, r64, ld64, ctl, scale, s, W.r.template as<T>(),
+      if (tl_df)
+        k_to_inner_ctl<T, VW, true><<<nodegrid(n, ng), NB, 0, cs>>>(n, b64, r64, ld64, ctl, scale, s,
+                                                                    W.r.template as<T>(), gs);
+      else
+        k_to_inner_ctl<T, VW, false><<<nodegrid(n, ng), NB, 0, cs>>>(n, b64, r64, ld64, ctl, scale, s, W.r.template as<T>(),
                                                             gs);
       e = end_capture(body, true);
     }
     if (e == cudaSuccess) e = append_pcg<T, VW>(P, op, s, tol_in, maxit, body, leaf, &pw);
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, &pw, nullptr, 1, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-      k_accum<T, VW><<<nodegrid(n, ng), NB, 0, cs>>>(n, W.x.template as<T>(), gs, iscale, s, x64, ld64);
+      if (tl_df)
+        k_accum<T, VW, true><<<nodegrid(n, ng), NB, 0, cs>>>(n, W.x.template as<T>(), gs, iscale, s, x64, ld64);
+      else
+        k_accum<T, VW, false><<<nodegrid(n, ng), NB, 0, cs>>>(n, W.x.template as<T>(), gs, iscale, s, x64, ld64);
       const int rc = residual64(P, op, b64, ld64, x64, ld64, r64, ld64, s);
       k_refine_ctl<<<1, 256, 0, cs>>>(s, rr, bb, rtol, tol_in, scale, iscale, tol2col, iter, 1, max_outer, ctl, ho);
       e = end_capture(body, false);
@@ -2661,6 +3015,7 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
   const long gs = W.ldn * VW;
   HP_TRY(ensure_kept(P, P->r64, sizeof(double) * ld64 * s));
   HP_TRY(ensure_kept(P, P->b64, sizeof(double) * ld64 * s));
+  tl_df = use_df(P, (int)sizeof(T), rtol);
   // from x = 0 with graphs on, the whole refinement runs as one captured loop
   if (P->use_graphs && !P->prof_on && !(op == OP_K && warm_attached(P)))
     return ir_solve_graph<T, VW>(P, op, B, ldb, X, ldx, s, rtol, tol_in, stats);
@@ -2724,8 +3079,12 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
     HP_CUDA(cudaMemcpyAsync(P->sc.tol2col.p, htol2.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
     // the first residual of a solve from zero is b64 (r64 not yet written)
     const double *rsrc = (outer == 0 && !warm) ? b64 : r64;
-    k_to_inner<T, VW><<<nodegrid(n, ng), NB, 0, st>>>(n, rsrc, ld64, P->sc.scale.as<double>(), s,
-                                                      W.r.template as<T>(), gs);
+    if (tl_df)
+      k_to_inner<T, VW, true><<<nodegrid(n, ng), NB, 0, st>>>(n, rsrc, ld64, P->sc.scale.as<double>(), s,
+                                                              W.r.template as<T>(), gs);
+    else
+      k_to_inner<T, VW, false><<<nodegrid(n, ng), NB, 0, st>>>(n, rsrc, ld64, P->sc.scale.as<double>(), s,
+                                                               W.r.template as<T>(), gs);
     count_launch();
     count_bytes(BY_REFINE, (8.0 + sizeof(T)) * (double)n * s);  // read the FP64 residual, write the inner one
     int its = 0;
@@ -2734,8 +3093,12 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
     if (prc && prc != HP_ERR_NOT_CONVERGED) return prc;
     total_its += its;
     prof_spin(P);
-    k_accum<T, VW><<<nodegrid(n, ng), NB, 0, st>>>(n, W.x.template as<T>(), gs, P->sc.iscale.as<double>(), s, X,
-                                                   ldx);
+    if (tl_df)
+      k_accum<T, VW, true><<<nodegrid(n, ng), NB, 0, st>>>(n, W.x.template as<T>(), gs, P->sc.iscale.as<double>(),
+                                                           s, X, ldx);
+    else
+      k_accum<T, VW, false><<<nodegrid(n, ng), NB, 0, st>>>(n, W.x.template as<T>(), gs, P->sc.iscale.as<double>(),
+                                                            s, X, ldx);
     count_launch();
     count_bytes(BY_REFINE, (16.0 + sizeof(T)) * (double)n * s);  // read the correction, read and write x
     HP_TRY(residual64(P, op, b64, ld64, X, ldx, r64, ld64, s));

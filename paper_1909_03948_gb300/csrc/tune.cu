@@ -24,14 +24,17 @@ int hp_set_tuning(hp_problem *P, const hp_tuning *t) {
       t->max_blocks > (1 << 20) || t->fuse_from < 0 || t->fuse_from >= HP_MAXL || t->smoother < 0 ||
       t->smoother > 1 || (t->smoother == 1 && !(t->cheb_alpha > 1.0 && t->cheb_alpha < 1e6)) ||
       t->fuse_transfer < 0 || t->fuse_transfer > 2 || t->tma_tiles < 0 || t->tma_tiles > 1 ||
-      t->smem_tail < 0 || t->smem_tail >= HP_MAXL)
+      t->smem_tail < 0 || t->smem_tail >= HP_MAXL || t->refine_df < 0 || t->refine_df > 2)
     return set_error(HP_ERR_INVALID, "hp_set_tuning: nu in [1,4], omega in (0,1), col_chunk >= 0, max_blocks >= 64, "
-                                     "fuse_from in [0, 15], smoother 0/1, cheb_alpha > 1, fuse_transfer 0..2, tma_tiles 0/1, smem_tail in [0, 15]");
+                                     "fuse_from in [0, 15], smoother 0/1, cheb_alpha > 1, fuse_transfer 0..2, tma_tiles 0/1, smem_tail in [0, 15], "
+                                     "refine_df 0..2");
   HP_CUDA(cudaStreamSynchronize(P->st));
   if (t->nu != P->nu || t->nu_coarse != P->nu_coarse || t->omega != P->omega || t->max_blocks != P->max_blocks || t->fuse_from != P->fuse_from ||
       t->smoother != P->smoother || (t->smoother == 1 && t->cheb_alpha != P->cheb_alpha) ||
-      t->fuse_transfer != P->fuse_transfer || t->tma_tiles != P->tma_tiles || t->smem_tail != P->smem_tail)
+      t->fuse_transfer != P->fuse_transfer || t->tma_tiles != P->tma_tiles || t->smem_tail != P->smem_tail ||
+      t->refine_df != P->refine_df)
     drop_graphs(P);
+  P->refine_df = t->refine_df;
   P->tma_tiles = t->tma_tiles;
   P->smem_tail = t->smem_tail;
   P->fuse_transfer = t->fuse_transfer;
@@ -59,6 +62,7 @@ int hp_get_tuning(const hp_problem *P, hp_tuning *t) {
   t->fuse_transfer = P->fuse_transfer;
   t->tma_tiles = P->tma_tiles;
   t->smem_tail = P->smem_tail;
+  t->refine_df = P->refine_df;
   return HP_OK;
 }
 

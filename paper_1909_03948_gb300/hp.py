@@ -60,7 +60,7 @@ class SolveStats(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("nu", C.c_int), ("nu_coarse", C.c_int), ("omega", C.c_double), ("col_chunk", C.c_int), ("max_blocks", C.c_int),
                 ("smoother", C.c_int), ("cheb_alpha", C.c_double), ("fuse_transfer", C.c_int),
-                ("fuse_from", C.c_int), ("tma_tiles", C.c_int), ("smem_tail", C.c_int)]
+                ("fuse_from", C.c_int), ("tma_tiles", C.c_int), ("smem_tail", C.c_int), ("refine_df", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -430,6 +430,10 @@ class Problem:
         (nrhs <= 64, n * nrhs <= 262144; calls must not overlap on the GPU)."""
         B2, s, n = _block(B, self.n, "B")
         X2 = _block(out, self.n, "out")[0]
+        # the library writes s columns of n values into out: it must hold exactly B's block
+        if X2.shape != B2.shape or X2.device != B2.device:
+            raise ValueError(f"out: expected a {tuple(B2.shape)} block on {B2.device}, got "
+                             f"{tuple(X2.shape)} on {X2.device}")
         st = SolveStats()
         _check(lib().hp_mass_solve_noalloc(self._h, _dptr(B2), n, _dptr(X2), n, s, C.byref(st)),
                "hp_mass_solve_noalloc")
@@ -455,10 +459,10 @@ class Problem:
         return t.as_dict()
 
     def set_tuning(self, nu=3, omega=0.7, col_chunk=0, max_blocks=4096, smoother=1, cheb_alpha=10.0,
-                   fuse_transfer=0, fuse_from=0, nu_coarse=0, tma_tiles=0, smem_tail=0):
+                   fuse_transfer=0, fuse_from=0, nu_coarse=0, tma_tiles=0, smem_tail=0, refine_df=0):
         t = Tuning(nu=nu, nu_coarse=nu_coarse, omega=omega, col_chunk=col_chunk, max_blocks=max_blocks,
                    smoother=smoother, cheb_alpha=cheb_alpha, fuse_transfer=fuse_transfer, fuse_from=fuse_from,
-                   tma_tiles=tma_tiles, smem_tail=smem_tail)
+                   tma_tiles=tma_tiles, smem_tail=smem_tail, refine_df=refine_df)
         _check(lib().hp_set_tuning(self._h, C.byref(t)), "hp_set_tuning")
 
     def autotune(self, nrhs, reps=2):

@@ -49,21 +49,30 @@ def test_newton_map_matches_oracle(small2d, precision):
     assert abs(st["J"] - orc.cost(ref)[0]) <= 1e-8 * abs(st["J"])
 
 
-@pytest.mark.parametrize("precision", ["fp32_ir", "fp64"])
-def test_3d_newton_map_matches_oracle(precision):
-    """Newton-CG (Algorithm 1) on a 16^3 Kuhn-tetrahedron problem (4,913 nodes, 60
-    observations, gamma 0.05, delta 0.5 as the 3D workload) to relative gradient 1e-9, PDE
-    solves to 1e-12: the MAP point within 1e-6 of the oracle's, and the same final cost."""
-    w = W.make_workload(3, 16, 60, gamma=0.05, seed=W.SEED_BASE + 89)
+@pytest.fixture(scope="module")
+def newton3d():
+    """A 16^3 Kuhn-tetrahedron problem (4,913 nodes, 60 observations, gamma 0.1, delta 0.5)
+    and the oracle's Gauss-Newton MAP at relative gradient 1e-9 (24 Newton iterations)."""
+    w = W.make_workload(3, 16, 60, gamma=0.1, seed=W.SEED_BASE + 89)
     orc, m_true, _ = make_problem(w, W.draws(w))
     ref = A.newton_cg(orc, rel_tol=1e-9)
     assert ref.converged
+    return dict(w=w, orc=orc, ref=ref)
+
+
+@pytest.mark.parametrize("precision", ["fp32_ir", "fp64"])
+def test_3d_newton_map_matches_oracle(newton3d, precision):
+    """Newton-CG (Algorithm 1) in 3D to relative gradient 1e-9, PDE solves to 1e-12: the
+    MAP point within 1e-6 of the oracle's, the same final cost, and the same number of
+    Newton iterations give or take one."""
+    w, orc, ref = newton3d["w"], newton3d["orc"], newton3d["ref"]
     P = _gpu_problem(orc, w, rtol=1e-12, precision=precision)
     try:
         m, st = P.newton_cg_map(rel_tol=1e-9)
     finally:
         P.close()
     assert st["converged"], st
+    assert abs(st["iterations"] - ref.iterations) <= 1
     assert np.linalg.norm(m.cpu().numpy() - ref.m) <= 1e-6 * np.linalg.norm(ref.m)
     assert abs(st["J"] - orc.cost(ref.m)[0]) <= 1e-8 * abs(st["J"])
 
@@ -501,7 +510,7 @@ def test_tma_tiles_keep_results(dim, N, ncols):
     tolerance, within one PCG iteration (the two differ only in the order of the
     inner-product partial sums), with column counts that leave part of the last group of 4
     empty."""
-    from paper_1909_03948_gb300 import Problem
+    from paper_1909_03948_gb300 import Problem, tiled_kernel_launches
     w = W.make_workload(dim, N, 30, seed=83)
     dr = W.draws(w)
     P = Problem(dim, N, w.gamma, w.delta, 0.01, dr.obs_xyz, rtol=1e-10)
@@ -511,7 +520,13 @@ def test_tma_tiles_keep_results(dim, N, ncols):
     for tt in (0, 1):
         P.set_tuning(tma_tiles=tt)
         P.set_point(m)
-        out[tt] = P.hessian_apply(X) + (P.state_solve(X)[0],)
+        t0 = tiled_kernel_launches()
+        P.profile_enable(True)       # direct launches, which the tiled-launch counter sees
+        try:
+            out[tt] = P.hessian_apply(X) + (P.state_solve(X)[0],)
+        finally:
+            P.profile_enable(False)
+        assert (tiled_kernel_launches() > t0) == bool(tt), (tt, "tiled launches")
     (Y0, st0, U0), (Y1, st1, U1) = out[0], out[1]
     assert float(torch.linalg.norm(Y1 - Y0) / torch.linalg.norm(Y0)) <= 1e-8
     assert float(torch.linalg.norm(U1 - U0) / torch.linalg.norm(U0)) <= 1e-8

@@ -89,7 +89,11 @@ def test_cube3d_block_against_the_oracle(tmp_path):
         P.set_point(m)
         Om = W.omega(w)
         t0 = tiled_kernel_launches()
-        Y, _ = P.hessian_apply(torch.tensor(np.ascontiguousarray(Om.T), device=DEV))
+        P.profile_enable(True)       # direct launches, so that the tiled-launch counter sees them
+        try:
+            Y, _ = P.hessian_apply(torch.tensor(np.ascontiguousarray(Om.T), device=DEV))
+        finally:
+            P.profile_enable(False)
         tiled = tiled_kernel_launches() > t0
         Y = Y.cpu().numpy().T
         assert np.isfinite(Y).all()

@@ -191,3 +191,19 @@ def test_workload_problem_builds():
     prob, m_true, u_true = make_problem(w, W.draws(w))
     assert prob.B.shape == (50, 33 * 33)
     assert np.isclose(prob.sigma, 0.01 * np.abs(u_true).max())
+
+
+@pytest.mark.parametrize("dim,N", [(2, 9), (3, 4)])
+def test_prior_precision_on_constants(dim, N):
+    """R = A M^{-1} A with A = gamma K(Theta) + delta M and zero Neumann: K(Theta) 1 = 0, so
+    A 1 = delta M 1, M^{-1} A 1 = delta 1 and R 1 = delta^2 M 1; with 1^T M 1 = |D| = 1,
+    1^T R 1 = delta^2.  Holds for any s.p.d. Theta, so a random one is used."""
+    mesh = Mesh(dim, N)
+    rng = np.random.default_rng(11)
+    G = rng.standard_normal((dim, dim))
+    theta = G @ G.T + dim * np.eye(dim)
+    prob = Problem(mesh, 0.13, 0.7, np.zeros((0, dim)), np.zeros(0), 1.0, theta=theta)
+    one = np.ones(mesh.n)
+    R1 = prob.R_apply(one)
+    assert np.abs(R1 - 0.7 ** 2 * (mesh.mass @ one)).max() <= 1e-9 * np.abs(mesh.mass @ one).max()
+    assert abs(one @ R1 - 0.7 ** 2) <= 1e-11
