@@ -724,7 +724,7 @@ def run_batch(args, rank, world):
     """64 uneven problems concurrently: MAP + k=30 eigenpairs for all, then one block of
     k+p = 40 Hessian actions per problem at its MAP (the timed step)."""
     import torch
-    from paper_1909_03948_gb300 import Batch, kernel_launches
+    from paper_1909_03948_gb300 import Batch, algorithmic_bytes, kernel_launches
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dev = torch.device("cuda", torch.cuda.current_device())
     ws = W.batch_workloads(seed=W.SEED_BASE + 3 + 1000 * rank)
@@ -757,6 +757,48 @@ def run_batch(args, rank, world):
     launches = kernel_launches() - l0
     units = sum(w.k + w.p for w in ws)
     value, t_total = weak_scaling_value(sum(times), args.steps * units, world, dev)
+    # algorithmic bytes of one batch step, counted on a pass with profiling on (direct launches)
+    for P in Ps:
+        P.profile_enable(True)
+    b0 = algorithmic_bytes()
+    B.hessian_apply(Om)
+    torch.cuda.synchronize()
+    b1 = algorithmic_bytes()
+    for P in Ps:
+        P.profile_enable(False)
+    step_bytes = {k: b1[k] - b0[k] for k in b0}
+    tot = sum(step_bytes.values())
+    ms_step = 1e3 * t_total / args.steps
+    peak, src = measured_peak()
+    roof = {"bound": "hbm", "achieved": tot / (ms_step * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": tot / (ms_step * 1e-3) / 1e9 / peak, "traffic": None, "kernel": "whole batch step",
+            "peak_source": src,
+            "step": {"bytes_per_step": tot, "ms_per_step": ms_step,
+                     "families": {k: {"bytes_per_step": v, "share_of_bytes": v / tot if tot else None}
+                                  for k, v in step_bytes.items()},
+                     "how": ("algorithmic bytes of every launch of one batch step (library counter, direct-launch "
+                             "pass) over the timed steps' mean duration")}}
+    # e2e: every problem's block copied from pinned host memory and the results read back
+    Xh = [torch.empty(X.shape, dtype=torch.float64).pin_memory() for X in Om]
+    for xh, X in zip(Xh, Om):
+        xh.copy_(X.cpu())
+    Yh = [torch.empty_like(x).pin_memory() for x in Xh]
+    Xd = [torch.empty_like(X) for X in Om]
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        for xd, xh in zip(Xd, Xh):
+            xd.copy_(xh, non_blocking=True)
+        torch.cuda.synchronize()      # the problems run on their own non-blocking streams
+        Ys = B.hessian_apply(Xd)
+        for yh, y in zip(Yh, Ys):
+            yh.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - ta)
+    e2e_val = weak_scaling_value(sum(e2e_times), args.steps * units, world, dev)[0]
+    io_bytes = sum(X.numel() * 8 for X in Om)
     # the same blocks one problem after another (no concurrency), for the per-problem rates
     alone = []
     for P, X in zip(Ps, Om):
@@ -785,7 +827,9 @@ def run_batch(args, rank, world):
                                f"(multiples of 32), q in [100, 800], one block of k+p=40 GN Hessian actions per "
                                f"problem at its MAP, problems concurrent on per-problem streams",
                    "l2": "flushed (512 MB write) before every timed step"},
-        "gpu_launches": launches, "clocks": clk, "e2e": None, "roofline": None, "cpu_baseline": cpu,
+        "gpu_launches": launches, "clocks": clk,
+        "e2e": {"value": e2e_val, "unit": "actions/s", "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+        "roofline": roof, "cpu_baseline": cpu,
         "time_to_map_eig_s": t_me,
         "map_eig_actions_per_s": sum(x["cg_iterations"] + 2 * 40 for x in nst) / t_me,
         "sequential_seconds_per_step": sum(alone), "concurrency_speedup": sum(alone) / (t_total / args.steps),

@@ -338,8 +338,9 @@ typedef struct {
                       kernels work on tiles that bulk tensor copies (TMA) bring into shared
                       memory with their halo -- 32 x 16 nodes in 2D, 32 x 8 nodes marching
                       through z segments of 16 or 8 planes in 3D (the launch picks the
-                      length that fills the GPU's last wave of CTAs better); 0: every warp
-                      loads its own row of nodes */
+                      length that fills the GPU's last wave of CTAs better); 2: the same on
+                      the finest level only (the coarser levels keep the row kernels); 0:
+                      every warp loads its own row of nodes */
   int smem_tail;   /* k >= 1: the coarse end of the V-cycle -- from the finest level l >= k
                       whose vectors, and those of every level below it, fit in one CTA's
                       shared memory -- runs as one launch of one CTA per column group, its
@@ -348,12 +349,13 @@ typedef struct {
                       0: off */
   int refine_df;   /* arithmetic of the FP64 iterative refinement around FP32 inner solves
                       (the residual b - K x with its norm, the scaling into the inner
-                      precision and the update x += d): 0 (default) FP64 instructions; 1
-                      double-float arithmetic (pairs of floats, about 48 significand
-                      bits: compensated products and sums on the FP32 pipe, FP64 data
-                      converted by bit manipulation) for solve tolerances >= 1e-9, FP64
-                      below; 2 double-float at every tolerance.  The data stay FP64 in
-                      memory either way. */
+                      precision and the update x += d): 0 FP64 instructions; 1 (default)
+                      double-float arithmetic for solve tolerances >= 1e-9, FP64 below:
+                      b and x held as pairs of floats (about 48 significand bits) in the
+                      refinement's workspace, compensated products and sums on the FP32
+                      pipe, the caller's FP64 blocks converted once per solve by bit
+                      manipulation; 2 the same at every tolerance, and the C and C^T
+                      stencils in double-float too. */
 } hp_tuning;
 int hp_set_tuning(hp_problem *P, const hp_tuning *t);
 int hp_get_tuning(const hp_problem *P, hp_tuning *t);

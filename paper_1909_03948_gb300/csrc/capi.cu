@@ -559,13 +559,16 @@ void hp_problem_destroy(hp_problem *P) {
     for (void *p : {(void *)lv.kappa, (void *)lv.K64.diag, (void *)lv.K64.invdiag, (void *)lv.K64.c,
                     (void *)lv.K32.diag, (void *)lv.K32.invdiag, (void *)lv.K32.c, (void *)lv.K32.pk, (void *)lv.A64.diag,
                     (void *)lv.A64.invdiag, (void *)lv.A64.c, (void *)lv.A32.diag, (void *)lv.A32.invdiag,
-                    (void *)lv.A32.c})
+                    (void *)lv.A32.c, (void *)lv.K64.cpr, (void *)lv.A64.cpr})
       if (p) cudaFree(p);
   }
   for (CoarseInv *C : {&P->cK, &P->cA})
     for (void *p : {(void *)C->dense, (void *)C->inv64, (void *)C->inv32})
       if (p) cudaFree(p);
-  for (void *p : {(void *)P->M64.diag, (void *)P->M64.invdiag, (void *)P->M64.c, (void *)P->M32.diag,
+  for (void *p : {(void *)P->CbetaE_pr, (void *)P->Cbeta_pr, (void *)P->E_pr})
+    if (p) cudaFree(p);
+  P->xpairs.release();
+  for (void *p : {(void *)P->M64.diag, (void *)P->M64.invdiag, (void *)P->M64.c, (void *)P->M64.cpr, (void *)P->M32.diag,
                   (void *)P->M32.invdiag, (void *)P->M32.c, (void *)P->m, (void *)P->E, (void *)P->u,
                   (void *)P->lift, (void *)P->Cbeta, (void *)P->CbetaE, (void *)P->padj, (void *)P->Cbeta_p, (void *)P->CbetaE_p, (void *)P->wmm, (void *)P->m_prior, (void *)P->f_load, (void *)P->d_obs, (void *)P->obs_node,
                   (void *)P->obs_w, (void *)P->bt_row, (void *)P->bt_ptr, (void *)P->bt_ent})

@@ -19,9 +19,9 @@
 // cannot contract them into fused operations that would break the transformations.
 //
 // Conversions: d2df splits a double into hi (its 24 leading significand bits) and lo
-// (the next 24, rounded toward zero), and df2d joins a pair back into a double, both by
-// integer operations on the bit patterns, so that loading and storing FP64 data costs no
-// FP64 instruction.
+// (the next 24, rounded toward zero) by integer operations on its bit pattern, so that
+// loading FP64 data costs no FP64 instruction; df2d widens both floats the same way and
+// joins them with one FP64 addition.
 #pragma once
 #include <cstdint>
 
@@ -98,37 +98,18 @@ __device__ __forceinline__ dfl d2df(double x) {
   return {hi, lo};
 }
 
-// double-float -> double by integer arithmetic on the two significands (no FP64
-// instruction): hi's 24-bit significand is widened to 53 bits, lo's is aligned to it
-// (bits below the double's last place are dropped) and added or subtracted, and the sum
-// is renormalised by at most one place.  The result is within one unit in the last place
-// of hi + lo.  Needs |lo| < 2 ulp(hi), which every pair made by d2df or by the operations
-// above satisfies (anything else, and a hi outside the normal range, goes through the
-// FP64 conversion).
-__device__ __forceinline__ double df2d(dfl v) {
-  const unsigned uh = __float_as_uint(v.hi), ul = __float_as_uint(v.lo);
-  const int eh = static_cast<int>((uh >> 23) & 0xffu), el = static_cast<int>((ul >> 23) & 0xffu);
-  if (eh == 0 || eh == 255) return (double)v.hi + (double)v.lo;
-  long long E = eh - 127 + 1023;
-  unsigned long long S = static_cast<unsigned long long>((uh & 0x7FFFFFu) | 0x800000u) << 29;
-  if ((ul & 0x7FFFFFFFu) != 0u && el != 0) {
-    const int sh = eh - el;  // >= 22 for |lo| < 2 ulp(hi)
-    if (sh < 22) return (double)v.hi + (double)v.lo;
-    const unsigned long long L = static_cast<unsigned long long>((ul & 0x7FFFFFu) | 0x800000u);
-    const unsigned long long La = sh <= 29 ? (L << (29 - sh)) : (sh - 29 < 64 ? (L >> (sh - 29)) : 0ull);
-    S = ((uh ^ ul) & 0x80000000u) ? S - La : S + La;
-    if (S >= (1ull << 53)) {
-      S >>= 1;
-      E += 1;
-    } else if (S < (1ull << 52)) {
-      S <<= 1;
-      E -= 1;
-    }
-  }
-  const unsigned long long bits =
-      (static_cast<unsigned long long>(uh & 0x80000000u) << 32) | (static_cast<unsigned long long>(E) << 52) |
-      (S & 0xFFFFFFFFFFFFFull);
-  return __longlong_as_double(static_cast<long long>(bits));
+// float -> double, exact, by bit manipulation (zero and normal floats; anything else
+// through the FP64 conversion)
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 255u) return (u << 1) == 0u ? __hiloint2double((int)(u & 0x80000000u), 0) : (double)x;
+  const unsigned m = u & 0x7FFFFFu;
+  return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
 }
+
+// double-float -> double: hi and lo widened exactly by bit manipulation, then one FP64
+// addition (the correctly rounded hi + lo)
+__device__ __forceinline__ double df2d(dfl v) { return f2d(v.hi) + f2d(v.lo); }
 
 }  // namespace hp

@@ -679,6 +679,7 @@ int build_point(hp_problem *P, const double *m_dev) {
                                                            lv.K32.diag, lv.K32.invdiag, lv.K32.c, lift, P->u_top,
                                                            P->u_bottom);
     count_launch();
+    lv.K64.cpr_ok = false;  // the double-float coefficient pairs follow on first use
     if (lv.K32.pk) {
       if (D == 2)
         k_pack_K2<<<grid_blocks(lv.g.n), 256, 0, P->st>>>(lv.g.n, lv.K32.diag, lv.K32.invdiag, lv.K32.c,
@@ -832,99 +833,162 @@ __global__ void k_Ct_apply(GridDesc g, const double *__restrict__ E, const doubl
   }
 }
 
-// The same two stencils in double-float arithmetic on the FP32 pipe (FP64 data converted
-// by bit manipulation, the products summed by the compensated Dot2 scheme): four columns
-// per thread share the converted coefficients.  The result's error is about 2^-47 of the
-// sum of the terms' magnitudes, far below the solve tolerances these are used with; the
-// final scaling (and the accumulation into Y when yb != 0) stays in FP64, one or two
-// operations per element.
-template <int D>
-__global__ void __launch_bounds__(NT, 3) k_C_apply_df(GridDesc g, const double *__restrict__ betaE, const double *__restrict__ X, long ldx,
-                             double *__restrict__ Y, long ldy, int s, double scale, double yb) {
-  constexpr int NC = (1 << (D + 1)) - 1;
+// The same two stencils in double-float arithmetic on the FP32 pipe (at the solve
+// tolerances where the refinement runs in double-float): the input block is split into
+// pairs once (k_to_pairs, grouped by 4 columns: one {hi x4, lo x4} record per node, 32
+// bytes), the coefficients are kept as pairs (made once per linearisation point), and each
+// thread forms the compensated (Dot2) sums of one node for 4 columns, its stencil's points
+// taken in chunks whose loads are all issued before their arithmetic.  The final scaling
+// (and the accumulation into Y when yb != 0) is one FP64 operation or two per element.
+__global__ void k_to_pairs(const double *__restrict__ X, long ldx, int s, long n, float4 *__restrict__ Xp, long ldp) {
   const int grp = blockIdx.y;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
-    int v[3];
-    node_coords<D>(g, i, v);
-    dfl cq[NC];
-    int oq[NC];  // offsets of the neighbours (|offset| < n fits in an int)
-    bool okq[NC];
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    float hi[4], lo[4];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      int sg;
-      const int m = coff_mask<D>(q, &sg);
-      okq[q] = q == 0 || shift_ok<D>(g, v, m, sg);
-      oq[q] = q == 0 ? 0 : sg * (int)mask_offset(g, m);
-      cq[q] = okq[q] ? d2df(betaE[(long)q * g.n + i]) : dfl{0.f, 0.f};
+    for (int q = 0; q < 4; ++q) {
+      const int col = grp * 4 + q;
+      const dfl d = d2df(col < s ? X[ldx * col + i] : 0.0);
+      hi[q] = d.hi;
+      lo[q] = d.lo;
     }
-    // four columns term by term: four independent compensated sums (columns past s
-    // repeat the last column and are not stored)
-    const double *xj[4];
+    const long k = 2 * ((long)grp * ldp + i);
+    Xp[k] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+    Xp[k + 1] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+  }
+}
+
+__global__ void k_pairs_of(const double *__restrict__ a, long m, float2 *__restrict__ out) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < m; i += (long)gridDim.x * blockDim.x) {
+    const dfl d = d2df(a[i]);
+    out[i] = make_float2(d.hi, d.lo);
+  }
+}
+
+// TRANS false: Y = scale * sum_q cpr[q][i] x[i + o_q] (+ yb Y)            (C, coefficients betaE)
+// TRANS true:  Y = scale * E_i sum_q cpr[q][i + o'_q] x[i + o'_q] (+ yb Y)  (C^T, coefficients beta)
+template <int D, bool TRANS>
+__global__ void __launch_bounds__(NT, 2) k_cct_dfp(GridDesc g, const float2 *__restrict__ cpr,
+                                                   const float2 *__restrict__ Epr, const float4 *__restrict__ Xp,
+                                                   long ldp, double *__restrict__ Y, long ldy, int s, double scale,
+                                                   double yb) {
+  constexpr int NC = (1 << (D + 1)) - 1;
+  constexpr int CH = 5;  // points per chunk of loads
+  const int grp = blockIdx.y;
+  const float4 *xg = Xp + 2 * (long)grp * ldp;
+  const unsigned np = (unsigned)g.np, n = (unsigned)g.n;
+  for (unsigned i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) {
+    int v[3];
+    const unsigned t = i / np;
+    v[0] = (int)(i - t * np);
+    v[1] = D == 2 ? (int)t : (int)(t % np);
+    v[2] = D == 2 ? 0 : (int)(t / np);
     Dot2 a[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) xj[j] = X + ldx * min(grp * 4 + j, s - 1);
+    for (int q0 = 0; q0 < NC; q0 += CH) {
+      float4 xh[CH], xl[CH];
+      float2 cp[CH];
+      bool ok[CH];
 #pragma unroll
-    for (int q = 0; q < NC; ++q)
-      if (okq[q])
+      for (int k = 0; k < CH; ++k) {
+        const int q = q0 + k;
+        ok[k] = false;
+        if (q >= NC) continue;
+        int sg;
+        const int m = coff_mask<D>(q, &sg);
+        const int sgn = TRANS ? -sg : sg;
+        ok[k] = q == 0 || shift_ok<D>(g, v, m, sgn);
+        const unsigned pt = ok[k] && q > 0 ? (unsigned)((long)i + sgn * mask_offset(g, m)) : i;
+        xh[k] = xg[2 * pt];
+        xl[k] = xg[2 * pt + 1];
+        cp[k] = cpr[(unsigned)q * n + (TRANS ? pt : i)];
+      }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) a[j].fma(cq[q], d2df(xj[j][i + oq[q]]));
+      for (int k = 0; k < CH; ++k) {
+        if (!ok[k]) continue;
+        const dfl c{cp[k].x, cp[k].y};
+        a[0].fma(c, dfl{xh[k].x, xl[k].x});
+        a[1].fma(c, dfl{xh[k].y, xl[k].y});
+        a[2].fma(c, dfl{xh[k].z, xl[k].z});
+        a[3].fma(c, dfl{xh[k].w, xl[k].w});
+      }
+    }
+    dfl e{1.f, 0.f};
+    if (TRANS) {
+      const float2 ep = Epr[i];
+      e = dfl{ep.x, ep.y};
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int col = grp * 4 + j;
-      if (col < s) {
-        const double val = scale * df2d(a[j].result());
-        Y[ldy * col + i] = yb == 0.0 ? val : val + yb * Y[ldy * col + i];
+      if (col >= s) break;
+      dfl r = a[j].result();
+      if (TRANS) {
+        Dot2 b;  // e^{m_i} times the sum
+        b.fma(e, r);
+        r = b.result();
       }
+      const double val = scale * df2d(r);
+      Y[ldy * col + i] = yb == 0.0 ? val : val + yb * Y[ldy * col + i];
     }
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(NT, 3) k_Ct_apply_df(GridDesc g, const double *__restrict__ E, const double *__restrict__ beta,
-                              const double *__restrict__ W, long ldw, double *__restrict__ Y, long ldy, int s,
-                              double scale, double yb) {
-  constexpr int NC = (1 << (D + 1)) - 1;
-  const int grp = blockIdx.y;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.n; i += (long)gridDim.x * blockDim.x) {
-    int v[3];
-    node_coords<D>(g, i, v);
-    dfl cq[NC];
-    int oq[NC];  // the row r whose offset q points at node i is r = i + oq
-    bool okq[NC];
-#pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      int sg;
-      const int m = coff_mask<D>(q, &sg);
-      okq[q] = q == 0 || shift_ok<D>(g, v, m, -sg);
-      oq[q] = q == 0 ? 0 : -sg * (int)mask_offset(g, m);
-      cq[q] = okq[q] ? d2df(beta[(long)q * g.n + i + oq[q]]) : dfl{0.f, 0.f};
-    }
-    const dfl e = d2df(E[i]);
-    const double *wj[4];
-    Dot2 a[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) wj[j] = W + ldw * min(grp * 4 + j, s - 1);
-#pragma unroll
-    for (int q = 0; q < NC; ++q)
-      if (okq[q])
-#pragma unroll
-        for (int j = 0; j < 4; ++j) a[j].fma(cq[q], d2df(wj[j][i + oq[q]]));
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int col = grp * 4 + j;
-      if (col < s) {
-        Dot2 b;  // e^{m_i} times the sum, as a double-float product
-        b.fma(e, a[j].result());
-        const double val = scale * df2d(b.result());
-        Y[ldy * col + i] = yb == 0.0 ? val : val + yb * Y[ldy * col + i];
-      }
-    }
-  }
-}
-
-// double-float C and C^T at the solve tolerances where the refinement runs in double-float
+// double-float C and C^T where the refinement runs in double-float
 static bool cct_df(const hp_problem *P) {
   return P->precision == HP_FP32_IR && (P->refine_df == 2 || (P->refine_df == 1 && P->rtol >= 1e-9));
+}
+
+// the coefficient and e^m pairs of the u-based C, made when missing or stale
+static int ensure_cct_pairs(hp_problem *P) {
+  const long n = P->n, nc = P->dim == 2 ? 7 : 15;
+  if (!P->CbetaE_pr) {
+    HP_CUDA(cudaMalloc(&P->CbetaE_pr, sizeof(float2) * nc * n));
+    HP_CUDA(cudaMalloc(&P->Cbeta_pr, sizeof(float2) * nc * n));
+    HP_CUDA(cudaMalloc(&P->E_pr, sizeof(float2) * n));
+  }
+  if (!P->cct_pr_ok) {
+    k_pairs_of<<<blocks_for(nc * n, 1), NT, 0, P->st>>>(P->CbetaE, nc * n, P->CbetaE_pr);
+    k_pairs_of<<<blocks_for(nc * n, 1), NT, 0, P->st>>>(P->Cbeta, nc * n, P->Cbeta_pr);
+    k_pairs_of<<<blocks_for(n, 1), NT, 0, P->st>>>(P->E, n, P->E_pr);
+    count_launch(3);
+    P->cct_pr_ok = true;
+  }
+  return cuda_check(cudaGetLastError(), "C pairs");
+}
+
+// Y = scale (C or C^T) X (+ yb Y) in double-float; false when not applicable (the caller
+// then runs the FP64 kernel)
+static bool cct_dfp(hp_problem *P, bool trans, const double *X, long ldx, double *Y, long ldy, int s, double scale,
+                    double yb) {
+  const long n = P->n, ldp = (n + 63) / 64 * 64;
+  const int ng = (s + 3) / 4;
+  if (ensure_cct_pairs(P) || P->xpairs.ensure(sizeof(float4) * 2 * (size_t)ldp * ng)) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  float4 *Xp = P->xpairs.as<float4>();
+  const dim3 gd(blocks_for(n, ng), ng);
+  k_to_pairs<<<gd, NT, 0, P->st>>>(X, ldx, s, n, Xp, ldp);
+  const GridDesc &g = P->lv[0].g;
+  const dim3 gc(blocks_for(n, ng), ng);
+  if (P->dim == 2) {
+    if (trans)
+      k_cct_dfp<2, true><<<gc, NT, 0, P->st>>>(g, P->Cbeta_pr, P->E_pr, Xp, ldp, Y, ldy, s, scale, yb);
+    else
+      k_cct_dfp<2, false><<<gc, NT, 0, P->st>>>(g, P->CbetaE_pr, nullptr, Xp, ldp, Y, ldy, s, scale, yb);
+  } else {
+    if (trans)
+      k_cct_dfp<3, true><<<gc, NT, 0, P->st>>>(g, P->Cbeta_pr, P->E_pr, Xp, ldp, Y, ldy, s, scale, yb);
+    else
+      k_cct_dfp<3, false><<<gc, NT, 0, P->st>>>(g, P->CbetaE_pr, nullptr, Xp, ldp, Y, ldy, s, scale, yb);
+  }
+  count_launch(2);
+  const double nc = P->dim == 2 ? 7.0 : 15.0;
+  // the split: read X, write the pairs; the stencil: the pairs, Y (read as well when yb != 0)
+  // and the coefficient pairs (and e^m for C^T)
+  count_bytes(BY_CCT, 16.0 * (double)n * s);
+  count_bytes(BY_CCT, (double)n * ((yb == 0.0 ? 16.0 : 24.0) * s + 8.0 * (nc + (trans ? 1.0 : 0.0))));
+  return true;
 }
 
 void launch_build_C_from(hp_problem *P, const double *w, double *beta, double *betaE) {
@@ -938,22 +1002,14 @@ void launch_build_C_from(hp_problem *P, const double *w, double *beta, double *b
   count_launch(2);
 }
 
-void launch_build_C(hp_problem *P) { launch_build_C_from(P, P->u, P->Cbeta, P->CbetaE); }
+void launch_build_C(hp_problem *P) {
+  launch_build_C_from(P, P->u, P->Cbeta, P->CbetaE);
+  P->cct_pr_ok = false;  // the double-float pairs follow on first use
+}
 
 void launch_C_apply_beta(hp_problem *P, const double *betaE, const double *X, long ldx, double *Y, long ldy, int s,
                          double scale, double yb) {
-  if (cct_df(P)) {
-    const int ng = (s + 3) / 4;
-    dim3 gd(blocks_for(P->n, ng), ng);
-    if (P->dim == 2)
-      k_C_apply_df<2><<<gd, NT, 0, P->st>>>(P->lv[0].g, betaE, X, ldx, Y, ldy, s, scale, yb);
-    else
-      k_C_apply_df<3><<<gd, NT, 0, P->st>>>(P->lv[0].g, betaE, X, ldx, Y, ldy, s, scale, yb);
-    count_launch();
-    const double nc = P->dim == 2 ? 7.0 : 15.0;
-    count_bytes(BY_CCT, 8.0 * (double)P->n * ((yb == 0.0 ? 2.0 : 3.0) * s + nc));
-    return;
-  }
+  if (betaE == P->CbetaE && cct_df(P) && cct_dfp(P, false, X, ldx, Y, ldy, s, scale, yb)) return;
   dim3 grid(blocks_for(P->n, s), s);
   if (P->dim == 2)
     k_C_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, betaE, X, ldx, Y, ldy, scale, yb);
@@ -972,18 +1028,7 @@ void launch_C_apply(hp_problem *P, const double *X, long ldx, double *Y, long ld
 
 void launch_Ct_apply_beta(hp_problem *P, const double *beta_c, const double *W, long ldw, double *Y, long ldy, int s,
                           double scale, double beta) {
-  if (cct_df(P)) {
-    const int ng = (s + 3) / 4;
-    dim3 gd(blocks_for(P->n, ng), ng);
-    if (P->dim == 2)
-      k_Ct_apply_df<2><<<gd, NT, 0, P->st>>>(P->lv[0].g, P->E, beta_c, W, ldw, Y, ldy, s, scale, beta);
-    else
-      k_Ct_apply_df<3><<<gd, NT, 0, P->st>>>(P->lv[0].g, P->E, beta_c, W, ldw, Y, ldy, s, scale, beta);
-    count_launch();
-    const double nc = P->dim == 2 ? 7.0 : 15.0;
-    count_bytes(BY_CCT, 8.0 * (double)P->n * ((beta == 0.0 ? 2.0 : 3.0) * s + nc + 1.0));
-    return;
-  }
+  if (beta_c == P->Cbeta && cct_df(P) && cct_dfp(P, true, W, ldw, Y, ldy, s, scale, beta)) return;
   dim3 grid(blocks_for(P->n, s), s);
   if (P->dim == 2)
     k_Ct_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, beta_c, W, ldw, Y, ldy, scale, beta);

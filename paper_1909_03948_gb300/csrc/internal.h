@@ -42,6 +42,11 @@ template <typename T> struct Stencil {
   int nf = 0;
   bool full = false;
   double lmax = 2.0;  // upper bound of the spectrum of diag^-1 S (Gershgorin)
+  // FP64 stencils: the coefficients as double-float pairs {hi, lo} (c_f at [f n + i], the
+  // diagonal at [nf n + i]) for the double-float refinement, made on first use after the
+  // coefficients change (cpr_ok is cleared wherever they are rebuilt)
+  float2 *cpr = nullptr;
+  bool cpr_ok = false;
 };
 
 struct Level {
@@ -142,7 +147,7 @@ struct hp_problem {
   double cheb_alpha = 10.0;     // Chebyshev interval [lmax / alpha, lmax]             (tuning)
   int tma_tiles = 0;            // 2D stiffness levels as TMA-tiled stencil kernels       (tuning)
   int smem_tail = 0;            // coarse V-cycle levels in one shared-memory CTA per group (tuning)
-  int refine_df = 0;            // FP64 refinement arithmetic in double-float on the FP32 pipe:
+  int refine_df = 1;            // FP64 refinement arithmetic in double-float on the FP32 pipe:
                                 // 0 never, 1 for tolerances >= DF_MIN_RTOL, 2 always (tuning)
   cudaStream_t st = nullptr;
   cudaStream_t cap = nullptr;   // private stream used to capture CUDA graphs
@@ -159,6 +164,11 @@ struct hp_problem {
   bool have_point = false;
   double *m = nullptr, *E = nullptr, *u = nullptr, *lift = nullptr;
   double *Cbeta = nullptr;      // C as a stencil on e^m (.) X: (2^{D+1}-1) x n, built from u
+  // double-float pairs of CbetaE, Cbeta and e^m for the double-float C / C^T kernels, made on
+  // first use after C is rebuilt; the input block of those kernels as pairs (grouped by 4)
+  float2 *CbetaE_pr = nullptr, *Cbeta_pr = nullptr, *E_pr = nullptr;
+  bool cct_pr_ok = false;
+  hp::DBuf xpairs;
   double *CbetaE = nullptr;     // the same coefficients with e^m folded in (C X = CbetaE-stencil X)
   // adjoint terms of the full Newton Hessian (built on demand at the current point)
   double *padj = nullptr;       // adjoint p
@@ -287,6 +297,7 @@ void unet_run(hp_unet *U, int N, cudaStream_t st);  // forward of the first N in
 int warm_guess(hp_problem *P, const double *B, long ldb, double *X, long ldx, int s);
 // True when warm_guess would try a guess (a network attached and enabled, 2D).
 bool warm_attached(const hp_problem *P);
+bool warm_recording(const hp_problem *P);  // stiffness solves are being recorded as training samples
 // Columns j with flag[j] != 0 restart from zero: X_j = 0, R_j = B_j.
 void warm_fallback(hp_problem *P, const int *flag_host, int s, const double *B, long ldb, double *X, long ldx,
                    double *R, long ldr);

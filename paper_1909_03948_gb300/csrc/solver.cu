@@ -47,6 +47,7 @@ struct Fin {
   int *active = nullptr;
   int *iter = nullptr;  // PCG iteration counter (FIN_BETA: beta = 0 on the first iteration)
   const double *tol2col = nullptr;  // per-column squared relative tolerance (FIN_RR), else tol2
+  const double *open = nullptr;     // FIN_INIT: columns with open[j] == 0 start inactive
   double tol2 = 0.0;
 };
 
@@ -66,7 +67,7 @@ __device__ __forceinline__ void fin_apply(const Fin &f, int j, double s) {
     case FIN_INIT:
       f.bb[j] = s;
       f.rr[j] = s;
-      f.active[j] = s > 0.0;
+      f.active[j] = s > 0.0 && (f.open == nullptr || f.open[j] != 0.0);
       break;
   }
 }
@@ -966,33 +967,17 @@ __global__ void __launch_bounds__(NB) k_dot(long n, long gs, const T *__restrict
 }
 
 // r_T (grouped) = scale * r64 (column-major); columns >= s and converged ones are 0
-// One element of the inner right-hand side: scale * r.  In double-float mode (DF, FP32
-// inner solves only) r's leading 24 bits times the float scale, on the FP32 pipe: the
-// inner solve sees its right-hand side to FP32 precision either way.
-template <typename T, bool DF>
-__device__ __forceinline__ T inner_value(double r, double scale, float scale_f) {
-  if constexpr (DF) return d2df(r).hi * scale_f;
-  else return (T)(scale * r);
-}
-
-template <typename T, int VW, bool DF>
+template <typename T, int VW>
 __global__ void __launch_bounds__(NB) k_to_inner(long n, const double *__restrict__ R, long ldr,
                                                  const double *__restrict__ scale, int s, T *__restrict__ rt, long gs) {
   using PK = Pack<T, VW>;
   const int grp = blockIdx.y;
-  double sc[VW];
-  float scf[VW];
-#pragma unroll
-  for (int q = 0; q < VW; ++q) {
-    sc[q] = grp * VW + q < s ? scale[grp * VW + q] : 0.0;
-    scf[q] = (float)sc[q];
-  }
   for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
     PK o;
 #pragma unroll
     for (int q = 0; q < VW; ++q) {
       const int col = grp * VW + q;
-      o.v[q] = col < s ? inner_value<T, DF>(R[ldr * col + i], sc[q], scf[q]) : T(0);
+      o.v[q] = col < s ? (T)(scale[col] * R[ldr * col + i]) : T(0);
     }
     o.st(rt + grp * gs + i * VW);
   }
@@ -1000,7 +985,7 @@ __global__ void __launch_bounds__(NB) k_to_inner(long n, const double *__restric
 
 // The same scaling inside a graph-driven refinement: the first step (ctl->outer == 1,
 // counted before the step runs) starts from x = 0, so its residual is b0 itself.
-template <typename T, int VW, bool DF>
+template <typename T, int VW>
 __global__ void __launch_bounds__(NB) k_to_inner_ctl(long n, const double *__restrict__ B0,
                                                      const double *__restrict__ R, long ldr,
                                                      const RefineCtl *__restrict__ ctl,
@@ -1009,19 +994,12 @@ __global__ void __launch_bounds__(NB) k_to_inner_ctl(long n, const double *__res
   using PK = Pack<T, VW>;
   const double *src = ctl->outer == 1 ? B0 : R;
   const int grp = blockIdx.y;
-  double sc[VW];
-  float scf[VW];
-#pragma unroll
-  for (int q = 0; q < VW; ++q) {
-    sc[q] = grp * VW + q < s ? scale[grp * VW + q] : 0.0;
-    scf[q] = (float)sc[q];
-  }
   for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
     PK o;
 #pragma unroll
     for (int q = 0; q < VW; ++q) {
       const int col = grp * VW + q;
-      o.v[q] = col < s ? inner_value<T, DF>(src[ldr * col + i], sc[q], scf[q]) : T(0);
+      o.v[q] = col < s ? (T)(scale[col] * src[ldr * col + i]) : T(0);
     }
     o.st(rt + grp * gs + i * VW);
   }
@@ -1082,115 +1060,143 @@ __global__ void k_refine_ctl(int s, const double *__restrict__ rr, const double 
   }
 }
 
-// X (column-major FP64) += d / scale for the columns with scale != 0.  In double-float
-// mode (DF, FP32 inner solves only) the sum is formed on the FP32 pipe: x as a
-// double-float pair plus the exact product of d and the float |r| (two_prod), then
-// joined back into a double; the correction carries the inner solve's accuracy only, so
-// rounding |r| to float changes nothing that matters.
-template <typename T, int VW, bool DF>
+// X (column-major FP64) += d / scale for the columns with scale != 0
+template <typename T, int VW>
 __global__ void __launch_bounds__(NB) k_accum(long n, const T *__restrict__ d, long gs, const double *__restrict__ iscale,
                                               int s, double *__restrict__ X, long ldx) {
   using PK = Pack<T, VW>;
   const int grp = blockIdx.y;
-  double is[VW];
-  float isf[VW];
-#pragma unroll
-  for (int q = 0; q < VW; ++q) {
-    is[q] = grp * VW + q < s ? iscale[grp * VW + q] : 0.0;  // |r| of the column, 0 once converged
-    isf[q] = (float)is[q];
-  }
   for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
     const PK v = PK::ld(d + grp * gs + i * VW);
 #pragma unroll
     for (int q = 0; q < VW; ++q) {
       const int col = grp * VW + q;
-      if (col < s && is[q] != 0.0) {
-        double *xp = X + ldx * col + i;
-        if constexpr (DF) {
-          Dot2 a;
-          a.add(d2df(*xp));
-          a.add(two_prod((float)v.v[q], isf[q]));
-          *xp = df2d(a.result());
-        } else {
-          *xp += (double)v.v[q] * is[q];
-        }
+      if (col < s) {
+        const double is = iscale[col];  // |r| of the column, 0 when it has converged
+        if (is != 0.0) X[ldx * col + i] += (double)v.v[q] * is;
       }
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// FP64 refinement with its data held as double-float pairs (float2 {hi, lo}, 8 bytes per
-// value like a double): the right-hand side b and the iterate x of a solve live in the
-// refinement's own workspace in this form, so the residual and the update read and write
-// pairs directly and execute no conversion and no FP64 instruction per value.  The
-// caller's FP64 B is converted once when the solve starts (k_ir_start_df) and the result
-// joined back into its FP64 X once when it ends (k_df_out).  The residual is kept as its
-// leading float (the inner solve's right-hand side needs no more), so the scaling into the
-// inner precision reads 4 bytes per value.
+// FP64 iterative refinement in double-float arithmetic (tuning refine_df).  GB300 runs
+// FP64 at a small fraction of its FP32 rate, so around FP32 inner solves the refinement
+// can keep its right-hand side b and iterate x as double-float pairs (about 48
+// significand bits) and do its arithmetic on the FP32 pipe:
+//  * the pairs live in the refinement's workspace in the inner solver's grouped layout,
+//    one record {hi of 4 columns, lo of 4 columns} (two float4) per node and group, so
+//    every access is a 16-byte load or store and no value is converted on the way;
+//  * the caller's FP64 B is split into pairs once when the solve starts and x joined back
+//    into its FP64 X once when it ends (bit manipulation, no FP64 instruction);
+//  * the residual b - S x is a compensated (Dot2) sum of pair products with the level-0
+//    stencil's coefficients, also held as pairs; its leading float, scaled per column by
+//    a power of two sb with sb |b| in [0.5, 1), is written straight into the inner solve's
+//    right-hand side (the scaling is exact, and keeps the FP32 inner solve's values far
+//    from the float range's ends), with the column's |r|^2;
+//  * the update x += d / sb adds the inner solution to the pairs (two_sum).
+// Columns that have converged keep their residual in the inner right-hand side, but the
+// PCG starts them inactive (the open mask of FIN_INIT), so their x stays as it is.
 // ---------------------------------------------------------------------------
 
-// b = B (Dirichlet rows of a stiffness solve zeroed) as pairs, x = 0, the first residual
-// r = hi(b), and the per-block partials of |B|^2 (FP64)
-__global__ void __launch_bounds__(NB) k_ir_start_df(const double *__restrict__ B, long ldb, float2 *__restrict__ Bd,
-                                                    float2 *__restrict__ Xd, float *__restrict__ Rf, long ld, long n,
-                                                    long face, double *__restrict__ part) {
-  const int j = blockIdx.y;
-  double acc = 0.0;
-  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
-    const double v = (i < face || i >= n - face) ? 0.0 : B[ldb * j + i];
-    const dfl d = d2df(v);
-    Bd[ld * j + i] = make_float2(d.hi, d.lo);
-    Xd[ld * j + i] = make_float2(0.f, 0.f);
-    Rf[ld * j + i] = d.hi;
-    acc = fma(v, v, acc);
-  }
-  acc = block_sum<NB>(acc);
-  if (threadIdx.x == 0) part[(long)j * gridDim.x + blockIdx.x] = acc;
+// sb for a column with |b|^2 = b2 (1 when b = 0)
+__device__ __forceinline__ float col_scale(double b2) {
+  if (!(b2 > 0.0)) return 1.f;
+  int e;
+  (void)frexp(sqrt(b2), &e);  // |b| = f 2^e, f in [0.5, 1)
+  e = max(-125, min(125, e));
+  return __uint_as_float((unsigned)(127 - e) << 23);  // 2^-e
 }
 
-// r = b - S x from pairs, its leading float stored, and the per-column |r|^2 partials:
-// the squares are summed in FP32 on r scaled by 1/|b| (so that they stay far from the
-// float range's ends) and each block's sum is scaled back by |b|^2 in FP64.
-template <int D, bool FULL>
-__global__ void __launch_bounds__(NB) k_resid_df2(GridDesc g, const double *__restrict__ diag,
-                                                  const double *__restrict__ c, const float2 *__restrict__ Xd,
-                                                  const float2 *__restrict__ Bd, long ld, float *__restrict__ Rf,
-                                                  int s, const double *__restrict__ bb, Fin fin) {
-  constexpr int NF = FULL ? (1 << D) - 1 : D;
-  const int lane = threadIdx.x & 31;
-  const int i0 = blockIdx.x * 32 + lane;
-  const int nrows = D == 2 ? g.np : g.np * g.np;
-  const int grp = blockIdx.z;
-  float sb[4], accf[4] = {0.f, 0.f, 0.f, 0.f};
-  const float2 *xq[4];
-  const float2 *bq[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int col = min(grp * 4 + q, s - 1);  // columns past s repeat the last one, unstored
-    const double b2 = bb[col];
-    sb[q] = b2 > 0.0 ? (float)(1.0 / sqrt(b2)) : 1.f;
-    xq[q] = Xd + ld * col;
-    bq[q] = Bd + ld * col;
+// coefficient pairs of a stencil: c_f at [f n + i] (f < nf), the diagonal at [nf n + i]
+__global__ void k_coef_pairs(long n, int nf, const double *__restrict__ diag, const double *__restrict__ c,
+                             float2 *__restrict__ cpr) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    for (int f = 0; f < nf; ++f) {
+      const dfl d = d2df(c[(long)f * n + i]);
+      cpr[(long)f * n + i] = make_float2(d.hi, d.lo);
+    }
+    const dfl d = d2df(diag[i]);
+    cpr[(long)nf * n + i] = make_float2(d.hi, d.lo);
   }
-  for (int row = blockIdx.y * (NB / 32) + (threadIdx.x >> 5); row < nrows; row += gridDim.y * (NB / 32)) {
-    if (i0 >= g.np) break;
-    const int v[3] = {i0, D == 2 ? row : row % g.np, D == 2 ? 0 : row / g.np};
-    const long id = i0 + (long)g.np * row;
-    Dot2 a[4];
+}
+
+// b pairs = B (the `face` nodes at each end zeroed), x pairs = 0, |B|^2 block partials;
+// columns past s are zero
+__global__ void __launch_bounds__(NB) k_ir_start_dfp(const double *__restrict__ B, long ldb, int s, float4 *Bp,
+                                                     float4 *Xp, long ldp, long n, long face, double *part) {
+  const int grp = blockIdx.y;
+  Pack<double, 4> acc = Pack<double, 4>::zero();
+  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
+    const bool inner = i >= face && i < n - face;
+    float hi[4], lo[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float2 t = bq[q][id];
-      a[q].add(dfl{t.x, t.y});
+      const int col = grp * 4 + q;
+      const double v = (inner && col < s) ? B[ldb * col + i] : 0.0;
+      const dfl d = d2df(v);
+      hi[q] = d.hi;
+      lo[q] = d.lo;
+      acc.v[q] = fma(v, v, acc.v[q]);
     }
-    {
-      const dfl dg = d2df(diag[id]);
+    const long k = 2 * ((long)grp * ldp + i);
+    Bp[k] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+    Bp[k + 1] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    Xp[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    Xp[k + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  dot_partial<double, 4>(acc, part, grp, s, blockIdx.x, gridDim.x);
+}
+
+// the first inner right-hand side, from x = 0: rt = hi(b) sb
+__global__ void __launch_bounds__(NB) k_first_inner_dfp(const float4 *__restrict__ Bp, long ldp, long n,
+                                                        const double *__restrict__ bb, int s, float *__restrict__ rt,
+                                                        long gs) {
+  const int grp = blockIdx.y;
+  float sb[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float2 t = xq[q][id];
-        a[q].fms(dg, dfl{t.x, t.y});
-      }
-    }
+  for (int q = 0; q < 4; ++q) sb[q] = col_scale(grp * 4 + q < s ? bb[grp * 4 + q] : 0.0);
+  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
+    const float4 h = Bp[2 * ((long)grp * ldp + i)];
+    *reinterpret_cast<float4 *>(rt + grp * gs + i * 4) = make_float4(h.x * sb[0], h.y * sb[1], h.z * sb[2], h.w * sb[3]);
+  }
+}
+
+__device__ __forceinline__ void ld_pair4(const float4 *p, long k, dfl out[4]) {
+  const float4 h = p[k], l = p[k + 1];
+  out[0] = {h.x, l.x};
+  out[1] = {h.y, l.y};
+  out[2] = {h.z, l.z};
+  out[3] = {h.w, l.w};
+}
+
+// rt = (b - S x) sb from the pairs (four columns per thread, one node per thread over the
+// flattened grid), |r|^2 block partials.  Every load of a node's stencil is issued before
+// the arithmetic starts (2 NF + 2 pair records and 2 NF + 1 coefficient pairs in flight
+// per thread), and the four columns' compensated sums advance term by term.
+template <int D, bool FULL>
+__global__ void __launch_bounds__(NB) k_resid_dfp(GridDesc g, const float2 *__restrict__ cpr,
+                                                  const float4 *__restrict__ Xp, const float4 *__restrict__ Bp,
+                                                  long ldp, float *__restrict__ rt, long gs, int s,
+                                                  const double *__restrict__ bb, Fin fin) {
+  constexpr int NF = FULL ? (1 << D) - 1 : D;
+  const int grp = blockIdx.y;
+  float sb[4], accf[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sb[q] = col_scale(grp * 4 + q < s ? bb[grp * 4 + q] : 0.0);
+  const float4 *xg = Xp + 2 * (long)grp * ldp, *bg = Bp + 2 * (long)grp * ldp;
+  const unsigned np = (unsigned)g.np, n = (unsigned)g.n;
+  for (unsigned i = blockIdx.x * NB + threadIdx.x; i < n; i += gridDim.x * NB) {
+    int v[3];
+    const unsigned t = i / np;
+    v[0] = (int)(i - t * np);
+    v[1] = D == 2 ? (int)t : (int)(t % np);
+    v[2] = D == 2 ? 0 : (int)(t / np);
+    // the stencil's points: 0 the node, 1 + 2f / 2 + 2f the forward / backward neighbour f
+    unsigned pt[2 * NF + 1];
+    bool ok[2 * NF + 1];
+    pt[0] = i;
+    ok[0] = true;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       const int b = FULL ? f + 1 : (1 << f);
@@ -1201,177 +1207,98 @@ __global__ void __launch_bounds__(NB) k_resid_df2(GridDesc g, const double *__re
           fw = fw && (v[k] < g.N);
           bw = bw && (v[k] > 0);
         }
-      const long off = mask_offset(g, b);
-      if (fw) {
-        const dfl cf = d2df(c[(long)f * g.n + id]);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float2 t = xq[q][id + off];
-          a[q].fms(cf, dfl{t.x, t.y});
-        }
-      }
-      if (bw) {
-        const dfl cb = d2df(c[(long)f * g.n + id - off]);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float2 t = xq[q][id - off];
-          a[q].fms(cb, dfl{t.x, t.y});
-        }
-      }
+      const unsigned off = (unsigned)mask_offset(g, b);
+      ok[1 + 2 * f] = fw;
+      ok[2 + 2 * f] = bw;
+      pt[1 + 2 * f] = fw ? i + off : i;
+      pt[2 + 2 * f] = bw ? i - off : i;
     }
+    // loads: b, x at every point, the coefficient pair of every coupling
+    const float4 bh = bg[2 * i], bl = bg[2 * i + 1];
+    float4 xh[2 * NF + 1], xl[2 * NF + 1];
+    float2 cp[2 * NF + 1];
+#pragma unroll
+    for (int k = 0; k < 2 * NF + 1; ++k) {
+      xh[k] = xg[2 * pt[k]];
+      xl[k] = xg[2 * pt[k] + 1];
+    }
+    cp[0] = cpr[(unsigned)NF * n + i];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      cp[1 + 2 * f] = cpr[(unsigned)f * n + i];
+      cp[2 + 2 * f] = cpr[(unsigned)f * n + pt[2 + 2 * f]];
+    }
+    Dot2 a[4];
+    a[0].add(dfl{bh.x, bl.x});
+    a[1].add(dfl{bh.y, bl.y});
+    a[2].add(dfl{bh.z, bl.z});
+    a[3].add(dfl{bh.w, bl.w});
+#pragma unroll
+    for (int k = 0; k < 2 * NF + 1; ++k) {
+      if (!ok[k]) continue;
+      const dfl c{cp[k].x, cp[k].y};
+      a[0].fms(c, dfl{xh[k].x, xl[k].x});
+      a[1].fms(c, dfl{xh[k].y, xl[k].y});
+      a[2].fms(c, dfl{xh[k].z, xl[k].z});
+      a[3].fms(c, dfl{xh[k].w, xl[k].w});
+    }
+    float r[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int col = grp * 4 + q;
-      if (col < s) {
-        const float r = a[q].result().hi;
-        Rf[ld * col + id] = r;
-        const float t = r * sb[q];
-        accf[q] = fmaf(t, t, accf[q]);
-      }
+      r[q] = a[q].result().hi * sb[q];
+      accf[q] = fmaf(r[q], r[q], accf[q]);
     }
+    *reinterpret_cast<float4 *>(rt + grp * gs + (long)i * 4) = make_float4(r[0], r[1], r[2], r[3]);
   }
   Pack<double, 4> acc;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) acc.v[q] = (double)accf[q];
-  __shared__ double bbs[4];
-  if (threadIdx.x < 4) bbs[threadIdx.x] = grp * 4 + threadIdx.x < s ? bb[grp * 4 + threadIdx.x] : 0.0;
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 4; ++q) acc.v[q] *= bbs[q] > 0.0 ? bbs[q] : 1.0;
-  dot_partial<double, 4>(acc, fin.part, grp, s, blockIdx.x + gridDim.x * blockIdx.y, gridDim.x * gridDim.y);
+  for (int q = 0; q < 4; ++q) acc.v[q] = (double)accf[q] / ((double)sb[q] * (double)sb[q]);
+  dot_partial<double, 4>(acc, fin.part, grp, s, blockIdx.x, gridDim.x);
 }
 
-// inner right-hand side rt = r * scale from the residual's leading floats
-template <int VW>
-__global__ void __launch_bounds__(NB) k_to_inner_df2(long n, const float *__restrict__ Rf, long ld,
-                                                     const double *__restrict__ scale, int s, float *__restrict__ rt,
-                                                     long gs) {
-  using PK = Pack<float, VW>;
+// x pairs += d / sb for the open columns (iscale != 0)
+__global__ void __launch_bounds__(NB) k_accum_dfp(long n, const float *__restrict__ d, long gs,
+                                                  const double *__restrict__ iscale, const double *__restrict__ bb,
+                                                  int s, float4 *__restrict__ Xp, long ldp) {
   const int grp = blockIdx.y;
-  float sc[VW];
+  float isb[4];
+  bool open[4];
 #pragma unroll
-  for (int q = 0; q < VW; ++q) sc[q] = grp * VW + q < s ? (float)scale[grp * VW + q] : 0.f;
-  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
-    PK o;
-#pragma unroll
-    for (int q = 0; q < VW; ++q) {
-      const int col = grp * VW + q;
-      o.v[q] = col < s ? Rf[ld * col + i] * sc[q] : 0.f;
-    }
-    o.st(rt + grp * gs + i * VW);
+  for (int q = 0; q < 4; ++q) {
+    const int col = grp * 4 + q;
+    open[q] = col < s && iscale[col] != 0.0;
+    isb[q] = 1.f / col_scale(col < s ? bb[col] : 0.0);  // a power of two: exact
   }
-}
-
-// x += d * |r| on the pairs, for the columns with |r| != 0
-template <int VW>
-__global__ void __launch_bounds__(NB) k_accum_df2(long n, const float *__restrict__ d, long gs,
-                                                  const double *__restrict__ iscale, int s, float2 *__restrict__ Xd,
-                                                  long ld) {
-  using PK = Pack<float, VW>;
-  const int grp = blockIdx.y;
-  float isf[VW];
-#pragma unroll
-  for (int q = 0; q < VW; ++q) isf[q] = grp * VW + q < s ? (float)iscale[grp * VW + q] : 0.f;
   for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
-    const PK v = PK::ld(d + grp * gs + i * VW);
-#pragma unroll
-    for (int q = 0; q < VW; ++q) {
-      const int col = grp * VW + q;
-      if (col < s && isf[q] != 0.f) {
-        float2 *xp = Xd + ld * col + i;
-        const float2 x = *xp;
-        Dot2 a;
-        a.add(dfl{x.x, x.y});
-        a.add(two_prod(v.v[q], isf[q]));
-        const dfl r = a.result();
-        *xp = make_float2(r.hi, r.lo);
-      }
-    }
-  }
-}
-
-// X (FP64) = the pairs joined, column by column
-__global__ void __launch_bounds__(NB) k_df_out(const float2 *__restrict__ Xd, long ld, double *__restrict__ X,
-                                               long ldx, long n) {
-  const int j = blockIdx.y;
-  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
-    const float2 t = Xd[ld * j + i];
-    X[ldx * j + i] = df2d(dfl{t.x, t.y});
-  }
-}
-
-// FP64 refinement residual R = B - S X with its per-column norm, evaluated in
-// double-float arithmetic on the FP32 pipe (Dot2 accumulation of the stencil's products,
-// FP64 data converted by bit manipulation).  Stencil as k_st (the same coefficient
-// arrays); four columns per thread share the converted coefficients; the squared norm is
-// summed in FP64 (one FP64 operation per element, under the memory time).
-template <int D, bool FULL>
-__global__ void __launch_bounds__(NB) k_resid_df(GridDesc g, const double *__restrict__ diag,
-                                                 const double *__restrict__ c, const double *__restrict__ X, long ldx,
-                                                 const double *__restrict__ B, long ldb, double *__restrict__ R,
-                                                 long ldr, int s, Fin fin) {
-  constexpr int NF = FULL ? (1 << D) - 1 : D;
-  const int lane = threadIdx.x & 31;
-  const int i0 = blockIdx.x * 32 + lane;
-  const int nrows = D == 2 ? g.np : g.np * g.np;
-  const int grp = blockIdx.z;
-  Pack<double, 4> acc = Pack<double, 4>::zero();
-  for (int row = blockIdx.y * (NB / 32) + (threadIdx.x >> 5); row < nrows; row += gridDim.y * (NB / 32)) {
-    if (i0 >= g.np) break;
-    const int v[3] = {i0, D == 2 ? row : row % g.np, D == 2 ? 0 : row / g.np};
-    const long id = i0 + (long)g.np * row;
-    const dfl dg = d2df(diag[id]);
-    dfl cf[NF], cb[NF];
-    long off[NF];
-    bool fw[NF], bw[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const int b = FULL ? f + 1 : (1 << f);
-      fw[f] = true;
-      bw[f] = true;
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-        if ((b >> a) & 1) {
-          fw[f] = fw[f] && (v[a] < g.N);
-          bw[f] = bw[f] && (v[a] > 0);
-        }
-      off[f] = mask_offset(g, b);
-      cf[f] = fw[f] ? d2df(c[(long)f * g.n + id]) : dfl{0.f, 0.f};
-      cb[f] = bw[f] ? d2df(c[(long)f * g.n + id - off[f]]) : dfl{0.f, 0.f};
-    }
-    // the group's four columns advance together, term by term, so that their four
-    // compensated sums are independent dependency chains (columns past s repeat the
-    // last column and are not stored)
-    const double *xq[4];
-    Dot2 a[4];
+    const float4 dv = *reinterpret_cast<const float4 *>(d + grp * gs + i * 4);
+    const float dd[4] = {dv.x, dv.y, dv.z, dv.w};
+    const long k = 2 * ((long)grp * ldp + i);
+    dfl x[4];
+    ld_pair4(Xp, k, x);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int col = min(grp * 4 + q, s - 1);
-      xq[q] = X + ldx * col;
-      a[q].add(d2df(B[ldb * col + id]));
+      if (!open[q]) continue;
+      Dot2 a;
+      a.add(x[q]);
+      a.add(dfl{dd[q] * isb[q], 0.f});
+      x[q] = a.result();
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) a[q].fms(dg, d2df(xq[q][id]));
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      if (fw[f])
-#pragma unroll
-        for (int q = 0; q < 4; ++q) a[q].fms(cf[f], d2df(xq[q][id + off[f]]));
-      if (bw[f])
-#pragma unroll
-        for (int q = 0; q < 4; ++q) a[q].fms(cb[f], d2df(xq[q][id - off[f]]));
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int col = grp * 4 + q;
-      if (col < s) {
-        const double r = df2d(a[q].result());
-        R[ldr * col + id] = r;
-        acc.v[q] = fma(r, r, acc.v[q]);
-      }
-    }
+    Xp[k] = make_float4(x[0].hi, x[1].hi, x[2].hi, x[3].hi);
+    Xp[k + 1] = make_float4(x[0].lo, x[1].lo, x[2].lo, x[3].lo);
   }
-  dot_partial<double, 4>(acc, fin.part, grp, s, blockIdx.x + gridDim.x * blockIdx.y, gridDim.x * gridDim.y);
+}
+
+// X (FP64, column-major) = the x pairs joined, for the s columns
+__global__ void __launch_bounds__(NB) k_df_out_dfp(const float4 *__restrict__ Xp, long ldp, long n, int s,
+                                                   double *__restrict__ X, long ldx) {
+  const int grp = blockIdx.y;
+  for (long i = blockIdx.x * (long)NB + threadIdx.x; i < n; i += (long)gridDim.x * NB) {
+    dfl x[4];
+    ld_pair4(Xp, 2 * ((long)grp * ldp + i), x);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (grp * 4 + q < s) X[ldx * (grp * 4 + q) + i] = df2d(x[q]);
+  }
 }
 
 // End of a PCG iteration: count it and decide whether another one runs.  In
@@ -1669,10 +1596,12 @@ static void st_launch(const GridDesc &g, const Stencil<T> &S, const T *X, long g
                       int s, T omega, const Fin &fin, cudaStream_t st, T omega2 = T(0)) {
   count_bytes(sizeof(T) == 8 && MODE == M_RESID_DOT ? BY_REFINE : level_family(g.n), st_bytes<T, MODE>(g, S, s));
   if constexpr (sizeof(T) == 4 && VW == 4 && MODE != M_RESID_DOT) {
-    if (tl_tma && S.pk && !S.full && tile_grid(g) &&
+    // tma_tiles 1: every eligible level; 2: the finest level only
+    const bool tma = tl_tma == 1 || (tl_tma == 2 && g.n == tl_n0);
+    if (tma && S.pk && !S.full && tile_grid(g) &&
         tile_launch<MODE>(g, S, X, gx, B, gb, Y, gy, s, omega, omega2, fin, st))
       return;
-    if (tl_tma && S.pk && !S.full && tile3_grid(g) &&
+    if (tma && S.pk && !S.full && tile3_grid(g) &&
         tile3_launch<MODE>(g, S, X, gx, B, gb, Y, gy, s, omega, omega2, fin, st))
       return;
   }
@@ -1786,8 +1715,13 @@ int ensure_scalars(hp_problem *P, int s) {
   return 0;
 }
 
+// set while a double-float refinement runs: its converged columns start each inner PCG
+// inactive (their scale is 0)
+static thread_local const double *tl_open = nullptr;
+
 static Fin make_fin(hp_problem *P, int kind, double tol2 = 0.0, double *out = nullptr) {
   Fin f;
+  if (kind == FIN_INIT) f.open = tl_open;
   f.part = P->sc.partial.as<double>();
   f.cnt = P->sc.counter.as<unsigned>();
   f.kind = kind;
@@ -2835,38 +2769,15 @@ int apply_op64(hp_problem *P, OpKind op, const double *X, long ldx, double *Y, l
 // FP64 residual is checked against the oracle at 1e-8), below it the solve keeps the FP64
 // arithmetic.
 constexpr double DF_MIN_RTOL = 1e-9;
-static thread_local bool tl_df = false;
 static bool use_df(const hp_problem *P, int tbytes, double rtol) {
   return tbytes == 4 && (P->refine_df == 2 || (P->refine_df == 1 && rtol >= DF_MIN_RTOL));
-}
-
-template <bool FULL>
-static void launch_resid_df(const GridDesc &g, const Stencil<double> &S, const double *X, long ldx, const double *B,
-                            long ldb, double *R, long ldr, int s, const Fin &fin, cudaStream_t st) {
-  const int ng = (s + 3) / 4;
-  const dim3 grid = rowgrid_capped(g, ng);
-  if (g.dim == 2)
-    k_resid_df<2, FULL><<<grid, NB, 0, st>>>(g, S.diag, S.c, X, ldx, B, ldb, R, ldr, s, fin);
-  else
-    k_resid_df<3, FULL><<<grid, NB, 0, st>>>(g, S.diag, S.c, X, ldx, B, ldb, R, ldr, s, fin);
-  count_launch();
-  count_bytes(BY_REFINE, 8.0 * (double)g.n * (3.0 * s + 1.0 + S.nf));
-  dot_finalize(fin, grid.x * grid.y, s, st);
 }
 
 static int residual64(hp_problem *P, OpKind op, const double *B, long ldb, const double *X, long ldx, double *R,
                       long ldr, int s) {
   const int pr = prof_start(P, PROF_RESID64);
-  const Stencil<double> &S = stencil_of<double>(P, op, 0);
-  const Fin fin = make_fin(P, FIN_STORE, 0.0, P->sc.rr.as<double>());
-  if (tl_df) {
-    if (S.full)
-      launch_resid_df<true>(P->lv[0].g, S, X, ldx, B, ldb, R, ldr, s, fin, P->st);
-    else
-      launch_resid_df<false>(P->lv[0].g, S, X, ldx, B, ldb, R, ldr, s, fin, P->st);
-  } else {
-    st_launch<double, 1, M_RESID_DOT>(P->lv[0].g, S, X, ldx, B, ldb, R, ldr, s, 0.0, fin, P->st);
-  }
+  st_launch<double, 1, M_RESID_DOT>(P->lv[0].g, stencil_of<double>(P, op, 0), X, ldx, B, ldb, R, ldr, s, 0.0,
+                                    make_fin(P, FIN_STORE, 0.0, P->sc.rr.as<double>()), P->st);
   prof_stop(P, pr);
   return cuda_check(cudaGetLastError(), "residual");
 }
@@ -2926,21 +2837,14 @@ static int build_solve_graph(hp_problem *P, OpKind op, int s, double rtol, doubl
     }
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-      if (tl_df)
-        k_to_inner_ctl<T, VW, true><<<nodegrid(n, ng), NB, 0, cs>>>(n, b64, r64, ld64, ctl, scale, s,
-                                                                    W.r.template as<T>(), gs);
-      else
-        k_to_inner_ctl<T, VW, false><<<nodegrid(n, ng), NB, 0, cs>>>(n, b64, r64, ld64, ctl, scale, s, W.r.template as<T>(),
+      k_to_inner_ctl<T, VW><<<nodegrid(n, ng), NB, 0, cs>>>(n, b64, r64, ld64, ctl, scale, s, W.r.template as<T>(),
                                                             gs);
       e = end_capture(body, true);
     }
     if (e == cudaSuccess) e = append_pcg<T, VW>(P, op, s, tol_in, maxit, body, leaf, &pw);
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, &pw, nullptr, 1, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-      if (tl_df)
-        k_accum<T, VW, true><<<nodegrid(n, ng), NB, 0, cs>>>(n, W.x.template as<T>(), gs, iscale, s, x64, ld64);
-      else
-        k_accum<T, VW, false><<<nodegrid(n, ng), NB, 0, cs>>>(n, W.x.template as<T>(), gs, iscale, s, x64, ld64);
+      k_accum<T, VW><<<nodegrid(n, ng), NB, 0, cs>>>(n, W.x.template as<T>(), gs, iscale, s, x64, ld64);
       const int rc = residual64(P, op, b64, ld64, x64, ld64, r64, ld64, s);
       k_refine_ctl<<<1, 256, 0, cs>>>(s, rr, bb, rtol, tol_in, scale, iscale, tol2col, iter, 1, max_outer, ctl, ho);
       e = end_capture(body, false);
@@ -3004,6 +2908,247 @@ static int ir_solve_graph(hp_problem *P, OpKind op, const double *B, long ldb, d
   return cuda_check(cudaGetLastError(), "ir_solve");
 }
 
+// ---- the double-float refinement (tuning refine_df; FP32 inner solves, 4 columns per group)
+
+// the double-float coefficient pairs of a level-0 FP64 stencil, made when missing or stale
+static int ensure_cpr(hp_problem *P, OpKind op) {
+  Stencil<double> &S = const_cast<Stencil<double> &>(stencil_of<double>(P, op, 0));
+  const long n = P->lv[0].g.n;
+  if (!S.cpr) HP_CUDA(cudaMalloc(&S.cpr, sizeof(float2) * (size_t)(S.nf + 1) * n));
+  if (!S.cpr_ok) {
+    k_coef_pairs<<<blocks_for(n, 1), NT, 0, P->st>>>(n, S.nf, S.diag, S.c, S.cpr);
+    count_launch();
+    S.cpr_ok = true;
+  }
+  return cuda_check(cudaGetLastError(), "coefficient pairs");
+}
+
+// rt = (b - S x) sb and the columns' |r|^2 -> sc.rr
+static void launch_resid_dfp(hp_problem *P, OpKind op, const float4 *Xp, const float4 *Bp, long ldp, float *rt,
+                             long gs, int s, const double *bb) {
+  const Stencil<double> &S = stencil_of<double>(P, op, 0);
+  const GridDesc &g = P->lv[0].g;
+  const int ng = (s + 3) / 4;
+  const dim3 gr = nodegrid(g.n, ng);
+  const Fin fin = make_fin(P, FIN_STORE, 0.0, P->sc.rr.as<double>());
+  const int pr = prof_start(P, PROF_RESID64);
+  if (g.dim == 2) {
+    if (S.full)
+      k_resid_dfp<2, true><<<gr, NB, 0, P->st>>>(g, S.cpr, Xp, Bp, ldp, rt, gs, s, bb, fin);
+    else
+      k_resid_dfp<2, false><<<gr, NB, 0, P->st>>>(g, S.cpr, Xp, Bp, ldp, rt, gs, s, bb, fin);
+  } else {
+    if (S.full)
+      k_resid_dfp<3, true><<<gr, NB, 0, P->st>>>(g, S.cpr, Xp, Bp, ldp, rt, gs, s, bb, fin);
+    else
+      k_resid_dfp<3, false><<<gr, NB, 0, P->st>>>(g, S.cpr, Xp, Bp, ldp, rt, gs, s, bb, fin);
+  }
+  count_launch();
+  // x and b pairs, the inner right-hand side written, the coefficient pairs
+  count_bytes(BY_REFINE, (double)g.n * (20.0 * s + 8.0 * (S.nf + 1)));
+  dot_finalize(fin, gr.x, s, P->st);
+  prof_stop(P, pr);
+}
+
+static void launch_accum_dfp(hp_problem *P, const float *d, long gs, int s, float4 *Xp, long ldp) {
+  const int ng = (s + 3) / 4;
+  k_accum_dfp<<<nodegrid(P->n, ng), NB, 0, P->st>>>(P->n, d, gs, P->sc.iscale.as<double>(), P->sc.bbr.as<double>(),
+                                                     s, Xp, ldp);
+  count_launch();
+  count_bytes(BY_REFINE, 20.0 * (double)P->n * s);  // read the correction, read and write the x pairs
+}
+
+static void launch_first_inner_dfp(hp_problem *P, const float4 *Bp, long ldp, int s, float *rt, long gs) {
+  const int ng = (s + 3) / 4;
+  k_first_inner_dfp<<<nodegrid(P->n, ng), NB, 0, P->st>>>(Bp, ldp, P->n, P->sc.bbr.as<double>(), s, rt, gs);
+  count_launch();
+  count_bytes(BY_REFINE, 8.0 * (double)P->n * s);  // hi(b) read, the inner right-hand side written
+}
+
+// Captures the double-float refinement loop of one configuration: the first convergence
+// check and the first inner right-hand side, then a WHILE node over the steps -- the PCG
+// (a nested WHILE node), the update of the x pairs, the residual into the next inner
+// right-hand side with its norm, and the control kernel.
+template <typename T, int VW>
+static int build_solve_graph_dfp(hp_problem *P, OpKind op, int s, double rtol, double tol_in, SolveGraph *out) {
+  BlockWS<T> &W = ws_of<T>(P);
+  const long ldp = padded(P->n);
+  const long gs = W.ldn * VW;
+  float4 *Bp = reinterpret_cast<float4 *>(P->b64.p), *Xp = reinterpret_cast<float4 *>(P->x64.p);
+  RefineCtl *ctl = P->rctl.as<RefineCtl>();
+  const int maxit = P->max_iter, max_outer = P->max_outer;
+  double *scale = P->sc.scale.as<double>(), *iscale = P->sc.iscale.as<double>();
+  double *tol2col = P->sc.tol2col.as<double>(), *rr = P->sc.rr.as<double>(), *bb = P->sc.bbr.as<double>();
+  const int *iter = P->sc.iter.as<int>();
+  float *rt = reinterpret_cast<float *>(W.r.p), *d = reinterpret_cast<float *>(W.x.p);
+  return with_capture_stream(P, [&]() -> int {
+    cudaStream_t cs = P->cap;
+    cudaGraph_t g = nullptr, body = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    cudaGraphConditionalHandle ho;
+    cudaGraphNode_t leaf = nullptr, wn = nullptr, pw = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&ho, g, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      cudaMemsetAsync(ctl, 0, sizeof(RefineCtl), cs);
+      k_refine_ctl<<<1, 256, 0, cs>>>(s, rr, bb, rtol, tol_in, scale, iscale, tol2col, iter, 0, max_outer, ctl, ho);
+      launch_first_inner_dfp(P, Bp, ldp, s, rt, gs);
+      const cudaError_t el = capture_leaf(cs, &leaf);
+      cudaGraph_t gg = g;
+      e = cudaStreamEndCapture(cs, &gg);
+      if (e == cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) {
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = ho;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&wn, g, &leaf, nullptr, 1, &cp);
+      if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess) e = append_pcg<T, VW>(P, op, s, tol_in, maxit, body, nullptr, &pw);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, &pw, nullptr, 1, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      launch_accum_dfp(P, d, gs, s, Xp, ldp);
+      launch_resid_dfp(P, op, Xp, Bp, ldp, rt, gs, s, bb);
+      k_refine_ctl<<<1, 256, 0, cs>>>(s, rr, bb, rtol, tol_in, scale, iscale, tol2col, iter, 1, max_outer, ctl, ho);
+      cudaGraph_t bg = body;
+      e = cudaStreamEndCapture(cs, &bg);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_check(e, "double-float refinement graph");
+    *out = SolveGraph{(int)op, 100 + (int)sizeof(T), VW, s, maxit, max_outer, rtol, tol_in, ex};
+    return 0;
+  });
+}
+
+// The refinement of ir_solve in double-float (from x = 0): b and x as pairs in the
+// workspace, the loop as one graph launch (or, with profiling or graphs off, a host loop
+// over the same kernels), the pairs joined into X at the end.
+template <typename T, int VW>
+static int ir_solve_dfp(hp_problem *P, OpKind op, const double *B, long ldb, double *X, long ldx, int s, double rtol,
+                        double tol_in, hp_solve_stats *stats) {
+  if constexpr (sizeof(T) != 4 || VW != 4) {
+    return set_error(HP_ERR_INVALID, "double-float refinement needs FP32 inner solves");
+  } else {
+    BlockWS<T> &W = ws_of<T>(P);
+    cudaStream_t st = P->st;
+    const long n = P->n, ldp = padded(n);
+    const int ng = (s + 3) / 4;
+    const long gs = W.ldn * VW;
+    const size_t pbytes = sizeof(float4) * 2 * (size_t)ldp * ng;
+    HP_TRY(ensure_kept(P, P->b64, pbytes));
+    HP_TRY(ensure_kept(P, P->x64, pbytes));
+    HP_TRY(ensure_kept(P, P->rctl, sizeof(RefineCtl)));
+    if (!P->h_rctl) HP_CUDA(cudaMallocHost(&P->h_rctl, sizeof(RefineCtl)));
+    HP_TRY(ensure_cpr(P, op));
+    struct OpenGuard {
+      OpenGuard(const double *p) { tl_open = p; }
+      ~OpenGuard() { tl_open = nullptr; }
+    } open_guard(P->sc.scale.as<double>());
+    float4 *Bp = reinterpret_cast<float4 *>(P->b64.p), *Xp = reinterpret_cast<float4 *>(P->x64.p);
+    float *rt = reinterpret_cast<float *>(W.r.p), *d = reinterpret_cast<float *>(W.x.p);
+    double *bb = P->sc.bbr.as<double>(), *rr = P->sc.rr.as<double>();
+    const GridDesc &g0 = P->lv[0].g;
+    const long face = op == OP_K ? (P->dim == 2 ? g0.np : (long)g0.np * g0.np) : 0;
+    {  // b, x = 0 and |b|^2 (= the first |r|^2) in one pass over B
+      const dim3 gr = nodegrid(n, ng);
+      const Fin fin = make_fin(P, FIN_STORE, 0.0, bb);
+      k_ir_start_dfp<<<gr, NB, 0, st>>>(B, ldb, s, Bp, Xp, ldp, n, face, fin.part);
+      count_launch();
+      count_bytes(BY_REFINE, 24.0 * (double)n * s);  // B read, b and x pairs written
+      dot_finalize(fin, gr.x, s, st);
+      launch_copy(bb, 0, rr, 0, s, 1, st);
+    }
+    int total_its = 0, outer = 0, rc = 0;
+    double worst = 0.0;
+    if (P->use_graphs && !P->prof_on) {
+      SolveGraph *G = nullptr;
+      for (auto &sg : P->sgraphs)
+        if (sg.op == (int)op && sg.tbytes == 100 + (int)sizeof(T) && sg.vw == VW && sg.s == s &&
+            sg.maxit == P->max_iter && sg.max_outer == P->max_outer && sg.rtol == rtol && sg.tol_in == tol_in)
+          G = &sg;
+      if (!G) {
+        SolveGraph ngr;
+        HP_TRY((build_solve_graph_dfp<T, VW>(P, op, s, rtol, tol_in, &ngr)));
+        P->sgraphs.push_back(ngr);
+        G = &P->sgraphs.back();
+      }
+      HP_CUDA(cudaGraphLaunch(G->exec, st));
+      k_df_out_dfp<<<nodegrid(n, ng), NB, 0, st>>>(Xp, ldp, n, s, X, ldx);
+      count_launch();
+      count_bytes(BY_REFINE, 16.0 * (double)n * s);
+      int *h_it = P->sc.h_iter;
+      HP_CUDA(cudaMemcpyAsync(P->h_rctl, P->rctl.p, sizeof(RefineCtl), cudaMemcpyDeviceToHost, st));
+      HP_CUDA(cudaMemcpyFromSymbolAsync(h_it + 1, g_tile_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+      HP_CUDA(cudaStreamSynchronize(st));
+      const RefineCtl c = *P->h_rctl;
+      HP_TRY(tile_timeout_check(P, h_it));
+      // kernels run: the first check and right-hand side, per step the PCG init (3) and
+      // iterations, the update, the residual with its finalisation and the check
+      count_launch(2ull + 7ull * (unsigned long long)c.outer +
+                   (unsigned long long)c.total_its * (unsigned long long)kernels_per_iteration(P, op, (int)(sizeof(T) * VW)));
+      if (c.flags & 2) return set_error(HP_ERR_NONFINITE, "non-finite residual in a PDE solve");
+      total_its = c.total_its;
+      outer = c.outer;
+      worst = c.worst;
+      if (c.flags & 1) rc = HP_ERR_NOT_CONVERGED;
+    } else {
+      double *hrr = P->sc.h_rr, *hbb = P->sc.h_bb;
+      HP_CUDA(cudaMemcpyAsync(hbb, bb, sizeof(double) * s, cudaMemcpyDeviceToHost, st));
+      std::vector<double> hscale(s), hiscale(s), htol2(s);
+      for (outer = 0; outer <= P->max_outer; ++outer) {
+        HP_CUDA(cudaMemcpyAsync(hrr, rr, sizeof(double) * s, cudaMemcpyDeviceToHost, st));
+        HP_CUDA(cudaStreamSynchronize(st));
+        int nact = 0;
+        worst = 0.0;
+        for (int j = 0; j < s; ++j) {  // the test and inner tolerance of k_refine_ctl
+          if (!std::isfinite(hrr[j])) return set_error(HP_ERR_NONFINITE, "non-finite residual in a PDE solve");
+          const double rel = hbb[j] > 0 ? std::sqrt(hrr[j] / hbb[j]) : 0.0;
+          worst = std::max(worst, rel);
+          const bool done = hbb[j] == 0.0 || hrr[j] <= rtol * rtol * hbb[j];
+          hscale[j] = done ? 0.0 : 1.0 / std::sqrt(hrr[j]);
+          hiscale[j] = done ? 0.0 : std::sqrt(hrr[j]);
+          const double need = hrr[j] > 0 ? 0.25 * rtol * std::sqrt(hbb[j] / hrr[j]) : 1.0;
+          const double t = std::min(0.5, std::max(tol_in, need));
+          htol2[j] = t * t;
+          nact += !done;
+        }
+        if (nact == 0) break;
+        if (outer == P->max_outer) {
+          rc = HP_ERR_NOT_CONVERGED;
+          break;
+        }
+        HP_CUDA(cudaMemcpyAsync(P->sc.scale.p, hscale.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
+        HP_CUDA(cudaMemcpyAsync(P->sc.iscale.p, hiscale.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
+        HP_CUDA(cudaMemcpyAsync(P->sc.tol2col.p, htol2.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
+        if (outer == 0) launch_first_inner_dfp(P, Bp, ldp, s, rt, gs);
+        int its = 0;
+        const int prc = pcg<T, VW>(P, op, s, tol_in, P->max_iter, &its);
+        if (prc && prc != HP_ERR_NOT_CONVERGED) return prc;
+        total_its += its;
+        prof_spin(P);
+        launch_accum_dfp(P, d, gs, s, Xp, ldp);
+        launch_resid_dfp(P, op, Xp, Bp, ldp, rt, gs, s, bb);
+      }
+      k_df_out_dfp<<<nodegrid(n, ng), NB, 0, st>>>(Xp, ldp, n, s, X, ldx);
+      count_launch();
+      count_bytes(BY_REFINE, 16.0 * (double)n * s);
+    }
+    if (stats) {
+      stats->iterations += total_its;
+      stats->outer += outer;
+      stats->solves += 1;
+      stats->rel_res = std::max(stats->rel_res, worst);
+    }
+    if (rc) return set_error(rc, "PDE solve did not reach the requested tolerance");
+    return cuda_check(cudaGetLastError(), "ir_solve (double-float)");
+  }
+}
+
 template <typename T, int VW>
 static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double *X, long ldx, int s, double rtol,
                     double tol_in, hp_solve_stats *stats) {
@@ -3015,7 +3160,10 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
   const long gs = W.ldn * VW;
   HP_TRY(ensure_kept(P, P->r64, sizeof(double) * ld64 * s));
   HP_TRY(ensure_kept(P, P->b64, sizeof(double) * ld64 * s));
-  tl_df = use_df(P, (int)sizeof(T), rtol);
+  // double-float refinement (not with a learned initial guess, nor while stiffness solves are
+  // recorded for its training: those paths keep the FP64 layout)
+  if (use_df(P, (int)sizeof(T), rtol) && VW == 4 && !(op == OP_K && (warm_attached(P) || warm_recording(P))))
+    return ir_solve_dfp<T, VW>(P, op, B, ldb, X, ldx, s, rtol, tol_in, stats);
   // from x = 0 with graphs on, the whole refinement runs as one captured loop
   if (P->use_graphs && !P->prof_on && !(op == OP_K && warm_attached(P)))
     return ir_solve_graph<T, VW>(P, op, B, ldb, X, ldx, s, rtol, tol_in, stats);
@@ -3079,12 +3227,8 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
     HP_CUDA(cudaMemcpyAsync(P->sc.tol2col.p, htol2.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
     // the first residual of a solve from zero is b64 (r64 not yet written)
     const double *rsrc = (outer == 0 && !warm) ? b64 : r64;
-    if (tl_df)
-      k_to_inner<T, VW, true><<<nodegrid(n, ng), NB, 0, st>>>(n, rsrc, ld64, P->sc.scale.as<double>(), s,
-                                                              W.r.template as<T>(), gs);
-    else
-      k_to_inner<T, VW, false><<<nodegrid(n, ng), NB, 0, st>>>(n, rsrc, ld64, P->sc.scale.as<double>(), s,
-                                                               W.r.template as<T>(), gs);
+    k_to_inner<T, VW><<<nodegrid(n, ng), NB, 0, st>>>(n, rsrc, ld64, P->sc.scale.as<double>(), s,
+                                                      W.r.template as<T>(), gs);
     count_launch();
     count_bytes(BY_REFINE, (8.0 + sizeof(T)) * (double)n * s);  // read the FP64 residual, write the inner one
     int its = 0;
@@ -3093,12 +3237,8 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
     if (prc && prc != HP_ERR_NOT_CONVERGED) return prc;
     total_its += its;
     prof_spin(P);
-    if (tl_df)
-      k_accum<T, VW, true><<<nodegrid(n, ng), NB, 0, st>>>(n, W.x.template as<T>(), gs, P->sc.iscale.as<double>(),
-                                                           s, X, ldx);
-    else
-      k_accum<T, VW, false><<<nodegrid(n, ng), NB, 0, st>>>(n, W.x.template as<T>(), gs, P->sc.iscale.as<double>(),
-                                                            s, X, ldx);
+    k_accum<T, VW><<<nodegrid(n, ng), NB, 0, st>>>(n, W.x.template as<T>(), gs, P->sc.iscale.as<double>(), s, X,
+                                                   ldx);
     count_launch();
     count_bytes(BY_REFINE, (16.0 + sizeof(T)) * (double)n * s);  // read the correction, read and write x
     HP_TRY(residual64(P, op, b64, ld64, X, ldx, r64, ld64, s));

@@ -23,10 +23,10 @@ int hp_set_tuning(hp_problem *P, const hp_tuning *t) {
   if (t->nu < 1 || t->nu > 4 || t->nu_coarse < 0 || t->nu_coarse > 4 || !(t->omega > 0.0 && t->omega < 1.0) || t->col_chunk < 0 || t->max_blocks < 64 ||
       t->max_blocks > (1 << 20) || t->fuse_from < 0 || t->fuse_from >= HP_MAXL || t->smoother < 0 ||
       t->smoother > 1 || (t->smoother == 1 && !(t->cheb_alpha > 1.0 && t->cheb_alpha < 1e6)) ||
-      t->fuse_transfer < 0 || t->fuse_transfer > 2 || t->tma_tiles < 0 || t->tma_tiles > 1 ||
+      t->fuse_transfer < 0 || t->fuse_transfer > 2 || t->tma_tiles < 0 || t->tma_tiles > 2 ||
       t->smem_tail < 0 || t->smem_tail >= HP_MAXL || t->refine_df < 0 || t->refine_df > 2)
     return set_error(HP_ERR_INVALID, "hp_set_tuning: nu in [1,4], omega in (0,1), col_chunk >= 0, max_blocks >= 64, "
-                                     "fuse_from in [0, 15], smoother 0/1, cheb_alpha > 1, fuse_transfer 0..2, tma_tiles 0/1, smem_tail in [0, 15], "
+                                     "fuse_from in [0, 15], smoother 0/1, cheb_alpha > 1, fuse_transfer 0..2, tma_tiles 0..2, smem_tail in [0, 15], "
                                      "refine_df 0..2");
   HP_CUDA(cudaStreamSynchronize(P->st));
   if (t->nu != P->nu || t->nu_coarse != P->nu_coarse || t->omega != P->omega || t->max_blocks != P->max_blocks || t->fuse_from != P->fuse_from ||
@@ -172,7 +172,7 @@ int hp_autotune(hp_problem *P, int nrhs, int reps, hp_tuning *best, double *best
       cur_ms = ms;
     }
   }
-  for (int tt : {0, 1}) {
+  for (int tt : {0, 1, 2}) {
     if (tt == cur.tma_tiles) continue;
     hp_tuning t = cur;
     t.tma_tiles = tt;

@@ -154,8 +154,10 @@ void warm_fallback(hp_problem *P, const int *flag_host, int s, const double *B, 
   count_launch();
 }
 
+bool warm_recording(const hp_problem *P) { return P->ws_rx && P->dim == 2 && P->ws_rcount < P->ws_rcap; }
+
 void warm_record(hp_problem *P, const double *B, long ldb, const double *X, long ldx, int s) {
-  if (!P->ws_rx || P->dim != 2 || P->ws_rcount >= P->ws_rcap) return;
+  if (!warm_recording(P)) return;
   int H, W;
   padded_grid(P, &H, &W);
   const long HW = (long)H * W;

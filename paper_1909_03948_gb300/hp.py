@@ -459,7 +459,7 @@ class Problem:
         return t.as_dict()
 
     def set_tuning(self, nu=3, omega=0.7, col_chunk=0, max_blocks=4096, smoother=1, cheb_alpha=10.0,
-                   fuse_transfer=0, fuse_from=0, nu_coarse=0, tma_tiles=0, smem_tail=0, refine_df=0):
+                   fuse_transfer=0, fuse_from=0, nu_coarse=0, tma_tiles=0, smem_tail=0, refine_df=1):
         t = Tuning(nu=nu, nu_coarse=nu_coarse, omega=omega, col_chunk=col_chunk, max_blocks=max_blocks,
                    smoother=smoother, cheb_alpha=cheb_alpha, fuse_transfer=fuse_transfer, fuse_from=fuse_from,
                    tma_tiles=tma_tiles, smem_tail=smem_tail, refine_df=refine_df)

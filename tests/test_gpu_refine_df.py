@@ -4,8 +4,8 @@ FP64 oracle.
 Around the FP32 inner solves, the refinement's residual b - K x (with its norm), the
 scaling of the residual into the inner precision and the update x += d run either with
 FP64 instructions (refine_df 0) or in double-float arithmetic on the FP32 pipe (pairs of
-floats, compensated products and sums; refine_df 1 at tolerances >= 1e-9, the default,
-and 2 at every tolerance).  The data stay FP64 either way.  Checked here:
+floats, compensated products and sums; refine_df 1, the default, at tolerances >= 1e-9,
+and 2 at every tolerance, with the C and C^T stencils in double-float too).  The data stay FP64 either way.  Checked here:
 
 * at the production tolerance 1e-8, the oracle's own FP64 relative residual of every
   column is at most 1e-8, and the solution's error against the oracle's exact solve is
@@ -134,3 +134,19 @@ def test_df_C_and_Ct_equal_the_fp64_kernels(case):
     u = orc.forward(m)
     assert _rel_cols(out[2][0], orc.C_apply(m, u, X)).max() < 1e-9
     assert _rel_cols(out[2][1], orc.Ct_apply(m, u, Wm)).max() < 1e-9
+
+
+def test_df_host_loop_equals_graph(case):
+    """The double-float refinement as one graph launch and as a host loop over the same
+    kernels (profiling on) gives the same solution bit for bit."""
+    P, m, X = case["P"], case["m"], case["X"]
+    try:
+        Ug, _ = _solve(P, m, X, 1, 1e-8)
+        P.profile_enable(True)
+        try:
+            U = P.state_solve(_T(X))[0].cpu().numpy().T
+        finally:
+            P.profile_enable(False)
+    finally:
+        P.set_tuning()
+    assert np.array_equal(U, Ug)
