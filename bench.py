@@ -729,6 +729,10 @@ def run_batch(args, rank, world):
     dev = torch.device("cuda", torch.cuda.current_device())
     ws = W.batch_workloads(seed=W.SEED_BASE + 3 + 1000 * rank)
     Ps = [synthetic_problem(w, dev, args.precision) for w in ws]
+    if args.tuning:                       # fixed solver settings on every problem
+        fixed = parse_tuning(args.tuning)
+        for P in Ps:
+            P.set_tuning(**fixed)
     Om = [torch.tensor(np.ascontiguousarray(W.omega(w).T), device=dev) for w in ws]
     B = Batch(Ps)
     torch.cuda.synchronize()

@@ -350,20 +350,25 @@ typedef struct {
   int refine_df;   /* arithmetic of the FP64 iterative refinement around FP32 inner solves
                       (the residual b - K x with its norm, the scaling into the inner
                       precision and the update x += d): 0 FP64 instructions; 1 (default)
-                      double-float arithmetic for solve tolerances >= 1e-9, FP64 below:
+                      double-float arithmetic for solve tolerances >= 1e-9 on blocks of at
+                      least 2^24 values (n times the columns), FP64 otherwise:
                       b and x held as pairs of floats (about 48 significand bits) in the
                       refinement's workspace, compensated products and sums on the FP32
                       pipe, the caller's FP64 blocks converted once per solve by bit
-                      manipulation; 2 the same at every tolerance, and the C and C^T
-                      stencils in double-float too. */
+                      manipulation (C and C^T follow the same rule); 2 the same at every
+                      tolerance and block size.  Any nonzero value also runs the eigensolver's
+                      dense products (Gram, triangular solve, block product, the small
+                      Jacobi eigensolver) in double-float with compensated sums. */
 } hp_tuning;
 int hp_set_tuning(hp_problem *P, const hp_tuning *t);
 int hp_get_tuning(const hp_problem *P, hp_tuning *t);
 /* Times one block of nrhs Gauss-Newton Hessian actions at the current point
- * (CUDA events, reps timed runs after a warm-up per candidate) over a small
- * candidate set by coordinate descent (smoother, column chunk, grid cap) and
- * applies the fastest.  best / best_ms (HOST, may be NULL) receive it.  Needs
- * hp_set_point first; allocates its test block (setup-time call). */
+ * (CUDA events, the mean of reps timed runs after a warm-up per candidate) over a
+ * small candidate set by coordinate descent in two passes (smoother, column
+ * chunk, fused transfers, coarse tails, tiled kernels, grid cap; a candidate must
+ * be at least 1 % faster to be taken) and applies the fastest.  best / best_ms
+ * (HOST, may be NULL) receive it.  Needs hp_set_point first; allocates its test
+ * block (setup-time call). */
 int hp_autotune(hp_problem *P, int nrhs, int reps, hp_tuning *best, double *best_ms);
 
 /* ---- learned warm start (2D stiffness solves; no counterpart in the paper) --

@@ -568,6 +568,7 @@ void hp_problem_destroy(hp_problem *P) {
   for (void *p : {(void *)P->CbetaE_pr, (void *)P->Cbeta_pr, (void *)P->E_pr})
     if (p) cudaFree(p);
   P->xpairs.release();
+  P->dense_tmp.release();
   for (void *p : {(void *)P->M64.diag, (void *)P->M64.invdiag, (void *)P->M64.c, (void *)P->M64.cpr, (void *)P->M32.diag,
                   (void *)P->M32.invdiag, (void *)P->M32.c, (void *)P->m, (void *)P->E, (void *)P->u,
                   (void *)P->lift, (void *)P->Cbeta, (void *)P->CbetaE, (void *)P->padj, (void *)P->Cbeta_p, (void *)P->CbetaE_p, (void *)P->wmm, (void *)P->m_prior, (void *)P->f_load, (void *)P->d_obs, (void *)P->obs_node,
@@ -865,7 +866,7 @@ int hp_newton_cg_map(hp_problem *P, double *m, const hp_newton_opts *opts_in, hp
     HP_TRY(gram(P, Vl, n, lk, rv, n, 1, tk, lk, n));
     k_lowrank_scale<<<1, 256, 0, P->st>>>(tk, laml, lk);
     count_launch();
-    launch_gemm_nn(Vl, n, lk, tk, lk, 1, zv, n, n, -1.0, 1.0, P->st);
+    launch_gemm_nn(Vl, n, lk, tk, lk, 1, zv, n, n, -1.0, 1.0, P);
     return 0;
   };
   int rc = 0;
@@ -1083,7 +1084,7 @@ int hp_lowrank_eig(hp_problem *P, const double *m_map, int k, int p, const doubl
   k_symmetrize<<<(s * s + 255) / 256, 256, 0, P->st>>>(G, Ts, s);
   count_launch();
   HP_TRY(small_cholesky(P, Ts, s));
-  launch_trsm_right_upper(Y, ld, n, s, Ts, P->st);
+  launch_trsm_right_upper(Y, ld, n, s, Ts, P);
   if (!single_pass) {
     // Algorithm 2: T = Q^T A Q (the second pass)
     HP_TRY(hessian_block(P, Y, ld, H, ld, s, HP_MISFIT_ONLY, st));
@@ -1093,7 +1094,7 @@ int hp_lowrank_eig(hp_problem *P, const double *m_map, int k, int p, const doubl
     // W = Qb^T Omega, Zs = Qb^T Y.  Its normal equations restricted to symmetric X are the
     // Lyapunov equation X M + M X = C, M = W W^T, C = Zs W^T + W Zs^T, solved in the
     // eigenbasis of M: with M = U D U^T, (U^T X U)_ij = (U^T C U)_ij / (d_i + d_j).
-    launch_trsm_right_upper(Zb, ld, n, s, Ts, P->st);
+    launch_trsm_right_upper(Zb, ld, n, s, Ts, P);
     HP_TRY(gram(P, Zb, ld, s, Omega, ldo, s, Wm, s, n));
     HP_TRY(gram(P, Zb, ld, s, Ysave, ld, s, Zs, s, n));
     small_gemm(P, s, 0, 1, Wm, Wm, M);   // M = W W^T
@@ -1113,7 +1114,7 @@ int hp_lowrank_eig(hp_problem *P, const double *m_map, int k, int p, const doubl
   count_launch();
   HP_TRY(small_symeig(P, Ts, s, lam, Sm));
   // V = Q S(:, 1:k), Lambda_r = Lambda(1:k)
-  launch_gemm_nn(Y, ld, s, Sm, s, k, V, ldv, n, 1.0, 0.0, P->st);
+  launch_gemm_nn(Y, ld, s, Sm, s, k, V, ldv, n, 1.0, 0.0, P);
   k_sign_normalise<<<k, NT, 0, P->st>>>(V, ldv, n);
   count_launch();
   HP_CUDA(cudaMemcpyAsync(lambda, lam, sizeof(double) * k, cudaMemcpyDeviceToDevice, P->st));
@@ -1159,7 +1160,7 @@ int hp_pointwise_variance(hp_problem *P, int method, const double *Z, int ldz, i
     k_symmetrize<<<(unsigned)((r2 + 255) / 256), 256, 0, P->st>>>(T, Ts, r);
     count_launch();
     HP_TRY(small_symeig(P, Ts, r, mu, Sm));
-    launch_gemm_nn(Y, ld, r, Sm, r, r, Vb, ld, n, 1.0, 0.0, P->st);
+    launch_gemm_nn(Y, ld, r, Sm, r, r, Vb, ld, n, 1.0, 0.0, P);
     k_diag_lowrank<<<nb, NT, 0, P->st>>>(Vb, ld, n, r, mu, 0, 1.0, nullptr, prior_var);
     count_launch();
   }
@@ -1227,7 +1228,7 @@ int hp_laplace_sample(hp_problem *P, const double *m_map, const double *lambda, 
         HP_TRY(gram(P, V, ldv, k, RX, ld, cs, z, k, n));
         k_scale_rows_S<<<(k * cs + 255) / 256, 256, 0, P->st>>>(z, k, cs, lambda);
         count_launch();
-        launch_gemm_nn(V, ldv, k, z, k, cs, X, ld, n, -1.0, 1.0, P->st);
+        launch_gemm_nn(V, ldv, k, z, k, cs, X, ld, n, -1.0, 1.0, P);
       }
       k_add_vec_cols<<<dim3(blocks_for(n, cs), cs), NT, 0, P->st>>>(X, ld, m_map, post + (long)lds * c0, lds, n);
       count_launch();

@@ -27,7 +27,21 @@ struct GridDesc {
   int np;     // N + 1
   long n;     // nodes
   double h;   // 1/N
+  unsigned mnp = 0;  // floor(2^32 / np): division by np as a multiplication (div_np)
 };
+
+// i / np for i < 2^32 without an integer division: floor(i mnp / 2^32) is the quotient or
+// one less, and the remainder test corrects it
+__device__ __forceinline__ unsigned div_np(const GridDesc &g, unsigned i) {
+  unsigned q = __umulhi(i, g.mnp);
+  unsigned r = i - q * (unsigned)g.np;
+  if (r >= (unsigned)g.np) {
+    ++q;
+    r -= (unsigned)g.np;
+  }
+  if (r >= (unsigned)g.np) ++q;
+  return q;
+}
 
 // chain masks of the permutations, [perm][k], k = 0..D
 __constant__ static int c_chain2[2][3] = {{0, 1, 3}, {0, 2, 3}};

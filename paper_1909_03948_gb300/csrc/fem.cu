@@ -591,6 +591,7 @@ int build_hierarchy_geometry(hp_problem *P) {
     lv.g.dim = D;
     lv.g.N = P->N >> l;
     lv.g.np = lv.g.N + 1;
+    lv.g.mnp = (unsigned)((1ull << 32) / (unsigned long long)lv.g.np);
     lv.g.n = 1;
     for (int a = 0; a < D; ++a) lv.g.n *= lv.g.np;
     lv.g.h = 1.0 / lv.g.N;
@@ -878,10 +879,10 @@ __global__ void __launch_bounds__(NT, 2) k_cct_dfp(GridDesc g, const float2 *__r
   const unsigned np = (unsigned)g.np, n = (unsigned)g.n;
   for (unsigned i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) {
     int v[3];
-    const unsigned t = i / np;
+    const unsigned t = div_np(g, i), t2 = D == 2 ? 0u : div_np(g, t);
     v[0] = (int)(i - t * np);
-    v[1] = D == 2 ? (int)t : (int)(t % np);
-    v[2] = D == 2 ? 0 : (int)(t / np);
+    v[1] = D == 2 ? (int)t : (int)(t - t2 * np);
+    v[2] = (int)t2;
     Dot2 a[4];
 #pragma unroll
     for (int q0 = 0; q0 < NC; q0 += CH) {
@@ -933,9 +934,11 @@ __global__ void __launch_bounds__(NT, 2) k_cct_dfp(GridDesc g, const float2 *__r
   }
 }
 
-// double-float C and C^T where the refinement runs in double-float
-static bool cct_df(const hp_problem *P) {
-  return P->precision == HP_FP32_IR && (P->refine_df == 2 || (P->refine_df == 1 && P->rtol >= 1e-9));
+// double-float C and C^T where the refinement runs in double-float (the same tolerance and
+// block-size rule as the solves')
+static bool cct_df(const hp_problem *P, int s) {
+  return P->precision == HP_FP32_IR &&
+         (P->refine_df == 2 || (P->refine_df == 1 && P->rtol >= 1e-9 && (double)P->n * s >= 16.0 * 1024 * 1024));
 }
 
 // the coefficient and e^m pairs of the u-based C, made when missing or stale
@@ -1009,7 +1012,7 @@ void launch_build_C(hp_problem *P) {
 
 void launch_C_apply_beta(hp_problem *P, const double *betaE, const double *X, long ldx, double *Y, long ldy, int s,
                          double scale, double yb) {
-  if (betaE == P->CbetaE && cct_df(P) && cct_dfp(P, false, X, ldx, Y, ldy, s, scale, yb)) return;
+  if (betaE == P->CbetaE && cct_df(P, s) && cct_dfp(P, false, X, ldx, Y, ldy, s, scale, yb)) return;
   dim3 grid(blocks_for(P->n, s), s);
   if (P->dim == 2)
     k_C_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, betaE, X, ldx, Y, ldy, scale, yb);
@@ -1028,7 +1031,7 @@ void launch_C_apply(hp_problem *P, const double *X, long ldx, double *Y, long ld
 
 void launch_Ct_apply_beta(hp_problem *P, const double *beta_c, const double *W, long ldw, double *Y, long ldy, int s,
                           double scale, double beta) {
-  if (beta_c == P->Cbeta && cct_df(P) && cct_dfp(P, true, W, ldw, Y, ldy, s, scale, beta)) return;
+  if (beta_c == P->Cbeta && cct_df(P, s) && cct_dfp(P, true, W, ldw, Y, ldy, s, scale, beta)) return;
   dim3 grid(blocks_for(P->n, s), s);
   if (P->dim == 2)
     k_Ct_apply<2><<<grid, NT, 0, P->st>>>(P->lv[0].g, P->E, beta_c, W, ldw, Y, ldy, scale, beta);

@@ -169,6 +169,7 @@ struct hp_problem {
   float2 *CbetaE_pr = nullptr, *Cbeta_pr = nullptr, *E_pr = nullptr;
   bool cct_pr_ok = false;
   hp::DBuf xpairs;
+  hp::DBuf dense_tmp;  // n x s scratch of the eigensolver's double-float triangular solves
   double *CbetaE = nullptr;     // the same coefficients with e^m folded in (C X = CbetaE-stencil X)
   // adjoint terms of the full Newton Hessian (built on demand at the current point)
   double *padj = nullptr;       // adjoint p
@@ -318,14 +319,14 @@ int gram(hp_problem *P, const double *X, long ldx, int s1, const double *Y, long
          int ldg, long n);
 // Y (n x s2) = X (n x s1) * S (s1 x s2, ld lds) [+ beta * Y]
 void launch_gemm_nn(const double *X, long ldx, int s1, const double *S, int lds, int s2, double *Y,
-                    long ldy, long n, double alpha, double beta, cudaStream_t st);
+                    long ldy, long n, double alpha, double beta, hp_problem *P);
 // in-place CGS2 orthonormalisation of the columns of Y (n x s)
 int cgs2_qr(hp_problem *P, double *Y, long ldy, long n, int s);
 int thin_qr(hp_problem *P, double *Y, long ldy, long n, int s);  // shifted Cholesky QR, cgs2_qr fallback
 // upper Cholesky R^T R = G (s x s, ld s) in place; returns HP_ERR_NONFINITE if not SPD
 int small_cholesky(hp_problem *P, double *G, int s);
 // Y <- Y R^{-1}, R upper (s x s)
-void launch_trsm_right_upper(double *Y, long ldy, long n, int s, const double *R, cudaStream_t st);
+void launch_trsm_right_upper(double *Y, long ldy, long n, int s, const double *R, hp_problem *P);
 // symmetric eigen-decomposition of T (s x s) by cyclic Jacobi: lambda (s), S (s x s) columns
 int small_symeig(hp_problem *P, const double *T, int s, double *lambda, double *S);
 

@@ -1188,10 +1188,10 @@ __global__ void __launch_bounds__(NB) k_resid_dfp(GridDesc g, const float2 *__re
   const unsigned np = (unsigned)g.np, n = (unsigned)g.n;
   for (unsigned i = blockIdx.x * NB + threadIdx.x; i < n; i += gridDim.x * NB) {
     int v[3];
-    const unsigned t = i / np;
+    const unsigned t = div_np(g, i), t2 = D == 2 ? 0u : div_np(g, t);
     v[0] = (int)(i - t * np);
-    v[1] = D == 2 ? (int)t : (int)(t % np);
-    v[2] = D == 2 ? 0 : (int)(t / np);
+    v[1] = D == 2 ? (int)t : (int)(t - t2 * np);
+    v[2] = (int)t2;
     // the stencil's points: 0 the node, 1 + 2f / 2 + 2f the forward / backward neighbour f
     unsigned pt[2 * NF + 1];
     bool ok[2 * NF + 1];
@@ -2245,6 +2245,26 @@ static int tail_level(const hp_problem *P, int node_bytes) {
   return (f >= 1 && f + 2 <= P->L) ? f : P->L;
 }
 
+// Algorithmic bytes of the V-cycle's levels l0 .. L-1 as the per-level kernels would move
+// them (smoothing sweeps, residual, restriction, prolongation, the dense coarse solve): the
+// fused tails do the same work in fewer launches, and are counted with these bytes.
+template <typename T>
+static double tail_bytes(const hp_problem *P, OpKind op, int s, int l0) {
+  const double w = sizeof(T);
+  double b = 0.0;
+  for (int l = l0; l + 1 < P->L; ++l) {
+    const double n = (double)P->lv[l].g.n, nc = (double)P->lv[l + 1].g.n;
+    const double nf = stencil_of<T>(P, op, l).nf;
+    const int nu = nu_at(P, l);
+    const double sweep = (3.0 * s + 2.0 + nf) * n * w;
+    b += nu >= 2 ? (2.0 * s + 2.0 + nf) * n * w + (nu - 2) * sweep : (2.0 * s + 1.0) * n * w;  // pre-smoothing
+    b += (3.0 * s + 1.0 + nf) * n * w + s * (n + nc) * w;                                     // residual, restriction
+    b += s * (2.0 * n + nc) * w + nu * sweep;                                                  // prolongation, post-smoothing
+  }
+  const double nc = (double)P->lv[P->L - 1].g.n;
+  return b + (nc * nc + 2.0 * nc * s) * w;
+}
+
 // The shared-memory tail as its two launches around the dense coarse solve.
 template <typename T, int VW>
 static void launch_vtail_smem(hp_problem *P, OpKind op, int s, int l0, const T *const *rl, T *const *ea,
@@ -2300,6 +2320,7 @@ static void launch_vtail_smem(hp_problem *P, OpKind op, int s, int l0, const T *
       coarse_inv<T>(P, op), nc, rl[lc], gsl[lc], ea[lc], gsl[lc]);
   up<<<dim3(1, ng), VS_NT, bytes, P->st>>>(vt);
   count_launch(3);
+  count_bytes(BY_STENCILC, tail_bytes<T>(P, op, s, l0));
 }
 
 template <typename T, int VW>
@@ -2352,6 +2373,7 @@ static void launch_vtail(hp_problem *P, OpKind op, int s, int l0, const T *const
       cudaLaunchKernelEx(&cfg, k_vcycle_tail<T, VW, 3, false>, vt);
   }
   count_launch();
+  count_bytes(BY_STENCILC, tail_bytes<T>(P, op, s, l0));
 }
 
 // Preconditioner z = M^{-1} r with the fused <r, z> -> fin.
@@ -2769,8 +2791,15 @@ int apply_op64(hp_problem *P, OpKind op, const double *X, long ldx, double *Y, l
 // FP64 residual is checked against the oracle at 1e-8), below it the solve keeps the FP64
 // arithmetic.
 constexpr double DF_MIN_RTOL = 1e-9;
-static bool use_df(const hp_problem *P, int tbytes, double rtol) {
-  return tbytes == 4 && (P->refine_df == 2 || (P->refine_df == 1 && rtol >= DF_MIN_RTOL));
+// Blocks below DF_MIN_ENTRIES values (n times s) keep the FP64 refinement with refine_df 1:
+// there the FP64 kernels are latency-bound rather than FP64-bound, and the double-float path's
+// extra passes (the pair conversions at a solve's start and end) cost more than they save
+// (measured: 64 uneven 2D problems with 40 columns each, 24,738 vs 27,940 actions/s; a
+// 257^2 x 60 block, 18,357 vs 18,108; 65^3 x 120, 3,735 vs 3,275).
+constexpr double DF_MIN_ENTRIES = 16.0 * 1024 * 1024;
+static bool use_df(const hp_problem *P, int tbytes, double rtol, int s) {
+  return tbytes == 4 && (P->refine_df == 2 || (P->refine_df == 1 && rtol >= DF_MIN_RTOL &&
+                                               (double)P->n * s >= DF_MIN_ENTRIES));
 }
 
 static int residual64(hp_problem *P, OpKind op, const double *B, long ldb, const double *X, long ldx, double *R,
@@ -3162,7 +3191,7 @@ static int ir_solve(hp_problem *P, OpKind op, const double *B, long ldb, double 
   HP_TRY(ensure_kept(P, P->b64, sizeof(double) * ld64 * s));
   // double-float refinement (not with a learned initial guess, nor while stiffness solves are
   // recorded for its training: those paths keep the FP64 layout)
-  if (use_df(P, (int)sizeof(T), rtol) && VW == 4 && !(op == OP_K && (warm_attached(P) || warm_recording(P))))
+  if (use_df(P, (int)sizeof(T), rtol, s) && VW == 4 && !(op == OP_K && (warm_attached(P) || warm_recording(P))))
     return ir_solve_dfp<T, VW>(P, op, B, ldb, X, ldx, s, rtol, tol_in, stats);
   // from x = 0 with graphs on, the whole refinement runs as one captured loop
   if (P->use_graphs && !P->prof_on && !(op == OP_K && warm_attached(P)))

@@ -111,86 +111,74 @@ int hp_autotune(hp_problem *P, int nrhs, int reps, hp_tuning *best, double *best
   double cur_ms = 0.0;
   int rc = time_it(cur, &cur_ms);
   if (rc) return cleanup(rc);
+  // a candidate replaces the current settings only when it is at least 1 % faster, so that
+  // timing noise does not walk the search away from a good point
+  auto consider = [&](const hp_tuning &t) -> int {
+    double ms;
+    const int r = time_it(t, &ms);
+    if (r) return r;
+    if (ms < 0.99 * cur_ms) {
+      cur = t;
+      cur_ms = ms;
+    }
+    return 0;
+  };
   struct SmoothC {
     int nu, kind;
     double omega, alpha;
   };
-  const SmoothC smooth[] = {{2, 0, 0.8, 10.0}, {2, 1, 0.7, 5.0}, {3, 1, 0.7, 8.0}, {3, 1, 0.7, 12.0},
-                            {4, 1, 0.7, 12.0}};
-  for (const SmoothC &sm : smooth) {
-    hp_tuning t = cur;
-    t.nu = sm.nu;
-    t.omega = sm.omega;
-    t.smoother = sm.kind;
-    t.cheb_alpha = sm.alpha;
-    double ms;
-    if ((rc = time_it(t, &ms))) return cleanup(rc);
-    if (ms < cur_ms) {
-      cur = t;
-      cur_ms = ms;
+  const SmoothC smooth[] = {{2, 0, 0.8, 10.0}, {2, 1, 0.7, 5.0}, {3, 1, 0.7, 8.0}, {3, 1, 0.7, 10.0},
+                            {3, 1, 0.7, 12.0}, {4, 1, 0.7, 12.0}};
+  // coordinate descent over the settings, twice: the second pass re-times the point the first
+  // one reached and revisits every coordinate from there
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass > 0 && (rc = time_it(cur, &cur_ms))) return cleanup(rc);
+    for (const SmoothC &sm : smooth) {
+      if (sm.nu == cur.nu && sm.kind == cur.smoother && (sm.kind == 0 ? sm.omega == cur.omega
+                                                                       : sm.alpha == cur.cheb_alpha))
+        continue;
+      hp_tuning t = cur;
+      t.nu = sm.nu;
+      t.omega = sm.omega;
+      t.smoother = sm.kind;
+      t.cheb_alpha = sm.alpha;
+      if ((rc = consider(t))) return cleanup(rc);
     }
-  }
-  for (int w : {0, 32, 16}) {
-    if (w >= nrhs) continue;
-    hp_tuning t = cur;
-    t.col_chunk = w;
-    double ms;
-    if ((rc = time_it(t, &ms))) return cleanup(rc);
-    if (ms < cur_ms) {
-      cur = t;
-      cur_ms = ms;
+    for (int w : {0, 32, 16}) {
+      if (w >= nrhs || w == cur.col_chunk) continue;
+      hp_tuning t = cur;
+      t.col_chunk = w;
+      if ((rc = consider(t))) return cleanup(rc);
     }
-  }
-  for (int ft : {2, 1}) {
-    hp_tuning t = cur;
-    t.fuse_transfer = ft;
-    double ms;
-    if ((rc = time_it(t, &ms))) return cleanup(rc);
-    if (ms < cur_ms) {
-      cur = t;
-      cur_ms = ms;
+    for (int ft : {0, 2, 1}) {
+      if (ft == cur.fuse_transfer) continue;
+      hp_tuning t = cur;
+      t.fuse_transfer = ft;
+      if ((rc = consider(t))) return cleanup(rc);
     }
-  }
-  for (int st : {1}) {
-    hp_tuning t = cur;
-    t.smem_tail = st;
-    double ms;
-    if ((rc = time_it(t, &ms))) return cleanup(rc);
-    if (ms < cur_ms) {
-      cur = t;
-      cur_ms = ms;
+    for (int st : {0, 1}) {
+      if (st == cur.smem_tail) continue;
+      hp_tuning t = cur;
+      t.smem_tail = st;
+      if ((rc = consider(t))) return cleanup(rc);
     }
-  }
-  for (int ff : {1, 2}) {
-    if (ff + 2 > P->L || cur.smem_tail) continue;
-    hp_tuning t = cur;
-    t.fuse_from = ff;
-    double ms;
-    if ((rc = time_it(t, &ms))) return cleanup(rc);
-    if (ms < cur_ms) {
-      cur = t;
-      cur_ms = ms;
+    for (int ff : {0, 1, 2}) {
+      if (ff == cur.fuse_from || (ff > 0 && (ff + 2 > P->L || cur.smem_tail))) continue;
+      hp_tuning t = cur;
+      t.fuse_from = ff;
+      if ((rc = consider(t))) return cleanup(rc);
     }
-  }
-  for (int tt : {0, 1, 2}) {
-    if (tt == cur.tma_tiles) continue;
-    hp_tuning t = cur;
-    t.tma_tiles = tt;
-    double ms;
-    if ((rc = time_it(t, &ms))) return cleanup(rc);
-    if (ms < cur_ms) {
-      cur = t;
-      cur_ms = ms;
+    for (int tt : {0, 1, 2}) {
+      if (tt == cur.tma_tiles) continue;
+      hp_tuning t = cur;
+      t.tma_tiles = tt;
+      if ((rc = consider(t))) return cleanup(rc);
     }
-  }
-  for (int mb : {1024, 2048, 4096}) {
-    hp_tuning t = cur;
-    t.max_blocks = mb;
-    double ms;
-    if ((rc = time_it(t, &ms))) return cleanup(rc);
-    if (ms < cur_ms) {
-      cur = t;
-      cur_ms = ms;
+    for (int mb : {1024, 2048, 4096}) {
+      if (mb == cur.max_blocks) continue;
+      hp_tuning t = cur;
+      t.max_blocks = mb;
+      if ((rc = consider(t))) return cleanup(rc);
     }
   }
   if ((rc = hp_set_tuning(P, &cur))) return cleanup(rc);

@@ -465,7 +465,7 @@ class Problem:
                    tma_tiles=tma_tiles, smem_tail=smem_tail, refine_df=refine_df)
         _check(lib().hp_set_tuning(self._h, C.byref(t)), "hp_set_tuning")
 
-    def autotune(self, nrhs, reps=2):
+    def autotune(self, nrhs, reps=3):
         """Runs the autotuner at the current point; returns (settings, ms per block)."""
         t = Tuning()
         ms = C.c_double()
