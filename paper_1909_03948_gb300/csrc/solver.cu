@@ -645,12 +645,11 @@ template <typename T, int VW, int D>
 __global__ void __launch_bounds__(NB) k_restrict(GridDesc gf, GridDesc gc, const T *__restrict__ rf, long gsf,
                                                  T *__restrict__ rc, long gsc, int zero_dirichlet) {
   using PK = Pack<T, VW>;
-  const int I0 = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int row = blockIdx.y * (NB / 32) + (threadIdx.x >> 5);
-  const int nrows = D == 2 ? gc.np : gc.np * gc.np;
-  if (I0 >= gc.np || row >= nrows) return;
-  const int J[3] = {I0, D == 2 ? row : row % gc.np, D == 2 ? 0 : row / gc.np};
-  const long I = I0 + (long)gc.np * row;
+  // one coarse node per thread over the flattened grid (every lane busy whatever np is)
+  const unsigned I = blockIdx.x * NB + threadIdx.x;
+  if (I >= (unsigned)gc.n) return;
+  const unsigned t = div_np(gc, I), t2 = D == 2 ? 0u : div_np(gc, t);
+  const int J[3] = {(int)(I - t * (unsigned)gc.np), D == 2 ? (int)t : (int)(t - t2 * (unsigned)gc.np), (int)t2};
   const T *r = rf + blockIdx.z * gsf;
   PK out = PK::zero();
   if (!(zero_dirichlet && (J[D - 1] == 0 || J[D - 1] == gc.N))) {
@@ -679,12 +678,11 @@ template <typename T, int VW, int D>
 __global__ void __launch_bounds__(NB) k_prolong_add(GridDesc gf, GridDesc gc, const T *__restrict__ ec, long gsc,
                                                     T *__restrict__ ef, long gsf) {
   using PK = Pack<T, VW>;
-  const int i0 = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int row = blockIdx.y * (NB / 32) + (threadIdx.x >> 5);
-  const int nrows = D == 2 ? gf.np : gf.np * gf.np;
-  if (i0 >= gf.np || row >= nrows) return;
-  const int v[3] = {i0, D == 2 ? row : row % gf.np, D == 2 ? 0 : row / gf.np};
-  const long i = i0 + (long)gf.np * row;
+  // one fine node per thread over the flattened grid (every lane busy whatever np is)
+  const unsigned i = blockIdx.x * NB + threadIdx.x;
+  if (i >= (unsigned)gf.n) return;
+  const unsigned t = div_np(gf, i), t2 = D == 2 ? 0u : div_np(gf, t);
+  const int v[3] = {(int)(i - t * (unsigned)gf.np), D == 2 ? (int)t : (int)(t - t2 * (unsigned)gf.np), (int)t2};
   const T *e = ec + blockIdx.z * gsc;
   const int b = (v[0] & 1) | ((v[1] & 1) << 1) | ((v[2] & 1) << 2);
   const long ic = (v[0] >> 1) + (long)gc.np * ((v[1] >> 1) + (long)gc.np * (v[2] >> 1));
@@ -1395,10 +1393,14 @@ template <> const double *coarse_inv<double>(const hp_problem *P, OpKind op) {
 // a launch's tail short), set per solve from the problem's tuning
 static thread_local long tl_max_blocks = 4096;
 
-// uncapped row grid (grid transfer kernels: one node per thread)
+// uncapped row grid: one node per thread, warps along x rows
 static dim3 rowgrid(const GridDesc &g, int ngroups) {
   const long nrows = g.dim == 2 ? g.np : (long)g.np * g.np;
   return dim3((g.np + 31) / 32, (unsigned)((nrows + NB / 32 - 1) / (NB / 32)), ngroups);
+}
+// one node per thread over the flattened grid, column groups over blockIdx.z (grid transfers)
+static dim3 flatgrid(const GridDesc &g, int ngroups) {
+  return dim3((unsigned)((g.n + NB - 1) / NB), 1, (unsigned)ngroups);
 }
 // row grid of the stencil kernels: warps loop over rows so that the grid stays near
 // the grid-size cap (fewer per-block dot partials)
@@ -2474,9 +2476,9 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
       st_launch<T, VW, M_RESID>(g, S, c, gsl[l], rl[l], gsl[l], o, gsl[l], s, om, nofin, st);
       prof_stop(P, pr);
       if (g.dim == 2)
-        k_restrict<T, VW, 2><<<rowgrid(gc, ng), NB, 0, st>>>(g, gc, o, gsl[l], rc, gsl[l + 1], op == OP_K);
+        k_restrict<T, VW, 2><<<flatgrid(gc, ng), NB, 0, st>>>(g, gc, o, gsl[l], rc, gsl[l + 1], op == OP_K);
       else
-        k_restrict<T, VW, 3><<<rowgrid(gc, ng), NB, 0, st>>>(g, gc, o, gsl[l], rc, gsl[l + 1], op == OP_K);
+        k_restrict<T, VW, 3><<<flatgrid(gc, ng), NB, 0, st>>>(g, gc, o, gsl[l], rc, gsl[l + 1], op == OP_K);
       count_launch();
       count_bytes(BY_TRANSFER, (double)sizeof(T) * s * ((double)g.n + (double)gc.n));
     }
@@ -2536,9 +2538,9 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
       k0 = 1;
     } else {
       if (g.dim == 2)
-        k_prolong_add<T, VW, 2><<<rowgrid(g, ng), NB, 0, st>>>(g, gc, cur[l + 1], gsl[l + 1], cur[l], gsl[l]);
+        k_prolong_add<T, VW, 2><<<flatgrid(g, ng), NB, 0, st>>>(g, gc, cur[l + 1], gsl[l + 1], cur[l], gsl[l]);
       else
-        k_prolong_add<T, VW, 3><<<rowgrid(g, ng), NB, 0, st>>>(g, gc, cur[l + 1], gsl[l + 1], cur[l], gsl[l]);
+        k_prolong_add<T, VW, 3><<<flatgrid(g, ng), NB, 0, st>>>(g, gc, cur[l + 1], gsl[l + 1], cur[l], gsl[l]);
       count_launch();
       count_bytes(BY_TRANSFER, (double)sizeof(T) * s * (2.0 * (double)g.n + (double)gc.n));
     }
