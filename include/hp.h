@@ -412,6 +412,17 @@ int hp_unet_loss_grad(hp_unet *U, const float *x, const float *aux, int N, doubl
  * loss of each epoch. */
 int hp_unet_train(hp_unet *U, const float *X, const float *A, int nsamples, int epochs, int batch, double lr,
                   unsigned long long seed, double *loss_per_epoch);
+/* Where the 3x3 convolutions with a multiple of 16 output channels run (the forward
+ * pass, and the input gradient of the backward pass): on = 1 (the default), on the
+ * tensor cores as implicit GEMMs (tcgen05 MMAs on BF16 operands, FP32 accumulators in
+ * tensor memory; each FP32 activation or gradient enters as three BF16 terms, so the
+ * products see the FP32 values, as on the FP32 pipes); on = 0, on the FP32 pipes.  The
+ * weight gradients and the 1x1 output layer use the FP32 pipes either way.  A
+ * tensor-core convolution whose MMAs have not completed after about a second gives up
+ * and makes the forward, gradient or training call fail with HP_ERR_CUDA.
+ * get_tensor_cores returns the setting (-1 for NULL).  Not part of the paper. */
+int hp_unet_set_tensor_cores(hp_unet *U, int on);
+int hp_unet_get_tensor_cores(const hp_unet *U);
 
 /* The network's view of a 2D problem: grid H = W = the node count per axis
  * rounded up to a multiple of 8; node (ix, iy) sits at row iy, column ix.  For a

@@ -18,11 +18,13 @@
 #include <algorithm>
 #include <cmath>
 #include <cuda_bf16.h>
+#include <mutex>
 #include <numeric>
 #include <random>
 #include <vector>
 
 #include "internal.h"
+#include "tc.cuh"
 
 namespace hp {
 
@@ -54,6 +56,10 @@ struct hp_unet {
   float *da = nullptr, *db = nullptr, *dc = nullptr;  // gradient scratch (largest activation)
   double *lossbuf = nullptr;      // [0, 64): per-sample loss weights; then block partials
   cudaStream_t st = nullptr;
+  // 3x3 convolutions on the tensor cores (default) or on the FP32 pipes
+  int tensor_cores = 1;
+  __nv_bfloat16 *wtc = nullptr;   // BF16 weights packed for the tensor-core kernel (forward and data-backward)
+  long tc_fo[hp::kUL] = {}, tc_bo[hp::kUL] = {};  // offsets of each layer's packs in wtc (-1: none)
 };
 
 namespace hp {
@@ -132,6 +138,223 @@ __global__ void __launch_bounds__(256) k_conv_fwd(ConvIn I, const __nv_bfloat16 
       float r = acc[q];
       if (relu) r = fmaxf(r, 0.f);
       out[(((long)n * co_n + cob + q) * H + y) * W + x] = r;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3x3 convolutions on the tensor cores, as implicit GEMMs:
+//   D[pixel, o] = sum_{tap, c} A[pixel, (tap, c)] B[(tap, c), o],
+//   A[pixel, (tap, c)] = in[c, pixel + tap offset],  B[(tap, c), o] = w[o, c, tap].
+// A CTA of 128 threads computes a tile of TC_TR rows x 8 tx columns: tx MMAs of M = 128
+// pixels (MMA row group j = tile row j, 8 pixels), N = the output channels, accumulating
+// in tensor memory.  K runs over 16-channel slabs and the 9 taps.  Per slab the CTA
+// stages in shared memory the input halo ((TC_TR + 2) x (8 tx + 2) pixels, 16 channels)
+// and the slab's weights, both in the no-swizzle core-matrix layout:
+//   halo:    [term][channel group of 8][halo row][halo column][8 channels] BF16,
+//   weights: [tap][channel group of 8][o][8 channels] BF16.
+// A tap is the same halo with the descriptor's start moved by (dy rows, dx columns):
+// the 8 pixels of an MMA row group are consecutive halo columns, 16 bytes apart, and
+// consecutive row groups are consecutive halo rows (SBO = the halo row's bytes).
+// The FP32 inputs enter as three BF16 terms (hi + mid + lo, each the rounded remainder of
+// the previous ones: 24 significant bits, the FP32 significand) multiplied by the same
+// BF16 weights, so the products carry FP32 inputs, as the FP32-pipe kernels do, and the
+// accumulation is FP32.  Two stages: the loads of slab s + 1 overlap the MMAs of slab s;
+// a stage is refilled once the tcgen05.commit of the MMAs that read it has arrived on
+// its mbarrier.
+// ---------------------------------------------------------------------------
+constexpr int TC_NT = 128;   // threads per CTA: one accumulator row (tensor-memory lane) each
+constexpr int TC_TR = 16;    // tile rows
+constexpr int TC_TERMS = 3;  // BF16 terms of an FP32 input
+
+__host__ __device__ constexpr int tc_hx(int tx) { return 8 * tx + 2; }                // halo columns
+__host__ __device__ constexpr int tc_rs(int tx) { return tc_hx(tx) * 16; }            // bytes per halo row
+__host__ __device__ constexpr int tc_g(int tx) { return (TC_TR + 2) * tc_rs(tx); }    // bytes per 8-channel group
+__host__ __device__ constexpr int tc_halo_bytes(int tx) { return TC_TERMS * 2 * tc_g(tx); }
+__host__ __device__ constexpr int tc_w_bytes(int co) { return 9 * 2 * co * 16; }
+__host__ __device__ constexpr int tc_stage_bytes(int tx, int co) { return tc_halo_bytes(tx) + tc_w_bytes(co); }
+// the most dynamic shared memory a launch takes: two stages of 16-row x 8-column tiles with up
+// to 256 output channels (two 16 x 16 strips take less for the <= 128 channels they serve)
+constexpr int TC_MAX_SMEM = 2 * tc_stage_bytes(1, 256);
+static_assert(2 * tc_stage_bytes(2, 128) <= TC_MAX_SMEM, "stage size");
+
+// set by a tensor-core convolution whose MMAs did not complete within its wait limit
+__device__ int g_tc_timeout;
+
+struct TcArgs {
+  ConvIn I;
+  int cin;             // input channels (I.c1 + I.c2)
+  const uint4 *w;      // packed weights, one slab after another
+  const float *bias;   // co values, or null
+  float *out;          // (N, co, H, W)
+  int co, H, W, relu;
+  int tx, ntx;         // MMAs per tile (8-column strips), tiles per image row
+  int cs;              // tensor-memory columns between the strips' accumulators
+  unsigned ncols;      // tensor-memory columns allocated
+};
+
+__device__ __forceinline__ unsigned bf16_bits(float v) {
+  return static_cast<unsigned>(__bfloat16_as_ushort(__float2bfloat16_rn(v)));
+}
+
+// v = hi + mid + lo (+ a remainder below 2^-24 |v|); the two subtractions are exact
+__device__ __forceinline__ void split3(float v, unsigned &h, unsigned &m, unsigned &l) {
+  const __nv_bfloat16 bh = __float2bfloat16_rn(v);
+  const float r1 = __fsub_rn(v, __bfloat162float(bh));
+  const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
+  const float r2 = __fsub_rn(r1, __bfloat162float(bm));
+  h = __bfloat16_as_ushort(bh);
+  m = __bfloat16_as_ushort(bm);
+  l = bf16_bits(r2);
+}
+
+__global__ void __launch_bounds__(TC_NT) k_conv_tc(TcArgs a) {
+  extern __shared__ __align__(128) unsigned char tc_smem[];
+  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ unsigned tslot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int bx = blockIdx.x % a.ntx, by = blockIdx.x / a.ntx, n = blockIdx.y;
+  const int x0 = bx * 8 * a.tx, y0 = by * TC_TR;
+  const int HX = tc_hx(a.tx), RS = tc_rs(a.tx), G = tc_g(a.tx);
+  const int stage = tc_stage_bytes(a.tx, a.co), hbytes = tc_halo_bytes(a.tx), wbytes = tc_w_bytes(a.co);
+  const uint32_t sbase = tc::saddr(tc_smem);
+  const uint32_t bar0 = tc::saddr(&bars[0]), bar1 = tc::saddr(&bars[1]);
+  auto bar = [&](int i) { return i ? bar1 : bar0; };
+  if (warp == 0) tc::tmem_alloc(tc::saddr(&tslot), a.ncols);
+  if (tid == 0) {
+    tc::mbar_init(bar0, 1);
+    tc::mbar_init(bar1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  const int nslab = (a.cin + 15) / 16;
+  const uint32_t idesc = tc::idesc_bf16(128, a.co);
+  const int items = 2 * (TC_TR + 2) * HX;
+  bool ok = true;
+  int last = -1;  // the last slab whose MMAs were committed
+  for (int s = 0; s < nslab; ++s) {
+    const int b = s & 1;
+    unsigned char *stg = tc_smem + b * stage;
+    if (s >= 2 && !(ok = __syncthreads_and(tc::mbar_wait(bar(b), ((s - 2) >> 1) & 1)))) break;
+    for (int it = tid; it < items; it += TC_NT) {
+      const int cg = it / ((TC_TR + 2) * HX), rem = it - cg * ((TC_TR + 2) * HX);
+      const int hy = rem / HX, hx = rem - hy * HX;
+      const int y = y0 - 1 + hy, x = x0 - 1 + hx;
+      unsigned h[8], m[8], l[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int c = 16 * s + 8 * cg + e;
+        split3(c < a.cin ? read_in(a.I, n, c, y, x, a.H, a.W) : 0.f, h[e], m[e], l[e]);
+      }
+      const int off = cg * G + hy * RS + hx * 16;
+      *reinterpret_cast<uint4 *>(stg + off) =
+          make_uint4(h[0] | h[1] << 16, h[2] | h[3] << 16, h[4] | h[5] << 16, h[6] | h[7] << 16);
+      *reinterpret_cast<uint4 *>(stg + 2 * G + off) =
+          make_uint4(m[0] | m[1] << 16, m[2] | m[3] << 16, m[4] | m[5] << 16, m[6] | m[7] << 16);
+      *reinterpret_cast<uint4 *>(stg + 4 * G + off) =
+          make_uint4(l[0] | l[1] << 16, l[2] | l[3] << 16, l[4] | l[5] << 16, l[6] | l[7] << 16);
+    }
+    const uint4 *wsrc = a.w + (long)s * (wbytes / 16);
+    uint4 *wdst = reinterpret_cast<uint4 *>(stg + hbytes);
+    for (int i = tid; i < wbytes / 16; i += TC_NT) wdst[i] = wsrc[i];
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t hb = sbase + b * stage, wb = hb + hbytes;
+#pragma unroll 1
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap - 3 * (tap / 3);
+        const uint64_t bd = tc::sdesc(wb + tap * 2 * a.co * 16, a.co * 16, 128);
+        for (int t = 0; t < a.tx; ++t)
+#pragma unroll
+          for (int q = 0; q < TC_TERMS; ++q)
+            tc::mma_bf16(tmem + t * a.cs, tc::sdesc(hb + q * 2 * G + dy * RS + (8 * t + dx) * 16, G, RS), bd,
+                         idesc, (s | tap | q) != 0);
+      }
+      tc::commit(bar(b));
+    }
+    last = s;
+  }
+  if (ok && last >= 0) ok = __syncthreads_and(tc::mbar_wait(bar(last & 1), (last >> 1) & 1));
+  if (!ok) {
+    // raise the flag; wait once more (bounded) for the MMAs already issued before the
+    // tensor memory and the shared memory they use are released
+    if (tid == 0) {
+      atomicExch(&g_tc_timeout, 1);
+      if (last >= 0) (void)tc::mbar_wait(bar(last & 1), (last >> 1) & 1);
+    }
+  } else {
+    tc::fence_after_sync();
+    const int j = tid >> 3, r = tid & 7;  // accumulator row tid = tile row j, pixel r of the strip
+    const int y = y0 + j;
+    const long HW = (long)a.H * a.W;
+    for (int t = 0; t < a.tx; ++t) {
+      const int x = x0 + 8 * t + r;
+      const bool in = y < a.H && x < a.W;
+      float *o = a.out + (long)n * a.co * HW + (long)y * a.W + x;
+      for (int c0 = 0; c0 < a.co; c0 += 16) {
+        float v[16];
+        tc::ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * a.cs + c0), v);
+        if (in) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            float z = v[i] + (a.bias ? a.bias[c0 + i] : 0.f);
+            if (a.relu) z = fmaxf(z, 0.f);
+            o[(long)(c0 + i) * HW] = z;
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, a.ncols);
+  }
+}
+
+// Weight packs of the tensor-core kernel, from the BF16 weights w[o, c, 3, 3]:
+//   forward (N = co, K over c):      [slab][tap][kq][o][8]  = w[o, 16 slab + 8 kq + e, tap]
+//   data-backward (N = ci, K over o): [slab][tap][kq][c][8] = w[16 slab + 8 kq + e, c, 8 - tap]
+// (the data-backward is the forward convolution of dz with the flipped, transposed
+// filter); channels past the end of a slab are zero.
+struct TcPackL {
+  long woff, fo, bo;  // source offset, forward / backward pack offsets (-1: none)
+  int ci, co;
+};
+struct TcPack {
+  TcPackL L[kUL];
+};
+
+__global__ void k_pack_tc(const __nv_bfloat16 *__restrict__ w16, TcPack P, __nv_bfloat16 *__restrict__ dst) {
+  const TcPackL L = P.L[blockIdx.y];
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+  const long stride = (long)gridDim.x * blockDim.x;
+  if (L.fo >= 0) {
+    const long nf = (long)((L.ci + 15) / 16) * 16 * 9 * L.co;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nf; i += stride) {
+      long t = i >> 3;
+      const int e = (int)(i & 7), o = (int)(t % L.co);
+      t /= L.co;
+      const int kq = (int)(t & 1), tap = (int)((t >> 1) % 9), sl = (int)((t >> 1) / 9);
+      const int c = 16 * sl + 8 * kq + e;
+      dst[L.fo + i] = c < L.ci ? w16[L.woff + ((long)o * L.ci + c) * 9 + tap] : zero;
+    }
+  }
+  if (L.bo >= 0) {
+    const long nb = (long)((L.co + 15) / 16) * 16 * 9 * L.ci;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nb; i += stride) {
+      long t = i >> 3;
+      const int e = (int)(i & 7), c = (int)(t % L.ci);
+      t /= L.ci;
+      const int kq = (int)(t & 1), tap = (int)((t >> 1) % 9), sl = (int)((t >> 1) / 9);
+      const int o = 16 * sl + 8 * kq + e;
+      dst[L.bo + i] = o < L.co ? w16[L.woff + ((long)o * L.ci + c) * 9 + (8 - tap)] : zero;
     }
   }
 }
@@ -355,8 +578,55 @@ static int gblocks(long cnt) { return (int)std::max<long>(1, std::min<long>((cnt
 // ---------------------------------------------------------------------------
 // forward / backward of a batch of N <= cap samples held in U->x (N,3,H,W)
 // ---------------------------------------------------------------------------
+// the tensor-core convolution of I (cin channels) with a weight pack into co output channels
+static void conv_tc(hp_unet *U, const ConvIn &I, int cin, const __nv_bfloat16 *pack, const float *bias, float *out,
+                    int co, int N, int H, int W, int relu) {
+  // (a failure here surfaces as the launch's error, which the calling entry point returns)
+  static std::once_flag attr;
+  std::call_once(attr, [] { cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_MAX_SMEM); });
+  TcArgs a;
+  a.I = I;
+  a.cin = cin;
+  a.w = reinterpret_cast<const uint4 *>(pack);
+  a.bias = bias;
+  a.out = out;
+  a.co = co;
+  a.H = H;
+  a.W = W;
+  a.relu = relu;
+  a.tx = co <= 128 ? 2 : 1;
+  a.ntx = (W + 8 * a.tx - 1) / (8 * a.tx);
+  a.cs = (co + 31) / 32 * 32;
+  unsigned nc = 32;
+  while (nc < (unsigned)(a.tx * a.cs)) nc <<= 1;
+  a.ncols = nc;
+  const dim3 grid(a.ntx * ((H + TC_TR - 1) / TC_TR), N);
+  k_conv_tc<<<grid, TC_NT, 2 * tc_stage_bytes(a.tx, co), U->st>>>(a);
+  count_launch();
+}
+
+// whether layer li runs on the tensor cores (3x3, output channels a multiple of 16 up to 256)
+static bool use_tc(const hp_unet *U, int li) { return U->tensor_cores && U->tc_fo[li] >= 0; }
+
+// rebuilds the tensor-core weight packs from the BF16 weights (after every change of them)
+static void tc_repack(hp_unet *U) {
+  TcPack P;
+  long most = 0;
+  for (int l = 0; l < kUL; ++l) {
+    const ULayer &L = U->L[l];
+    P.L[l] = TcPackL{L.woff, U->tc_fo[l], U->tc_bo[l], L.ci, L.co};
+    most = std::max(most, (long)(L.ci + 15) / 16 * 16 * 9 * L.co);
+  }
+  k_pack_tc<<<dim3((unsigned)std::min<long>((most + 255) / 256, 256), kUL), 256, 0, U->st>>>(U->w16, P, U->wtc);
+  count_launch();
+}
+
 static void conv_fwd(hp_unet *U, int li, ConvIn I, float *out, int N, int H, int W, int relu) {
   const ULayer &L = U->L[li];
+  if (use_tc(U, li)) {
+    conv_tc(U, I, L.ci, U->wtc + U->tc_fo[li], U->p32 + L.boff, out, L.co, N, H, W, relu);
+    return;
+  }
   const int tiles = ((W + TB - 1) / TB) * ((H + TB - 1) / TB);
   dim3 grid(tiles, (L.co + OCB - 1) / OCB, N);
   k_conv_fwd<<<grid, 256, 0, U->st>>>(I, U->w16 + L.woff, U->p32 + L.boff, out, L.co, H, W, L.k, relu);
@@ -403,7 +673,9 @@ static void conv_bwd(hp_unet *U, int li, ConvIn I, float *d, const float *a_out,
   k_conv_bwd_weight<<<L.co * L.ci, 256, 0, U->st>>>(I, d, U->g + L.woff, L.co, N, H, W, L.k);
   k_bias_grad<<<L.co, 256, 0, U->st>>>(d, U->g + L.boff, L.co, N, (long)H * W);
   count_launch(2);
-  if (d_in) {
+  if (d_in && use_tc(U, li) && U->tc_bo[li] >= 0) {
+    conv_tc(U, ConvIn{d, L.co, 0, nullptr, 0}, L.co, U->wtc + U->tc_bo[li], nullptr, d_in, L.ci, N, H, W, 0);
+  } else if (d_in) {
     const int tiles = ((W + TB - 1) / TB) * ((H + TB - 1) / TB);
     dim3 grid(tiles, (L.ci + OCB - 1) / OCB, N);
     k_conv_bwd_data<<<grid, 256, 0, U->st>>>(d, U->w16 + L.woff, d_in, L.ci, L.co, H, W, L.k);
@@ -454,6 +726,17 @@ void unet_dims(const hp_unet *U, int *H, int *W) {
   *H = U->H;
   *W = U->W;
 }
+// after the network's stream has synchronised: fails the call if a tensor-core convolution
+// gave up waiting for its MMAs, and clears the flag
+static int tc_status() {
+  int f = 0;
+  HP_CUDA(cudaMemcpyFromSymbol(&f, g_tc_timeout, sizeof(int)));
+  if (!f) return HP_OK;
+  const int zero = 0;
+  HP_CUDA(cudaMemcpyToSymbol(g_tc_timeout, &zero, sizeof(int)));
+  return set_error(HP_ERR_CUDA, "a tensor-core convolution timed out waiting for its MMAs");
+}
+
 void unet_run(hp_unet *U, int N, cudaStream_t st) {
   cudaStream_t own = U->st;
   U->st = st;
@@ -483,10 +766,25 @@ int hp_unet_create(int H, int W, int batch_cap, hp_unet **out) {
     off += U->L[l].co;
   }
   U->nparam = off;
+  // tensor-core weight packs: forward for every 3x3 layer, data-backward where the input
+  // gradient is needed and the input channels are a multiple of 16 (not the first layer)
+  long toff = 0;
+  for (int l = 0; l < kUL; ++l) {
+    const ULayer &L = U->L[l];
+    U->tc_fo[l] = U->tc_bo[l] = -1;
+    if (L.k != 3 || L.co % 16 || L.co > 256) continue;
+    U->tc_fo[l] = toff;
+    toff += (long)(L.ci + 15) / 16 * 16 * 9 * L.co;
+    if (l > 0 && L.ci % 16 == 0 && L.ci <= 256) {
+      U->tc_bo[l] = toff;
+      toff += (long)(L.co + 15) / 16 * 16 * 9 * L.ci;
+    }
+  }
   auto fail = [&](const char *w) {
     hp_unet_destroy(U);
     return set_error(HP_ERR_NOMEM, w);
   };
+  if (cudaMalloc(&U->wtc, sizeof(__nv_bfloat16) * toff)) return fail("hp_unet_create: tensor-core weights");
   if (cudaMalloc(&U->p32, sizeof(float) * off) || cudaMalloc(&U->w16, sizeof(__nv_bfloat16) * off) ||
       cudaMalloc(&U->g, sizeof(float) * off) || cudaMalloc(&U->am, sizeof(float) * off) ||
       cudaMalloc(&U->av, sizeof(float) * off))
@@ -515,7 +813,7 @@ int hp_unet_create(int H, int W, int batch_cap, hp_unet **out) {
 void hp_unet_destroy(hp_unet *U) {
   if (!U) return;
   cudaDeviceSynchronize();
-  for (void *p : {(void *)U->p32, (void *)U->w16, (void *)U->g, (void *)U->am, (void *)U->av, (void *)U->x,
+  for (void *p : {(void *)U->p32, (void *)U->w16, (void *)U->wtc, (void *)U->g, (void *)U->am, (void *)U->av, (void *)U->x,
                   (void *)U->aux, (void *)U->da, (void *)U->db, (void *)U->dc, (void *)U->lossbuf})
     if (p) cudaFree(p);
   for (int l = 0; l < kUL; ++l)
@@ -527,11 +825,21 @@ void hp_unet_destroy(hp_unet *U) {
 
 long hp_unet_num_params(const hp_unet *U) { return U ? U->nparam : 0; }
 
+int hp_unet_set_tensor_cores(hp_unet *U, int on) {
+  if (!U || (on != 0 && on != 1)) return set_error(HP_ERR_INVALID, "hp_unet_set_tensor_cores: on is 0 or 1");
+  HP_CUDA(cudaStreamSynchronize(U->st));
+  U->tensor_cores = on;
+  return HP_OK;
+}
+
+int hp_unet_get_tensor_cores(const hp_unet *U) { return U ? U->tensor_cores : -1; }
+
 int hp_unet_set_params(hp_unet *U, const float *params_host) {
   if (!U || !params_host) return set_error(HP_ERR_INVALID, "null");
   HP_CUDA(cudaMemcpy(U->p32, params_host, sizeof(float) * U->nparam, cudaMemcpyHostToDevice));
   k_to_bf16<<<gblocks(U->nparam), 256, 0, U->st>>>(U->p32, U->w16, U->nparam);
   count_launch();
+  tc_repack(U);
   HP_CUDA(cudaMemset(U->am, 0, sizeof(float) * U->nparam));
   HP_CUDA(cudaMemset(U->av, 0, sizeof(float) * U->nparam));
   U->step = 0;
@@ -553,7 +861,8 @@ int hp_unet_forward(hp_unet *U, const float *x_dev, int N, float *y_dev) {
   unet_forward(U, N);
   HP_CUDA(cudaMemcpyAsync(y_dev, U->a[14], sizeof(float) * N * HW, cudaMemcpyDeviceToDevice, U->st));
   HP_CUDA(cudaStreamSynchronize(U->st));
-  return HP_OK;
+  HP_CUDA(cudaGetLastError());
+  return tc_status();
 }
 
 // loss and parameter gradients of one batch: x (N,3,H,W), aux (N,4,H,W)
@@ -574,6 +883,7 @@ static int unet_grad(hp_unet *U, const float *x, const float *aux, int N, double
   HP_CUDA(cudaMemcpyAsync(hp.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost, U->st));
   HP_CUDA(cudaStreamSynchronize(U->st));
   if (loss) *loss = std::accumulate(hp.begin(), hp.end(), 0.0);
+  HP_TRY(tc_status());
   return cuda_check(cudaGetLastError(), "unet_grad");
 }
 
@@ -627,6 +937,7 @@ int hp_unet_train(hp_unet *U, const float *X, const float *A, int nsamples, int 
       k_adam<<<gblocks(U->nparam), 256, 0, U->st>>>(U->p32, U->w16, U->g, U->am, U->av, U->nparam, isw, (float)lr, b1,
                                                    b2, 1e-8f, c1, c2);
       count_launch();
+      tc_repack(U);
       ep_loss += l;
       ++nbat;
     }

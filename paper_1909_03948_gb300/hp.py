@@ -144,6 +144,8 @@ _SIGS = {
     "hp_unet_forward": (_I, [C.c_void_p, _D, _I, _D]),
     "hp_unet_loss_grad": (_I, [C.c_void_p, _D, _D, _I, C.POINTER(C.c_double), C.POINTER(C.c_float)]),
     "hp_unet_train": (_I, [C.c_void_p, _D, _D, _I, _I, _I, C.c_double, C.c_ulonglong, C.POINTER(C.c_double)]),
+    "hp_unet_set_tensor_cores": (_I, [C.c_void_p, _I]),
+    "hp_unet_get_tensor_cores": (_I, [C.c_void_p]),
     "hp_warmstart_grid": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "hp_warmstart_attach": (_I, [_P, C.c_void_p]),
     "hp_warmstart_enable": (_I, [_P, _I]),
@@ -594,11 +596,21 @@ class UNet:
     """The warm-start network (owns an hp_unet handle).  Parameters travel as one
     packed float32 numpy vector (per layer: weights (co, ci, k, k), then biases)."""
 
-    def __init__(self, H: int, W: int, batch_cap: int = 16):
+    def __init__(self, H: int, W: int, batch_cap: int = 16, tensor_cores: bool = True):
         h = C.c_void_p()
         _check(lib().hp_unet_create(H, W, batch_cap, C.byref(h)), "hp_unet_create")
         self._h, self.H, self.W, self.cap = h, H, W, batch_cap
         self.nparam = int(lib().hp_unet_num_params(h))
+        self.tensor_cores = tensor_cores
+
+    @property
+    def tensor_cores(self) -> bool:
+        """Whether the 3x3 convolutions run on the tensor cores (hp_unet_set_tensor_cores)."""
+        return bool(lib().hp_unet_get_tensor_cores(self._h))
+
+    @tensor_cores.setter
+    def tensor_cores(self, on: bool):
+        _check(lib().hp_unet_set_tensor_cores(self._h, int(bool(on))), "hp_unet_set_tensor_cores")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
