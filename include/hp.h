@@ -415,8 +415,9 @@ int hp_unet_train(hp_unet *U, const float *X, const float *A, int nsamples, int 
 /* Where the 3x3 convolutions with a multiple of 16 output channels run (the forward
  * pass, and the input gradient of the backward pass): on = 1 (the default), on the
  * tensor cores as implicit GEMMs (tcgen05 MMAs on BF16 operands, FP32 accumulators in
- * tensor memory; each FP32 activation or gradient enters as three BF16 terms, so the
- * products see the FP32 values, as on the FP32 pipes); on = 0, on the FP32 pipes.  The
+ * tensor memory; each FP32 activation or gradient enters as three BF16 terms, its full
+ * significand, and the tensor core's accumulation truncates: outputs agree with the
+ * FP32-pipe kernels to about 1e-5 relative); on = 0, on the FP32 pipes.  The
  * weight gradients and the 1x1 output layer use the FP32 pipes either way.  A
  * tensor-core convolution whose MMAs have not completed after about a second gives up
  * and makes the forward, gradient or training call fail with HP_ERR_CUDA.

@@ -157,9 +157,11 @@ __global__ void __launch_bounds__(256) k_conv_fwd(ConvIn I, const __nv_bfloat16 
 // the 8 pixels of an MMA row group are consecutive halo columns, 16 bytes apart, and
 // consecutive row groups are consecutive halo rows (SBO = the halo row's bytes).
 // The FP32 inputs enter as three BF16 terms (hi + mid + lo, each the rounded remainder of
-// the previous ones: 24 significant bits, the FP32 significand) multiplied by the same
-// BF16 weights, so the products carry FP32 inputs, as the FP32-pipe kernels do, and the
-// accumulation is FP32.  Two stages: the loads of slab s + 1 overlap the MMAs of slab s;
+// the previous ones: the FP32 significand) multiplied by the same BF16 weights, so the
+// products carry the FP32 inputs, as the FP32-pipe kernels do.  The accumulation is the
+// tensor core's FP32, which aligns and truncates each MMA's sum: a relative error of order
+// 1e-5 over a layer.  (Two terms, 16 significant bits, flip ReLU decisions near zero
+// often enough to move the first layer's weight gradient by 2.5e-3; three do not.)  Two stages: the loads of slab s + 1 overlap the MMAs of slab s;
 // a stage is refilled once the tcgen05.commit of the MMAs that read it has arrived on
 // its mbarrier.
 // ---------------------------------------------------------------------------
@@ -191,7 +193,14 @@ struct TcArgs {
   int tx, ntx;         // MMAs per tile (8-column strips), tiles per image row
   int cs;              // tensor-memory columns between the strips' accumulators
   unsigned ncols;      // tensor-memory columns allocated
+  // optional 1x1 head on the activated outputs: hout[n, 0, y, x] = hb + sum_o hw[o] out[n, o, y, x]
+  const __nv_bfloat16 *hw;
+  const float *hb;
+  float *hout;
 };
+
+constexpr int TC_IPT = 6;  // halo items per thread: 2 x (TC_TR + 2) x (8 tx + 2) <= TC_IPT x TC_NT
+static_assert(2 * (TC_TR + 2) * tc_hx(2) <= TC_IPT * TC_NT, "halo items");
 
 __device__ __forceinline__ unsigned bf16_bits(float v) {
   return static_cast<unsigned>(__bfloat16_as_ushort(__float2bfloat16_rn(v)));
@@ -202,21 +211,21 @@ __device__ __forceinline__ void split3(float v, unsigned &h, unsigned &m, unsign
   const __nv_bfloat16 bh = __float2bfloat16_rn(v);
   const float r1 = __fsub_rn(v, __bfloat162float(bh));
   const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
-  const float r2 = __fsub_rn(r1, __bfloat162float(bm));
   h = __bfloat16_as_ushort(bh);
   m = __bfloat16_as_ushort(bm);
-  l = bf16_bits(r2);
+  l = bf16_bits(__fsub_rn(r1, __bfloat162float(bm)));
 }
 
-__global__ void __launch_bounds__(TC_NT) k_conv_tc(TcArgs a) {
+template <int TX>
+__global__ void __launch_bounds__(TC_NT, 4) k_conv_tc(TcArgs a) {
   extern __shared__ __align__(128) unsigned char tc_smem[];
   __shared__ __align__(8) unsigned long long bars[2];
   __shared__ unsigned tslot;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int bx = blockIdx.x % a.ntx, by = blockIdx.x / a.ntx, n = blockIdx.y;
-  const int x0 = bx * 8 * a.tx, y0 = by * TC_TR;
-  const int HX = tc_hx(a.tx), RS = tc_rs(a.tx), G = tc_g(a.tx);
-  const int stage = tc_stage_bytes(a.tx, a.co), hbytes = tc_halo_bytes(a.tx), wbytes = tc_w_bytes(a.co);
+  const int x0 = bx * 8 * TX, y0 = by * TC_TR;
+  constexpr int HX = tc_hx(TX), RS = tc_rs(TX), G = tc_g(TX), hbytes = tc_halo_bytes(TX);
+  const int stage = tc_stage_bytes(TX, a.co), wbytes = tc_w_bytes(a.co);
   const uint32_t sbase = tc::saddr(tc_smem);
   const uint32_t bar0 = tc::saddr(&bars[0]), bar1 = tc::saddr(&bars[1]);
   auto bar = [&](int i) { return i ? bar1 : bar0; };
@@ -232,23 +241,42 @@ __global__ void __launch_bounds__(TC_NT) k_conv_tc(TcArgs a) {
   const uint32_t tmem = tslot;
   const int nslab = (a.cin + 15) / 16;
   const uint32_t idesc = tc::idesc_bf16(128, a.co);
-  const int items = 2 * (TC_TR + 2) * HX;
+  constexpr int items = 2 * (TC_TR + 2) * HX;
   bool ok = true;
   int last = -1;  // the last slab whose MMAs were committed
   for (int s = 0; s < nslab; ++s) {
     const int b = s & 1;
     unsigned char *stg = tc_smem + b * stage;
     if (s >= 2 && !(ok = __syncthreads_and(tc::mbar_wait(bar(b), ((s - 2) >> 1) & 1)))) break;
-    for (int it = tid; it < items; it += TC_NT) {
+    // the slab's 16 channels come from one input tensor (c1 is a multiple of 16 when c2 > 0)
+    const bool first = 16 * s < a.I.c1;
+    const int up = first && a.I.up1;
+    const int Hs = up ? a.H >> 1 : a.H, Ws = up ? a.W >> 1 : a.W;
+    const int nsrc = first ? a.I.c1 : a.I.c2, cb = first ? 16 * s : 16 * s - a.I.c1;
+    const long plane = (long)Hs * Ws;
+    const float *src = (first ? a.I.in1 : a.I.in2) + ((long)n * nsrc + cb) * plane;
+    // every load of this thread's items is issued before any is converted
+    float v[TC_IPT][8];
+#pragma unroll
+    for (int k = 0; k < TC_IPT; ++k) {
+      const int it = tid + k * TC_NT;
       const int cg = it / ((TC_TR + 2) * HX), rem = it - cg * ((TC_TR + 2) * HX);
       const int hy = rem / HX, hx = rem - hy * HX;
       const int y = y0 - 1 + hy, x = x0 - 1 + hx;
+      const bool inb = it < items && y >= 0 && y < a.H && x >= 0 && x < a.W;
+      const float *p = src + 8 * cg * plane + (long)(up ? y >> 1 : y) * Ws + (up ? x >> 1 : x);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[k][e] = (inb && cb + 8 * cg + e < nsrc) ? p[e * plane] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < TC_IPT; ++k) {
+      const int it = tid + k * TC_NT;
+      if (it >= items) break;
+      const int cg = it / ((TC_TR + 2) * HX), rem = it - cg * ((TC_TR + 2) * HX);
+      const int hy = rem / HX, hx = rem - hy * HX;
       unsigned h[8], m[8], l[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int c = 16 * s + 8 * cg + e;
-        split3(c < a.cin ? read_in(a.I, n, c, y, x, a.H, a.W) : 0.f, h[e], m[e], l[e]);
-      }
+      for (int e = 0; e < 8; ++e) split3(v[k][e], h[e], m[e], l[e]);
       const int off = cg * G + hy * RS + hx * 16;
       *reinterpret_cast<uint4 *>(stg + off) =
           make_uint4(h[0] | h[1] << 16, h[2] | h[3] << 16, h[4] | h[5] << 16, h[6] | h[7] << 16);
@@ -269,7 +297,8 @@ __global__ void __launch_bounds__(TC_NT) k_conv_tc(TcArgs a) {
       for (int tap = 0; tap < 9; ++tap) {
         const int dy = tap / 3, dx = tap - 3 * (tap / 3);
         const uint64_t bd = tc::sdesc(wb + tap * 2 * a.co * 16, a.co * 16, 128);
-        for (int t = 0; t < a.tx; ++t)
+#pragma unroll
+        for (int t = 0; t < TX; ++t)
 #pragma unroll
           for (int q = 0; q < TC_TERMS; ++q)
             tc::mma_bf16(tmem + t * a.cs, tc::sdesc(hb + q * 2 * G + dy * RS + (8 * t + dx) * 16, G, RS), bd,
@@ -292,10 +321,12 @@ __global__ void __launch_bounds__(TC_NT) k_conv_tc(TcArgs a) {
     const int j = tid >> 3, r = tid & 7;  // accumulator row tid = tile row j, pixel r of the strip
     const int y = y0 + j;
     const long HW = (long)a.H * a.W;
-    for (int t = 0; t < a.tx; ++t) {
+#pragma unroll
+    for (int t = 0; t < TX; ++t) {
       const int x = x0 + 8 * t + r;
       const bool in = y < a.H && x < a.W;
       float *o = a.out + (long)n * a.co * HW + (long)y * a.W + x;
+      float head = a.hout ? a.hb[0] : 0.f;
       for (int c0 = 0; c0 < a.co; c0 += 16) {
         float v[16];
         tc::ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * a.cs + c0), v);
@@ -305,9 +336,11 @@ __global__ void __launch_bounds__(TC_NT) k_conv_tc(TcArgs a) {
             float z = v[i] + (a.bias ? a.bias[c0 + i] : 0.f);
             if (a.relu) z = fmaxf(z, 0.f);
             o[(long)(c0 + i) * HW] = z;
+            if (a.hout) head = fmaf(__bfloat162float(a.hw[c0 + i]), z, head);
           }
         }
       }
+      if (in && a.hout) a.hout[(long)n * HW + (long)y * a.W + x] = head;
     }
   }
   tc::fence_before_sync();
@@ -580,10 +613,14 @@ static int gblocks(long cnt) { return (int)std::max<long>(1, std::min<long>((cnt
 // ---------------------------------------------------------------------------
 // the tensor-core convolution of I (cin channels) with a weight pack into co output channels
 static void conv_tc(hp_unet *U, const ConvIn &I, int cin, const __nv_bfloat16 *pack, const float *bias, float *out,
-                    int co, int N, int H, int W, int relu) {
+                    int co, int N, int H, int W, int relu, const __nv_bfloat16 *hw = nullptr,
+                    const float *hb = nullptr, float *hout = nullptr) {
   // (a failure here surfaces as the launch's error, which the calling entry point returns)
   static std::once_flag attr;
-  std::call_once(attr, [] { cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_MAX_SMEM); });
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_MAX_SMEM);
+    cudaFuncSetAttribute(k_conv_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_MAX_SMEM);
+  });
   TcArgs a;
   a.I = I;
   a.cin = cin;
@@ -600,8 +637,15 @@ static void conv_tc(hp_unet *U, const ConvIn &I, int cin, const __nv_bfloat16 *p
   unsigned nc = 32;
   while (nc < (unsigned)(a.tx * a.cs)) nc <<= 1;
   a.ncols = nc;
+  a.hw = hw;
+  a.hb = hb;
+  a.hout = hout;
   const dim3 grid(a.ntx * ((H + TC_TR - 1) / TC_TR), N);
-  k_conv_tc<<<grid, TC_NT, 2 * tc_stage_bytes(a.tx, co), U->st>>>(a);
+  const int stages = cin > 16 ? 2 : 1;  // one 16-channel slab needs no second stage
+  if (a.tx == 2)
+    k_conv_tc<2><<<grid, TC_NT, stages * tc_stage_bytes(2, co), U->st>>>(a);
+  else
+    k_conv_tc<1><<<grid, TC_NT, stages * tc_stage_bytes(1, co), U->st>>>(a);
   count_launch();
 }
 
@@ -623,7 +667,7 @@ static void tc_repack(hp_unet *U) {
 
 static void conv_fwd(hp_unet *U, int li, ConvIn I, float *out, int N, int H, int W, int relu) {
   const ULayer &L = U->L[li];
-  if (use_tc(U, li)) {
+  if (use_tc(U, li) && (I.c2 == 0 || I.c1 % 16 == 0)) {  // a 16-channel slab reads one input tensor
     conv_tc(U, I, L.ci, U->wtc + U->tc_fo[li], U->p32 + L.boff, out, L.co, N, H, W, relu);
     return;
   }
@@ -656,8 +700,15 @@ static void unet_forward(hp_unet *U, int N) {
   conv_fwd(U, 10, cin(U->a[9], 64, 1, U->a[3], 32), U->a[10], N, h[1], w[1], 1);
   conv_fwd(U, 11, cin(U->a[10], 32), U->a[11], N, h[1], w[1], 1);
   conv_fwd(U, 12, cin(U->a[11], 32, 1, U->a[1], 16), U->a[12], N, h[0], w[0], 1);
-  conv_fwd(U, 13, cin(U->a[12], 16), U->a[13], N, h[0], w[0], 1);
-  conv_fwd(U, 14, cin(U->a[13], 16), U->a[14], N, h[0], w[0], 0);
+  if (use_tc(U, 13)) {
+    // dec1b with the 1x1 output layer folded into its epilogue
+    const ULayer &L = U->L[13], &O = U->L[14];
+    conv_tc(U, cin(U->a[12], 16), L.ci, U->wtc + U->tc_fo[13], U->p32 + L.boff, U->a[13], L.co, N, h[0], w[0], 1,
+            U->w16 + O.woff, U->p32 + O.boff, U->a[14]);
+  } else {
+    conv_fwd(U, 13, cin(U->a[12], 16), U->a[13], N, h[0], w[0], 1);
+    conv_fwd(U, 14, cin(U->a[13], 16), U->a[14], N, h[0], w[0], 0);
+  }
   count_launch(3);
 }
 

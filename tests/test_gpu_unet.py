@@ -14,13 +14,13 @@ BF16 weights and accumulate in FP32):
 
 Grids 16 x 40 (a ragged last 16-wide tile), 24 x 24 and 72 x 24, batches of 2 and 3, with the 3x3
 convolutions on the FP32 pipes and on the tensor cores (the default).  The tensor-core
-kernels take each FP32 activation as three BF16 terms (the FP32 significand), but the
-tensor core's FP32 accumulation is not IEEE round-to-nearest: each MMA aligns its 16
-products and the accumulator and truncates the sum (Fasi, Higham, Mikaitis and Pranesh,
-"Numerical behavior of NVIDIA tensor cores", PeerJ Comput. Sci. 2021), an error of up
-to ~2^-23 of the accumulator per MMA, of one sign, over 27 MMAs per 16-channel slab.
-That is a relative bias of order 1e-5 per layer where FP32 FMAs make ~1e-7, so with the
-tensor cores the loss bound is 1e-4 relative and the gradient bound's relative term 1e-3.
+kernels take each FP32 activation as three BF16 terms (its full significand), and the tensor
+core's FP32 accumulation is not IEEE round-to-nearest: each MMA aligns its 16 products
+and the accumulator and truncates the sum (Fasi, Higham, Mikaitis and Pranesh, "Numerical
+behavior of NVIDIA tensor cores", PeerJ Comput. Sci. 2021), an error of up to ~2^-23 of
+the accumulator per MMA, of one sign, over 27 MMAs per 16-channel slab.  That is a
+relative bias of order 1e-5 per layer where FP32 FMAs make ~1e-7, so with the tensor
+cores the loss bound is 1e-4 relative and the gradient bound's relative term 1e-3.
 Between the two kernel families, on grids whose tiles are ragged in both directions:
 forward outputs within 1e-4 of the largest output and loss within 1e-4 relative (their
 gradients are compared with the oracle above: where the residual loss's gradient sums
