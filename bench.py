@@ -703,19 +703,24 @@ def warmstart_leg(P, Omega, m_lin, args, dev):
     H, Wd = P.warmstart_grid()
     xin = torch.zeros((net.cap, 3, H, Wd), dtype=torch.float32, device=dev)
     net.forward(xin)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(3):
+    fwd_ms = {}
+    for tc in (True, False):  # the tensor-core convolutions (the default), then the FP32-pipe kernels
+        net.tensor_cores = tc
         net.forward(xin)
-    e1.record()
-    e1.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            net.forward(xin)
+        e1.record()
+        e1.synchronize()
+        fwd_ms[tc] = e0.elapsed_time(e1) / 3 / net.cap
     P.warmstart_attach(None)
     P.set_point(m_lin)
     net.close()
     return {"train_samples": nsamp, "prior_draws": args.ws_draws, "epochs": args.ws_epochs,
             "generate_s": t_gen, "train_s": t_train, "loss_first_epoch": float(losses[0]),
             "loss_last_epoch": float(losses[-1]), **out, "guesses": c["guesses"], "fallbacks": c["fallbacks"],
-            "forward_ms_per_column": e0.elapsed_time(e1) / 3 / net.cap,
+            "forward_ms_per_column": fwd_ms[True], "forward_ms_per_column_fp32_pipes": fwd_ms[False],
             "note": ("same tolerance either way; the zero start stays the default of the timed step, "
                      "the learned start pays only if its inference costs less than the iterations it saves")}
 
