@@ -1359,11 +1359,12 @@ void prof_harvest(hp_problem *P, size_t from, size_t to, bool keep) {
     const int id = P->prof_id[r];
     if (id < 0 || id >= 16) continue;
     float ms = 0.f;
+    const bool clean = cudaPeekAtLastError() == cudaSuccess;  // an earlier error stays for the caller
     if (cudaEventElapsedTime(&ms, P->prof_ev[2 * r], P->prof_ev[2 * r + 1]) == cudaSuccess) {
       P->prof_cnt[id] += 1;
       P->prof_ms[id] += ms;
     } else {
-      cudaGetLastError();  // a failed timing query must not surface as a solver error
+      if (clean) (void)cudaGetLastError();  // a failed timing query must not surface as a solver error
       P->prof_failed = true;
     }
     if (!keep) P->prof_id[r] = -1;
@@ -2308,9 +2309,10 @@ static void launch_vtail_smem(hp_problem *P, OpKind op, int s, int l0, const T *
   auto allow = [&](void (*k)(VTailS<T>)) {
     cudaFuncAttributes fa{};
     int cap = smem_optin();
+    const bool clean = cudaPeekAtLastError() == cudaSuccess;  // an earlier error stays for the caller
     if (cudaFuncGetAttributes(&fa, k) == cudaSuccess) cap -= (int)fa.sharedSizeBytes;
     if (cap < (int)bytes || cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess) {
-      (void)cudaGetLastError();  // a refused limit is not an error of the solve
+      if (clean) (void)cudaGetLastError();  // a refused limit is not an error of the solve
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     }
   };
