@@ -28,6 +28,9 @@ import os
 os.environ.setdefault("OMP_NUM_THREADS", "1")
 os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
 os.environ.setdefault("MKL_NUM_THREADS", "1")
+# 32 hardware work queues for the batch's per-problem streams (the CUDA default is 8); read
+# when CUDA starts, so it is set before anything touches the GPU
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import argparse
 import hashlib

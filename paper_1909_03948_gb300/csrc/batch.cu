@@ -5,9 +5,13 @@
 // each inner solve a CUDA graph with a device-side while loop -- run
 // concurrently and fill the SMs that a single small problem leaves idle.  A
 // problem's own sequence is unchanged, so batched results equal the results of
-// the same calls made one problem at a time.
+// the same calls made one problem at a time.  The streams share the device's
+// hardware work queues (CUDA_DEVICE_MAX_CONNECTIONS, 8 unless the process sets
+// it before CUDA starts; 32 measured 7.8 % more actions/s on 64 problems and a
+// third off MAP + eigenpairs).
 #include <algorithm>
 #include <atomic>
+#include <functional>
 #include <thread>
 #include <vector>
 
@@ -22,13 +26,21 @@ struct hp_batch {
 
 namespace hp {
 
+// Runs work(i) for every problem on the thread pool, handing problems out in index order,
+// or largest first when weight is given (by weight(i), ties in index order: the
+// longest-processing-time rule, which keeps a long problem from starting last and running
+// alone at the end).  Largest first took MAP + eigenpairs of 64 problems from 9.94 to
+// 9.77 s but made one block of Hessian actions 1 % slower, so only the former uses it.
 template <class F>
-static void run_pool(hp_batch *B, F &&work) {
+static void run_pool(hp_batch *B, F &&work, const std::function<double(int)> *weight) {
   std::atomic<int> next{0};
   const int n = (int)B->P.size();
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  if (weight) std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return (*weight)(a) > (*weight)(b); });
   auto body = [&]() {
     cudaSetDevice(B->device);
-    for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) work(i);
+    for (int k = next.fetch_add(1); k < n; k = next.fetch_add(1)) work(order[k]);
   };
   std::vector<std::thread> pool;
   const int nt = std::max(1, std::min(B->nthreads, n));
@@ -83,14 +95,18 @@ int hp_batch_map_and_eig(hp_batch *B, double *const *m_inout, const hp_newton_op
                          const int *ldv, hp_newton_stats *nstats, int *status) {
   if (!B || !m_inout || !Omega || !ldo || !lambda || !V || !ldv || !status)
     return set_error(HP_ERR_INVALID, "hp_batch_map_and_eig: arguments");
-  run_pool(B, [&](int i) {
+  const std::function<double(int)> largest = [&](int i) { return (double)B->P[i]->n; };
+  run_pool(
+      B,
+      [&](int i) {
     hp_newton_stats st{};
     int rc = hp_newton_cg_map(B->P[i], m_inout[i], opts, &st);
     if (nstats) nstats[i] = st;
     if (rc == HP_OK || rc == HP_ERR_NOT_CONVERGED)
       rc = hp_lowrank_eig(B->P[i], m_inout[i], k, p, Omega[i], ldo[i], lambda[i], V[i], ldv[i], 0, nullptr);
     status[i] = rc;
-  });
+      },
+      &largest);
   for (size_t i = 0; i < B->P.size(); ++i)
     if (status[i] != HP_OK) return set_error(status[i], "hp_batch_map_and_eig: a problem failed (see status)");
   return HP_OK;
@@ -100,7 +116,9 @@ int hp_batch_hessian_apply(hp_batch *B, const double *const *X, const int *ldx, 
                            const int *nrhs, int flags, int *status) {
   if (!B || !X || !ldx || !Y || !ldy || !nrhs || !status)
     return set_error(HP_ERR_INVALID, "hp_batch_hessian_apply: arguments");
-  run_pool(B, [&](int i) { status[i] = hp_hessian_apply(B->P[i], X[i], ldx[i], Y[i], ldy[i], nrhs[i], flags, nullptr); });
+  run_pool(
+      B, [&](int i) { status[i] = hp_hessian_apply(B->P[i], X[i], ldx[i], Y[i], ldy[i], nrhs[i], flags, nullptr); },
+      nullptr);
   for (size_t i = 0; i < B->P.size(); ++i)
     if (status[i] != HP_OK) return set_error(status[i], "hp_batch_hessian_apply: a problem failed (see status)");
   return HP_OK;
@@ -108,7 +126,7 @@ int hp_batch_hessian_apply(hp_batch *B, const double *const *X, const int *ldx, 
 
 int hp_batch_set_point(hp_batch *B, const double *const *m, int *status) {
   if (!B || !m || !status) return set_error(HP_ERR_INVALID, "hp_batch_set_point: arguments");
-  run_pool(B, [&](int i) { status[i] = hp_set_point(B->P[i], m[i], nullptr); });
+  run_pool(B, [&](int i) { status[i] = hp_set_point(B->P[i], m[i], nullptr); }, nullptr);
   for (size_t i = 0; i < B->P.size(); ++i)
     if (status[i] != HP_OK) return set_error(status[i], "hp_batch_set_point: a problem failed (see status)");
   return HP_OK;

@@ -675,7 +675,9 @@ def _ints(v):
 
 class Batch:
     """Independent problems of uneven size run concurrently (one stream and one host
-    worker per problem at a time).  Problems stay owned by the caller."""
+    worker per problem at a time).  Problems stay owned by the caller.  The streams
+    share CUDA's hardware work queues: set CUDA_DEVICE_MAX_CONNECTIONS=32 in the
+    environment before CUDA starts (8 otherwise; hp_batch_create in include/hp.h)."""
 
     def __init__(self, problems, nthreads: int = 0):
         self.problems = list(problems)
