@@ -277,6 +277,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def build_record():
+    """Which machine and compiler built the loaded libhp.so (build.py's stamp) and when: the
+    library is rebuilt whenever the stamp differs from the machine it runs on."""
+    pkg = os.path.join(ROOT, "paper_1909_03948_gb300")
+    out = {"machine": os.uname().machine}
+    try:
+        stamp = open(os.path.join(pkg, "_build", "STAMP")).read().split("\n")
+        out["built_on"], out["nvcc"] = stamp[0], stamp[1] if len(stamp) > 1 else None
+        out["lib_mtime"] = time.strftime("%Y-%m-%dT%H:%M:%S", time.gmtime(os.path.getmtime(os.path.join(pkg, "libhp.so"))))
+    except OSError as ex:
+        out["error"] = str(ex)
+    return out
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -604,6 +618,7 @@ def run_ours(args, rank, world):
         "roofline": roof,
         "cpu_baseline": cpu,
         "pcg": {"inner_iterations_per_step": statistics.median(iters), "refinement_steps": statistics.median(outers)},
+        "build": build_record(),
         **extra,
     }
     print(json.dumps(line), flush=True)
@@ -839,7 +854,7 @@ def run_batch(args, rank, world):
                                f"(multiples of 32), q in [100, 800], one block of k+p=40 GN Hessian actions per "
                                f"problem at its MAP, problems concurrent on per-problem streams",
                    "l2": "flushed (512 MB write) before every timed step"},
-        "gpu_launches": launches, "clocks": clk,
+        "gpu_launches": launches, "clocks": clk, "build": build_record(),
         "e2e": {"value": e2e_val, "unit": "actions/s", "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
         "roofline": roof, "cpu_baseline": cpu,
         "time_to_map_eig_s": t_me,
