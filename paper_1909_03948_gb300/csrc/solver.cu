@@ -441,8 +441,14 @@ constexpr unsigned TL3_OFF_C = (TL3_XB + 127u) / 128u * 128u;
 constexpr unsigned TL3_OFF_Z = TL3_OFF_C + (TL3_CB + 127u) / 128u * 128u;
 constexpr unsigned TL3_OFF_R = TL3_OFF_Z + (TL3_ZB + 127u) / 128u * 128u;
 constexpr unsigned TL3_SLOT = TL3_OFF_R + (TL3_RB + 127u) / 128u * 128u;
-constexpr unsigned TL3_OFF_BAR = TL3_NS * TL3_SLOT;
-constexpr unsigned TL3_SMEM = TL3_OFF_BAR + 8u * TL3_NS + 128u;  // + alignment slack
+// A mode that reads no b (the matvecs, the two fused sweeps from zero, which take r as x)
+// has slots that end before the b plane: 42 KB instead of 56.6 KB per CTA, so five CTAs fit
+// on an SM instead of four.
+template <int MODE> constexpr bool tl3_has_b() { return MODE == M_RESID || MODE == M_JACOBI || MODE == M_JACOBI_DOT; }
+template <int MODE> constexpr unsigned tl3_slot() { return tl3_has_b<MODE>() ? TL3_SLOT : TL3_OFF_R; }
+template <int MODE> constexpr unsigned tl3_smem() {
+  return TL3_NS * tl3_slot<MODE>() + 8u * TL3_NS + 128u;  // slots, barriers, alignment slack
+}
 
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
                                             uint32_t bar) {
@@ -487,12 +493,13 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
   const int x0 = tx * TILE3_X, y0 = ty * TILE3_Y, zb = tz * zs;
   const int wx = TILE3_X + (tx == ntx - 1), hy = TILE3_Y + (ty == nty - 1);
   const int ze = zb + zs + (tz == nzs - 1);  // planes zb .. ze - 1
-  const uint32_t bar0 = smem_u32(sm + TL3_OFF_BAR);
+  constexpr unsigned SLOT = tl3_slot<MODE>();
+  const uint32_t bar0 = smem_u32(sm + TL3_NS * SLOT);
   const unsigned bytes = TL3_XB + TL3_CB + TL3_ZB + (HAS_B ? TL3_RB : 0u);
   // plane q sits in slot (q - zb) % NS; its barrier's phase is the slot's use count
   auto issue = [&](int q) {
     const int r = q - zb, k = r % TL3_NS;
-    unsigned char *sl = sm + k * TL3_SLOT;
+    unsigned char *sl = sm + k * SLOT;
     const uint32_t bar = bar0 + 8u * k;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
     tma_load_4d(smem_u32(sl), &mx, 4 * (x0 - 1), y0 - 1, q, grp, bar);
@@ -545,8 +552,8 @@ __global__ void __launch_bounds__(TL3_NT) k_st_tile3(const __grid_constant__ CUt
       p_fail = p;
       break;
     }
-    const unsigned char *sm_0 = sm + ((p - zb) % TL3_NS) * TL3_SLOT;       // plane p
-    const unsigned char *sm_p = sm + ((p - zb + 1) % TL3_NS) * TL3_SLOT;   // plane p + 1
+    const unsigned char *sm_0 = sm + ((p - zb) % TL3_NS) * SLOT;       // plane p
+    const unsigned char *sm_p = sm + ((p - zb + 1) % TL3_NS) * SLOT;   // plane p + 1
     const float *x0s = reinterpret_cast<const float *>(sm_0), *xp = reinterpret_cast<const float *>(sm_p);
     const float4 *c0s = reinterpret_cast<const float4 *>(sm_0 + TL3_OFF_C),
                  *cp = reinterpret_cast<const float4 *>(sm_p + TL3_OFF_C);
@@ -1548,9 +1555,9 @@ static bool tile3_launch(const GridDesc &g, const Stencil<float> &S, const float
     // form for this launch without touching it
     if (cudaPeekAtLastError() != cudaSuccess) return false;
     int per_sm = 0, sms = 0;
-    if (cudaFuncSetAttribute(k_st_tile3<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL3_SMEM) !=
+    if (cudaFuncSetAttribute(k_st_tile3<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tl3_smem<MODE>()) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_st_tile3<MODE>, TL3_NT, TL3_SMEM) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_st_tile3<MODE>, TL3_NT, tl3_smem<MODE>()) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1) {
       (void)cudaGetLastError();  // clears only the refused set-up call's error: the row kernels run instead
       return false;
@@ -1577,7 +1584,7 @@ static bool tile3_launch(const GridDesc &g, const Stencil<float> &S, const float
       }
     }
   }
-  k_st_tile3<MODE><<<dim3(ntx * nty * nzs, ng), TL3_NT, TL3_SMEM, st>>>(
+  k_st_tile3<MODE><<<dim3(ntx * nty * nzs, ng), TL3_NT, tl3_smem<MODE>(), st>>>(
       mx, mr, mc, mz, g, ntx, nty, nzs, X, gx, S.pk, S.pk + 4 * g.n, Y, gy, s, omega, omega2, fin);
   count_launch();
   if (!tl_no_count) g_tiled_launches.fetch_add(1, std::memory_order_relaxed);
