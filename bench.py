@@ -454,7 +454,9 @@ def run_ours(args, rank, world):
         P.set_tuning()
         tune, tune_ms, tune_src = P.get_tuning(), None, "library defaults"
     else:
-        tune, tune_ms, tune_src = tuning.tuned(P, s, args.precision)
+        # tuned on the timed block itself: a candidate's PCG iteration count depends on the
+        # right-hand sides, so a random block can favour another smoother
+        tune, tune_ms, tune_src = tuning.tuned(P, s, args.precision, X=Omega)
     Y = torch.empty_like(Omega)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 

@@ -375,6 +375,12 @@ int hp_get_tuning(const hp_problem *P, hp_tuning *t);
  * (HOST, may be NULL) receive it.  Needs hp_set_point first; allocates its test
  * block (setup-time call). */
 int hp_autotune(hp_problem *P, int nrhs, int reps, hp_tuning *best, double *best_ms);
+/* The same search timed on the caller's block: X (DEVICE, column-major n x nrhs,
+ * ldx >= n) is the block of directions the settings are for (the iteration count
+ * of a candidate depends on the right-hand sides, so a random block can favour
+ * another smoother than the block that will run).  X is only read. */
+int hp_autotune_block(hp_problem *P, const double *X, int ldx, int nrhs, int reps, hp_tuning *best,
+                      double *best_ms);
 
 /* ---- learned warm start (2D stiffness solves; no counterpart in the paper) --
  * A 4-level U-Net (16-32-64-128 channels, 3x3 convolutions with zero padding,

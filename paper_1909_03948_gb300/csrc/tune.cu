@@ -66,36 +66,32 @@ int hp_get_tuning(const hp_problem *P, hp_tuning *t) {
   return HP_OK;
 }
 
-int hp_autotune(hp_problem *P, int nrhs, int reps, hp_tuning *best, double *best_ms) {
-  if (!P || nrhs < 1 || reps < 1) return set_error(HP_ERR_INVALID, "hp_autotune: arguments");
-  if (!P->have_point) return set_error(HP_ERR_STATE, "hp_set_point must be called first");
+}  // extern "C"
+
+// The search of hp_autotune / hp_autotune_block on the device block X (n x nrhs, ldx).
+static int autotune_on(hp_problem *P, const double *X, int ldx, int nrhs, int reps, hp_tuning *best,
+                       double *best_ms) {
   const long n = P->n;
-  double *X = nullptr, *Y = nullptr;
-  HP_CUDA(cudaMalloc(&X, sizeof(double) * n * nrhs));
-  if (cudaMalloc(&Y, sizeof(double) * n * nrhs) != cudaSuccess) {
-    cudaFree(X);
-    return set_error(HP_ERR_NOMEM, "hp_autotune: workspace");
-  }
-  launch_philox_normals(0x7475ULL, 0, nrhs, (int)n, X, n, 0, P->st);
+  double *Y = nullptr;
+  if (cudaMalloc(&Y, sizeof(double) * n * nrhs) != cudaSuccess) return set_error(HP_ERR_NOMEM, "autotune: workspace");
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   auto cleanup = [&](int rc) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(X);
     cudaFree(Y);
     return rc;
   };
   auto time_it = [&](const hp_tuning &t, double *ms) -> int {
     int rc = hp_set_tuning(P, &t);
     if (rc) return rc;
-    rc = hp_hessian_apply(P, X, (int)n, Y, (int)n, nrhs, HP_MISFIT_ONLY, nullptr);  // warm: builds graphs
+    rc = hp_hessian_apply(P, X, ldx, Y, (int)n, nrhs, HP_MISFIT_ONLY, nullptr);  // warm: builds graphs
     if (rc) return rc;
     double acc = 0.0;
     for (int r = 0; r < reps; ++r) {
       cudaEventRecord(e0, P->st);
-      rc = hp_hessian_apply(P, X, (int)n, Y, (int)n, nrhs, HP_MISFIT_ONLY, nullptr);
+      rc = hp_hessian_apply(P, X, ldx, Y, (int)n, nrhs, HP_MISFIT_ONLY, nullptr);
       if (rc) return rc;
       cudaEventRecord(e1, P->st);
       cudaEventSynchronize(e1);
@@ -185,6 +181,27 @@ int hp_autotune(hp_problem *P, int nrhs, int reps, hp_tuning *best, double *best
   if (best) *best = cur;
   if (best_ms) *best_ms = cur_ms;
   return cleanup(HP_OK);
+}
+
+extern "C" {
+
+int hp_autotune(hp_problem *P, int nrhs, int reps, hp_tuning *best, double *best_ms) {
+  if (!P || nrhs < 1 || reps < 1) return set_error(HP_ERR_INVALID, "hp_autotune: arguments");
+  if (!P->have_point) return set_error(HP_ERR_STATE, "hp_set_point must be called first");
+  const long n = P->n;
+  double *X = nullptr;
+  HP_CUDA(cudaMalloc(&X, sizeof(double) * n * nrhs));
+  launch_philox_normals(0x7475ULL, 0, nrhs, (int)n, X, n, 0, P->st);
+  const int rc = autotune_on(P, X, (int)n, nrhs, reps, best, best_ms);
+  cudaFree(X);
+  return rc;
+}
+
+int hp_autotune_block(hp_problem *P, const double *X, int ldx, int nrhs, int reps, hp_tuning *best,
+                      double *best_ms) {
+  if (!P || !X || nrhs < 1 || reps < 1 || ldx < P->n) return set_error(HP_ERR_INVALID, "hp_autotune_block: arguments");
+  if (!P->have_point) return set_error(HP_ERR_STATE, "hp_set_point must be called first");
+  return autotune_on(P, X, ldx, nrhs, reps, best, best_ms);
 }
 
 }  // extern "C"

@@ -136,6 +136,7 @@ _SIGS = {
     "hp_set_tuning": (_I, [_P, C.POINTER(Tuning)]),
     "hp_get_tuning": (_I, [_P, C.POINTER(Tuning)]),
     "hp_autotune": (_I, [_P, _I, _I, C.POINTER(Tuning), C.POINTER(C.c_double)]),
+    "hp_autotune_block": (_I, [_P, _D, _I, _I, _I, C.POINTER(Tuning), C.POINTER(C.c_double)]),
     "hp_unet_create": (_I, [_I, _I, _I, C.POINTER(C.c_void_p)]),
     "hp_unet_destroy": (None, [C.c_void_p]),
     "hp_unet_num_params": (C.c_long, [C.c_void_p]),
@@ -467,11 +468,20 @@ class Problem:
                    tma_tiles=tma_tiles, smem_tail=smem_tail, refine_df=refine_df)
         _check(lib().hp_set_tuning(self._h, C.byref(t)), "hp_set_tuning")
 
-    def autotune(self, nrhs, reps=3):
-        """Runs the autotuner at the current point; returns (settings, ms per block)."""
+    def autotune(self, nrhs, reps=3, X=None):
+        """Runs the autotuner at the current point, timing a random block of nrhs directions
+        or, if X is given, the caller's block X (CUDA float64 (nrhs, n), as hessian_apply
+        takes it); returns (settings, ms per block)."""
         t = Tuning()
         ms = C.c_double()
-        _check(lib().hp_autotune(self._h, nrhs, reps, C.byref(t), C.byref(ms)), "hp_autotune")
+        if X is None:
+            _check(lib().hp_autotune(self._h, nrhs, reps, C.byref(t), C.byref(ms)), "hp_autotune")
+        else:
+            X2, s, n = _block(X, self.n, "X")
+            if s != nrhs:
+                raise ValueError(f"X has {s} columns, nrhs is {nrhs}")
+            _check(lib().hp_autotune_block(self._h, _dptr(X2), n, nrhs, reps, C.byref(t), C.byref(ms)),
+                   "hp_autotune_block")
         return t.as_dict(), ms.value
 
     # ---- measurement -------------------------------------------------------------

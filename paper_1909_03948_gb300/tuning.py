@@ -33,17 +33,17 @@ def save(table: dict, path: str = DEFAULT_PATH) -> None:
     os.replace(tmp, path)
 
 
-def tuned(problem, nrhs: int, precision: str = "fp32_ir", path: str = DEFAULT_PATH, retune: bool = False):
+def tuned(problem, nrhs: int, precision: str = "fp32_ir", path: str = DEFAULT_PATH, retune: bool = False, X=None):
     """Applies the stored settings for this problem size and block width, running the
-    autotuner (at the problem's current point) when there are none.  Returns
-    (settings, ms per block, 'table' | 'autotune')."""
+    autotuner (at the problem's current point, on the block X when given, else on a random
+    block) when there are none.  Returns (settings, ms per block, 'table' | 'autotune')."""
     table = load(path)
     key = _key(problem, nrhs, precision)
     if key in table and not retune:
         s = table[key]["settings"]
         problem.set_tuning(**s)
         return s, table[key]["ms"], "table"
-    s, ms = problem.autotune(nrhs)
+    s, ms = problem.autotune(nrhs, X=X)
     table[key] = {"settings": s, "ms": ms}
     save(table, path)
     return s, ms, "autotune"

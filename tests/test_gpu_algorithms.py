@@ -339,6 +339,27 @@ def test_autotune_keeps_results(small2d):
     P.set_tuning()  # back to the defaults for the other tests
 
 
+def test_autotune_on_the_callers_block(small2d):
+    """hp_autotune_block times the caller's own block: the block is only read, the chosen
+    settings change the Hessian block by no more than the solve tolerance, and a block
+    whose column count differs from nrhs is refused."""
+    orc, P = small2d["orc"], small2d["P"]
+    P.set_point(torch.tensor(small2d["m_map"], device=DEV))
+    X = torch.tensor(np.ascontiguousarray(W.random_block(orc.n, 8, 56).T), device=DEV)
+    X0 = X.clone()
+    Y0, _ = P.hessian_apply(X)
+    try:
+        best, ms = P.autotune(8, X=X)
+        assert torch.equal(X, X0)
+        assert 1 <= best["nu"] <= 4 and ms > 0
+        Y1, _ = P.hessian_apply(X)
+        assert float((Y1 - Y0).norm() / Y0.norm()) < 1e-7
+        with pytest.raises(ValueError):
+            P.autotune(6, X=X)
+    finally:
+        P.set_tuning()
+
+
 @pytest.mark.parametrize("dim,N,precision", [(2, 64, "fp32_ir"), (2, 64, "fp64"), (3, 16, "fp32_ir"),
                                              (2, 48, "fp32_ir")])
 def test_fused_coarse_tail_matches_separate_launches(dim, N, precision):

@@ -12,8 +12,9 @@ class FakeProblem:
     def set_tuning(self, **kw):
         self.applied = kw
 
-    def autotune(self, nrhs):
+    def autotune(self, nrhs, X=None):
         self.autotuned += 1
+        self.block = X
         return {"nu": 1, "omega": 0.8, "col_chunk": 0, "max_blocks": 4096}, 1.5
 
 
@@ -27,5 +28,10 @@ def test_autotune_once_then_reuse(tmp_path):
     assert src2 == "table" and q.autotuned == 0 and q.applied == s
     # other block widths and sizes are separate entries
     s3, _, src3 = tuning.tuned(q, 8, path=path)
-    assert src3 == "autotune"
+    assert src3 == "autotune" and q.block is None
     assert len(tuning.load(path)) == 2
+    # the caller's block, when given, is what the autotuner times
+    r = FakeProblem()
+    blk = object()
+    tuning.tuned(r, 12, path=path, X=blk)
+    assert r.autotuned == 1 and r.block is blk
