@@ -333,11 +333,7 @@ typedef struct {
                         do the prolongation and the first post-smoothing sweep (the
                         fine residual and the prolonged iterate are never stored);
                         2: the same on the levels below the finest only */
-  int fuse_from;   /* 0 = off, else the first multigrid level (>= 1) whose whole
-                      coarse tail of the V-cycle runs as one launch: one thread-block
-                      cluster of 8 CTAs per column group, steps separated by the
-                      hardware cluster barrier (ignored when fewer than 2 levels
-                      remain below it) */
+  int fuse_from;   /* reserved: must be 0 (HP_ERR_INVALID otherwise) */
   int tma_tiles;   /* 1: on the multigrid levels of stiffness solves whose grid has np - 1 a
                       multiple of 32 (2D: and of 16; 3D: and of 16 planes), the stencil
                       kernels work on tiles that bulk tensor copies (TMA) bring into shared
@@ -349,8 +345,8 @@ typedef struct {
   int smem_tail;   /* k >= 1: the coarse end of the V-cycle -- from the finest level l >= k
                       whose vectors, and those of every level below it, fit in one CTA's
                       shared memory -- runs as one launch of one CTA per column group, its
-                      steps separated by block barriers only (takes precedence over
-                      fuse_from); the result equals the per-level kernels' bit for bit.
+                      steps separated by block barriers only; the result equals the
+                      per-level kernels' bit for bit.
                       0: off */
   int refine_df;   /* arithmetic of the FP64 iterative refinement around FP32 inner solves
                       (the residual b - K x with its norm, the scaling into the inner

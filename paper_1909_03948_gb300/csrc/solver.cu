@@ -1754,36 +1754,9 @@ static dim3 nodegrid(long n, int ng) {
 }
 
 // ---------------------------------------------------------------------------
-// Coarse tail of the V-cycle in one launch: levels l0 .. L-1 of every column
-// group run inside one thread-block cluster of VC_CL CTAs (blockIdx.y = group).
-// The coarse levels are small, so as separate launches they cost launch latency,
-// not bandwidth; here the steps of the cycle (the same smoothing, residual,
-// transfer and coarse-solve arithmetic as the per-level kernels, node by node)
-// are separated by the hardware cluster barrier, whose release/acquire
-// semantics make each step's global writes visible to the next step's ordinary
-// loads in every CTA of the cluster (no CTA can read a stale L1 line after it).
-// Measured on GB300 (medium2d, 60 columns): no faster than the per-level
-// launches inside the CUDA graph, so it is a tuning knob, off by default.
+// Node steps shared by the coarse-tail kernel below (the same arithmetic as the per-level
+// kernels, node by node).
 // ---------------------------------------------------------------------------
-constexpr int VC_CL = 8;     // CTAs per cluster (portable maximum)
-constexpr int VC_NT = 512;   // threads per CTA
-
-template <typename T> struct VTail {
-  int l0, L, full, zero_dirichlet, nc;
-  int nu[HP_MAXL];  // smoothing sweeps per level
-  T omega;
-  T w[HP_MAXL][4];  // smoothing weights per level and sweep
-  GridDesc g[HP_MAXL];
-  const T *diag[HP_MAXL], *invdiag[HP_MAXL], *c[HP_MAXL];
-  T *rl[HP_MAXL], *ea[HP_MAXL], *eb[HP_MAXL];
-  long gs[HP_MAXL];
-  const T *cinv;
-};
-
-__device__ __forceinline__ void cluster_barrier() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
-
 // S x at node id with the centre value xc given; JS: the
 // neighbour values enter as omega D^-1 x (the first sweep of a pair from zero),
 // in the same operation order as k_st
@@ -1826,175 +1799,6 @@ __device__ __forceinline__ void vt_coords(const GridDesc &g, long id, int v[3]) 
   const long t = id / g.np;
   v[1] = D == 2 ? (int)t : (int)(t % g.np);
   v[2] = D == 2 ? 0 : (int)(t / g.np);
-}
-
-template <typename T, int VW, int D, bool FULL>
-__global__ void __launch_bounds__(VC_NT) k_vcycle_tail(VTail<T> vt) {
-  using PK = Pack<T, VW>;
-  extern __shared__ unsigned char vt_smem[];
-  __shared__ T red[VC_NT / 32][32][VW];
-  unsigned rank, ncta;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
-  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
-  const int grp = blockIdx.y;
-  const long gt = (long)rank * VC_NT + threadIdx.x, gstride = (long)ncta * VC_NT;
-  T *cur[HP_MAXL], *oth[HP_MAXL];
-
-  // one damped-Jacobi-type node step over level l: mode 0 two sweeps from zero (rhs in,
-  // weights w1, w2), 1 one sweep from zero (w1), 2 sweep (x in, rhs b, w1), 3 residual b - S x
-  auto sweep = [&](int l, int mode, const T *x, const T *b, T *y, T w1, T w2) {
-    const GridDesc &g = vt.g[l];
-    const long gs = vt.gs[l];
-    const T *xg = x + grp * gs, *bg = b ? b + grp * gs : nullptr;
-    T *yg = y + grp * gs;
-    for (long id = gt; id < g.n; id += gstride) {
-      int v[3];
-      vt_coords<D>(g, id, v);
-      PK out;
-      if (mode == 0) {
-        // two sweeps from zero: e1 = w1 D^-1 r, e2 = e1 + w2 D^-1 (r - S e1)
-        const T wi = w1 * vt.invdiag[l][id], wi2 = w2 * vt.invdiag[l][id];
-        const PK r = PK::ld(xg + id * VW);
-        PK e1c;
-#pragma unroll
-        for (int q = 0; q < VW; ++q) e1c.v[q] = wi * r.v[q];
-        const PK sx = vt_apply<T, VW, D, FULL, true>(g, vt.diag[l], vt.invdiag[l], vt.c[l], xg, id, v, w1, e1c);
-#pragma unroll
-        for (int q = 0; q < VW; ++q) out.v[q] = fmadd(wi2, r.v[q] - sx.v[q], e1c.v[q]);
-      } else if (mode == 1) {
-        const T wi = w1 * vt.invdiag[l][id];
-        const PK r = PK::ld(xg + id * VW);
-#pragma unroll
-        for (int q = 0; q < VW; ++q) out.v[q] = wi * r.v[q];
-      } else {
-        const PK xc = PK::ld(xg + id * VW);
-        const PK sx = vt_apply<T, VW, D, FULL, false>(g, vt.diag[l], vt.invdiag[l], vt.c[l], xg, id, v, T(0), xc);
-        const PK bb = PK::ld(bg + id * VW);
-        if (mode == 3) {
-#pragma unroll
-          for (int q = 0; q < VW; ++q) out.v[q] = bb.v[q] - sx.v[q];
-        } else {
-          const T wi = w1 * vt.invdiag[l][id];
-#pragma unroll
-          for (int q = 0; q < VW; ++q) out.v[q] = fmadd(wi, bb.v[q] - sx.v[q], xc.v[q]);
-        }
-      }
-      out.st(yg + id * VW);
-    }
-  };
-
-  for (int l = vt.l0; l + 1 < vt.L; ++l) {
-    const int nul = vt.nu[l];
-    T *c = nul >= 2 ? vt.ea[l] : vt.eb[l], *o = nul >= 2 ? vt.eb[l] : vt.ea[l];
-    sweep(l, nul >= 2 ? 0 : 1, vt.rl[l], nullptr, c, vt.w[l][0], vt.w[l][1]);
-    cluster_barrier();
-    for (int k = 2; k < nul; ++k) {
-      sweep(l, 2, c, vt.rl[l], o, vt.w[l][k], T(0));
-      cluster_barrier();
-      T *t = c; c = o; o = t;
-    }
-    sweep(l, 3, c, vt.rl[l], o, T(0), T(0));
-    cluster_barrier();
-    // restriction to level l + 1 (transpose of the P1 prolongation)
-    {
-      const GridDesc &gf = vt.g[l], &gc = vt.g[l + 1];
-      const T *r = o + grp * vt.gs[l];
-      T *rc = vt.rl[l + 1] + grp * vt.gs[l + 1];
-      for (long I = gt; I < gc.n; I += gstride) {
-        int J[3];
-        vt_coords<D>(gc, I, J);
-        PK out = PK::zero();
-        if (!(vt.zero_dirichlet && (J[D - 1] == 0 || J[D - 1] == gc.N))) {
-          const long f0 = 2 * (long)J[0] + (long)gf.np * (2 * (long)J[1] + (D == 3 ? (long)gf.np * 2 * J[2] : 0));
-          out = PK::ld(r + f0 * VW);
-#pragma unroll
-          for (int b = 1; b < (1 << D); ++b) {
-            bool fw = true, bw = true;
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-              if ((b >> a) & 1) {
-                fw = fw && (J[a] < gc.N);
-                bw = bw && (J[a] > 0);
-              }
-            const long off = mask_offset(gf, b);
-            if (fw) out.axpy(T(0.5), PK::ld(r + (f0 + off) * VW));
-            if (bw) out.axpy(T(0.5), PK::ld(r + (f0 - off) * VW));
-          }
-        }
-        out.st(rc + I * VW);
-      }
-    }
-    cluster_barrier();
-    cur[l] = c;
-    oth[l] = o;
-  }
-  // coarsest level: e = A_c^{-1} r (dense inverse), row tiles of 32 over the cluster,
-  // the 16 warps of a CTA splitting the k sum
-  {
-    const int lc = vt.L - 1, nc = vt.nc;
-    const T *rg = vt.rl[lc] + grp * vt.gs[lc];
-    T *r = reinterpret_cast<T *>(vt_smem);
-    for (int k = threadIdx.x; k < nc * VW; k += VC_NT) r[k] = __ldcg(rg + k);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    T *eg = vt.ea[lc] + grp * vt.gs[lc];
-    for (int tile = (int)rank; tile * 32 < nc; tile += (int)ncta) {
-      const int i = tile * 32 + lane;
-      PK acc = PK::zero();
-      if (i < nc)
-        for (int k = w; k < nc; k += VC_NT / 32) {
-          const T a = vt.cinv[(long)k * nc + i];
-#pragma unroll
-          for (int q = 0; q < VW; ++q) acc.v[q] = fmadd(a, r[k * VW + q], acc.v[q]);
-        }
-#pragma unroll
-      for (int q = 0; q < VW; ++q) red[w][lane][q] = acc.v[q];
-      __syncthreads();
-      if (w == 0 && i < nc) {
-        PK out = PK::zero();
-#pragma unroll
-        for (int ww = 0; ww < VC_NT / 32; ++ww)
-#pragma unroll
-          for (int q = 0; q < VW; ++q) out.v[q] += red[ww][lane][q];
-        out.st(eg + (long)i * VW);
-      }
-      __syncthreads();
-    }
-    cluster_barrier();
-    cur[lc] = vt.ea[lc];
-  }
-  for (int l = vt.L - 2; l >= vt.l0; --l) {
-    // e_l += P e_{l+1}
-    {
-      const GridDesc &gf = vt.g[l], &gc = vt.g[l + 1];
-      const T *e = cur[l + 1] + grp * vt.gs[l + 1];
-      T *ef = cur[l] + grp * vt.gs[l];
-      for (long i = gt; i < gf.n; i += gstride) {
-        int v[3];
-        vt_coords<D>(gf, i, v);
-        const int b = (v[0] & 1) | ((v[1] & 1) << 1) | ((v[2] & 1) << 2);
-        const long ic = (v[0] >> 1) + (long)gc.np * ((v[1] >> 1) + (long)gc.np * (v[2] >> 1));
-        PK val = PK::ld(e + ic * VW);
-        if (b) {
-          const PK v2 = PK::ld(e + (ic + mask_offset(gc, b)) * VW);
-#pragma unroll
-          for (int q = 0; q < VW; ++q) val.v[q] = mulr(T(0.5), val.v[q] + v2.v[q]);
-        }
-        PK cv = PK::ld(ef + i * VW);
-#pragma unroll
-        for (int q = 0; q < VW; ++q) cv.v[q] = addr(cv.v[q], val.v[q]);
-        cv.st(ef + i * VW);
-      }
-    }
-    cluster_barrier();
-    T *c = cur[l], *o = oth[l];
-    for (int k = 0; k < vt.nu[l]; ++k) {
-      sweep(l, 2, c, vt.rl[l], o, vt.w[l][vt.nu[l] - 1 - k], T(0));
-      cluster_barrier();
-      T *t = c; c = o; o = t;
-    }
-    cur[l] = c;
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -2241,18 +2045,16 @@ static size_t smem_tail_layout(const hp_problem *P, int l0, int node_bytes, VTai
   return off;
 }
 
-// first level of the fused coarse tail for this solve, or L (no fusion): with the
-// shared-memory tail the lowest level, from smem_tail on, whose tail fits in a CTA's shared
-// memory (at least one level above the coarsest), else the cluster tail's fuse_from
+// first level of the shared-memory coarse tail for this solve, or L (no fusion): the lowest
+// level, from smem_tail on, whose tail fits in a CTA's shared memory (at least one level
+// above the coarsest)
 static int tail_level(const hp_problem *P, int node_bytes) {
   if (P->smem_tail) {
     const size_t cap = (size_t)smem_optin();
     for (int l0 = std::max(1, P->smem_tail); l0 + 2 <= P->L; ++l0)
       if (smem_tail_layout<float>(P, l0, node_bytes, nullptr) <= cap) return l0;
-    return P->L;
   }
-  const int f = P->fuse_from;
-  return (f >= 1 && f + 2 <= P->L) ? f : P->L;
+  return P->L;
 }
 
 // Algorithmic bytes of the V-cycle's levels l0 .. L-1 as the per-level kernels would move
@@ -2331,59 +2133,6 @@ static void launch_vtail_smem(hp_problem *P, OpKind op, int s, int l0, const T *
       coarse_inv<T>(P, op), nc, rl[lc], gsl[lc], ea[lc], gsl[lc]);
   up<<<dim3(1, ng), VS_NT, bytes, P->st>>>(vt);
   count_launch(3);
-  count_bytes(BY_STENCILC, tail_bytes<T>(P, op, s, l0));
-}
-
-template <typename T, int VW>
-static void launch_vtail(hp_problem *P, OpKind op, int s, int l0, const T *const *rl, T *const *ea, T *const *eb,
-                         const long *gsl) {
-  const int L = P->L, ng = (s + VW - 1) / VW;
-  VTail<T> vt{};
-  vt.l0 = l0;
-  vt.L = L;
-  vt.zero_dirichlet = op == OP_K;
-  vt.nc = (int)P->lv[L - 1].g.n;
-  vt.omega = (T)P->omega;
-  for (int l = 0; l < L; ++l) {
-    vt.nu[l] = nu_at(P, l);
-    smooth_weights<T>(P, op, l, vt.w[l]);
-    const Stencil<T> &S = stencil_of<T>(P, op, l);
-    vt.g[l] = P->lv[l].g;
-    vt.diag[l] = S.diag;
-    vt.invdiag[l] = S.invdiag;
-    vt.c[l] = S.c;
-    vt.rl[l] = const_cast<T *>(rl[l]);
-    vt.ea[l] = ea[l];
-    vt.eb[l] = eb[l];
-    vt.gs[l] = gsl[l];
-  }
-  vt.full = stencil_of<T>(P, op, l0).full;
-  vt.cinv = coarse_inv<T>(P, op);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(VC_CL, ng);
-  cfg.blockDim = dim3(VC_NT);
-  cfg.dynamicSmemBytes = sizeof(T) * (size_t)vt.nc * VW;
-  cfg.stream = P->st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = VC_CL;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  const int D = P->lv[0].g.dim;
-  if (D == 2) {
-    if (vt.full)
-      cudaLaunchKernelEx(&cfg, k_vcycle_tail<T, VW, 2, true>, vt);
-    else
-      cudaLaunchKernelEx(&cfg, k_vcycle_tail<T, VW, 2, false>, vt);
-  } else {
-    if (vt.full)
-      cudaLaunchKernelEx(&cfg, k_vcycle_tail<T, VW, 3, true>, vt);
-    else
-      cudaLaunchKernelEx(&cfg, k_vcycle_tail<T, VW, 3, false>, vt);
-  }
-  count_launch();
   count_bytes(BY_STENCILC, tail_bytes<T>(P, op, s, l0));
 }
 
@@ -2501,10 +2250,7 @@ static void precondition(hp_problem *P, OpKind op, int s, const T *r0, T *z0, co
       for (int k = 0; k < nu_at(P, l); ++k) std::swap(c, o);
       cur[l] = c;
     }
-    if (P->smem_tail)  // the level-l0 correction lands where the cluster tail would leave it
-      launch_vtail_smem<T, VW>(P, op, s, l0, rl, ea, gsl, cur[l0]);
-    else
-      launch_vtail<T, VW>(P, op, s, l0, rl, ea, eb, gsl);
+    launch_vtail_smem<T, VW>(P, op, s, l0, rl, ea, gsl, cur[l0]);
   } else {
     const int lc = L - 1;
     const int nc = (int)P->lv[lc].g.n;
@@ -2716,9 +2462,8 @@ static int build_graph(hp_problem *P, OpKind op, int s, double tol, int maxit, P
 static int kernels_per_iteration(const hp_problem *P, OpKind op, int node_bytes) {
   if (op == OP_M) return 8;
   // V-cycle: per non-coarsest level pre (1 + nu - 2), resid, restrict, prolong, nu post; coarse 1
-  // (or one fused launch for the levels from tail_level on); plus p update, matvec, cg update,
-  // condition and three dot finalisations
-  // (the shared-memory tail: down leg, coarse solve, up leg = 3 launches)
+  // (with the shared-memory tail from tail_level on: down leg, coarse solve, up leg = 3
+  // launches); plus p update, matvec, cg update, condition and three dot finalisations
   const int tl = tail_level(P, node_bytes);
   const int separate = std::min(P->L, tl) - 1 + (tl < P->L ? 1 : 0);
   int vc = 0;

@@ -1,14 +1,13 @@
 // tune.cu -- solver tuning knobs and the autotuner.
 //
 // Knobs: the V-cycle's smoother (nu sweeps, damped Jacobi with omega or Chebyshev
-// weights on [lmax / alpha, lmax]), the RHS column
-// chunk processed per solve (0 = all columns at once), the level from which the
-// coarse tail of the V-cycle runs as one cluster launch, and the grid-size cap
-// of the node kernels.  hp_autotune times one block of Gauss-Newton Hessian
-// actions at the current linearisation point (CUDA events on the problem's
-// stream) for each candidate, by coordinate descent over the four groups of
-// knobs, and keeps the fastest.  Every candidate solves to the same tolerance,
-// so tuning changes speed, not the stopping rule.
+// weights on [lmax / alpha, lmax]), the RHS column chunk processed per solve (0 = all
+// columns at once), fused grid transfers, the shared-memory coarse tail, the TMA-tiled
+// stencil kernels, the double-float refinement and the grid-size cap of the node
+// kernels.  hp_autotune times one block of Gauss-Newton Hessian actions at the current
+// linearisation point (CUDA events on the problem's stream) for each candidate, by
+// coordinate descent over the groups of knobs, and keeps the fastest.  Every candidate
+// solves to the same tolerance, so tuning changes speed, not the stopping rule.
 #include <algorithm>
 #include <vector>
 
@@ -21,12 +20,12 @@ extern "C" {
 int hp_set_tuning(hp_problem *P, const hp_tuning *t) {
   if (!P || !t) return set_error(HP_ERR_INVALID, "hp_set_tuning: null");
   if (t->nu < 1 || t->nu > 4 || t->nu_coarse < 0 || t->nu_coarse > 4 || !(t->omega > 0.0 && t->omega < 1.0) || t->col_chunk < 0 || t->max_blocks < 64 ||
-      t->max_blocks > (1 << 20) || t->fuse_from < 0 || t->fuse_from >= HP_MAXL || t->smoother < 0 ||
+      t->max_blocks > (1 << 20) || t->fuse_from != 0 || t->smoother < 0 ||
       t->smoother > 1 || (t->smoother == 1 && !(t->cheb_alpha > 1.0 && t->cheb_alpha < 1e6)) ||
       t->fuse_transfer < 0 || t->fuse_transfer > 2 || t->tma_tiles < 0 || t->tma_tiles > 2 ||
       t->smem_tail < 0 || t->smem_tail >= HP_MAXL || t->refine_df < 0 || t->refine_df > 2)
     return set_error(HP_ERR_INVALID, "hp_set_tuning: nu in [1,4], omega in (0,1), col_chunk >= 0, max_blocks >= 64, "
-                                     "fuse_from in [0, 15], smoother 0/1, cheb_alpha > 1, fuse_transfer 0..2, tma_tiles 0..2, smem_tail in [0, 15], "
+                                     "fuse_from 0 (reserved), smoother 0/1, cheb_alpha > 1, fuse_transfer 0..2, tma_tiles 0..2, smem_tail in [0, 15], "
                                      "refine_df 0..2");
   HP_CUDA(cudaStreamSynchronize(P->st));
   if (t->nu != P->nu || t->nu_coarse != P->nu_coarse || t->omega != P->omega || t->max_blocks != P->max_blocks || t->fuse_from != P->fuse_from ||
@@ -156,12 +155,6 @@ static int autotune_on(hp_problem *P, const double *X, int ldx, int nrhs, int re
       if (st == cur.smem_tail) continue;
       hp_tuning t = cur;
       t.smem_tail = st;
-      if ((rc = consider(t))) return cleanup(rc);
-    }
-    for (int ff : {0, 1, 2}) {
-      if (ff == cur.fuse_from || (ff > 0 && (ff + 2 > P->L || cur.smem_tail))) continue;
-      hp_tuning t = cur;
-      t.fuse_from = ff;
       if ((rc = consider(t))) return cleanup(rc);
     }
     for (int tt : {0, 1, 2}) {

@@ -360,29 +360,15 @@ def test_autotune_on_the_callers_block(small2d):
         P.set_tuning()
 
 
-@pytest.mark.parametrize("dim,N,precision", [(2, 64, "fp32_ir"), (2, 64, "fp64"), (3, 16, "fp32_ir"),
-                                             (2, 48, "fp32_ir")])
-def test_fused_coarse_tail_matches_separate_launches(dim, N, precision):
-    """The coarse tail of the V-cycle in one cluster launch (fuse_from = 1, 2) gives the
-    same Hessian actions as the per-level launches, to the solve tolerance, and the
-    same iteration counts give or take one."""
-    from paper_1909_03948_gb300 import Problem
-    w = W.make_workload(dim, N, 30, seed=77)
-    dr = W.draws(w)
-    P = Problem(dim, N, w.gamma, w.delta, 0.01, dr.obs_xyz, rtol=1e-10, precision=precision)
-    m = 0.3 * torch.tensor(np.random.default_rng(5).standard_normal(P.n), device=DEV)
-    X = torch.tensor(np.random.default_rng(6).standard_normal((9, P.n)), device=DEV)
-    P.set_point(m)
-    Y0, st0 = P.hessian_apply(X)
-    for ff in (1, 2):
-        P.set_tuning(fuse_from=ff)
-        P.set_point(m)
-        Y1, st1 = P.hessian_apply(X)
-        rel = float(torch.linalg.norm(Y1 - Y0) / torch.linalg.norm(Y0))
-        assert rel <= 1e-8, (ff, rel)
-        assert abs(st1["iterations"] - st0["iterations"]) <= 2, (ff, st0, st1)
-    P.set_tuning()
-    P.close()
+def test_fuse_from_is_reserved(small2d):
+    """The tuning field fuse_from is reserved: any value but 0 is refused and the settings
+    stay as they were."""
+    from paper_1909_03948_gb300 import HPError
+    P = small2d["P"]
+    before = P.get_tuning()
+    with pytest.raises(HPError):
+        P.set_tuning(fuse_from=1)
+    assert P.get_tuning() == before
 
 
 def test_single_pass_matches_oracle(small2d):
@@ -466,8 +452,8 @@ def test_randomized_prior_variance_is_exact_with_full_rank(dim, N):
 @pytest.mark.parametrize("dim,N,precision", [(2, 64, "fp32_ir"), (2, 48, "fp64"), (3, 16, "fp32_ir")])
 def test_chebyshev_smoother_keeps_results(dim, N, precision):
     """Chebyshev smoothing weights change only the speed: Hessian actions and prior solves
-    agree with the damped-Jacobi runs to the solve tolerance, also with the fused coarse
-    tail and with fewer sweeps on the coarse levels (nu_coarse)."""
+    agree with the damped-Jacobi runs to the solve tolerance, also with fewer sweeps on the
+    coarse levels (nu_coarse)."""
     from paper_1909_03948_gb300 import Problem
     w = W.make_workload(dim, N, 30, seed=78)
     dr = W.draws(w)
@@ -477,8 +463,8 @@ def test_chebyshev_smoother_keeps_results(dim, N, precision):
     P.set_point(m)
     Y0, _ = P.hessian_apply(X)
     Z0, _ = P.prior_solve(X)
-    for alpha, ff, nc in ((3.0, 0, 0), (8.0, 0, 1), (5.0, 2, 2), (10.0, 1, 1)):
-        P.set_tuning(smoother=1, cheb_alpha=alpha, fuse_from=ff, nu_coarse=nc)
+    for alpha, nc in ((3.0, 0), (8.0, 1), (5.0, 2), (10.0, 1)):
+        P.set_tuning(smoother=1, cheb_alpha=alpha, nu_coarse=nc)
         P.set_point(m)
         Y1, st1 = P.hessian_apply(X)
         Z1, _ = P.prior_solve(X)
@@ -497,7 +483,7 @@ def test_fused_transfers_keep_results(dim, N, precision, nu):
     """Residual + restriction and prolongation + first post sweep fused (the fine residual
     and the prolonged iterate never stored): the same Hessian actions and prior solves to
     the solve tolerance, for the stiffness (axis stencil) and the prior (full stencil),
-    on every level or below the finest only, alone and with the fused coarse tail."""
+    on every level or below the finest only."""
     from paper_1909_03948_gb300 import Problem
     w = W.make_workload(dim, N, 30, seed=79)
     dr = W.draws(w)
@@ -508,13 +494,13 @@ def test_fused_transfers_keep_results(dim, N, precision, nu):
     P.set_point(m)
     Y0, st0 = P.hessian_apply(X)
     Z0, _ = P.prior_solve(X)
-    for ft, ff in ((1, 0), (1, 2), (2, 0)):
-        P.set_tuning(nu=nu, fuse_transfer=ft, fuse_from=ff)
+    for ft in (1, 2):
+        P.set_tuning(nu=nu, fuse_transfer=ft)
         P.set_point(m)
         Y1, st1 = P.hessian_apply(X)
         Z1, _ = P.prior_solve(X)
-        assert float(torch.linalg.norm(Y1 - Y0) / torch.linalg.norm(Y0)) <= 1e-8, (ft, ff)
-        assert float(torch.linalg.norm(Z1 - Z0) / torch.linalg.norm(Z0)) <= 1e-8, (ft, ff)
+        assert float(torch.linalg.norm(Y1 - Y0) / torch.linalg.norm(Y0)) <= 1e-8, ft
+        assert float(torch.linalg.norm(Z1 - Z0) / torch.linalg.norm(Z0)) <= 1e-8, ft
         assert abs(st1["iterations"] - st0["iterations"]) <= 2, (st0, st1)
     P.set_tuning()
     P.close()
