@@ -77,3 +77,15 @@ def test_3d_workload_oracle_solves_iteratively():
     from oracle.inverse import CG_NODES_3D
     assert W.WORKLOADS["cube3d"].nnodes > CG_NODES_3D
     assert W.WORKLOADS["medium2d"].dim == 2
+
+
+def test_committed_sweep_traffic_belongs_to_the_committed_kernel():
+    # the cube3d z-march sweep's DRAM traffic in profiles/traffic.json was captured on the
+    # kernel source as it stands: a kernel change without a new capture fails here
+    assert bench.traffic_record("smooth", "cube3d", "tiled") is not None
+
+
+def test_build_record_names_the_machine_and_compiler():
+    rec = bench.build_record()
+    assert rec["machine"]
+    assert ("built_on" in rec and "nvcc" in rec and "lib_mtime" in rec) or "error" in rec
