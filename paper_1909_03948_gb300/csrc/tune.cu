@@ -122,8 +122,8 @@ static int autotune_on(hp_problem *P, const double *X, int ldx, int nrhs, int re
     int nu, kind;
     double omega, alpha;
   };
-  const SmoothC smooth[] = {{2, 0, 0.8, 10.0}, {2, 1, 0.7, 5.0}, {3, 1, 0.7, 8.0}, {3, 1, 0.7, 10.0},
-                            {3, 1, 0.7, 12.0}, {4, 1, 0.7, 12.0}};
+  const SmoothC smooth[] = {{2, 0, 0.8, 10.0}, {2, 1, 0.7, 5.0}, {2, 1, 0.7, 12.0}, {3, 1, 0.7, 8.0},
+                            {3, 1, 0.7, 10.0}, {3, 1, 0.7, 12.0}, {4, 1, 0.7, 12.0}};
   // coordinate descent over the settings, twice: the second pass re-times the point the first
   // one reached and revisits every coordinate from there
   for (int pass = 0; pass < 2; ++pass) {
